@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Benchmark: 3D heat diffusion sweeps at 1024^3, space orders 2/4/8, 50 steps each (FP32).
+
+One bench step = stencil_run(50) on the 1024^3 grid for each of the space
+orders 2, 4 and 8 (3 x 50 sweeps, 1.61e11 point-updates), inputs resident in
+HBM.  The metric is GPoints/s (the paper's GPts/s, Section 6: interior point
+updates per second).  Each field is 4.3 GB, far larger than the 129 MB L2, so
+no explicit L2 flush is needed between iterations.
+
+Also reported:
+  roofline      dominant sweep kernel: algorithmic bytes (8 B per point-update:
+                read u, write u+) / its CUDA-event launch time, against the
+                measured HBM copy bandwidth;
+  e2e           the same metric through the C ABI with host buffers
+                (set_field from pinned host memory, run, get_field to host);
+  cpu_baseline  the FP64 oracle on the host cores over a bounded slab sample;
+  per_stencil   GPoints/s and GB/s of each space order's sweep kernel.
+
+``--impl reference`` times the FP64 oracle instead (the reference arm).
+Multi-GPU (torchrun, N > 1): independent replicas, one 1024^3 problem per GPU
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GPoints/s and achieved HBM GB/s vs peak per stencil; BF16/batched/learned vs FP32"
+UNIT = "GPoints/s"
+N = 1024
+SOS = (2, 4, 8)
+STEPS_PER_RUN = 50
+BYTES_PER_PT = 8  # FP32 heat: read u, write u+
+WORKLOAD = "heat3d 1024^3 FP32, space orders 2/4/8, 50 steps each, zero Dirichlet halo"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="gbst_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ cpu oracle ---
+def oracle_sample(nz_sample: int = 128, steps: int = 3):
+    """The FP64 oracle on a 1024 x 1024 x nz_sample slab, `steps` steps per space order."""
+    import numpy as np
+    import oracle
+    import synthetic
+    oracle.lib()
+    shape = (nz_sample, N, N)
+    u0 = synthetic.uniform_field(2, shape).astype(np.float64)
+    pts = 0
+    t0 = time.perf_counter()
+    for so in SOS:
+        case = synthetic.heat3d(N, so)
+        oracle.heat_run(u0, so, case.a, steps)
+        pts += steps * u0.size
+    dt = time.perf_counter() - t0
+    return pts / dt / 1e9, f"heat3d slab {N}x{N}x{nz_sample}, {steps} steps per space order 2/4/8, FP64 oracle", dt
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    cores = host_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    for _ in range(args.warmup):
+        oracle_sample(nz_sample=16, steps=1)
+    vals, secs = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, desc, dt = oracle_sample(nz_sample=16, steps=1)
+        vals.append(v)
+        secs += dt
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------- our path ---
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("sweep_stream.cu", "gbst_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2404_02218_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel_key)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import synthetic
+    from paper_2404_02218_gb300.grid import Grid
+
+    stream = torch.cuda.Stream()
+    shape = (N, N, N)
+    u0 = synthetic.uniform_field_torch(2, shape, "cuda")
+    grids = {}
+    for so in SOS:
+        case = synthetic.heat3d(N, so)
+        g = Grid(3, case.dims, so, "heat", h=1.0, dt=case.a, alpha=1.0, stream=stream)
+        g.set_field("u", u0)
+        grids[so] = g
+    torch.cuda.synchronize()
+
+    def one_step():
+        for so in SOS:
+            grids[so].run(STEPS_PER_RUN)
+
+    for _ in range(max(3, args.warmup)):
+        one_step()
+    torch.cuda.synchronize()
+    for g in grids.values():
+        g.set_profile(True)
+    one_step()  # capture the profiled graphs outside the timed region
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pts_per_step = len(SOS) * STEPS_PER_RUN * N ** 3
+    value = world * args.steps * pts_per_step / (ms / 1e3) / 1e9
+
+    # per-kernel device time: CUDA events around every sweep launch of the last timed step
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    per = {}
+    for so, g in grids.items():
+        kms, nl = g.last_kernel_time()
+        avg = kms / nl / 1e3
+        gbs = BYTES_PER_PT * N ** 3 / avg / 1e9
+        per[f"heat3d_so{so}"] = {"gpts": N ** 3 / avg / 1e9, "gbs": gbs, "frac": gbs / hbm,
+                                 "avg_launch_ms": avg * 1e3, "plan": json.loads(g.describe())}
+    dom = max(per, key=lambda k: per[k]["avg_launch_ms"])
+    traffic = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "achieved": per[dom]["gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": per[dom]["gbs"] / hbm, "traffic": traffic, "kernel": dom,
+                "algorithmic_bytes_per_launch": BYTES_PER_PT * N ** 3, "peak_source": peak_kind}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        for g in grids.values():
+            g.set_profile(False)
+        hin = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+        hin.copy_(u0)
+        hout = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+        del u0
+        torch.cuda.synchronize()
+        for so in SOS:  # warm the staging path
+            grids[so].set_field("u", hin)
+            grids[so].get_field("u", out=hout)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for so in SOS:
+                g = grids[so]
+                g.set_field("u", hin)
+                g.run(STEPS_PER_RUN)
+                g.get_field("u", out=hout)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        nbytes = len(SOS) * 4 * N ** 3
+        e2e = {"value": world * args.e2e_steps * pts_per_step / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+        v, desc, _ = oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+               "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": [N, N, N], "space_orders": list(SOS),
+                           "steps_per_run": STEPS_PER_RUN, "parallelism": f"replicas{world}",
+                           "l2": "inputs larger than L2 (4.3 GB per field), no flush"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * len(SOS) * STEPS_PER_RUN, "clocks": clocks,
+                "per_stencil": per}
+        print(json.dumps(line), flush=True)
+    for g in grids.values():
+        g.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * gbstencil -- explicit finite-difference stencil sweeps on GB300 (sm_103a).
+ *
+ * C ABI of the library.  Every entry point is `extern "C"`, takes plain
+ * pointers and sizes, returns a gbst_status (0 = OK, < 0 = error), never
+ * aborts and never prints (unless the environment variable GBST_LOG=1).
+ * After an error, stencil_last_error() returns a message for the calling
+ * thread.
+ *
+ * What is computed (Bisbas et al., "A shared compilation stack for
+ * distributed-memory parallelism in stencil DSLs", ASPLOS 2024):
+ *  - Section 2: a grid point at step n+1 is a function of its neighbours at
+ *    earlier steps; the halo is read-only and as wide as the stencil radius.
+ *  - Section 5.1 (Devito heat listing): forward Euler for u_t = alpha Lap(u):
+ *        u^{n+1} = u^n + a L(u^n),  a = alpha dt / h^2.
+ *  - Section 6.1: heat diffusion and the isotropic acoustic wave equation,
+ *    2D and 3D, space orders 2/4/8; the wave is second order in time:
+ *        u^{n+1} = 2 u^n - u^{n-1} + kappa L(u^n),  kappa = c^2 dt^2 / h^2.
+ *  - L(u)_p = sum over axes, sum over m=-r..r of w_|m| u_{p + m e_axis},
+ *    r = space_order / 2, w the central second-derivative weights of accuracy
+ *    space_order (or caller-supplied weights).
+ *  - Section 4.2 (dmp.swap): in decomposition mode the domain is split into
+ *    equal subdomains, each with its own halo; before every sweep each
+ *    subdomain receives its neighbours' boundary slabs into its halo.
+ *
+ * Threading: handles are not thread-safe; distinct handles may be used from
+ * distinct threads.  Ownership: the library owns all device memory it
+ * allocates (through the optional allocator, else cudaMalloc) and frees it in
+ * the matching destroy call; caller buffers are only read or written during
+ * the call that receives them (asynchronously on the handle's stream where
+ * stated).
+ */
+#ifndef GBSTENCIL_H
+#define GBSTENCIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBST_OK = 0,
+    GBST_EINVAL = -1,     /* invalid argument (message says which) */
+    GBST_ENOMEM = -2,     /* device or host allocation failed */
+    GBST_ECUDA = -3,      /* a CUDA call failed; the handle is poisoned */
+    GBST_ETIMEOUT = -4,   /* a bounded device-side wait expired; the handle is poisoned */
+    GBST_EUNSTABLE = -5,  /* time step above the von Neumann limit, or NaN/Inf detected */
+    GBST_ESTATE = -6,     /* call not valid in the handle's current state */
+    GBST_ENOTSUP = -7     /* combination not supported by this build */
+} gbst_status;
+
+enum { GBST_HEAT = 0, GBST_WAVE = 1 };                    /* gbst_desc.eq */
+enum { GBST_BC_ZERO = 0, GBST_BC_PERIODIC = 1 };          /* gbst_desc.bc */
+enum { GBST_F32 = 0, GBST_BF16 = 1, GBST_F64 = 2 };       /* storage / transfer dtypes */
+enum { GBST_U = 0, GBST_U_PREV = 1, GBST_VEL = 2 };       /* fields */
+enum { GBST_RED_SUM = 0, GBST_RED_L2SQ = 1, GBST_RED_MAXABS = 2, GBST_RED_ENERGY = 3 };
+enum { GBST_KERNEL_AUTO = 0, GBST_KERNEL_STREAM = 1, GBST_KERNEL_SIMPLE = 2 };
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns a device pointer of at least `bytes` bytes, 256-byte aligned, or NULL;
+ * release frees it.  `stream` is the handle's cudaStream_t. */
+typedef struct gbst_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*release)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} gbst_allocator;
+
+/* Problem description.  Zero-initialise, then set the fields you need. */
+typedef struct gbst_desc {
+    int ndim;              /* 2 or 3 */
+    int64_t dims[3];       /* interior points; dims[0] = x (fastest); dims[2] ignored for 2D */
+    int space_order;       /* 2, 4 or 8 (radius r = space_order/2) */
+    int eq;                /* GBST_HEAT or GBST_WAVE */
+    int bc;                /* GBST_BC_ZERO (Dirichlet ghosts, the paper's read-only halo)
+                              or GBST_BC_PERIODIC (test mode, for closed forms) */
+    int storage;           /* GBST_F32 or GBST_BF16 (fields stored in BF16, FP32 arithmetic) */
+    double h;              /* grid spacing */
+    double dt;             /* time step */
+    double alpha;          /* heat: diffusivity, a = alpha dt / h^2 */
+    const double *coeffs;  /* optional r+1 one-sided weights w_0..w_r; NULL = standard central */
+    int decomp[3];         /* subdomains per axis ({0,0,0} or {1,1,1} = none; e.g. {2,2,2}) */
+    int allow_unstable;    /* 0: reject time steps above the von Neumann limit (GBST_EUNSTABLE) */
+    int kernel;            /* GBST_KERNEL_AUTO / STREAM (TMA 2.5D) / SIMPLE (one thread per point) */
+    int tile;              /* 0 = autotuned (cached per shape class); > 0 = fixed plan id */
+    int use_graph;         /* 0: direct launches; 1: capture the step loop as a CUDA graph */
+    void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
+    const gbst_allocator *allocator; /* NULL = cudaMalloc / cudaFree */
+} gbst_desc;
+
+typedef struct gbst_grid_s *gbst_handle;
+
+/* Version of this ABI (major*10000 + minor*100 + patch). */
+int gbst_version(void);
+
+/* Message of the last failed call on this thread ("" if none).  Never NULL. */
+const char *stencil_last_error(void);
+
+/* Central second-derivative weights w_0..w_r of accuracy `space_order` (2..16,
+ * even) written to out[0..r].  Defined by sum_m w_m m^k = 2[k==2], k <= 2r
+ * (the standard finite-difference scheme; the paper, Section 6.1, names only
+ * the orders).  Host only. */
+gbst_status stencil_fd_weights(int space_order, double *out);
+
+/* Create a grid: allocates the fields (interior + r-wide zero halo per axis,
+ * x pitch padded to 128 bytes) on the current CUDA device, sets u = u_prev = 0,
+ * kappa = 0.  `out` receives the handle.  Errors: EINVAL (bad desc), ENOMEM,
+ * EUNSTABLE (heat with a*ndim*S > 2 and allow_unstable == 0). */
+gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out);
+
+/* Copy a dense interior field in (x fastest, dims[0]*dims[1]*dims[2] values of
+ * `src_dtype`; GBST_F32, GBST_F64 or GBST_BF16).  src_on_device selects a
+ * device or host pointer (host memory may be pageable or pinned).  Values are
+ * rounded to the storage type (round-to-nearest-even).  For GBST_VEL the values
+ * are wave speeds c and the library stores kappa = c^2 dt^2 / h^2 (FP32); for
+ * the wave, a VEL whose kappa exceeds the stability limit returns EUNSTABLE
+ * unless allow_unstable.  Synchronous with respect to the caller's buffer. */
+gbst_status stencil_set_field(gbst_handle h, int field, const void *src, int src_dtype,
+                              int src_on_device);
+
+/* Copy a dense interior field out (same layout rules; GBST_VEL returns kappa).
+ * Synchronises the handle's stream and reports any deferred device error. */
+gbst_status stencil_get_field(gbst_handle h, int field, void *dst, int dst_dtype,
+                              int dst_on_device);
+
+/* Wave only: a Ricker point source at interior index idx = (i, j, k) (k ignored
+ * in 2D).  At the end of step n the value amp * c_s^2 dt^2 * R(n dt) is added to
+ * u^{n+1} at idx, R(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2).
+ * f0 <= 0 removes the source. */
+gbst_status stencil_set_source(gbst_handle h, const int64_t idx[3], double f0_hz, double t0_s,
+                               double amp);
+
+/* Advance nsteps time steps, asynchronously on the handle's stream.  Each step
+ * is: [decomposition/periodic: halo swap kernel] + one sweep kernel.  Device
+ * errors are reported by the next synchronising call. */
+gbst_status stencil_run(gbst_handle h, int64_t nsteps);
+
+/* Wait for the handle's stream; returns ETIMEOUT/ECUDA if a kernel failed. */
+gbst_status stencil_sync(gbst_handle h);
+
+/* Current step counter n (the field GBST_U holds u^n) and its setter (used to
+ * resume from a checkpoint made with get_field of U and U_PREV). */
+gbst_status stencil_get_step(gbst_handle h, int64_t *step);
+gbst_status stencil_set_step(gbst_handle h, int64_t step);
+
+/* FP64 reduction over the interior of the stored fields, synchronous:
+ *   GBST_RED_SUM    sum_p u_p            (heat mass)
+ *   GBST_RED_L2SQ   sum_p u_p^2
+ *   GBST_RED_MAXABS max_p |u_p|
+ *   GBST_RED_ENERGY wave only: E = sum_p (u_p - v_p)^2 / kappa_p + sum_p u_p (A v)_p,
+ *                   u = u^n, v = u^{n-1}, A = -L (zero halo): the leapfrog discrete
+ *                   energy, conserved by the source-free scheme.
+ * Returns EUNSTABLE (with *out set) if the result is NaN or Inf. */
+gbst_status stencil_reduce_f64(gbst_handle h, int kind, double *out);
+
+/* Describe the execution plan chosen for the sweep kernel (NUL-terminated
+ * text into buf of size len). */
+gbst_status stencil_describe(gbst_handle h, char *buf, size_t len);
+
+/* Destroy the handle and free its device memory (synchronises first). */
+gbst_status stencil_destroy(gbst_handle h);
+
+/* Device time of the last sweep kernel launches: the sum over the launches of
+ * the last stencil_run call, measured with CUDA events on the handle's stream
+ * when `profile` was enabled with stencil_set_profile.  ms receives the total,
+ * launches the count.  Synchronises. */
+gbst_status stencil_set_profile(gbst_handle h, int enable);
+gbst_status stencil_last_kernel_time(gbst_handle h, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBSTENCIL_H */

@@ -1,0 +1,1173 @@
+// C-ABI implementation: handles, field layout, decomposition (dmp.swap
+// exchanges), execution planning, TMA descriptors, CUDA-graph capture of the
+// step loop, field transfers and reductions.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "gbst_internal.h"
+
+namespace gbst {
+
+// ---------------------------------------------------------------- errors ---
+static thread_local std::string t_err;
+
+static bool log_enabled()
+{
+    static const bool on = [] {
+        const char *e = getenv("GBST_LOG");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
+static gbst_status fail(gbst_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    if (log_enabled())
+        fprintf(stderr, "[gbstencil] %s\n", buf);
+    return st;
+}
+
+#define GBST_CUDA(call)                                                                             \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(GBST_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                  \
+    } while (0)
+
+// ---------------------------------------------------------------- layout ---
+Layout make_layout(int ndim, int64_t nx, int64_t ny, int64_t nz, int r, int es, int G)
+{
+    Layout L;
+    L.nx = nx;
+    L.ny = ny;
+    L.nz = ndim == 3 ? nz : 1;
+    L.r = r;
+    L.rz = ndim == 3 ? r : 0;
+    L.G = G;
+    L.es = es;
+    const int64_t align = 128 / es;
+    L.pitch = (nx + 2 * G + align - 1) / align * align;
+    L.rows = ny + 2 * r;
+    L.planes = L.nz + 2 * L.rz;
+    L.origin = (L.rz * L.rows + r) * L.pitch + G;
+    L.elems = L.pitch * L.rows * L.planes;
+    L.bytes = (static_cast<size_t>(L.elems) * es + 255) / 256 * 256;
+    return L;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h, std::string *err)
+{
+    auto fn = tmap_encoder();
+    if (!fn) {
+        *err = "cuTensorMapEncodeTiled is not available from the driver";
+        return false;
+    }
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(L.pitch), static_cast<cuuint64_t>(L.rows),
+                                static_cast<cuuint64_t>(L.planes)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(L.pitch) * L.es,
+                                   static_cast<cuuint64_t>(L.pitch) * L.rows * L.es};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt =
+        storage == GBST_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = fn(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char b[160];
+        snprintf(b, sizeof b, "cuTensorMapEncodeTiled failed (%d) for box %dx%d, dims %lld x %lld x %lld",
+                 static_cast<int>(r), box_w, box_h, static_cast<long long>(L.pitch),
+                 static_cast<long long>(L.rows), static_cast<long long>(L.planes));
+        *err = b;
+        return false;
+    }
+    return true;
+}
+
+// Central second-derivative weights of accuracy 2r, closed form:
+//   w_m = 2 (-1)^{m+1} (r!)^2 / (m^2 (r-m)! (r+m)!),  w_0 = -2 sum_{m>=1} w_m.
+static void central_weights(int r, double *w)
+{
+    auto fact = [](int n) {
+        double f = 1.0;
+        for (int i = 2; i <= n; ++i)
+            f *= i;
+        return f;
+    };
+    double s = 0.0;
+    for (int m = 1; m <= r; ++m) {
+        const double v = 2.0 * ((m + 1) % 2 == 0 ? 1.0 : -1.0) * fact(r) * fact(r) /
+                         (static_cast<double>(m) * m * fact(r - m) * fact(r + m));
+        w[m] = v;
+        s += v;
+    }
+    w[0] = -2.0 * s;
+}
+
+// max over theta of |w_0 + 2 sum_m w_m cos(m theta)|, sampled densely (the
+// standard weights peak at theta = pi; caller weights may peak elsewhere).
+static double symbol_max(int r, const double *w)
+{
+    double best = 0.0;
+    const int n = 4096;
+    for (int i = 0; i <= n; ++i) {
+        const double th = M_PI * i / n;
+        double v = w[0];
+        for (int m = 1; m <= r; ++m)
+            v += 2.0 * w[m] * cos(m * th);
+        best = std::max(best, std::fabs(v));
+    }
+    return best;
+}
+
+// ---------------------------------------------------------------- memory ---
+struct Allocator {
+    gbst_allocator a{};
+    bool custom = false;
+    cudaStream_t s = nullptr;
+    void *alloc(size_t bytes)
+    {
+        if (bytes == 0)
+            bytes = 256;
+        if (custom)
+            return a.alloc(bytes, s, a.ctx);
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void release(void *p, size_t bytes)
+    {
+        if (!p)
+            return;
+        if (custom)
+            a.release(p, bytes, s, a.ctx);
+        else
+            cudaFree(p);
+    }
+};
+
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace gbst
+
+using namespace gbst;
+
+struct Sub {
+    Layout lu, lk;
+    int64_t g0[3];  // global interior offset (x, y, z)
+    int c[3];       // coordinates in the decomposition grid
+};
+
+struct Plan {
+    StreamVariant var{};
+    bool stream = false;
+    int txt = 16;
+    int zchunks = 1;
+    int ctas = 0;
+    size_t smem = 0;
+    int occupancy = 0;
+    int nunits = 0;
+    int max_box_bytes = 0;
+};
+
+struct gbst_grid_s {
+    gbst_desc d{};
+    int ndim = 3, R = 1, es = 4;
+    double w[kMaxRadius + 1] = {0};
+    double a = 0.0, S = 0.0;
+    int64_t dims[3] = {1, 1, 1};
+    int decomp[3] = {1, 1, 1};
+    cudaStream_t stream = nullptr;
+    Allocator mem;
+    std::vector<DevMem> owned;
+    std::vector<Sub> subs;
+    std::vector<GridDev> hgrids;
+    GridDev *dgrids = nullptr;
+    Unit *dunits = nullptr;
+    size_t units_cap = 0;
+    CopyBox *dboxes = nullptr;
+    int nboxes = 0;
+    int64_t max_box_elems = 0;
+    int64_t max_points = 0;
+    Plan plan;
+    int parity = 0;
+    int64_t step = 0;
+    int *derr = nullptr;
+    double *dpartials = nullptr;
+    int red_blocks_per_grid = 0;
+    double *dred_out = nullptr;
+    ReduceGrid *dred_grids = nullptr;
+    // source
+    bool has_src = false;
+    int src_sub = -1;
+    int64_t src_local[3] = {0, 0, 0};
+    double f0 = 0, t0 = 0, amp = 0;
+    double kappa_src = 0.0;
+    float *dsrc = nullptr;
+    float *hsrc = nullptr;
+    int64_t src_cap = 0;  // steps
+    cudaEvent_t src_ev = nullptr;
+    bool kappa_set = false, unstable = false;
+    gbst_status sticky = GBST_OK;
+    std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs;
+    bool profile = false;
+    std::vector<cudaEvent_t> prof_ev;
+    int64_t prof_launches = 0;
+};
+
+namespace {
+
+int num_sms()
+{
+    static int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
+    return n;
+}
+
+void *dalloc(gbst_handle h, size_t bytes)
+{
+    void *p = h->mem.alloc(bytes);
+    if (p)
+        h->owned.push_back(DevMem{p, bytes});
+    return p;
+}
+
+void dfree(gbst_handle h, void *p)
+{
+    for (size_t i = 0; i < h->owned.size(); ++i)
+        if (h->owned[i].p == p) {
+            h->mem.release(p, h->owned[i].bytes);
+            h->owned.erase(h->owned.begin() + i);
+            return;
+        }
+}
+
+gbst_status check_handle(gbst_handle h)
+{
+    if (!h)
+        return fail(GBST_EINVAL, "null handle");
+    if (h->sticky == GBST_ECUDA || h->sticky == GBST_ETIMEOUT)
+        return fail(h->sticky, "handle is poisoned by an earlier device error");
+    return GBST_OK;
+}
+
+// Read the device error word; converts a device-side failure into a sticky status.
+gbst_status poll_device_error(gbst_handle h)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        h->sticky = GBST_ECUDA;
+        return fail(GBST_ECUDA, "device error: %s", cudaGetErrorString(e));
+    }
+    int code = 0;
+    e = cudaMemcpy(&code, h->derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        h->sticky = GBST_ECUDA;
+        return fail(GBST_ECUDA, "reading the device error word: %s", cudaGetErrorString(e));
+    }
+    if (code != kDevOk) {
+        h->sticky = GBST_ETIMEOUT;
+        return fail(GBST_ETIMEOUT, "a bounded device-side wait expired (code %d)", code);
+    }
+    return GBST_OK;
+}
+
+void destroy_graphs(gbst_handle h)
+{
+    for (auto &kv : h->graphs)
+        cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+// ---- plan: tiles, TMA boxes, work units ----------------------------------
+gbst_status build_plan(gbst_handle h, int txt, int zchunks_req, int ctas_req)
+{
+    const int st = h->d.storage;
+    const int px = px_of(st);
+    const int G = px;
+    Plan p;
+    p.var = StreamVariant{h->R, h->d.eq, st, h->ndim == 3, 128, st == GBST_BF16 ? 1 : 2, 3};
+    p.stream = h->d.kernel != GBST_KERNEL_SIMPLE && stream_variant_exists(p.var);
+    if (h->d.kernel == GBST_KERNEL_STREAM && !p.stream)
+        return fail(GBST_ENOTSUP, "no streaming kernel for radius %d", h->R);
+    const int nt = p.var.nthreads;
+    // tile width: txt threads along x (tile width = txt*px <= 256 - 2G for the TMA box)
+    if (txt <= 0)
+        txt = st == GBST_BF16 ? 8 : 16;
+    while (txt * px + 2 * G > 256 && txt > 1)
+        txt /= 2;
+    if (nt % txt)
+        return fail(GBST_EINVAL, "tile: %d threads along x does not divide %d", txt, nt);
+    p.txt = txt;
+    const int TX = txt * px, TY = (nt / txt) * p.var.py;
+    const int box_w = TX + 2 * G, box_h = TY + 2 * h->R;
+    if (box_h > 256)
+        return fail(GBST_EINVAL, "tile height %d too large for a TMA box", TY);
+    p.max_box_bytes = box_w * box_h * h->es;
+
+    int64_t T = 0;
+    for (size_t i = 0; i < h->subs.size(); ++i) {
+        GridDev &g = h->hgrids[i];
+        const Sub &s = h->subs[i];
+        g.txt = txt;
+        g.tiles_x = static_cast<int>((s.lu.nx + TX - 1) / TX);
+        g.tiles_y = static_cast<int>((s.lu.ny + TY - 1) / TY);
+        g.box_bytes = p.max_box_bytes;
+        T += static_cast<int64_t>(g.tiles_x) * g.tiles_y;
+        if (p.stream) {
+            std::string err;
+            for (int b = 0; b < 2; ++b)
+                if (!encode_tmap(&g.tmap[b], g.buf[b], s.lu, st, box_w, box_h, &err))
+                    return fail(GBST_ECUDA, "%s", err.c_str());
+        }
+    }
+    if (p.stream) {
+        p.smem = stream_smem_bytes(p.var, p.max_box_bytes);
+        p.occupancy = stream_occupancy(p.var, p.smem);
+        if (p.occupancy <= 0)
+            return fail(GBST_ENOTSUP, "streaming kernel does not fit (smem %zu)", p.smem);
+        const int64_t cmax = static_cast<int64_t>(p.occupancy) * num_sms();
+        const int64_t nz = h->subs[0].lu.nz;
+        int zc = 1;
+        if (h->ndim == 3) {
+            if (zchunks_req > 0) {
+                zc = zchunks_req;
+            } else {
+                // minimise waves * (chunk length + 2r): a balance / halo-overhead trade-off
+                double best = 1e300;
+                for (int c = 1; c <= 64 && nz / c >= 2 * h->R + 1; ++c) {
+                    const int64_t units = T * c;
+                    const int64_t waves = (units + cmax - 1) / cmax;
+                    const double cost = static_cast<double>(waves) * ((nz + c - 1) / c + 2 * h->R);
+                    if (cost < best * 0.999) {
+                        best = cost;
+                        zc = c;
+                    }
+                }
+            }
+        }
+        p.zchunks = zc;
+        std::vector<Unit> units;
+        for (int c = 0; c < zc; ++c)
+            for (size_t i = 0; i < h->subs.size(); ++i) {
+                const GridDev &g = h->hgrids[i];
+                const int64_t n = h->subs[i].lu.nz;
+                const int z0 = static_cast<int>(n * c / zc), z1 = static_cast<int>(n * (c + 1) / zc);
+                if (z1 <= z0)
+                    continue;
+                for (int t = 0; t < g.tiles_x * g.tiles_y; ++t)
+                    units.push_back(Unit{static_cast<int>(i), t, z0, z1});
+            }
+        p.nunits = static_cast<int>(units.size());
+        p.ctas = static_cast<int>(std::min<int64_t>(p.nunits, ctas_req > 0 ? ctas_req : cmax));
+        if (units.size() > h->units_cap) {
+            if (h->dunits)
+                dfree(h, h->dunits);
+            h->dunits = static_cast<Unit *>(dalloc(h, units.size() * sizeof(Unit)));
+            if (!h->dunits)
+                return fail(GBST_ENOMEM, "work-unit list");
+            h->units_cap = units.size();
+        }
+        GBST_CUDA(cudaMemcpyAsync(h->dunits, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice,
+                                  h->stream));
+    }
+    GBST_CUDA(cudaMemcpyAsync(h->dgrids, h->hgrids.data(), h->hgrids.size() * sizeof(GridDev),
+                              cudaMemcpyHostToDevice, h->stream));
+    GBST_CUDA(cudaStreamSynchronize(h->stream));
+    h->plan = p;
+    destroy_graphs(h);
+    return GBST_OK;
+}
+
+// ---- halo copy list: dmp.swap exchanges (decomposition) or periodic wrap --
+struct Exch {
+    int64_t at[3], size[3], off[3];
+    int to[3];
+};
+
+// Exchanges of one subdomain, following Section 4.2: receive into [at, at+size)
+// from the neighbour at relative position `to`, send [at+off, at+off+size).
+// Coordinates are interior-relative (ghosts at negative / >= n indices).
+std::vector<Exch> exchanges(const Sub &s, const int grid[3], int ndim, int R)
+{
+    std::vector<Exch> out;
+    const int64_t n[3] = {s.lu.nx, s.lu.ny, s.lu.nz};
+    for (int a = 0; a < ndim; ++a)
+        for (int dir = -1; dir <= 1; dir += 2) {
+            const int nb = s.c[a] + dir;
+            if (nb < 0 || nb >= grid[a])
+                continue;
+            Exch e{};
+            for (int b = 0; b < 3; ++b) {
+                if (b == a) {
+                    e.at[b] = dir < 0 ? -R : n[b];
+                    e.size[b] = R;
+                    e.off[b] = dir < 0 ? R : -R;
+                    e.to[b] = dir;
+                } else {
+                    e.at[b] = 0;
+                    e.size[b] = b < ndim ? n[b] : 1;
+                    e.off[b] = 0;
+                    e.to[b] = 0;
+                }
+            }
+            out.push_back(e);
+        }
+    return out;
+}
+
+int64_t byte_off(const Layout &L, int64_t i, int64_t j, int64_t k)
+{
+    return ((k + L.rz) * L.rows + (j + L.r)) * L.pitch * L.es + (i + L.G) * L.es;
+}
+
+gbst_status build_copies(gbst_handle h)
+{
+    std::vector<CopyBox> boxes;
+    const int R = h->R;
+    if (h->subs.size() > 1) {
+        auto index_of = [&](const int c[3]) {
+            return (c[2] * h->decomp[1] + c[1]) * h->decomp[0] + c[0];
+        };
+        for (size_t i = 0; i < h->subs.size(); ++i) {
+            const Sub &s = h->subs[i];
+            for (const Exch &e : exchanges(s, h->decomp, h->ndim, R)) {
+                int nc[3] = {s.c[0] + e.to[0], s.c[1] + e.to[1], s.c[2] + e.to[2]};
+                const int ni = index_of(nc);
+                const Sub &ns = h->subs[ni];
+                // the neighbour's exchange that points back at us gives its send region
+                const int back[3] = {-e.to[0], -e.to[1], -e.to[2]};
+                bool found = false;
+                for (const Exch &f : exchanges(ns, h->decomp, h->ndim, R)) {
+                    if (f.to[0] != back[0] || f.to[1] != back[1] || f.to[2] != back[2])
+                        continue;
+                    CopyBox b{};
+                    b.dst_grid = static_cast<int>(i);
+                    b.src_grid = ni;
+                    b.dst_off = byte_off(s.lu, e.at[0], e.at[1], e.at[2]);
+                    b.src_off = byte_off(ns.lu, f.at[0] + f.off[0], f.at[1] + f.off[1], f.at[2] + f.off[2]);
+                    b.ex = e.size[0];
+                    b.ey = e.size[1];
+                    b.ez = e.size[2];
+                    boxes.push_back(b);
+                    found = true;
+                }
+                if (!found)
+                    return fail(GBST_EINVAL, "internal: unmatched exchange");
+            }
+        }
+    } else if (h->d.bc == GBST_BC_PERIODIC) {
+        const Sub &s = h->subs[0];
+        const int64_t n[3] = {s.lu.nx, s.lu.ny, s.lu.nz};
+        for (int a = 0; a < h->ndim; ++a)
+            for (int side = 0; side < 2; ++side) {
+                int64_t dst[3] = {0, 0, 0}, src[3] = {0, 0, 0}, ext[3] = {n[0], n[1], n[2]};
+                dst[a] = side == 0 ? -R : n[a];
+                src[a] = side == 0 ? n[a] - R : 0;
+                ext[a] = R;
+                CopyBox b{};
+                b.dst_grid = b.src_grid = 0;
+                b.dst_off = byte_off(s.lu, dst[0], dst[1], dst[2]);
+                b.src_off = byte_off(s.lu, src[0], src[1], src[2]);
+                b.ex = ext[0];
+                b.ey = ext[1];
+                b.ez = ext[2];
+                boxes.push_back(b);
+            }
+    }
+    h->nboxes = static_cast<int>(boxes.size());
+    h->max_box_elems = 0;
+    for (const CopyBox &b : boxes)
+        h->max_box_elems = std::max(h->max_box_elems, b.ex * b.ey * b.ez);
+    if (!boxes.empty()) {
+        h->dboxes = static_cast<CopyBox *>(dalloc(h, boxes.size() * sizeof(CopyBox)));
+        if (!h->dboxes)
+            return fail(GBST_ENOMEM, "halo copy list");
+        GBST_CUDA(cudaMemcpyAsync(h->dboxes, boxes.data(), boxes.size() * sizeof(CopyBox), cudaMemcpyHostToDevice,
+                                  h->stream));
+    }
+    return GBST_OK;
+}
+
+SweepArgs sweep_args(gbst_handle h, int parity, const float *srcval)
+{
+    SweepArgs a{};
+    a.grids = h->dgrids;
+    a.units = h->dunits;
+    a.nunits = h->plan.nunits;
+    a.parity = parity;
+    a.ndim = h->ndim;
+    a.wc = static_cast<float>(h->ndim * h->w[0]);
+    for (int m = 1; m <= h->R; ++m)
+        a.w[m] = static_cast<float>(h->w[m]);
+    a.a = static_cast<float>(h->a);
+    a.srcval = srcval;
+    a.err = h->derr;
+    return a;
+}
+
+// Enqueue one time step (halo copies + sweep) at the given parity.
+gbst_status enqueue_step(gbst_handle h, int parity, const float *srcval, int prof_index)
+{
+    if (h->nboxes > 0) {
+        cudaError_t e =
+            launch_halo_copies(h->dgrids, h->dboxes, h->nboxes, parity, h->es, h->max_box_elems, h->stream);
+        if (e != cudaSuccess)
+            return fail(GBST_ECUDA, "halo copy launch: %s", cudaGetErrorString(e));
+    }
+    const SweepArgs a = sweep_args(h, parity, srcval);
+    if (prof_index >= 0)
+        GBST_CUDA(cudaEventRecordWithFlags(h->prof_ev[2 * prof_index], h->stream,
+                                           cudaEventRecordExternal));
+    cudaError_t e;
+    if (h->plan.stream)
+        e = launch_stream_sweep(h->plan.var, a, h->plan.ctas, h->plan.smem, h->stream);
+    else
+        e = launch_simple_sweep(h->R, h->d.eq, h->d.storage, a, static_cast<int>(h->subs.size()), h->max_points,
+                                h->stream);
+    if (e != cudaSuccess)
+        return fail(GBST_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+    if (prof_index >= 0)
+        GBST_CUDA(cudaEventRecordWithFlags(h->prof_ev[2 * prof_index + 1], h->stream,
+                                           cudaEventRecordExternal));
+    return GBST_OK;
+}
+
+double ricker(double t, double f0, double t0)
+{
+    const double a = M_PI * f0 * (t - t0);
+    const double a2 = a * a;
+    return (1.0 - 2.0 * a2) * std::exp(-a2);
+}
+
+gbst_status ensure_src_capacity(gbst_handle h, int64_t nsteps)
+{
+    const int64_t ns = static_cast<int64_t>(h->subs.size());
+    if (nsteps <= h->src_cap)
+        return GBST_OK;
+    int64_t cap = std::max<int64_t>(nsteps, 64);
+    if (h->dsrc)
+        dfree(h, h->dsrc);
+    if (h->hsrc)
+        cudaFreeHost(h->hsrc);
+    h->hsrc = nullptr;
+    h->dsrc = static_cast<float *>(dalloc(h, cap * ns * sizeof(float)));
+    if (!h->dsrc)
+        return fail(GBST_ENOMEM, "source table");
+    GBST_CUDA(cudaMallocHost(&h->hsrc, cap * ns * sizeof(float)));
+    h->src_cap = cap;
+    destroy_graphs(h);  // graphs reference the table address
+    return GBST_OK;
+}
+
+gbst_status read_kappa_at_source(gbst_handle h)
+{
+    if (!h->has_src)
+        return GBST_OK;
+    const Sub &s = h->subs[h->src_sub];
+    const GridDev &g = h->hgrids[h->src_sub];
+    const int64_t k = h->ndim == 3 ? h->src_local[2] : 0;
+    const int64_t idx = s.lk.origin + (k * s.lk.rows + h->src_local[1]) * s.lk.pitch + h->src_local[0];
+    float v = 0.f;
+    GBST_CUDA(cudaStreamSynchronize(h->stream));
+    GBST_CUDA(cudaMemcpy(&v, g.kappa + idx, sizeof(float), cudaMemcpyDeviceToHost));
+    h->kappa_src = v;
+    return GBST_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+int gbst_version(void) { return 10000; }
+
+const char *stencil_last_error(void) { return t_err.c_str(); }
+
+gbst_status stencil_fd_weights(int space_order, double *out)
+{
+    if (!out || space_order < 2 || space_order > 16 || space_order % 2)
+        return fail(GBST_EINVAL, "space_order must be even in [2, 16]");
+    central_weights(space_order / 2, out);
+    return GBST_OK;
+}
+
+gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
+{
+    if (!desc || !out)
+        return fail(GBST_EINVAL, "null desc or out");
+    *out = nullptr;
+    const gbst_desc &d = *desc;
+    if (d.ndim != 2 && d.ndim != 3)
+        return fail(GBST_EINVAL, "ndim must be 2 or 3");
+    if (d.space_order != 2 && d.space_order != 4 && d.space_order != 8)
+        return fail(GBST_EINVAL, "space_order must be 2, 4 or 8");
+    if (d.eq != GBST_HEAT && d.eq != GBST_WAVE)
+        return fail(GBST_EINVAL, "eq must be GBST_HEAT or GBST_WAVE");
+    if (d.bc != GBST_BC_ZERO && d.bc != GBST_BC_PERIODIC)
+        return fail(GBST_EINVAL, "bc must be GBST_BC_ZERO or GBST_BC_PERIODIC");
+    if (d.storage != GBST_F32 && d.storage != GBST_BF16)
+        return fail(GBST_EINVAL, "storage must be GBST_F32 or GBST_BF16");
+    if (d.kernel < GBST_KERNEL_AUTO || d.kernel > GBST_KERNEL_SIMPLE)
+        return fail(GBST_EINVAL, "kernel must be GBST_KERNEL_AUTO, _STREAM or _SIMPLE");
+    const int R = d.space_order / 2;
+    int64_t dims[3] = {d.dims[0], d.dims[1], d.ndim == 3 ? d.dims[2] : 1};
+    for (int a = 0; a < d.ndim; ++a)
+        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
+            return fail(GBST_EINVAL, "dims[%d] = %lld out of range", a, static_cast<long long>(dims[a]));
+    int decomp[3];
+    for (int a = 0; a < 3; ++a) {
+        decomp[a] = d.decomp[a] <= 0 ? 1 : d.decomp[a];
+        if (a >= d.ndim && decomp[a] != 1)
+            return fail(GBST_EINVAL, "decomp[%d] must be 1 for a %dD grid", a, d.ndim);
+        if (decomp[a] > dims[a])
+            return fail(GBST_EINVAL, "decomp[%d] larger than the grid", a);
+    }
+    const bool decomposed = decomp[0] * decomp[1] * decomp[2] > 1;
+    if (decomposed && d.bc == GBST_BC_PERIODIC)
+        return fail(GBST_ENOTSUP, "periodic boundaries are not supported in decomposition mode");
+    if (d.bc == GBST_BC_PERIODIC)
+        for (int a = 0; a < d.ndim; ++a)
+            if (dims[a] < R)
+                return fail(GBST_EINVAL, "periodic boundaries need at least r points per axis");
+    if (d.h <= 0.0 || d.dt <= 0.0)
+        return fail(GBST_EINVAL, "h and dt must be positive");
+
+    gbst_handle h = new (std::nothrow) gbst_grid_s;
+    if (!h)
+        return fail(GBST_ENOMEM, "handle");
+    h->d = d;
+    h->d.coeffs = nullptr;
+    h->ndim = d.ndim;
+    h->R = R;
+    h->es = d.storage == GBST_BF16 ? 2 : 4;
+    for (int a = 0; a < 3; ++a) {
+        h->dims[a] = dims[a];
+        h->decomp[a] = decomp[a];
+    }
+    if (d.coeffs)
+        for (int m = 0; m <= R; ++m)
+            h->w[m] = d.coeffs[m];
+    else
+        central_weights(R, h->w);
+    h->S = symbol_max(R, h->w);
+    h->a = d.alpha * d.dt / (d.h * d.h);
+    h->stream = static_cast<cudaStream_t>(d.stream);
+    h->mem.s = h->stream;
+    if (d.allocator) {
+        if (!d.allocator->alloc || !d.allocator->release) {
+            delete h;
+            return fail(GBST_EINVAL, "allocator needs alloc and release");
+        }
+        h->mem.a = *d.allocator;
+        h->mem.custom = true;
+    }
+    if (d.eq == GBST_HEAT && !d.allow_unstable && h->a * h->ndim * h->S > 2.0 * (1.0 + 1e-12)) {
+        delete h;
+        return fail(GBST_EUNSTABLE, "heat step a*ndim*S = %g exceeds 2 (von Neumann limit)",
+                    h->a * d.ndim * h->S);
+    }
+
+    auto bail = [&](gbst_status st) {
+        stencil_destroy(h);
+        return st;
+    };
+
+    // subdomains: equal slicing, the first n mod D parts one larger
+    auto split = [](int64_t n, int parts, int i, int64_t *start) {
+        const int64_t base = n / parts, rem = n % parts;
+        *start = i * base + std::min<int64_t>(i, rem);
+        return base + (i < rem ? 1 : 0);
+    };
+    const int px = px_of(d.storage);
+    for (int cz = 0; cz < decomp[2]; ++cz)
+        for (int cy = 0; cy < decomp[1]; ++cy)
+            for (int cx = 0; cx < decomp[0]; ++cx) {
+                Sub s{};
+                s.c[0] = cx;
+                s.c[1] = cy;
+                s.c[2] = cz;
+                int64_t n[3];
+                n[0] = split(dims[0], decomp[0], cx, &s.g0[0]);
+                n[1] = split(dims[1], decomp[1], cy, &s.g0[1]);
+                n[2] = split(dims[2], decomp[2], cz, &s.g0[2]);
+                s.lu = make_layout(d.ndim, n[0], n[1], n[2], R, h->es, 16 / h->es);
+                s.lk = make_layout(d.ndim, n[0], n[1], n[2], R, 4, px);
+                h->subs.push_back(s);
+                h->max_points = std::max(h->max_points, n[0] * n[1] * n[2]);
+            }
+    const size_t ns = h->subs.size();
+    h->hgrids.assign(ns, GridDev{});
+    for (size_t i = 0; i < ns; ++i) {
+        const Sub &s = h->subs[i];
+        GridDev &g = h->hgrids[i];
+        for (int b = 0; b < 2; ++b) {
+            g.buf[b] = dalloc(h, s.lu.bytes);
+            if (!g.buf[b]) {
+                fail(GBST_ENOMEM, "field allocation of %zu bytes", s.lu.bytes);
+                return bail(GBST_ENOMEM);
+            }
+            if (cudaMemsetAsync(g.buf[b], 0, s.lu.bytes, h->stream) != cudaSuccess) {
+                fail(GBST_ECUDA, "memset of a field");
+                return bail(GBST_ECUDA);
+            }
+        }
+        if (d.eq == GBST_WAVE) {
+            g.kappa = static_cast<float *>(dalloc(h, s.lk.bytes));
+            if (!g.kappa) {
+                fail(GBST_ENOMEM, "kappa allocation");
+                return bail(GBST_ENOMEM);
+            }
+            if (cudaMemsetAsync(g.kappa, 0, s.lk.bytes, h->stream) != cudaSuccess) {
+                fail(GBST_ECUDA, "memset of kappa");
+                return bail(GBST_ECUDA);
+            }
+        }
+        g.nx = s.lu.nx;
+        g.ny = s.lu.ny;
+        g.nz = s.lu.nz;
+        g.pitch = s.lu.pitch;
+        g.rows = s.lu.rows;
+        g.origin = s.lu.origin;
+        g.kpitch = s.lk.pitch;
+        g.krows = s.lk.rows;
+        g.korigin = s.lk.origin;
+    }
+    h->dgrids = static_cast<GridDev *>(dalloc(h, ns * sizeof(GridDev)));
+    h->derr = static_cast<int *>(dalloc(h, 256));
+    h->red_blocks_per_grid = std::max(1, reduce_blocks_for(h->max_points) / static_cast<int>(ns));
+    h->dpartials = static_cast<double *>(dalloc(h, ns * h->red_blocks_per_grid * sizeof(double)));
+    h->dred_out = static_cast<double *>(dalloc(h, 256));
+    h->dred_grids = static_cast<ReduceGrid *>(dalloc(h, ns * sizeof(ReduceGrid)));
+    if (!h->dgrids || !h->derr || !h->dpartials || !h->dred_out || !h->dred_grids) {
+        fail(GBST_ENOMEM, "metadata allocation");
+        return bail(GBST_ENOMEM);
+    }
+    if (cudaMemsetAsync(h->derr, 0, 256, h->stream) != cudaSuccess) {
+        fail(GBST_ECUDA, "memset of the error word");
+        return bail(GBST_ECUDA);
+    }
+    gbst_status st = build_copies(h);
+    if (st != GBST_OK)
+        return bail(st);
+    st = build_plan(h, d.tile > 0 ? d.tile : 0, 0, 0);
+    if (st != GBST_OK)
+        return bail(st);
+    *out = h;
+    return GBST_OK;
+}
+
+gbst_status stencil_destroy(gbst_handle h)
+{
+    if (!h)
+        return GBST_OK;
+    cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    for (cudaEvent_t e : h->prof_ev)
+        cudaEventDestroy(e);
+    if (h->src_ev)
+        cudaEventDestroy(h->src_ev);
+    if (h->hsrc)
+        cudaFreeHost(h->hsrc);
+    for (DevMem &m : h->owned)
+        h->mem.release(m.p, m.bytes);
+    h->owned.clear();
+    delete h;
+    return GBST_OK;
+}
+
+static gbst_status transfer(gbst_handle h, int field, void *user, int dtype, int on_device, bool to_dev)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (!user)
+        return fail(GBST_EINVAL, "null buffer");
+    if (dtype != GBST_F32 && dtype != GBST_F64 && dtype != GBST_BF16)
+        return fail(GBST_EINVAL, "dtype must be GBST_F32, GBST_F64 or GBST_BF16");
+    if (field != GBST_U && field != GBST_U_PREV && field != GBST_VEL)
+        return fail(GBST_EINVAL, "unknown field %d", field);
+    if (h->d.eq == GBST_HEAT && field != GBST_U)
+        return fail(GBST_EINVAL, "heat grids have only the field GBST_U");
+    const size_t esz = dtype == GBST_F64 ? 8 : dtype == GBST_F32 ? 4 : 2;
+    const size_t n = static_cast<size_t>(h->dims[0] * h->dims[1] * h->dims[2]);
+    void *dense = user;
+    void *staging = nullptr;
+    if (!on_device) {
+        staging = h->mem.alloc(n * esz);
+        if (!staging)
+            return fail(GBST_ENOMEM, "staging buffer of %zu bytes", n * esz);
+        dense = staging;
+        if (to_dev) {
+            cudaError_t e = cudaMemcpyAsync(staging, user, n * esz, cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) {
+                h->mem.release(staging, n * esz);
+                return fail(GBST_ECUDA, "host-to-device copy: %s", cudaGetErrorString(e));
+            }
+        }
+    }
+    for (size_t i = 0; i < h->subs.size(); ++i) {
+        const Sub &s = h->subs[i];
+        const GridDev &g = h->hgrids[i];
+        XferArgs x{};
+        const bool kap = field == GBST_VEL;
+        const Layout &L = kap ? s.lk : s.lu;
+        x.padded = kap ? static_cast<void *>(g.kappa) : g.buf[field == GBST_U ? h->parity : 1 - h->parity];
+        x.storage = kap ? GBST_F32 : h->d.storage;
+        x.pitch = L.pitch;
+        x.rows = L.rows;
+        x.origin = L.origin;
+        x.nx = L.nx;
+        x.ny = L.ny;
+        x.nz = L.nz;
+        x.gx = s.g0[0];
+        x.gy = s.g0[1];
+        x.gz = s.g0[2];
+        x.gnx = h->dims[0];
+        x.gny = h->dims[1];
+        x.dense = dense;
+        x.dense_dtype = dtype;
+        x.scale_sq = (kap && to_dev) ? (h->d.dt * h->d.dt) / (h->d.h * h->d.h) : 0.0;
+        cudaError_t e = to_dev ? launch_scatter(x, h->stream) : launch_gather(x, h->stream);
+        if (e != cudaSuccess) {
+            if (staging)
+                h->mem.release(staging, n * esz);
+            return fail(GBST_ECUDA, "transfer kernel: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!on_device && !to_dev) {
+        cudaError_t e = cudaMemcpyAsync(user, staging, n * esz, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) {
+            h->mem.release(staging, n * esz);
+            return fail(GBST_ECUDA, "device-to-host copy: %s", cudaGetErrorString(e));
+        }
+    }
+    st = poll_device_error(h);
+    if (staging)
+        h->mem.release(staging, n * esz);
+    return st;
+}
+
+gbst_status stencil_reduce_f64(gbst_handle h, int kind, double *out);
+
+gbst_status stencil_set_field(gbst_handle h, int field, const void *src, int src_dtype, int src_on_device)
+{
+    gbst_status st = transfer(h, field, const_cast<void *>(src), src_dtype, src_on_device, true);
+    if (st != GBST_OK || field != GBST_VEL)
+        return st;
+    h->kappa_set = true;
+    st = read_kappa_at_source(h);
+    if (st != GBST_OK)
+        return st;
+    // stability of the leapfrog scheme: kappa_max * ndim * S <= 4
+    double kmax = 0.0;
+    {
+        // max |kappa| through the FP64 reduction kernel (kappa stored as FP32)
+        std::vector<ReduceGrid> rg(h->subs.size());
+        for (size_t i = 0; i < h->subs.size(); ++i) {
+            const Sub &s = h->subs[i];
+            rg[i] = ReduceGrid{h->hgrids[i].kappa, nullptr, nullptr, s.lk.pitch, s.lk.rows, s.lk.origin,
+                               0, 0, 0, s.lk.nx, s.lk.ny, s.lk.nz};
+        }
+        GBST_CUDA(cudaMemcpyAsync(h->dred_grids, rg.data(), rg.size() * sizeof(ReduceGrid), cudaMemcpyHostToDevice,
+                                  h->stream));
+        const int nb = h->red_blocks_per_grid * static_cast<int>(h->subs.size());
+        GBST_CUDA(launch_reduce_partials(GBST_RED_MAXABS, GBST_F32, h->ndim, h->R, h->w, h->dred_grids,
+                                         static_cast<int>(h->subs.size()), h->max_points, h->dpartials, nb,
+                                         h->stream));
+        GBST_CUDA(launch_reduce_final(GBST_RED_MAXABS, h->dpartials, nb, h->dred_out, h->stream));
+        GBST_CUDA(cudaMemcpyAsync(&kmax, h->dred_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        GBST_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    h->unstable = kmax * h->ndim * h->S > 4.0 * (1.0 + 1e-9);
+    if (h->unstable && !h->d.allow_unstable)
+        return fail(GBST_EUNSTABLE, "wave step: kappa_max*ndim*S = %g exceeds 4 (CFL limit)", kmax * h->ndim * h->S);
+    return GBST_OK;
+}
+
+gbst_status stencil_get_field(gbst_handle h, int field, void *dst, int dst_dtype, int dst_on_device)
+{
+    return transfer(h, field, dst, dst_dtype, dst_on_device, false);
+}
+
+gbst_status stencil_set_source(gbst_handle h, const int64_t idx[3], double f0_hz, double t0_s, double amp)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (h->d.eq != GBST_WAVE)
+        return fail(GBST_EINVAL, "sources are only defined for the wave equation");
+    for (GridDev &g : h->hgrids)
+        g.has_src = 0;
+    h->has_src = false;
+    h->src_sub = -1;
+    if (f0_hz > 0.0) {
+        if (!idx)
+            return fail(GBST_EINVAL, "null source index");
+        const int64_t k = h->ndim == 3 ? idx[2] : 0;
+        const int64_t p[3] = {idx[0], idx[1], k};
+        for (int a = 0; a < 3; ++a)
+            if (p[a] < 0 || p[a] >= h->dims[a])
+                return fail(GBST_EINVAL, "source index outside the grid");
+        for (size_t i = 0; i < h->subs.size(); ++i) {
+            const Sub &s = h->subs[i];
+            bool in = true;
+            for (int a = 0; a < 3; ++a)
+                in = in && p[a] >= s.g0[a] &&
+                     p[a] < s.g0[a] + (a == 0 ? s.lu.nx : a == 1 ? s.lu.ny : s.lu.nz);
+            if (in) {
+                h->src_sub = static_cast<int>(i);
+                for (int a = 0; a < 3; ++a)
+                    h->src_local[a] = p[a] - s.g0[a];
+                GridDev &g = h->hgrids[i];
+                g.has_src = 1;
+                g.src_x = static_cast<int>(h->src_local[0]);
+                g.src_y = static_cast<int>(h->src_local[1]);
+                g.src_z = static_cast<int>(h->src_local[2]);
+            }
+        }
+        h->has_src = true;
+        h->f0 = f0_hz;
+        h->t0 = t0_s;
+        h->amp = amp;
+    }
+    GBST_CUDA(cudaMemcpyAsync(h->dgrids, h->hgrids.data(), h->hgrids.size() * sizeof(GridDev),
+                              cudaMemcpyHostToDevice, h->stream));
+    st = read_kappa_at_source(h);
+    destroy_graphs(h);
+    return st;
+}
+
+gbst_status stencil_run(gbst_handle h, int64_t nsteps)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (nsteps < 0)
+        return fail(GBST_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0)
+        return GBST_OK;
+    if (h->unstable && !h->d.allow_unstable)
+        return fail(GBST_EUNSTABLE, "velocity model exceeds the stability limit");
+    const int64_t ns = static_cast<int64_t>(h->subs.size());
+    const bool src = h->d.eq == GBST_WAVE && h->has_src;
+    if (src) {
+        st = ensure_src_capacity(h, nsteps);
+        if (st != GBST_OK)
+            return st;
+        if (h->src_ev)
+            GBST_CUDA(cudaEventSynchronize(h->src_ev));  // previous upload finished reading hsrc
+        else
+            GBST_CUDA(cudaEventCreateWithFlags(&h->src_ev, cudaEventDisableTiming));
+        const double scale = h->amp * h->kappa_src * h->d.h * h->d.h;
+        for (int64_t k = 0; k < nsteps; ++k)
+            for (int64_t i = 0; i < ns; ++i)
+                h->hsrc[k * ns + i] =
+                    i == h->src_sub ? static_cast<float>(scale * ricker((h->step + k) * h->d.dt, h->f0, h->t0)) : 0.f;
+        GBST_CUDA(cudaMemcpyAsync(h->dsrc, h->hsrc, nsteps * ns * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        GBST_CUDA(cudaEventRecord(h->src_ev, h->stream));
+    }
+    if (h->profile) {
+        while (static_cast<int64_t>(h->prof_ev.size()) < 2 * nsteps) {
+            cudaEvent_t e;
+            GBST_CUDA(cudaEventCreate(&e));
+            h->prof_ev.push_back(e);
+        }
+        h->prof_launches = nsteps;
+    }
+    const bool graph = h->d.use_graph && h->stream != nullptr;
+    if (graph) {
+        const auto key = std::make_pair(nsteps, h->parity + (h->profile ? 2 : 0));
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            GBST_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            int par = h->parity;
+            for (int64_t k = 0; k < nsteps; ++k) {
+                st = enqueue_step(h, par, src ? h->dsrc + k * ns : nullptr, h->profile ? static_cast<int>(k) : -1);
+                if (st != GBST_OK) {
+                    cudaGraph_t g;
+                    cudaStreamEndCapture(h->stream, &g);
+                    if (g)
+                        cudaGraphDestroy(g);
+                    return st;
+                }
+                par ^= 1;
+            }
+            cudaGraph_t g = nullptr;
+            GBST_CUDA(cudaStreamEndCapture(h->stream, &g));
+            cudaGraphExec_t ge = nullptr;
+            cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess)
+                return fail(GBST_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            it = h->graphs.emplace(key, ge).first;
+        }
+        GBST_CUDA(cudaGraphLaunch(it->second, h->stream));
+    } else {
+        int par = h->parity;
+        for (int64_t k = 0; k < nsteps; ++k) {
+            st = enqueue_step(h, par, src ? h->dsrc + k * ns : nullptr, h->profile ? static_cast<int>(k) : -1);
+            if (st != GBST_OK)
+                return st;
+            par ^= 1;
+        }
+    }
+    h->parity ^= static_cast<int>(nsteps & 1);
+    h->step += nsteps;
+    return GBST_OK;
+}
+
+gbst_status stencil_sync(gbst_handle h)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    return poll_device_error(h);
+}
+
+gbst_status stencil_get_step(gbst_handle h, int64_t *step)
+{
+    if (!h || !step)
+        return fail(GBST_EINVAL, "null argument");
+    *step = h->step;
+    return GBST_OK;
+}
+
+gbst_status stencil_set_step(gbst_handle h, int64_t step)
+{
+    if (!h || step < 0)
+        return fail(GBST_EINVAL, "bad argument");
+    h->step = step;
+    return GBST_OK;
+}
+
+gbst_status stencil_reduce_f64(gbst_handle h, int kind, double *out)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (!out)
+        return fail(GBST_EINVAL, "null out");
+    if (kind < GBST_RED_SUM || kind > GBST_RED_ENERGY)
+        return fail(GBST_EINVAL, "unknown reduction %d", kind);
+    if (kind == GBST_RED_ENERGY && h->d.eq != GBST_WAVE)
+        return fail(GBST_EINVAL, "the energy reduction is defined for the wave equation only");
+    if (kind == GBST_RED_ENERGY && h->nboxes > 0) {
+        // ghosts of u^{n-1}: swap / wrap them so the stencil in the energy sees neighbours
+        cudaError_t e = launch_halo_copies(h->dgrids, h->dboxes, h->nboxes, 1 - h->parity, h->es, h->max_box_elems,
+                                           h->stream);
+        if (e != cudaSuccess)
+            return fail(GBST_ECUDA, "halo copies: %s", cudaGetErrorString(e));
+    }
+    std::vector<ReduceGrid> rg(h->subs.size());
+    for (size_t i = 0; i < h->subs.size(); ++i) {
+        const Sub &s = h->subs[i];
+        const GridDev &g = h->hgrids[i];
+        rg[i] = ReduceGrid{g.buf[h->parity], g.buf[1 - h->parity], g.kappa, s.lu.pitch, s.lu.rows, s.lu.origin,
+                           s.lk.pitch, s.lk.rows, s.lk.origin, s.lu.nx, s.lu.ny, s.lu.nz};
+    }
+    GBST_CUDA(cudaMemcpyAsync(h->dred_grids, rg.data(), rg.size() * sizeof(ReduceGrid), cudaMemcpyHostToDevice,
+                              h->stream));
+    const int nb = h->red_blocks_per_grid * static_cast<int>(h->subs.size());
+    GBST_CUDA(launch_reduce_partials(kind, h->d.storage, h->ndim, h->R, h->w, h->dred_grids,
+                                     static_cast<int>(h->subs.size()), h->max_points, h->dpartials, nb, h->stream));
+    GBST_CUDA(launch_reduce_final(kind, h->dpartials, nb, h->dred_out, h->stream));
+    double v = 0.0;
+    GBST_CUDA(cudaMemcpyAsync(&v, h->dred_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    st = poll_device_error(h);
+    if (st != GBST_OK)
+        return st;
+    *out = v;
+    if (!std::isfinite(v))
+        return fail(GBST_EUNSTABLE, "reduction result is not finite");
+    return GBST_OK;
+}
+
+gbst_status stencil_describe(gbst_handle h, char *buf, size_t len)
+{
+    if (!h || !buf || len == 0)
+        return fail(GBST_EINVAL, "bad argument");
+    const Plan &p = h->plan;
+    const int px = px_of(h->d.storage);
+    snprintf(buf, len,
+             "{\"kernel\": \"%s\", \"R\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, \"tile\": [%d, %d], "
+             "\"zchunks\": %d, \"units\": %d, \"ctas\": %d, \"occupancy\": %d, \"smem\": %zu, \"subdomains\": %zu, "
+             "\"halo_boxes\": %d}",
+             p.stream ? "stream" : "simple", h->R, p.var.nthreads, p.var.py, p.var.depth, p.txt * px,
+             (p.var.nthreads / std::max(1, p.txt)) * p.var.py, p.zchunks, p.nunits, p.ctas, p.occupancy, p.smem,
+             h->subs.size(), h->nboxes);
+    return GBST_OK;
+}
+
+gbst_status stencil_set_profile(gbst_handle h, int enable)
+{
+    if (!h)
+        return fail(GBST_EINVAL, "null handle");
+    h->profile = enable != 0;
+    return GBST_OK;
+}
+
+gbst_status stencil_last_kernel_time(gbst_handle h, double *ms, int64_t *launches)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (!ms || !launches)
+        return fail(GBST_EINVAL, "null argument");
+    st = poll_device_error(h);
+    if (st != GBST_OK)
+        return st;
+    double tot = 0.0;
+    for (int64_t k = 0; k < h->prof_launches; ++k) {
+        float t = 0.f;
+        GBST_CUDA(cudaEventElapsedTime(&t, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]));
+        tot += t;
+    }
+    *ms = tot;
+    *launches = h->prof_launches;
+    return GBST_OK;
+}
+
+}  // extern "C"

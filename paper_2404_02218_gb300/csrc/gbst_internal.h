@@ -1,0 +1,147 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gbstencil.h"
+
+namespace gbst {
+
+constexpr int kMaxRadius = 4;
+
+// Device-side error codes written to the per-handle error word.
+enum DevErr : int {
+    kDevOk = 0,
+    kDevTimeoutTma = 1,     // an mbarrier wait for a TMA plane expired
+    kDevTimeoutBarrier = 2, // a grid-wide barrier wait expired
+    kDevBadUnit = 3,        // a work unit outside its grid (host bug guard)
+};
+
+// Wall-clock limit of every device-side spin wait (nanoseconds, %globaltimer).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// Padded storage of one field of one (sub)domain.
+//   element (i, j, k) of the interior lives at  origin + (k*rows + j)*pitch + i
+//   x ghosts: G = 16 bytes / element size (>= r) on each side,
+//   y ghosts: r rows, z ghosts: rz = r (3D) or 0 (2D) planes.
+//   pitch = round_up(nx + 2G, 128 bytes / element size) elements.
+struct Layout {
+    int64_t nx = 0, ny = 0, nz = 0;
+    int r = 0, rz = 0, G = 0, es = 4;
+    int64_t pitch = 0, rows = 0, planes = 0;
+    int64_t origin = 0;  // elements
+    int64_t elems = 0;   // total allocated elements
+    size_t bytes = 0;    // total bytes, rounded up to 256
+};
+
+// G: x ghost width in elements (16 bytes of the field, or more for fields read with wider vectors).
+Layout make_layout(int ndim, int64_t nx, int64_t ny, int64_t nz, int r, int elem_size, int G);
+
+// One (sub)domain as the sweep kernels see it.  Lives in device global memory;
+// the tensor maps must be 64-byte aligned.
+struct alignas(128) GridDev {
+    CUtensorMap tmap[2];   // TMA descriptors of u buffers 0 and 1 (box = tile + halo)
+    void *buf[2];          // u buffers (padded, storage type)
+    float *kappa;          // wave: kappa (padded FP32 layout `klay`), else null
+    int64_t nx, ny, nz;    // interior
+    int64_t pitch, rows;   // u layout (elements)
+    int64_t origin;        // u layout interior origin (elements)
+    int64_t kpitch, krows, korigin;  // kappa layout
+    int tiles_x, tiles_y;  // tile grid of this (sub)domain
+    int txt;               // threads along x per tile (tile width = txt * PX)
+    int box_bytes;         // bytes of one TMA box (tile + halo)
+    int src_x, src_y, src_z, has_src;  // source position (interior coordinates)
+    int pad_[2];
+};
+
+// A unit of sweep work: one tile of one grid over planes [z0, z1).
+struct Unit {
+    int grid, tile, z0, z1;
+};
+
+// Per-launch arguments of the sweep kernels.
+struct SweepArgs {
+    const GridDev *grids;
+    const Unit *units;
+    int nunits;
+    int parity;            // u^n lives in buf[parity]; output goes to buf[1-parity]
+    int ndim;
+    float wc;              // ndim * w_0
+    float w[kMaxRadius + 1];  // w_1..w_r at w[1..r]
+    float a;               // heat: alpha dt / h^2
+    const float *srcval;   // wave: per-grid source value for this step (already scaled), or null
+    int *err;              // device error word
+};
+
+// Host-side entry points of the kernel translation units.
+struct StreamVariant {
+    int R;          // radius
+    int eq;         // GBST_HEAT / GBST_WAVE
+    int storage;    // GBST_F32 / GBST_BF16
+    bool has_z;     // 3D
+    int nthreads;   // threads per CTA
+    int py;         // output rows per thread
+    int depth;      // TMA prefetch depth (planes in flight beyond the current one)
+};
+
+// Number of element columns a thread owns (16 bytes of storage).
+inline int px_of(int storage) { return storage == GBST_BF16 ? 8 : 4; }
+
+// Shared-memory bytes of the streaming kernel for the given variant and max box size.
+size_t stream_smem_bytes(const StreamVariant &v, int max_box_bytes);
+// Launch the streaming (TMA, 2.5D) sweep.  Returns cudaSuccess or the launch error.
+cudaError_t launch_stream_sweep(const StreamVariant &v, const SweepArgs &a, int ctas, size_t smem,
+                                cudaStream_t s);
+// Max resident CTAs per SM of the variant at the given shared memory size (0 = unsupported).
+int stream_occupancy(const StreamVariant &v, size_t smem);
+bool stream_variant_exists(const StreamVariant &v);
+
+// Simple kernel: one thread per output point, plain global loads.
+cudaError_t launch_simple_sweep(int R, int eq, int storage, const SweepArgs &a, int ngrids,
+                                int64_t max_points, cudaStream_t s);
+
+// Halo copies (dmp.swap faces, periodic wrap): a list of boxes copied element-wise.
+struct CopyBox {
+    int64_t src_off, dst_off;  // bytes from the subdomain base pointers
+    int src_grid, dst_grid;
+    int64_t ex, ey, ez;        // extents (elements)
+};
+cudaError_t launch_halo_copies(const GridDev *grids, const CopyBox *boxes, int nboxes, int parity,
+                               int elem_size, int64_t max_box_elems, cudaStream_t s);
+
+// Field transfer kernels between dense (x fastest) and padded storage.
+// dense dtype: GBST_F32 / GBST_F64 / GBST_BF16.  Region: the subdomain interior
+// located at global offset (gx, gy, gz) of a dense global field (gnx, gny, gnz).
+struct XferArgs {
+    void *padded; int storage; int64_t pitch, rows, origin;  // padded field
+    int64_t nx, ny, nz;                                       // subdomain interior
+    int64_t gx, gy, gz, gnx, gny;                             // placement in the dense field
+    void *dense; int dense_dtype;
+    double scale_sq;   // VEL -> kappa: kappa = c^2 * scale_sq (0 = plain copy)
+};
+cudaError_t launch_scatter(const XferArgs &x, cudaStream_t s);
+cudaError_t launch_gather(const XferArgs &x, cudaStream_t s);
+
+// FP64 reductions.  kinds as GBST_RED_*.  Partials: one double per block.
+struct ReduceGrid {
+    const void *u; const void *v; const float *kappa;  // v = u^{n-1} (energy)
+    int64_t pitch, rows, origin, kpitch, krows, korigin;
+    int64_t nx, ny, nz;
+};
+int reduce_blocks_for(int64_t points);
+cudaError_t launch_reduce_partials(int kind, int storage, int ndim, int R, const double *w,
+                                   const ReduceGrid *grids_dev, int ngrids, int64_t max_points,
+                                   double *partials, int nblocks, cudaStream_t s);
+cudaError_t launch_reduce_final(int kind, const double *partials, int n, double *out,
+                                cudaStream_t s);
+
+// Tensor-map encoding through the driver entry point.
+bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h,
+                 std::string *err);
+
+}  // namespace gbst

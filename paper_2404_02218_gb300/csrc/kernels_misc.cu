@@ -1,0 +1,321 @@
+// Supporting kernels: the one-thread-per-point sweep, halo copies (dmp.swap
+// faces and periodic wrap), dense <-> padded field transfers and the FP64
+// reductions.
+#include "gbst_internal.h"
+
+namespace gbst {
+namespace {
+
+template <int ST>
+struct Elem;
+template <>
+struct Elem<GBST_F32> {
+    using T = float;
+    static constexpr int ES = 4;
+    __device__ __forceinline__ static float ld(const T *p) { return *p; }
+    __device__ __forceinline__ static void st(T *p, float v) { *p = v; }
+};
+template <>
+struct Elem<GBST_BF16> {
+    using T = __nv_bfloat16;
+    static constexpr int ES = 2;
+    __device__ __forceinline__ static float ld(const T *p) { return __bfloat162float(*p); }
+    __device__ __forceinline__ static void st(T *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// One thread per interior point.  Same per-point arithmetic (and order) as the
+// streaming kernel, so both give bit-identical results.
+template <int R, int EQ, int ST>
+__global__ void k_simple(const SweepArgs a)
+{
+    using E = Elem<ST>;
+    using T = typename E::T;
+    const GridDev &g = a.grids[blockIdx.y];
+    const int64_t nx = g.nx, ny = g.ny, nz = g.nz;
+    const int64_t n = nx * ny * nz;
+    const int64_t sy = g.pitch, sz = g.pitch * g.rows;
+    const T *u = static_cast<const T *>(g.buf[a.parity]) + g.origin;
+    T *out = static_cast<T *>(g.buf[1 - a.parity]) + g.origin;
+    const bool has_z = a.ndim == 3;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t x = p % nx, y = (p / nx) % ny, z = p / (nx * ny);
+        const int64_t idx = z * sz + y * sy + x;
+        const float c = E::ld(u + idx);
+        float s = a.wc * c;
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+            const float xm = E::ld(u + idx - m), xp = E::ld(u + idx + m);
+            const float ym = E::ld(u + idx - m * sy), yp = E::ld(u + idx + m * sy);
+            s = fmaf(a.w[m], xm + xp, s);
+            s = fmaf(a.w[m], ym + yp, s);
+            if (has_z) {
+                const float zm = E::ld(u + idx - m * sz), zp = E::ld(u + idx + m * sz);
+                s = fmaf(a.w[m], zm + zp, s);
+            }
+        }
+        float o;
+        if (EQ == GBST_HEAT) {
+            o = fmaf(a.a, s, c);
+        } else {
+            const float kap = g.kappa[g.korigin + z * g.kpitch * g.krows + y * g.kpitch + x];
+            const float um = E::ld(out + idx);
+            o = fmaf(kap, s, fmaf(2.0f, c, -um));
+            if (g.has_src && a.srcval && x == g.src_x && y == g.src_y && z == g.src_z)
+                o += a.srcval[blockIdx.y];
+        }
+        E::st(out + idx, o);
+    }
+}
+
+using SimpleFn = void (*)(const SweepArgs);
+template <int EQ, int ST>
+SimpleFn simple_for_r(int R)
+{
+    switch (R) {
+    case 1: return &k_simple<1, EQ, ST>;
+    case 2: return &k_simple<2, EQ, ST>;
+    case 4: return &k_simple<4, EQ, ST>;
+    default: return nullptr;
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_halo_copies(const GridDev *grids, const CopyBox *boxes, int parity, int es)
+{
+    const CopyBox b = boxes[blockIdx.y];
+    const GridDev &gs = grids[b.src_grid];
+    const GridDev &gd = grids[b.dst_grid];
+    const unsigned char *src = static_cast<const unsigned char *>(gs.buf[parity]) + b.src_off;
+    unsigned char *dst = static_cast<unsigned char *>(gd.buf[parity]) + b.dst_off;
+    const int64_t n = b.ex * b.ey * b.ez;
+    const int64_t sps = gs.pitch * es, spp = gs.pitch * gs.rows * es;
+    const int64_t dps = gd.pitch * es, dpp = gd.pitch * gd.rows * es;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = p % b.ex, j = (p / b.ex) % b.ey, k = p / (b.ex * b.ey);
+        const int64_t so = k * spp + j * sps + i * es, d = k * dpp + j * dps + i * es;
+        if (es == 4)
+            *reinterpret_cast<uint32_t *>(dst + d) = *reinterpret_cast<const uint32_t *>(src + so);
+        else
+            *reinterpret_cast<uint16_t *>(dst + d) = *reinterpret_cast<const uint16_t *>(src + so);
+    }
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double load_dense(const void *p, int dtype, int64_t i)
+{
+    if (dtype == GBST_F64)
+        return static_cast<const double *>(p)[i];
+    if (dtype == GBST_F32)
+        return static_cast<double>(static_cast<const float *>(p)[i]);
+    return static_cast<double>(__bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]));
+}
+
+__global__ void k_scatter(const XferArgs x)
+{
+    const int64_t n = x.nx * x.ny * x.nz;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = p % x.nx, j = (p / x.nx) % x.ny, k = p / (x.nx * x.ny);
+        const int64_t d = ((x.gz + k) * x.gny + (x.gy + j)) * x.gnx + (x.gx + i);
+        double v = load_dense(x.dense, x.dense_dtype, d);
+        if (x.scale_sq > 0.0)
+            v = v * v * x.scale_sq;
+        const int64_t o = x.origin + (k * x.rows + j) * x.pitch + i;
+        if (x.storage == GBST_BF16)
+            static_cast<__nv_bfloat16 *>(x.padded)[o] = __double2bfloat16(v);
+        else
+            static_cast<float *>(x.padded)[o] = __double2float_rn(v);
+    }
+}
+
+__global__ void k_gather(const XferArgs x)
+{
+    const int64_t n = x.nx * x.ny * x.nz;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = p % x.nx, j = (p / x.nx) % x.ny, k = p / (x.nx * x.ny);
+        const int64_t d = ((x.gz + k) * x.gny + (x.gy + j)) * x.gnx + (x.gx + i);
+        const int64_t o = x.origin + (k * x.rows + j) * x.pitch + i;
+        float v;
+        if (x.storage == GBST_BF16)
+            v = __bfloat162float(static_cast<const __nv_bfloat16 *>(x.padded)[o]);
+        else
+            v = static_cast<const float *>(x.padded)[o];
+        if (x.dense_dtype == GBST_F64)
+            static_cast<double *>(x.dense)[d] = static_cast<double>(v);
+        else if (x.dense_dtype == GBST_F32)
+            static_cast<float *>(x.dense)[d] = v;
+        else
+            static_cast<__nv_bfloat16 *>(x.dense)[d] = __float2bfloat16_rn(v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double combine(int kind, double a, double b)
+{
+    return kind == GBST_RED_MAXABS ? fmax(a, b) : a + b;
+}
+
+template <int ST>
+__device__ __forceinline__ double ldd(const void *base, int64_t i)
+{
+    return static_cast<double>(Elem<ST>::ld(static_cast<const typename Elem<ST>::T *>(base) + i));
+}
+
+struct RedW {
+    double w[kMaxRadius + 1];
+};
+
+template <int ST>
+__global__ void __launch_bounds__(kRedThreads) k_reduce(int kind, int ndim, int R, RedW rw,
+                                                        const ReduceGrid *grids, int ngrids,
+                                                        double *partials)
+{
+    double acc = 0.0;
+    const int bpg = gridDim.x / ngrids;  // blocks per grid
+    const int gi = blockIdx.x / bpg;
+    const int bi = blockIdx.x % bpg;
+    if (gi < ngrids) {
+        const ReduceGrid g = grids[gi];
+        const int64_t n = g.nx * g.ny * g.nz;
+        const int64_t sy = g.pitch, sz = g.pitch * g.rows;
+        for (int64_t p = bi * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+             p += static_cast<int64_t>(bpg) * blockDim.x) {
+            const int64_t x = p % g.nx, y = (p / g.nx) % g.ny, z = p / (g.nx * g.ny);
+            const int64_t idx = g.origin + z * sz + y * sy + x;
+            const double u = ldd<ST>(g.u, idx);
+            double t;
+            if (kind == GBST_RED_SUM) {
+                t = u;
+            } else if (kind == GBST_RED_L2SQ) {
+                t = u * u;
+            } else if (kind == GBST_RED_MAXABS) {
+                t = fabs(u);
+            } else {
+                const double v = ldd<ST>(g.v, idx);
+                const double kap =
+                    static_cast<double>(g.kappa[g.korigin + z * g.kpitch * g.krows + y * g.kpitch + x]);
+                double lv = static_cast<double>(ndim) * rw.w[0] * v;
+                for (int m = 1; m <= R; ++m) {
+                    lv += rw.w[m] * (ldd<ST>(g.v, idx - m) + ldd<ST>(g.v, idx + m));
+                    lv += rw.w[m] * (ldd<ST>(g.v, idx - m * sy) + ldd<ST>(g.v, idx + m * sy));
+                    if (ndim == 3)
+                        lv += rw.w[m] * (ldd<ST>(g.v, idx - m * sz) + ldd<ST>(g.v, idx + m * sz));
+                }
+                const double d = u - v;
+                t = d * d / kap - u * lv;
+            }
+            acc = combine(kind, acc, t);
+        }
+    }
+    // block reduction in a fixed order
+    __shared__ double sh[kRedThreads / 32];
+    for (int o = 16; o > 0; o >>= 1)
+        acc = combine(kind, acc, __shfl_down_sync(0xffffffffu, acc, o));
+    if ((threadIdx.x & 31) == 0)
+        sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < kRedThreads / 32 ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1)
+            v = combine(kind, v, __shfl_down_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0)
+            partials[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_final(int kind, const double *partials, int n,
+                                                              double *out)
+{
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        acc = combine(kind, acc, partials[i]);
+    __shared__ double sh[kRedThreads / 32];
+    for (int o = 16; o > 0; o >>= 1)
+        acc = combine(kind, acc, __shfl_down_sync(0xffffffffu, acc, o));
+    if ((threadIdx.x & 31) == 0)
+        sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < kRedThreads / 32 ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1)
+            v = combine(kind, v, __shfl_down_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0)
+            *out = v;
+    }
+}
+
+int grid_for(int64_t n, int threads, int cap)
+{
+    const int64_t b = (n + threads - 1) / threads;
+    return static_cast<int>(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+cudaError_t launch_simple_sweep(int R, int eq, int storage, const SweepArgs &a, int ngrids, int64_t max_points,
+                                cudaStream_t s)
+{
+    SimpleFn fn = nullptr;
+    if (eq == GBST_HEAT)
+        fn = storage == GBST_BF16 ? simple_for_r<GBST_HEAT, GBST_BF16>(R) : simple_for_r<GBST_HEAT, GBST_F32>(R);
+    else
+        fn = storage == GBST_BF16 ? simple_for_r<GBST_WAVE, GBST_BF16>(R) : simple_for_r<GBST_WAVE, GBST_F32>(R);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    dim3 grid(grid_for(max_points, 256, 4096), ngrids);
+    fn<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_copies(const GridDev *grids, const CopyBox *boxes, int nboxes, int parity, int elem_size,
+                               int64_t max_box_elems, cudaStream_t s)
+{
+    if (nboxes == 0)
+        return cudaSuccess;
+    dim3 grid(grid_for(max_box_elems, 256, 1024), nboxes);
+    k_halo_copies<<<grid, 256, 0, s>>>(grids, boxes, parity, elem_size);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const XferArgs &x, cudaStream_t s)
+{
+    k_scatter<<<grid_for(x.nx * x.ny * x.nz, 256, 8192), 256, 0, s>>>(x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const XferArgs &x, cudaStream_t s)
+{
+    k_gather<<<grid_for(x.nx * x.ny * x.nz, 256, 8192), 256, 0, s>>>(x);
+    return cudaGetLastError();
+}
+
+int reduce_blocks_for(int64_t points) { return grid_for(points, kRedThreads, 1024); }
+
+cudaError_t launch_reduce_partials(int kind, int storage, int ndim, int R, const double *w,
+                                   const ReduceGrid *grids_dev, int ngrids, int64_t max_points, double *partials,
+                                   int nblocks, cudaStream_t s)
+{
+    RedW rw{};
+    for (int m = 0; m <= R && m <= kMaxRadius; ++m)
+        rw.w[m] = w[m];
+    (void)max_points;
+    if (storage == GBST_BF16)
+        k_reduce<GBST_BF16><<<nblocks, kRedThreads, 0, s>>>(kind, ndim, R, rw, grids_dev, ngrids, partials);
+    else
+        k_reduce<GBST_F32><<<nblocks, kRedThreads, 0, s>>>(kind, ndim, R, rw, grids_dev, ngrids, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_final(int kind, const double *partials, int n, double *out, cudaStream_t s)
+{
+    k_reduce_final<<<1, kRedThreads, 0, s>>>(kind, partials, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace gbst

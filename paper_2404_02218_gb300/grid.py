@@ -1,0 +1,177 @@
+"""Convenience wrapper of one stencil handle, with PyTorch supplying device memory and streams.
+
+PyTorch is plumbing here: its caching allocator backs the library's device
+allocations (through the ``gbst_allocator`` hook) and its streams order the
+work.  Every step of the computation runs in ``libgbstencil.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+
+from . import native as N
+
+_EQ = {"heat": N.GBST_HEAT, "wave": N.GBST_WAVE}
+_BC = {"zero": N.GBST_BC_ZERO, "periodic": N.GBST_BC_PERIODIC}
+_ST = {"f32": N.GBST_F32, "bf16": N.GBST_BF16}
+_KER = {"auto": N.GBST_KERNEL_AUTO, "stream": N.GBST_KERNEL_STREAM, "simple": N.GBST_KERNEL_SIMPLE}
+_FIELD = {"u": N.GBST_U, "u_prev": N.GBST_U_PREV, "vel": N.GBST_VEL}
+_RED = {"sum": N.GBST_RED_SUM, "l2sq": N.GBST_RED_L2SQ, "maxabs": N.GBST_RED_MAXABS,
+        "energy": N.GBST_RED_ENERGY}
+
+
+def _np_dtype_code(dt) -> int:
+    dt = np.dtype(dt)
+    if dt == np.float32:
+        return N.GBST_F32
+    if dt == np.float64:
+        return N.GBST_F64
+    raise TypeError(f"unsupported dtype {dt}")
+
+
+def _torch_dtype_code(t) -> int:
+    import torch
+    return {torch.float32: N.GBST_F32, torch.float64: N.GBST_F64, torch.bfloat16: N.GBST_BF16}[t.dtype]
+
+
+class TorchAllocator:
+    """gbst_allocator backed by torch's CUDA caching allocator."""
+
+    def __init__(self, device: int):
+        import torch
+        self._torch = torch
+        self.device = device
+
+        def _alloc(size, stream, ctx):
+            try:
+                return self._torch.cuda.caching_allocator_alloc(int(size), self.device, int(stream or 0))
+            except Exception:  # out of memory -> NULL, the library reports ENOMEM
+                return None
+
+        def _release(ptr, size, stream, ctx):
+            if ptr:
+                self._torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._alloc = N.ALLOC_FN(_alloc)
+        self._release = N.RELEASE_FN(_release)
+        self.struct = N.gbst_allocator(self._alloc, self._release, None)
+
+
+class Grid:
+    """One heat or wave grid (see ``stencil_create`` in include/gbstencil.h)."""
+
+    def __init__(self, ndim: int, dims: Sequence[int], space_order: int, eq: str = "heat", *,
+                 bc: str = "zero", storage: str = "f32", h: float = 1.0, dt: float = 1.0,
+                 alpha: float = 1.0, coeffs=None, decomp=(1, 1, 1), allow_unstable: bool = False,
+                 kernel: str = "auto", tile: int = 0, use_graph: bool = True, stream=None,
+                 torch_allocator: bool = True):
+        import torch
+        self._torch = torch
+        self.ndim = ndim
+        self.dims = tuple(int(d) for d in dims)[:ndim]
+        self.eq = eq
+        self.storage = storage
+        dev = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        d = N.gbst_desc()
+        d.ndim = ndim
+        full = list(self.dims) + [1] * (3 - ndim)
+        for i in range(3):
+            d.dims[i] = full[i]
+        d.space_order = space_order
+        d.eq = _EQ[eq]
+        d.bc = _BC[bc]
+        d.storage = _ST[storage]
+        d.h, d.dt, d.alpha = float(h), float(dt), float(alpha)
+        self._coeffs = None
+        if coeffs is not None:
+            self._coeffs = (ctypes.c_double * len(coeffs))(*[float(c) for c in coeffs])
+            d.coeffs = self._coeffs
+        dec = list(decomp) + [1] * (3 - len(decomp))
+        for i in range(3):
+            d.decomp[i] = int(dec[i])
+        d.allow_unstable = int(allow_unstable)
+        d.kernel = _KER[kernel]
+        d.tile = int(tile)
+        d.use_graph = int(use_graph)
+        d.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self._alloc = TorchAllocator(dev) if torch_allocator else None
+        d.allocator = ctypes.pointer(self._alloc.struct) if self._alloc else None
+        self._desc = d
+        self.h = N.stencil_create(d)
+
+    # -- shape helpers -------------------------------------------------------
+    @property
+    def shape(self):
+        """numpy/torch shape of a dense field: (nz, ny, nx) or (ny, nx)."""
+        return tuple(reversed(self.dims))
+
+    def _prep_torch(self, t):
+        self.stream.wait_stream(self._torch.cuda.current_stream())
+        return t
+
+    def set_field(self, field: str, data):
+        f = _FIELD[field]
+        if isinstance(data, np.ndarray):
+            a = np.ascontiguousarray(data)
+            assert a.shape == self.shape, (a.shape, self.shape)
+            N.stencil_set_field(self.h, f, a.ctypes.data, _np_dtype_code(a.dtype), False)
+        else:
+            t = data.contiguous()
+            assert tuple(t.shape) == self.shape
+            if t.is_cuda:
+                self._prep_torch(t)
+            N.stencil_set_field(self.h, f, t.data_ptr(), _torch_dtype_code(t), t.is_cuda)
+
+    def get_field(self, field: str = "u", dtype=np.float64, out=None):
+        f = _FIELD[field]
+        if out is None:
+            out = np.empty(self.shape, dtype=dtype)
+        if isinstance(out, np.ndarray):
+            N.stencil_get_field(self.h, f, out.ctypes.data, _np_dtype_code(out.dtype), False)
+        else:
+            self._prep_torch(out)
+            N.stencil_get_field(self.h, f, out.data_ptr(), _torch_dtype_code(out), out.is_cuda)
+        return out
+
+    def set_source(self, idx, f0: float, t0: float, amp: float = 1.0):
+        N.stencil_set_source(self.h, idx, f0, t0, amp)
+
+    def run(self, nsteps: int):
+        N.stencil_run(self.h, nsteps)
+
+    def sync(self):
+        N.stencil_sync(self.h)
+
+    def reduce(self, kind: str) -> float:
+        return N.stencil_reduce_f64(self.h, _RED[kind])
+
+    @property
+    def step(self) -> int:
+        return N.stencil_get_step(self.h)
+
+    @step.setter
+    def step(self, v: int):
+        N.stencil_set_step(self.h, v)
+
+    def describe(self) -> str:
+        return N.stencil_describe(self.h)
+
+    def set_profile(self, on: bool):
+        N.stencil_set_profile(self.h, on)
+
+    def last_kernel_time(self):
+        return N.stencil_last_kernel_time(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.stencil_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

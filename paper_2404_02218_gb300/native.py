@@ -1,0 +1,191 @@
+"""ctypes binding of ``libgbstencil.so`` -- argument marshalling only.
+
+Every function here has the name of the C entry point it wraps (see
+``include/gbstencil.h``) and raises :class:`GbstError` on a non-zero status.
+All computation runs in the CUDA library; there is no fallback: if the library
+cannot be built or loaded, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+# ---- constants (mirror include/gbstencil.h) --------------------------------
+GBST_OK, GBST_EINVAL, GBST_ENOMEM, GBST_ECUDA, GBST_ETIMEOUT, GBST_EUNSTABLE, GBST_ESTATE, GBST_ENOTSUP = \
+    0, -1, -2, -3, -4, -5, -6, -7
+GBST_HEAT, GBST_WAVE = 0, 1
+GBST_BC_ZERO, GBST_BC_PERIODIC = 0, 1
+GBST_F32, GBST_BF16, GBST_F64 = 0, 1, 2
+GBST_U, GBST_U_PREV, GBST_VEL = 0, 1, 2
+GBST_RED_SUM, GBST_RED_L2SQ, GBST_RED_MAXABS, GBST_RED_ENERGY = 0, 1, 2, 3
+GBST_KERNEL_AUTO, GBST_KERNEL_STREAM, GBST_KERNEL_SIMPLE = 0, 1, 2
+
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNSTABLE",
+                -6: "ESTATE", -7: "ENOTSUP"}
+
+
+class GbstError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        self.status = status
+        super().__init__(f"{func}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class gbst_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class gbst_desc(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("dims", ctypes.c_int64 * 3),
+        ("space_order", ctypes.c_int),
+        ("eq", ctypes.c_int),
+        ("bc", ctypes.c_int),
+        ("storage", ctypes.c_int),
+        ("h", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("coeffs", ctypes.POINTER(ctypes.c_double)),
+        ("decomp", ctypes.c_int * 3),
+        ("allow_unstable", ctypes.c_int),
+        ("kernel", ctypes.c_int),
+        ("tile", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("allocator", ctypes.POINTER(gbst_allocator)),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Build (if needed) and load the CUDA library; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            H = ctypes.c_void_p
+            i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+            sig = {
+                "gbst_version": ([], i32),
+                "stencil_last_error": ([], ctypes.c_char_p),
+                "stencil_fd_weights": ([i32, ctypes.POINTER(dbl)], i32),
+                "stencil_create": ([ctypes.POINTER(gbst_desc), ctypes.POINTER(H)], i32),
+                "stencil_set_field": ([H, i32, vp, i32, i32], i32),
+                "stencil_get_field": ([H, i32, vp, i32, i32], i32),
+                "stencil_set_source": ([H, ctypes.POINTER(i64), dbl, dbl, dbl], i32),
+                "stencil_run": ([H, i64], i32),
+                "stencil_sync": ([H], i32),
+                "stencil_get_step": ([H, ctypes.POINTER(i64)], i32),
+                "stencil_set_step": ([H, i64], i32),
+                "stencil_reduce_f64": ([H, i32, ctypes.POINTER(dbl)], i32),
+                "stencil_describe": ([H, ctypes.c_char_p, ctypes.c_size_t], i32),
+                "stencil_destroy": ([H], i32),
+                "stencil_set_profile": ([H, i32], i32),
+                "stencil_last_kernel_time": ([H, ctypes.POINTER(dbl), ctypes.POINTER(i64)], i32),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(status: int, func: str):
+    if status != GBST_OK:
+        msg = lib().stencil_last_error()
+        raise GbstError(status, func, msg.decode() if msg else "")
+
+
+def last_error() -> str:
+    return lib().stencil_last_error().decode()
+
+
+def gbst_version() -> int:
+    return lib().gbst_version()
+
+
+def stencil_fd_weights(space_order: int) -> list[float]:
+    r = space_order // 2
+    out = (ctypes.c_double * (r + 1))()
+    _check(lib().stencil_fd_weights(space_order, out), "stencil_fd_weights")
+    return list(out)
+
+
+def stencil_create(desc: gbst_desc) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().stencil_create(ctypes.byref(desc), ctypes.byref(h)), "stencil_create")
+    return h
+
+
+def stencil_set_field(h, field: int, ptr: int, dtype: int, on_device: bool):
+    _check(lib().stencil_set_field(h, field, ctypes.c_void_p(ptr), dtype, int(on_device)), "stencil_set_field")
+
+
+def stencil_get_field(h, field: int, ptr: int, dtype: int, on_device: bool):
+    _check(lib().stencil_get_field(h, field, ctypes.c_void_p(ptr), dtype, int(on_device)), "stencil_get_field")
+
+
+def stencil_set_source(h, idx, f0: float, t0: float, amp: float):
+    arr = (ctypes.c_int64 * 3)(*(list(idx) + [0] * (3 - len(idx))))
+    _check(lib().stencil_set_source(h, arr, float(f0), float(t0), float(amp)), "stencil_set_source")
+
+
+def stencil_run(h, nsteps: int):
+    _check(lib().stencil_run(h, int(nsteps)), "stencil_run")
+
+
+def stencil_sync(h):
+    _check(lib().stencil_sync(h), "stencil_sync")
+
+
+def stencil_get_step(h) -> int:
+    v = ctypes.c_int64()
+    _check(lib().stencil_get_step(h, ctypes.byref(v)), "stencil_get_step")
+    return v.value
+
+
+def stencil_set_step(h, step: int):
+    _check(lib().stencil_set_step(h, int(step)), "stencil_set_step")
+
+
+def stencil_reduce_f64(h, kind: int) -> float:
+    v = ctypes.c_double()
+    _check(lib().stencil_reduce_f64(h, kind, ctypes.byref(v)), "stencil_reduce_f64")
+    return v.value
+
+
+def stencil_describe(h) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    _check(lib().stencil_describe(h, buf, 1024), "stencil_describe")
+    return buf.value.decode()
+
+
+def stencil_destroy(h):
+    _check(lib().stencil_destroy(h), "stencil_destroy")
+
+
+def stencil_set_profile(h, enable: bool):
+    _check(lib().stencil_set_profile(h, int(enable)), "stencil_set_profile")
+
+
+def stencil_last_kernel_time(h):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().stencil_last_kernel_time(h, ctypes.byref(ms), ctypes.byref(n)), "stencil_last_kernel_time")
+    return ms.value, n.value

@@ -232,3 +232,41 @@ def batch_wave_cases(count: int = 64, seed: int = 4, lo: int = 96, hi: int = 256
         cases.append(wave3d(so=so, nsteps=nsteps, seed=seed * 1000 + i, f0=float(np.float32(f0s[i])),
                             speeds=sp, h=h, dims=dims))
     return cases
+
+
+# --------------------------------------------------------------------------
+# The same counter-based generator in torch (for full-size device inputs)
+# --------------------------------------------------------------------------
+
+def _signed(u: int) -> int:
+    u &= (1 << 64) - 1
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def uniform_field_torch(seed: int, shape: Sequence[int], device, chunk: int = 1 << 26):
+    """Bit-identical to :func:`uniform_field`, computed with int64 torch ops on ``device``.
+
+    uint64 arithmetic is emulated on int64: multiplication and addition wrap
+    modulo 2**64 identically, and logical right shifts are arithmetic shifts
+    masked to the remaining bits.
+    """
+    import torch
+    n = int(np.prod(shape))
+    out = torch.empty(n, dtype=torch.float32, device=device)
+    key = _signed(int(stream_key(seed)))
+    g = _signed(int(GOLDEN))
+    m1 = _signed(int(_M1))
+    m2 = _signed(int(_M2))
+
+    def lsr(z, s):
+        return (z >> s) & ((1 << (64 - s)) - 1)
+
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        z = torch.arange(s + 1, e + 1, dtype=torch.int64, device=device)
+        z = z * g + key
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        z = z ^ lsr(z, 31)
+        out[s:e] = lsr(z, 40).to(torch.float32) * (1.0 / (1 << 24))
+    return out.reshape(tuple(shape))
