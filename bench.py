@@ -42,7 +42,8 @@ N = 1024
 SOS = (2, 4, 8)
 STEPS_PER_RUN = 50
 BYTES_PER_PT = 8  # FP32 heat: read u, write u+
-WORKLOAD = "heat3d 1024^3 FP32, space orders 2/4/8, 50 steps each, zero Dirichlet halo"
+def workload() -> str:
+    return f"heat3d {N}^3 FP32, space orders 2/4/8, 50 steps each, zero Dirichlet halo"
 
 
 def parse():
@@ -54,7 +55,11 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    return p.parse_args()
+    p.add_argument("--n", type=int, default=1024, help="grid edge (profiling runs use a smaller cube)")
+    a = p.parse_args()
+    global N
+    N = a.n
+    return a
 
 
 def env_rank():
@@ -156,7 +161,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+            "data": "synthetic", "config": {"workload": workload(), "sample": desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -308,9 +313,9 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "grid": [N, N, N], "space_orders": list(SOS),
+                "config": {"workload": workload(), "grid": [N, N, N], "space_orders": list(SOS),
                            "steps_per_run": STEPS_PER_RUN, "parallelism": f"replicas{world}",
-                           "l2": "inputs larger than L2 (4.3 GB per field), no flush"},
+                           "l2": f"inputs larger than L2 ({4 * N ** 3 / 1e9:.2f} GB per field), no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * len(SOS) * STEPS_PER_RUN, "clocks": clocks,
                 "per_stencil": per}
