@@ -43,7 +43,7 @@ SOS = (2, 4, 8)
 STEPS_PER_RUN = 50
 BYTES_PER_PT = 8  # FP32 heat: read u, write u+
 def workload() -> str:
-    return f"heat3d {N}^3 FP32, space orders 2/4/8, 50 steps each, zero Dirichlet halo"
+    return f"heat3d {N}^3 FP32, space orders {'/'.join(map(str, SOS))}, 50 steps each, zero Dirichlet halo"
 
 
 def parse():
@@ -56,9 +56,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--n", type=int, default=1024, help="grid edge (profiling runs use a smaller cube)")
+    p.add_argument("--sos", default="2,4,8", help="space orders to run (profiling runs use one)")
+    p.add_argument("--tune", default="on", choices=["on", "cache", "off"],
+                   help="on: autotune each kernel before timing; cache: use plans cached in "
+                        "GBST_TUNE_CACHE (no tuning launches); off: default plans")
     a = p.parse_args()
-    global N
+    global N, SOS
     N = a.n
+    SOS = tuple(int(x) for x in a.sos.split(","))
     return a
 
 
@@ -211,10 +216,14 @@ def run_ours(args):
     shape = (N, N, N)
     u0 = synthetic.uniform_field_torch(2, shape, "cuda")
     grids = {}
+    tuning = {}
     for so in SOS:
         case = synthetic.heat3d(N, so)
         g = Grid(3, case.dims, so, "heat", h=1.0, dt=case.a, alpha=1.0, stream=stream)
         g.set_field("u", u0)
+        if args.tune == "on":
+            rep = g.tune(reps=3)
+            tuning[f"heat3d_so{so}"] = {"candidates": len(rep["candidates"]), "best": rep["best"]}
         grids[so] = g
     torch.cuda.synchronize()
 
@@ -318,7 +327,7 @@ def run_ours(args):
                            "l2": f"inputs larger than L2 ({4 * N ** 3 / 1e9:.2f} GB per field), no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * len(SOS) * STEPS_PER_RUN, "clocks": clocks,
-                "per_stencil": per}
+                "per_stencil": per, "autotune": tuning or args.tune}
         print(json.dumps(line), flush=True)
     for g in grids.values():
         g.close()

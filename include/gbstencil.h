@@ -168,6 +168,25 @@ gbst_status stencil_destroy(gbst_handle h);
 gbst_status stencil_set_profile(gbst_handle h, int enable);
 gbst_status stencil_last_kernel_time(gbst_handle h, double *ms, int64_t *launches);
 
+/* Execution plan of the streaming sweep.  variant: index into the kernel
+ * table (stencil_variant_count / stencil_variant_info; -1 = the default for
+ * this grid); txt: threads along x of a tile (8, 16, 32; 0 = default); zchunks:
+ * z-chunks per tile column (0 = cost model); ctas: CTAs launched (0 = all
+ * that are resident).  Synchronises; invalidates captured graphs. */
+gbst_status stencil_set_plan(gbst_handle h, int variant, int txt, int zchunks, int ctas);
+
+/* Autotuner: times every applicable (kernel variant, tile width, z-chunking)
+ * on the handle's own fields with `reps` launches each (CUDA events on the
+ * handle's stream), keeps the fastest and caches it per shape class -- in the
+ * process, and appended to the file named by the environment variable
+ * GBST_TUNE_CACHE, which stencil_create reads.  The fields are left unchanged.
+ * report (optional, len bytes) receives a JSON summary of the candidates. */
+gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len);
+
+/* Number of compiled streaming-kernel variants, and a JSON description of one. */
+int stencil_variant_count(void);
+gbst_status stencil_variant_info(int i, char *buf, size_t len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -198,6 +198,8 @@ struct Sub {
 
 struct Plan {
     StreamVariant var{};
+    int variant = -1;
+    int req_txt = 0, req_zchunks = 0, req_ctas = 0;
     bool stream = false;
     int txt = 16;
     int zchunks = 1;
@@ -322,18 +324,38 @@ void destroy_graphs(gbst_handle h)
 }
 
 // ---- plan: tiles, TMA boxes, work units ----------------------------------
-gbst_status build_plan(gbst_handle h, int txt, int zchunks_req, int ctas_req)
+// Index of the first streaming variant matching the handle (the default), or -1.
+int default_variant(gbst_handle h)
+{
+    StreamVariant v;
+    for (int i = 0; stream_variant_get(i, &v); ++i)
+        if (v.R == h->R && v.eq == h->d.eq && v.storage == h->d.storage && v.has_z == (h->ndim == 3))
+            return i;
+    return -1;
+}
+
+gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int ctas_req)
 {
     const int st = h->d.storage;
     const int px = px_of(st);
     const int G = px;
     Plan p;
-    p.var = StreamVariant{h->R, h->d.eq, st, h->ndim == 3, 128, st == GBST_BF16 ? 1 : 2, 3};
-    p.stream = h->d.kernel != GBST_KERNEL_SIMPLE && stream_variant_exists(p.var);
+    if (variant < 0)
+        variant = default_variant(h);
+    p.stream = h->d.kernel != GBST_KERNEL_SIMPLE && variant >= 0;
     if (h->d.kernel == GBST_KERNEL_STREAM && !p.stream)
         return fail(GBST_ENOTSUP, "no streaming kernel for radius %d", h->R);
+    if (p.stream) {
+        if (!stream_variant_get(variant, &p.var))
+            return fail(GBST_EINVAL, "unknown kernel variant %d", variant);
+        if (p.var.R != h->R || p.var.eq != h->d.eq || p.var.storage != st || p.var.has_z != (h->ndim == 3))
+            return fail(GBST_EINVAL, "kernel variant %d does not match this grid", variant);
+        p.variant = variant;
+    } else {
+        p.var = StreamVariant{h->R, h->d.eq, st, h->ndim == 3, 128, 1, 1, 1};
+    }
     const int nt = p.var.nthreads;
-    // tile width: txt threads along x (tile width = txt*px <= 256 - 2G for the TMA box)
+    // tile width: txt threads along x (tile width txt*px; the TMA box is at most 256 wide)
     if (txt <= 0)
         txt = st == GBST_BF16 ? 8 : 16;
     while (txt * px + 2 * G > 256 && txt > 1)
@@ -373,7 +395,7 @@ gbst_status build_plan(gbst_handle h, int txt, int zchunks_req, int ctas_req)
         int zc = 1;
         if (h->ndim == 3) {
             if (zchunks_req > 0) {
-                zc = zchunks_req;
+                zc = static_cast<int>(std::min<int64_t>(zchunks_req, nz));
             } else {
                 // minimise waves * (chunk length + 2r): a balance / halo-overhead trade-off
                 double best = 1e300;
@@ -416,9 +438,75 @@ gbst_status build_plan(gbst_handle h, int txt, int zchunks_req, int ctas_req)
     GBST_CUDA(cudaMemcpyAsync(h->dgrids, h->hgrids.data(), h->hgrids.size() * sizeof(GridDev),
                               cudaMemcpyHostToDevice, h->stream));
     GBST_CUDA(cudaStreamSynchronize(h->stream));
+    p.req_txt = txt;
+    p.req_zchunks = zchunks_req;
+    p.req_ctas = ctas_req;
     h->plan = p;
     destroy_graphs(h);
     return GBST_OK;
+}
+
+// ---- autotuner cache --------------------------------------------------------
+struct TunedPlan {
+    int variant, txt, zchunks, ctas;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, TunedPlan> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string tune_key(gbst_handle h)
+{
+    char b[256];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    snprintf(b, sizeof b, "sm%d/r%d/eq%d/st%d/nd%d/%lldx%lldx%lld/sub%zu", num_sms(), h->R, h->d.eq, h->d.storage,
+             h->ndim, static_cast<long long>(h->subs[0].lu.nx), static_cast<long long>(h->subs[0].lu.ny),
+             static_cast<long long>(h->subs[0].lu.nz), h->subs.size());
+    return b;
+}
+
+// Cache file (GBST_TUNE_CACHE): one "key variant txt zchunks ctas" line per entry.
+void tune_cache_load()
+{
+    if (g_tune_loaded)
+        return;
+    g_tune_loaded = true;
+    const char *path = getenv("GBST_TUNE_CACHE");
+    if (!path)
+        return;
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return;
+    char key[256];
+    TunedPlan t;
+    while (fscanf(f, "%255s %d %d %d %d", key, &t.variant, &t.txt, &t.zchunks, &t.ctas) == 5)
+        g_tune_cache[key] = t;
+    fclose(f);
+}
+
+void tune_cache_store(const std::string &key, const TunedPlan &t)
+{
+    g_tune_cache[key] = t;
+    const char *path = getenv("GBST_TUNE_CACHE");
+    if (!path)
+        return;
+    FILE *f = fopen(path, "a");
+    if (!f)
+        return;
+    fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.variant, t.txt, t.zchunks, t.ctas);
+    fclose(f);
+}
+
+bool tune_cache_find(gbst_handle h, TunedPlan *t)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
+    auto it = g_tune_cache.find(tune_key(h));
+    if (it == g_tune_cache.end())
+        return false;
+    *t = it->second;
+    return true;
 }
 
 // ---- halo copy list: dmp.swap exchanges (decomposition) or periodic wrap --
@@ -792,7 +880,11 @@ gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
     gbst_status st = build_copies(h);
     if (st != GBST_OK)
         return bail(st);
-    st = build_plan(h, d.tile > 0 ? d.tile : 0, 0, 0);
+    TunedPlan tp{};
+    if (d.tile == 0 && d.kernel != GBST_KERNEL_SIMPLE && tune_cache_find(h, &tp))
+        st = build_plan(h, tp.variant, tp.txt, tp.zchunks, tp.ctas);
+    else
+        st = build_plan(h, -1, d.tile > 0 ? d.tile : 0, 0, 0);
     if (st != GBST_OK)
         return bail(st);
     *out = h;
@@ -1134,10 +1226,10 @@ gbst_status stencil_describe(gbst_handle h, char *buf, size_t len)
     snprintf(buf, len,
              "{\"kernel\": \"%s\", \"R\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, \"tile\": [%d, %d], "
              "\"zchunks\": %d, \"units\": %d, \"ctas\": %d, \"occupancy\": %d, \"smem\": %zu, \"subdomains\": %zu, "
-             "\"halo_boxes\": %d}",
+             "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d}",
              p.stream ? "stream" : "simple", h->R, p.var.nthreads, p.var.py, p.var.depth, p.txt * px,
              (p.var.nthreads / std::max(1, p.txt)) * p.var.py, p.zchunks, p.nunits, p.ctas, p.occupancy, p.smem,
-             h->subs.size(), h->nboxes);
+             h->subs.size(), h->nboxes, p.variant, p.var.minb);
     return GBST_OK;
 }
 
@@ -1170,4 +1262,138 @@ gbst_status stencil_last_kernel_time(gbst_handle h, double *ms, int64_t *launche
     return GBST_OK;
 }
 
+gbst_status stencil_set_plan(gbst_handle h, int variant, int txt, int zchunks, int ctas)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    GBST_CUDA(cudaStreamSynchronize(h->stream));
+    return build_plan(h, variant, txt, zchunks, ctas);
+}
+
+int stencil_variant_count(void) { return stream_variant_count(); }
+
+gbst_status stencil_variant_info(int i, char *buf, size_t len)
+{
+    StreamVariant v;
+    if (!buf || len == 0 || !stream_variant_get(i, &v))
+        return fail(GBST_EINVAL, "bad variant index or buffer");
+    snprintf(buf, len,
+             "{\"R\": %d, \"eq\": %d, \"storage\": %d, \"has_z\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, "
+             "\"minb\": %d}",
+             v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb);
+    return GBST_OK;
+}
+
+gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (!h->plan.stream) {
+        if (report && len)
+            snprintf(report, len, "{\"tuned\": false, \"reason\": \"simple kernel\"}");
+        return GBST_OK;
+    }
+    reps = std::max(1, reps);
+    GBST_CUDA(cudaStreamSynchronize(h->stream));
+    // Repeated launches at a fixed parity leave u^n intact; the wave's in-place
+    // update overwrites u^{n-1}, so that buffer is saved and restored.
+    std::vector<void *> saved(h->subs.size(), nullptr);
+    auto restore = [&]() {
+        for (size_t i = 0; i < h->subs.size(); ++i)
+            if (saved[i]) {
+                cudaMemcpyAsync(h->hgrids[i].buf[1 - h->parity], saved[i], h->subs[i].lu.bytes,
+                                cudaMemcpyDeviceToDevice, h->stream);
+                cudaStreamSynchronize(h->stream);
+                h->mem.release(saved[i], h->subs[i].lu.bytes);
+                saved[i] = nullptr;
+            }
+    };
+    if (h->d.eq == GBST_WAVE)
+        for (size_t i = 0; i < h->subs.size(); ++i) {
+            saved[i] = h->mem.alloc(h->subs[i].lu.bytes);
+            if (!saved[i]) {
+                restore();
+                return fail(GBST_ENOMEM, "autotuner save buffer");
+            }
+            GBST_CUDA(cudaMemcpyAsync(saved[i], h->hgrids[i].buf[1 - h->parity], h->subs[i].lu.bytes,
+                                      cudaMemcpyDeviceToDevice, h->stream));
+        }
+    cudaEvent_t e0, e1;
+    GBST_CUDA(cudaEventCreate(&e0));
+    GBST_CUDA(cudaEventCreate(&e1));
+    const Plan before = h->plan;
+    double best_ms = 1e300;
+    TunedPlan best{before.variant, before.req_txt, before.req_zchunks, before.req_ctas};
+    std::string rep = "{\"candidates\": [";
+    int ncand = 0;
+    StreamVariant v;
+    const int zlist_3d[] = {0, 1, 2, 4, 8, 16};
+    const int zlist_2d[] = {0};
+    for (int vi = 0; stream_variant_get(vi, &v); ++vi) {
+        if (v.R != h->R || v.eq != h->d.eq || v.storage != h->d.storage || v.has_z != (h->ndim == 3))
+            continue;
+        for (int txt : {8, 16, 32}) {
+            const int *zl = h->ndim == 3 ? zlist_3d : zlist_2d;
+            const int nz = h->ndim == 3 ? 6 : 1;
+            int last_units = -1;
+            for (int zi = 0; zi < nz; ++zi) {
+                if (build_plan(h, vi, txt, zl[zi], 0) != GBST_OK || h->plan.txt != txt)
+                    continue;
+                if (h->plan.nunits == last_units)
+                    continue;
+                last_units = h->plan.nunits;
+                const SweepArgs a = sweep_args(h, h->parity, nullptr);
+                cudaError_t e = launch_stream_sweep(h->plan.var, a, h->plan.ctas, h->plan.smem, h->stream);
+                cudaEventRecord(e0, h->stream);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r)
+                    e = launch_stream_sweep(h->plan.var, a, h->plan.ctas, h->plan.smem, h->stream);
+                cudaEventRecord(e1, h->stream);
+                if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double per = ms / reps;
+                char b[256];
+                snprintf(b, sizeof b,
+                         "%s{\"variant\": %d, \"txt\": %d, \"zchunks\": %d, \"units\": %d, \"ctas\": %d, \"ms\": %.5f}",
+                         ncand ? ", " : "", vi, txt, h->plan.zchunks, h->plan.nunits, h->plan.ctas, per);
+                rep += b;
+                ++ncand;
+                if (per < best_ms) {
+                    best_ms = per;
+                    best = TunedPlan{vi, txt, h->plan.zchunks, 0};
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st = build_plan(h, best.variant, best.txt, best.zchunks, best.ctas);
+    restore();
+    gbst_status pe = poll_device_error(h);
+    if (st != GBST_OK)
+        return st;
+    if (pe != GBST_OK)
+        return pe;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_load();
+        tune_cache_store(tune_key(h), best);
+    }
+    char b[256];
+    snprintf(b, sizeof b, "], \"best\": {\"variant\": %d, \"txt\": %d, \"zchunks\": %d, \"ms\": %.5f}}", best.variant,
+             best.txt, best.zchunks, best_ms);
+    rep += b;
+    if (report && len) {
+        strncpy(report, rep.c_str(), len - 1);
+        report[len - 1] = 0;
+    }
+    return GBST_OK;
+}
+
 }  // extern "C"
+

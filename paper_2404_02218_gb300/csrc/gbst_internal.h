@@ -84,9 +84,10 @@ struct StreamVariant {
     int eq;         // GBST_HEAT / GBST_WAVE
     int storage;    // GBST_F32 / GBST_BF16
     bool has_z;     // 3D
-    int nthreads;   // threads per CTA
+    int nthreads;   // consumer threads per CTA (one more warp issues the TMA loads)
     int py;         // output rows per thread
     int depth;      // TMA prefetch depth (planes in flight beyond the current one)
+    int minb;       // minimum resident CTAs per SM requested from the compiler (register bound)
 };
 
 // Number of element columns a thread owns (16 bytes of storage).
@@ -100,6 +101,8 @@ cudaError_t launch_stream_sweep(const StreamVariant &v, const SweepArgs &a, int 
 // Max resident CTAs per SM of the variant at the given shared memory size (0 = unsupported).
 int stream_occupancy(const StreamVariant &v, size_t smem);
 bool stream_variant_exists(const StreamVariant &v);
+int stream_variant_count();
+bool stream_variant_get(int i, StreamVariant *v);
 
 // Simple kernel: one thread per output point, plain global loads.
 cudaError_t launch_simple_sweep(int R, int eq, int storage, const SweepArgs &a, int ngrids,

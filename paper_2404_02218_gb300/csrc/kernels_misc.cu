@@ -48,12 +48,12 @@ __global__ void k_simple(const SweepArgs a)
         for (int m = 1; m <= R; ++m) {
             const float xm = E::ld(u + idx - m), xp = E::ld(u + idx + m);
             const float ym = E::ld(u + idx - m * sy), yp = E::ld(u + idx + m * sy);
-            s = fmaf(a.w[m], xm + xp, s);
-            s = fmaf(a.w[m], ym + yp, s);
+            float t = (xm + xp) + (ym + yp);
             if (has_z) {
                 const float zm = E::ld(u + idx - m * sz), zp = E::ld(u + idx + m * sz);
-                s = fmaf(a.w[m], zm + zp, s);
+                t = t + (zm + zp);
             }
+            s = fmaf(a.w[m], t, s);
         }
         float o;
         if (EQ == GBST_HEAT) {
@@ -61,7 +61,7 @@ __global__ void k_simple(const SweepArgs a)
         } else {
             const float kap = g.kappa[g.korigin + z * g.kpitch * g.krows + y * g.kpitch + x];
             const float um = E::ld(out + idx);
-            o = fmaf(kap, s, fmaf(2.0f, c, -um));
+            o = fmaf(kap, s, (c + c) - um);
             if (g.has_src && a.srcval && x == g.src_x && y == g.src_y && z == g.src_z)
                 o += a.srcval[blockIdx.y];
         }

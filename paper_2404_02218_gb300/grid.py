@@ -159,6 +159,13 @@ class Grid:
     def describe(self) -> str:
         return N.stencil_describe(self.h)
 
+    def set_plan(self, variant: int = -1, txt: int = 0, zchunks: int = 0, ctas: int = 0):
+        N.stencil_set_plan(self.h, variant, txt, zchunks, ctas)
+
+    def tune(self, reps: int = 5) -> dict:
+        import json
+        return json.loads(N.stencil_tune(self.h, reps))
+
     def set_profile(self, on: bool):
         N.stencil_set_profile(self.h, on)
 

@@ -97,6 +97,10 @@ def lib() -> ctypes.CDLL:
                 "stencil_destroy": ([H], i32),
                 "stencil_set_profile": ([H, i32], i32),
                 "stencil_last_kernel_time": ([H, ctypes.POINTER(dbl), ctypes.POINTER(i64)], i32),
+                "stencil_set_plan": ([H, i32, i32, i32, i32], i32),
+                "stencil_tune": ([H, i32, ctypes.c_char_p, ctypes.c_size_t], i32),
+                "stencil_variant_count": ([], i32),
+                "stencil_variant_info": ([i32, ctypes.c_char_p, ctypes.c_size_t], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -189,3 +193,23 @@ def stencil_last_kernel_time(h):
     n = ctypes.c_int64()
     _check(lib().stencil_last_kernel_time(h, ctypes.byref(ms), ctypes.byref(n)), "stencil_last_kernel_time")
     return ms.value, n.value
+
+
+def stencil_set_plan(h, variant: int = -1, txt: int = 0, zchunks: int = 0, ctas: int = 0):
+    _check(lib().stencil_set_plan(h, variant, txt, zchunks, ctas), "stencil_set_plan")
+
+
+def stencil_tune(h, reps: int = 5) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().stencil_tune(h, reps, buf, 1 << 16), "stencil_tune")
+    return buf.value.decode()
+
+
+def stencil_variant_count() -> int:
+    return lib().stencil_variant_count()
+
+
+def stencil_variant_info(i: int) -> str:
+    buf = ctypes.create_string_buffer(512)
+    _check(lib().stencil_variant_info(i, buf, 512), "stencil_variant_info")
+    return buf.value.decode()
