@@ -83,7 +83,7 @@ typedef struct gbst_desc {
     int decomp[3];         /* subdomains per axis ({0,0,0} or {1,1,1} = none; e.g. {2,2,2}) */
     int allow_unstable;    /* 0: reject time steps above the von Neumann limit (GBST_EUNSTABLE) */
     int kernel;            /* GBST_KERNEL_AUTO / STREAM (TMA 2.5D) / SIMPLE (one thread per point) */
-    int tile;              /* 0 = autotuned (cached per shape class); > 0 = fixed plan id */
+    int tile;              /* 0 = cached autotuned plan, else the default; k > 0 = kernel variant k-1 */
     int use_graph;         /* 0: direct launches; 1: capture the step loop as a CUDA graph */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
     const gbst_allocator *allocator; /* NULL = cudaMalloc / cudaFree */

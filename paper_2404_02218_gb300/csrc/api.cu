@@ -352,21 +352,18 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
             return fail(GBST_EINVAL, "kernel variant %d does not match this grid", variant);
         p.variant = variant;
     } else {
-        p.var = StreamVariant{h->R, h->d.eq, st, h->ndim == 3, 128, 1, 1, 1};
+        p.var = StreamVariant{h->R, h->d.eq, st, h->ndim == 3, 128, 1, 1, 1, 8};
     }
     const int nt = p.var.nthreads;
-    // tile width: txt threads along x (tile width txt*px; the TMA box is at most 256 wide)
-    if (txt <= 0)
-        txt = st == GBST_BF16 ? 8 : 16;
-    while (txt * px + 2 * G > 256 && txt > 1)
-        txt /= 2;
-    if (nt % txt)
-        return fail(GBST_EINVAL, "tile: %d threads along x does not divide %d", txt, nt);
-    p.txt = txt;
-    const int TX = txt * px, TY = (nt / txt) * p.var.py;
+    // tile: txt threads along x (fixed by the variant), nt / txt along y
+    if (!p.stream)
+        p.var.txt = 8;
+    (void)txt;
+    p.txt = p.var.txt;
+    const int TX = p.txt * px, TY = (nt / p.txt) * p.var.py;
     const int box_w = TX + 2 * G, box_h = TY + 2 * h->R;
-    if (box_h > 256)
-        return fail(GBST_EINVAL, "tile height %d too large for a TMA box", TY);
+    if (box_w > 256 || box_h > 256)
+        return fail(GBST_EINVAL, "tile %dx%d too large for a TMA box", TX, TY);
     p.max_box_bytes = box_w * box_h * h->es;
 
     int64_t T = 0;
@@ -884,7 +881,7 @@ gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
     if (d.tile == 0 && d.kernel != GBST_KERNEL_SIMPLE && tune_cache_find(h, &tp))
         st = build_plan(h, tp.variant, tp.txt, tp.zchunks, tp.ctas);
     else
-        st = build_plan(h, -1, d.tile > 0 ? d.tile : 0, 0, 0);
+        st = build_plan(h, d.tile > 0 ? d.tile - 1 : -1, 0, 0, 0);
     if (st != GBST_OK)
         return bail(st);
     *out = h;
@@ -1280,8 +1277,8 @@ gbst_status stencil_variant_info(int i, char *buf, size_t len)
         return fail(GBST_EINVAL, "bad variant index or buffer");
     snprintf(buf, len,
              "{\"R\": %d, \"eq\": %d, \"storage\": %d, \"has_z\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, "
-             "\"minb\": %d}",
-             v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb);
+             "\"minb\": %d, \"txt\": %d}",
+             v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb, v.txt);
     return GBST_OK;
 }
 
@@ -1334,12 +1331,13 @@ gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len)
     for (int vi = 0; stream_variant_get(vi, &v); ++vi) {
         if (v.R != h->R || v.eq != h->d.eq || v.storage != h->d.storage || v.has_z != (h->ndim == 3))
             continue;
-        for (int txt : {8, 16, 32}) {
+        {
+            const int txt = v.txt;
             const int *zl = h->ndim == 3 ? zlist_3d : zlist_2d;
             const int nz = h->ndim == 3 ? 6 : 1;
             int last_units = -1;
             for (int zi = 0; zi < nz; ++zi) {
-                if (build_plan(h, vi, txt, zl[zi], 0) != GBST_OK || h->plan.txt != txt)
+                if (build_plan(h, vi, txt, zl[zi], 0) != GBST_OK)
                     continue;
                 if (h->plan.nunits == last_units)
                     continue;

@@ -88,6 +88,7 @@ struct StreamVariant {
     int py;         // output rows per thread
     int depth;      // TMA prefetch depth (planes in flight beyond the current one)
     int minb;       // minimum resident CTAs per SM requested from the compiler (register bound)
+    int txt;        // threads along x of a tile (tile width = txt * 16 bytes of storage)
 };
 
 // Number of element columns a thread owns (16 bytes of storage).

@@ -11,14 +11,12 @@ struct Elem;
 template <>
 struct Elem<GBST_F32> {
     using T = float;
-    static constexpr int ES = 4;
     __device__ __forceinline__ static float ld(const T *p) { return *p; }
     __device__ __forceinline__ static void st(T *p, float v) { *p = v; }
 };
 template <>
 struct Elem<GBST_BF16> {
     using T = __nv_bfloat16;
-    static constexpr int ES = 2;
     __device__ __forceinline__ static float ld(const T *p) { return __bfloat162float(*p); }
     __device__ __forceinline__ static void st(T *p, float v) { *p = __float2bfloat16_rn(v); }
 };

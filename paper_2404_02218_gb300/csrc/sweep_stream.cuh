@@ -1,0 +1,538 @@
+// Streaming (2.5D) star-stencil sweep for sm_103a.
+//
+// One CTA owns an x-y tile and marches along z.  Every z-plane of the input
+// field (tile plus an r-wide halo, 16 bytes wide in x) is copied from HBM to
+// shared memory by a TMA tensor load (cp.async.bulk.tensor.3d) that completes
+// on an mbarrier; a ring of S = r + 1 + D plane slots keeps the planes
+// [z-r, z] resident while the next D planes are in flight.  Each thread owns
+// PY rows x PX consecutive x points (16 bytes of storage per row) and keeps
+// its 2r+1 z-neighbours in a register queue whose slot indices are resolved at
+// compile time by unrolling the z-loop by 2r+1.  x- and y-neighbours are read
+// from the centre plane in shared memory with 16-byte loads.
+//
+// Update (paper Section 5.1 heat listing, Section 6.1 acoustic wave):
+//   heat:  u+ = u + a * L(u)
+//   wave:  u+ = 2u - u- + kappa * L(u)   (written in place over u-)
+//   L(u)  = w0*ndim*u + sum_{m=1..r} w_m [((x-m + x+m) + (y-m + y+m)) + (z-m + z+m)]
+// The summation order per point is fixed and independent of the point's
+// position in its tile, so a decomposed run matches an undecomposed one bit
+// for bit.
+#pragma once
+#include "gbst_internal.h"
+
+namespace gbst {
+namespace sweep {
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase; false if it did not complete within kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > kWaitLimitNs)
+            return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_plane(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                               int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint4 lds128(const unsigned char *p)
+{
+    return *reinterpret_cast<const uint4 *>(p);
+}
+
+// ---- storage traits: 16 bytes = PX elements --------------------------------
+template <int ST>
+struct Storage;
+
+template <>
+struct Storage<GBST_F32> {
+    static constexpr int PX = 4, ES = 4;
+    __device__ __forceinline__ static float2 pair(const uint4 &v, int pp)
+    {
+        return pp == 0 ? make_float2(__uint_as_float(v.x), __uint_as_float(v.y))
+                       : make_float2(__uint_as_float(v.z), __uint_as_float(v.w));
+    }
+    __device__ __forceinline__ static float get(const uint4 &v, int i)
+    {
+        return __uint_as_float(i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w);
+    }
+    __device__ __forceinline__ static uint4 pack(const float *o)
+    {
+        return make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]),
+                          __float_as_uint(o[3]));
+    }
+    __device__ __forceinline__ static void store1(void *p, float v) { *reinterpret_cast<float *>(p) = v; }
+};
+
+template <>
+struct Storage<GBST_BF16> {
+    static constexpr int PX = 8, ES = 2;
+    __device__ __forceinline__ static float2 pair(const uint4 &v, int pp)
+    {
+        const uint32_t w = pp == 0 ? v.x : pp == 1 ? v.y : pp == 2 ? v.z : v.w;
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    __device__ __forceinline__ static float get(const uint4 &v, int i)
+    {
+        const uint32_t w = (i >> 1) == 0 ? v.x : (i >> 1) == 1 ? v.y : (i >> 1) == 2 ? v.z : v.w;
+        return __uint_as_float((i & 1) ? (w & 0xffff0000u) : (w << 16));
+    }
+    __device__ __forceinline__ static uint32_t pk2(float lo, float hi)
+    {
+        const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+        const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+        return l | (h << 16);
+    }
+    __device__ __forceinline__ static uint4 pack(const float *o)
+    {
+        return make_uint4(pk2(o[0], o[1]), pk2(o[2], o[3]), pk2(o[4], o[5]), pk2(o[6], o[7]));
+    }
+    __device__ __forceinline__ static void store1(void *p, float v)
+    {
+        *reinterpret_cast<__nv_bfloat16 *>(p) = __float2bfloat16_rn(v);
+    }
+};
+
+__device__ __forceinline__ float4 ldg_f4_nc(const float *p)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p));
+}
+
+// x-halo loads narrowed to the r elements next to the thread's column: the
+// returned 16-byte chunk holds them at their natural positions (zero elsewhere).
+template <int ST, int R>
+__device__ __forceinline__ uint4 load_left(const unsigned char *chunk)
+{
+    constexpr int B = R * Storage<ST>::ES <= 4 ? 4 : (R * Storage<ST>::ES <= 8 ? 8 : 16);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (B == 4) {
+        v.w = *reinterpret_cast<const uint32_t *>(chunk + 12);
+    } else if (B == 8) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(chunk + 8);
+        v.z = t.x;
+        v.w = t.y;
+    } else {
+        v = *reinterpret_cast<const uint4 *>(chunk);
+    }
+    return v;
+}
+
+template <int ST, int R>
+__device__ __forceinline__ uint4 load_right(const unsigned char *chunk)
+{
+    constexpr int B = R * Storage<ST>::ES <= 4 ? 4 : (R * Storage<ST>::ES <= 8 ? 8 : 16);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (B == 4) {
+        v.x = *reinterpret_cast<const uint32_t *>(chunk);
+    } else if (B == 8) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(chunk);
+        v.x = t.x;
+        v.y = t.y;
+    } else {
+        v = *reinterpret_cast<const uint4 *>(chunk);
+    }
+    return v;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another warp of the CTA has.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag)
+            return false;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Warp-specialised streaming sweep.  Warp NC is the TMA producer (one lane
+// issues a plane load per iteration into ring slot it % S, completing on
+// full[it % NB]); warps 0..NC-1 consume.  A consumer warp arrives on
+// empty[j % NB] when it has finished iteration j (its newest plane and its
+// centre plane, slot (j - rz) % S); the producer waits for empty of iteration
+// it - NB before reusing that iteration's slot for iteration it.
+template <int R, int EQ, int ST, bool HAS_Z, int NC, int PY, int D, int MINB, int TXT>
+__global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs a, const int slot_bytes)
+{
+    using St = Storage<ST>;
+    constexpr int NT = NC * 32;         // consumer threads
+    constexpr int PX = St::PX;
+    constexpr int ES = St::ES;
+    constexpr int G = PX;               // x halo in elements (16 bytes)
+    constexpr int RZ = HAS_Z ? R : 0;   // z radius
+    constexpr int QN = 2 * RZ + 1;      // register queue length
+    constexpr int S = RZ + 1 + D;       // plane slots
+    constexpr int NB = D + 1;           // barrier pairs (= loads in flight)
+    constexpr int TX = TXT * PX;                 // tile width (points)
+    constexpr int TY = (NT / TXT) * PY;          // tile height (rows)
+    constexpr int ROW_BYTES = (TX + 2 * G) * ES; // one row of a plane slot
+    static_assert(R <= G, "x halo must cover the radius");
+    static_assert(2 * NB * 8 + 16 <= 256, "barrier header");
+    static_assert(NT % TXT == 0, "tile shape");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + NB;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NB);
+    unsigned char *slots = smem + 256;
+
+    if (blockIdx.x >= a.nunits)
+        return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], NC);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // ------------------------------------------------------------ producer
+    if (warp == NC) {
+        if (lane != 0)
+            return;
+        int it = 0;
+        bool ok = true;
+        for (int ui = blockIdx.x; ok && ui < a.nunits; ui += gridDim.x) {
+            const Unit u = a.units[ui];
+            const GridDev &g = a.grids[u.grid];
+            const int bx = (u.tile % g.tiles_x) * TX, by = (u.tile / g.tiles_x) * TY;
+            const CUtensorMap *map = &g.tmap[a.parity];
+            const uint32_t bytes = static_cast<uint32_t>(g.box_bytes);
+            const int L = (u.z1 - u.z0) + 2 * RZ;
+            for (int l = 0; l < L; ++l, ++it) {
+                if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[it % NB], bytes);
+                tma_load_plane(slots + (it % S) * slot_bytes, map, &full[it % NB], bx, by, u.z0 + l);
+            }
+        }
+        if (!ok) {
+            atomicExch(a.err, kDevTimeoutTma);
+            // let the loads already issued land before the CTA can exit (short bound)
+            for (int k = it - NB < 0 ? 0 : it - NB; k < it; ++k) {
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try_wait(&full[k % NB], (k / NB) & 1) && global_ns() - t0 < 50000000ull) {
+                }
+            }
+        }
+        return;
+    }
+
+    // ----------------------------------------------------------- consumers
+    const int tid = threadIdx.x;
+    constexpr int PP = PX / 2;  // point pairs per row (packed FP32x2 arithmetic)
+    float2 q[QN][PY][PP];       // z-queue of the thread's own points, by local plane index mod QN
+    // iteration (plane) counter, kept as ring position, barrier index and phase parity
+    int slot_n = 0;             // ring slot of the newest plane   (j mod S)
+    int bar_i = 0;              // barrier pair of this iteration   (j mod NB)
+    uint32_t par = 0;           // phase parity                     ((j / NB) & 1)
+    auto advance = [&]() {
+        slot_n = slot_n + 1 == S ? 0 : slot_n + 1;
+        if (++bar_i == NB) {
+            bar_i = 0;
+            par ^= 1u;
+        }
+    };
+    const float2 wc2 = make_float2(a.wc, a.wc);
+    const float2 a2 = make_float2(a.a, a.a);
+    float2 w2[R + 1];
+#pragma unroll
+    for (int m = 0; m <= R; ++m)
+        w2[m] = make_float2(a.w[m], a.w[m]);
+
+    for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
+        const Unit u = a.units[ui];
+        // Copy the grid's descriptor into registers: the output stores below could
+        // alias it, which would otherwise force a reload after every store.
+        const GridDev *gp = a.grids + u.grid;
+        const int tiles_x = gp->tiles_x;
+        const int64_t nx = gp->nx, ny = gp->ny;
+        const int64_t pitch = gp->pitch, rows = gp->rows, origin = gp->origin;
+        const int64_t kpitch = gp->kpitch, krows = gp->krows, korigin = gp->korigin;
+        const float *__restrict__ kappa = gp->kappa;
+        unsigned char *__restrict__ outbase = static_cast<unsigned char *>(gp->buf[1 - a.parity]);
+        const bool src_unit = (EQ == GBST_WAVE) && gp->has_src;
+        const int src_x = gp->src_x, src_y = gp->src_y, src_z = gp->src_z;
+        const float srcv = (EQ == GBST_WAVE && a.srcval) ? a.srcval[u.grid] : 0.0f;
+        const int tx = tid % TXT, ty = tid / TXT;
+        const int x0 = (u.tile % tiles_x) * TX + tx * PX;
+        const int y0 = (u.tile / tiles_x) * TY + ty * PY;
+        constexpr int row_bytes = ROW_BYTES;
+        const int own_off = (R + ty * PY) * row_bytes + (G + tx * PX) * ES;
+        const bool xfull = x0 + PX <= nx;
+        bool row_ok[PY];
+#pragma unroll
+        for (int r_ = 0; r_ < PY; ++r_)
+            row_ok[r_] = y0 + r_ < ny && x0 < nx;
+        // running pointers to the thread's first row of the current output plane
+        const int64_t plane_elems = rows * pitch, kplane = krows * kpitch;
+        unsigned char *optr = outbase + (origin + (static_cast<int64_t>(u.z0) * rows + y0) * pitch + x0) * ES;
+        const float *kptr = kappa + korigin + (static_cast<int64_t>(u.z0) * krows + y0) * kpitch + x0;
+        const int64_t row_stride = pitch * ES;
+
+        // prologue: the 2*rz planes below the first output plane fill the queue
+#pragma unroll
+        for (int k = 0; k < 2 * RZ; ++k) {
+            if (!wait_or_abort(&full[bar_i], par, reinterpret_cast<volatile int *>(abort_flag)))
+                return;
+            const unsigned char *nb = slots + slot_n * slot_bytes + own_off;
+#pragma unroll
+            for (int r_ = 0; r_ < PY; ++r_) {
+                const uint4 v = lds128(nb + r_ * row_bytes);
+#pragma unroll
+                for (int pp = 0; pp < PP; ++pp)
+                    q[k][r_][pp] = St::pair(v, pp);
+            }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&empty[bar_i]);
+            advance();
+        }
+
+        const int nout = u.z1 - u.z0;
+        for (int c0 = 0; c0 < nout; c0 += QN) {
+#pragma unroll
+            for (int k = 0; k < QN; ++k) {
+                const int c = c0 + k;
+                if (c < nout) {
+                    const int qn = (k + 2 * RZ) % QN;  // slot of the newest plane (constant after unrolling)
+                    const int qc = (k + RZ) % QN;      // slot of the centre plane
+                    const int zc = u.z0 + c;
+
+                    // Wave: kappa and u- of the centre plane, issued before waiting on the TMA.
+                    float kap[PY][PX], um[PY][PX];
+                    if (EQ == GBST_WAVE) {
+#pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_) {
+                            const float *kp = kptr + r_ * kpitch;
+                            const unsigned char *up = optr + r_ * row_stride;
+#pragma unroll
+                            for (int v = 0; v < PX / 4; ++v) {
+                                const float4 kv = row_ok[r_] ? ldg_f4_nc(kp + 4 * v) : make_float4(0, 0, 0, 0);
+                                kap[r_][4 * v + 0] = kv.x;
+                                kap[r_][4 * v + 1] = kv.y;
+                                kap[r_][4 * v + 2] = kv.z;
+                                kap[r_][4 * v + 3] = kv.w;
+                            }
+                            const uint4 uv =
+                                row_ok[r_] ? __ldcs(reinterpret_cast<const uint4 *>(up)) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+                            for (int i = 0; i < PX; ++i)
+                                um[r_][i] = St::get(uv, i);
+                        }
+                    }
+
+                    if (!wait_or_abort(&full[bar_i], par, reinterpret_cast<volatile int *>(abort_flag)))
+                        return;
+                    {
+                        const unsigned char *nb = slots + slot_n * slot_bytes + own_off;
+#pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_) {
+                            const uint4 v = lds128(nb + r_ * row_bytes);
+#pragma unroll
+                            for (int pp = 0; pp < PP; ++pp)
+                                q[qn][r_][pp] = St::pair(v, pp);
+                        }
+                    }
+
+                    const int slot_c = slot_n >= RZ ? slot_n - RZ : slot_n - RZ + S;
+                    const unsigned char *cb = slots + slot_c * slot_bytes + own_off;
+                    uint4 ylo[R], yhi[R], xl[PY], xr[PY];
+#pragma unroll
+                    for (int m = 1; m <= R; ++m) {
+                        ylo[m - 1] = lds128(cb - m * row_bytes);
+                        yhi[m - 1] = lds128(cb + (PY - 1 + m) * row_bytes);
+                    }
+#pragma unroll
+                    for (int r_ = 0; r_ < PY; ++r_) {
+                        xl[r_] = load_left<ST, R>(cb + r_ * row_bytes - 16);
+                        xr[r_] = load_right<ST, R>(cb + r_ * row_bytes + 16);
+                    }
+
+                    // element e in [-G, PX+G) of centre row r_: own points or the x-halo chunks
+                    auto xel = [&](int r_, int e) -> float {
+                        if (e < 0)
+                            return St::get(xl[r_], PX + e);
+                        if (e >= PX)
+                            return St::get(xr[r_], e - PX);
+                        return (e & 1) ? q[qc][r_][e >> 1].y : q[qc][r_][e >> 1].x;
+                    };
+                    // pair pp of centre-plane row `row` (relative to the thread's first row)
+                    auto yrow = [&](int row, int pp) -> float2 {
+                        if (row < 0)
+                            return St::pair(ylo[-row - 1], pp);
+                        if (row >= PY)
+                            return St::pair(yhi[row - PY], pp);
+                        return q[qc][row][pp];
+                    };
+                    // Per point: t_m = ((x-m + x+m) + (y-m + y+m)) + (z-m + z+m) for every m
+                    // (independent of each other), then s = w0*ndim*c, s = fma(w_m, t_m, s)
+                    // for m = 1..r.  The dependent chain is r + 3 deep instead of 3r + 1.
+                    float2 sv[PY][PP];
+#pragma unroll
+                    for (int r_ = 0; r_ < PY; ++r_)
+#pragma unroll
+                        for (int pp = 0; pp < PP; ++pp)
+                            sv[r_][pp] = __fmul2_rn(wc2, q[qc][r_][pp]);
+#pragma unroll
+                    for (int m = 1; m <= R; ++m) {
+#pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_) {
+#pragma unroll
+                            for (int pp = 0; pp < PP; ++pp) {
+                                const int e = 2 * pp;
+                                const float2 xm = make_float2(xel(r_, e - m), xel(r_, e + 1 - m));
+                                const float2 xp = make_float2(xel(r_, e + m), xel(r_, e + 1 + m));
+                                float2 t = __fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
+                                if (HAS_Z)
+                                    t = __fadd2_rn(t, __fadd2_rn(q[(qc - m + 2 * QN) % QN][r_][pp], q[(qc + m) % QN][r_][pp]));
+                                sv[r_][pp] = __ffma2_rn(w2[m], t, sv[r_][pp]);
+                            }
+                        }
+                    }
+                    float o[PY][PX];
+#pragma unroll
+                    for (int r_ = 0; r_ < PY; ++r_) {
+#pragma unroll
+                        for (int pp = 0; pp < PP; ++pp) {
+                            const float2 cv = q[qc][r_][pp];
+                            float2 ov;
+                            if (EQ == GBST_HEAT) {
+                                ov = __ffma2_rn(a2, sv[r_][pp], cv);
+                            } else {
+                                const float2 k2 = make_float2(kap[r_][2 * pp], kap[r_][2 * pp + 1]);
+                                const float2 t2 = __fadd2_rn(__fadd2_rn(cv, cv),
+                                                             make_float2(-um[r_][2 * pp], -um[r_][2 * pp + 1]));
+                                ov = __ffma2_rn(k2, sv[r_][pp], t2);
+                            }
+                            o[r_][2 * pp] = ov.x;
+                            o[r_][2 * pp + 1] = ov.y;
+                        }
+                    }
+                    // all shared-memory reads of this iteration are done: release the planes
+                    __syncwarp();
+                    if (lane == 0)
+                        mbar_arrive(&empty[bar_i]);
+                    advance();
+
+                    if (src_unit && zc == src_z) {
+                        const int sr = src_y - y0, si = src_x - x0;
+                        if (sr >= 0 && sr < PY && si >= 0 && si < PX) {
+#pragma unroll
+                            for (int r_ = 0; r_ < PY; ++r_)
+#pragma unroll
+                                for (int i = 0; i < PX; ++i)
+                                    if (r_ == sr && i == si)
+                                        o[r_][i] += srcv;
+                        }
+                    }
+#pragma unroll
+                    for (int r_ = 0; r_ < PY; ++r_) {
+                        if (row_ok[r_]) {
+                            unsigned char *op = optr + r_ * row_stride;
+                            if (xfull) {
+                                *reinterpret_cast<uint4 *>(op) = St::pack(o[r_]);
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < PX; ++i)
+                                    if (x0 + i < nx)
+                                        St::store1(op + i * ES, o[r_][i]);
+                            }
+                        }
+                    }
+                    optr += plane_elems * ES;
+                    kptr += kplane;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// ---- variant tables ----------------------------------------------------------
+using KernelFn = void (*)(const SweepArgs, const int);
+
+struct Entry {
+    StreamVariant v;
+    KernelFn fn;
+};
+
+template <int R, int EQ, int ST, bool HZ, int NC, int PY, int D, int MINB, int TXT>
+constexpr Entry entry()
+{
+    return Entry{StreamVariant{R, EQ, ST, HZ, NC * 32, PY, D, MINB, TXT},
+                 &k_stream<R, EQ, ST, HZ, NC, PY, D, MINB, TXT>};
+}
+
+// both equations for one radius, storage, dimensionality and shape
+#define GBST_EQS(R, ST, HZ, NC, PY, D, MINB, TXT) \
+    entry<R, GBST_HEAT, ST, HZ, NC, PY, D, MINB, TXT>(), entry<R, GBST_WAVE, ST, HZ, NC, PY, D, MINB, TXT>()
+
+}  // namespace sweep
+}  // namespace gbst

@@ -107,12 +107,51 @@ def test_graph_equals_direct_bitwise(torch_cuda):
     np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("tile", [8, 16, 32])
-def test_tile_shapes_bitwise(torch_cuda, tile):
+def matching_variants(so, eq, storage, ndim):
+    import json
+    from paper_2404_02218_gb300 import native as N
+    codes = {"heat": 0, "wave": 1, "f32": 0, "bf16": 1}
+    out = []
+    for i in range(N.stencil_variant_count()):
+        v = json.loads(N.stencil_variant_info(i))
+        if (v["R"], v["eq"], v["storage"], v["has_z"]) == (so // 2, codes[eq], codes[storage], int(ndim == 3)):
+            out.append(i)
+    return out
+
+
+@pytest.mark.parametrize("so", [2, 4, 8])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_every_kernel_variant_bitwise(torch_cuda, so, storage):
+    """Every compiled tile shape / depth / register variant gives the same bits as the simple kernel."""
     dims = (130, 70, 19)
-    _, _, ref = heat_case_run(torch_cuda, dims, 8, 4, kernel="simple")
-    _, _, got = heat_case_run(torch_cuda, dims, 8, 4, tile=tile)
-    np.testing.assert_array_equal(got, ref)
+    u0 = synthetic.uniform_field(9, tuple(reversed(dims)))
+    a = float(np.float32(0.8 * synthetic.heat_a_max(3, so)))
+    ref = make_grid(torch_cuda, 3, dims, so, "heat", storage=storage, dt=a, kernel="simple")
+    ref.set_field("u", u0)
+    ref.run(4)
+    want = ref.get_field("u")
+    variants = matching_variants(so, "heat", storage, 3)
+    assert variants
+    g = make_grid(torch_cuda, 3, dims, so, "heat", storage=storage, dt=a)
+    for v in variants:
+        for zc in (0, 3):
+            g.set_field("u", u0)
+            g.set_plan(v, 0, zc, 0)
+            g.run(4)
+            np.testing.assert_array_equal(g.get_field("u"), want, err_msg=f"variant {v} zchunks {zc}")
+
+
+def test_autotuner_keeps_fields_and_picks_a_plan(torch_cuda):
+    import json
+    dims = (96, 64, 48)
+    g, *_ = wave_setup(torch_cuda, dims, 8)
+    g.run(9)
+    before_u, before_p = g.get_field("u"), g.get_field("u_prev")
+    rep = g.tune(reps=2)
+    assert rep["candidates"] and rep["best"]["variant"] in matching_variants(8, "wave", "f32", 3)
+    np.testing.assert_array_equal(g.get_field("u"), before_u)
+    np.testing.assert_array_equal(g.get_field("u_prev"), before_p)
+    assert json.loads(g.describe())["variant"] == rep["best"]["variant"]
 
 
 @pytest.mark.parametrize("so", [2, 8])
