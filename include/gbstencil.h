@@ -187,6 +187,28 @@ gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len);
 int stencil_variant_count(void);
 gbst_status stencil_variant_info(int i, char *buf, size_t len);
 
+/* FP64 reduction of a dense device array that allocates no device memory.
+ * The paper has no counterpart; this serves callers that cannot allocate
+ * device memory when they need the reduction -- applications whose device
+ * memory is all owned by their own pool, and latency-critical loops that must
+ * not call cudaMalloc/cudaFree because those can synchronise the device.
+ *   x      device pointer to n values of dtype GBST_F32, GBST_F64 or GBST_BF16
+ *   kind   GBST_RED_SUM, GBST_RED_L2SQ or GBST_RED_MAXABS (as stencil_reduce_f64)
+ *   out    device pointer to one double, written asynchronously on `stream`
+ *          (a cudaStream_t; NULL = legacy default stream); synchronise before reading
+ * The per-block partial sums go to a fixed 128 KB array inside the library's
+ * device image (16384 doubles, 256-byte aligned), which every GPU that loads the
+ * library keeps until the process exits.  n may be at most 2^30 (16384 blocks of
+ * 65536 values); larger n returns GBST_EINVAL.  The first call on each device
+ * looks up the array's device address with that device current (make that first
+ * call outside any stream capture).  All calls share the one array and it keeps
+ * the last call's contents; every call writes all the partials it reads, so no
+ * clearing is needed, but calls that overlap on the GPU (different streams,
+ * no ordering between them) race on it.  No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
+gbst_status gbst_reduce_dense_f64_noalloc(const void *x, int dtype, int64_t n, int kind, double *out,
+                                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

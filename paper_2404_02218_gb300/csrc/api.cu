@@ -43,6 +43,8 @@ static gbst_status fail(gbst_status st, const char *fmt, ...)
     return st;
 }
 
+gbst_status record_error(gbst_status st, const char *msg) { return fail(st, "%s", msg); }
+
 #define GBST_CUDA(call)                                                                             \
     do {                                                                                            \
         cudaError_t e_ = (call);                                                                    \

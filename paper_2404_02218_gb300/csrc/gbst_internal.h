@@ -144,6 +144,9 @@ cudaError_t launch_reduce_partials(int kind, int storage, int ndim, int R, const
 cudaError_t launch_reduce_final(int kind, const double *partials, int n, double *out,
                                 cudaStream_t s);
 
+// Record the message returned by stencil_last_error() for the calling thread.
+gbst_status record_error(gbst_status st, const char *msg);
+
 // Tensor-map encoding through the driver entry point.
 bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h,
                  std::string *err);

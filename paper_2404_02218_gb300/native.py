@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
                 "stencil_tune": ([H, i32, ctypes.c_char_p, ctypes.c_size_t], i32),
                 "stencil_variant_count": ([], i32),
                 "stencil_variant_info": ([i32, ctypes.c_char_p, ctypes.c_size_t], i32),
+                "gbst_reduce_dense_f64_noalloc": ([vp, i32, i64, i32, vp, vp], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -213,3 +214,10 @@ def stencil_variant_info(i: int) -> str:
     buf = ctypes.create_string_buffer(512)
     _check(lib().stencil_variant_info(i, buf, 512), "stencil_variant_info")
     return buf.value.decode()
+
+
+def gbst_reduce_dense_f64_noalloc(x_ptr: int, dtype: int, n: int, kind: int, out_ptr: int, stream: int = 0):
+    """Allocation-free FP64 reduction of a dense device array (result written to out_ptr on the device)."""
+    _check(lib().gbst_reduce_dense_f64_noalloc(ctypes.c_void_p(x_ptr), dtype, int(n), kind,
+                                               ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)),
+           "gbst_reduce_dense_f64_noalloc")
