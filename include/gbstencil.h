@@ -168,6 +168,39 @@ gbst_status stencil_destroy(gbst_handle h);
 gbst_status stencil_set_profile(gbst_handle h, int enable);
 gbst_status stencil_last_kernel_time(gbst_handle h, double *ms, int64_t *launches);
 
+/* ---- batches ---------------------------------------------------------------
+ * A batch handle holds n independent grids advanced together: every sweep
+ * launch (or, in persistent mode, the one launch of a whole run) covers the
+ * tiles of all of them.  All members share ndim, space_order, eq, storage,
+ * coefficients and kernel choice, have zero halos and no decomposition; each
+ * has its own dims, h, dt and alpha (descs[i]), its own fields and source.
+ * stream and allocator are taken from descs[0].  stencil_run, stencil_sync,
+ * stencil_tune, stencil_set_plan, stencil_describe, stencil_destroy,
+ * stencil_reduce_f64 (over all members) and the step counter apply to the whole
+ * batch; the functions below address one member, 0 <= grid < n.
+ * (Not in the paper: the batching of many small problems into one launch.) */
+gbst_status stencil_batch_create(const gbst_desc *descs, int n, gbst_handle *out);
+gbst_status stencil_batch_size(gbst_handle h, int *n);
+gbst_status stencil_batch_set_field(gbst_handle h, int grid, int field, const void *src, int src_dtype,
+                                    int src_on_device);
+gbst_status stencil_batch_get_field(gbst_handle h, int grid, int field, void *dst, int dst_dtype,
+                                    int dst_on_device);
+gbst_status stencil_batch_set_source(gbst_handle h, int grid, const int64_t idx[3], double f0_hz, double t0_s,
+                                     double amp);
+gbst_status stencil_batch_reduce_f64(gbst_handle h, int grid, int kind, double *out);
+
+/* Persistent mode (enable != 0): stencil_run(n) issues ONE cooperative launch
+ * that performs all n steps, with a grid-wide barrier between steps (every
+ * CTA resident; the barrier wait is bounded and reports GBST_ETIMEOUT at the
+ * next synchronising call if it expires).  Requires the streaming kernel and
+ * no halo exchanges (no decomposition, zero halos).  With use_graph the launch
+ * is captured as a single graph node. */
+gbst_status stencil_set_persistent(gbst_handle h, int enable);
+
+/* Test hook: make every grid barrier of persistent launches wait for `extra`
+ * arrivals that never come, so the bounded wait expires (0 restores normal use). */
+gbst_status stencil_debug_barrier_extra(gbst_handle h, unsigned int extra);
+
 /* Execution plan of the streaming sweep.  variant: index into the kernel
  * table (stencil_variant_count / stencil_variant_info; -1 = the default for
  * this grid); txt: threads along x of a tile (8, 16, 32; 0 = default); zchunks:

@@ -194,8 +194,16 @@ using namespace gbst;
 
 struct Sub {
     Layout lu, lk;
-    int64_t g0[3];  // global interior offset (x, y, z)
-    int c[3];       // coordinates in the decomposition grid
+    int64_t g0[3];      // offset of the interior in the caller's dense arrays (x, y, z)
+    int64_t dense[3];   // dims of those dense arrays: the whole grid, or the batch member itself
+    int c[3];           // coordinates in the decomposition grid
+    int member = 0;     // batch member (0 for a single, possibly decomposed, grid)
+    double dt = 0.0, h = 1.0, alpha = 0.0;
+    // Ricker point source of the wave equation
+    bool src_on = false;
+    int64_t src_local[3] = {0, 0, 0};
+    double f0 = 0.0, t0 = 0.0, amp = 0.0, kappa_src = 0.0;
+    bool unstable = false;  // kappa above the stability limit
 };
 
 struct Plan {
@@ -216,9 +224,10 @@ struct gbst_grid_s {
     gbst_desc d{};
     int ndim = 3, R = 1, es = 4;
     double w[kMaxRadius + 1] = {0};
-    double a = 0.0, S = 0.0;
-    int64_t dims[3] = {1, 1, 1};
+    double S = 0.0;
     int decomp[3] = {1, 1, 1};
+    bool batch = false;
+    int members = 1;
     cudaStream_t stream = nullptr;
     Allocator mem;
     std::vector<DevMem> owned;
@@ -235,21 +244,17 @@ struct gbst_grid_s {
     int parity = 0;
     int64_t step = 0;
     int *derr = nullptr;
+    unsigned int *dbarrier = nullptr;
+    unsigned int barrier_extra = 0;
+    bool persistent = false;
     double *dpartials = nullptr;
     int red_blocks_per_grid = 0;
     double *dred_out = nullptr;
     ReduceGrid *dred_grids = nullptr;
-    // source
-    bool has_src = false;
-    int src_sub = -1;
-    int64_t src_local[3] = {0, 0, 0};
-    double f0 = 0, t0 = 0, amp = 0;
-    double kappa_src = 0.0;
     float *dsrc = nullptr;
     float *hsrc = nullptr;
     int64_t src_cap = 0;  // steps
     cudaEvent_t src_ev = nullptr;
-    bool kappa_set = false, unstable = false;
     gbst_status sticky = GBST_OK;
     std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs;
     bool profile = false;
@@ -456,12 +461,17 @@ bool g_tune_loaded = false;
 
 std::string tune_key(gbst_handle h)
 {
+    // shape class: the first subdomain's sizes plus a hash of every subdomain's sizes
+    uint64_t hash = 1469598103934665603ull;
+    for (const Sub &s : h->subs)
+        for (int64_t v : {s.lu.nx, s.lu.ny, s.lu.nz}) {
+            hash ^= static_cast<uint64_t>(v);
+            hash *= 1099511628211ull;
+        }
     char b[256];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    snprintf(b, sizeof b, "sm%d/r%d/eq%d/st%d/nd%d/%lldx%lldx%lld/sub%zu", num_sms(), h->R, h->d.eq, h->d.storage,
-             h->ndim, static_cast<long long>(h->subs[0].lu.nx), static_cast<long long>(h->subs[0].lu.ny),
-             static_cast<long long>(h->subs[0].lu.nz), h->subs.size());
+    snprintf(b, sizeof b, "sm%d/r%d/eq%d/st%d/nd%d/%lldx%lldx%lld/sub%zu/%016llx", num_sms(), h->R, h->d.eq,
+             h->d.storage, h->ndim, static_cast<long long>(h->subs[0].lu.nx), static_cast<long long>(h->subs[0].lu.ny),
+             static_cast<long long>(h->subs[0].lu.nz), h->subs.size(), static_cast<unsigned long long>(hash));
     return b;
 }
 
@@ -629,9 +639,12 @@ SweepArgs sweep_args(gbst_handle h, int parity, const float *srcval)
     a.wc = static_cast<float>(h->ndim * h->w[0]);
     for (int m = 1; m <= h->R; ++m)
         a.w[m] = static_cast<float>(h->w[m]);
-    a.a = static_cast<float>(h->a);
     a.srcval = srcval;
     a.err = h->derr;
+    a.nsteps = 1;
+    a.ngrids = static_cast<int>(h->subs.size());
+    a.barrier = h->dbarrier;
+    a.barrier_extra = h->barrier_extra;
     return a;
 }
 
@@ -659,6 +672,22 @@ gbst_status enqueue_step(gbst_handle h, int parity, const float *srcval, int pro
     if (prof_index >= 0)
         GBST_CUDA(cudaEventRecordWithFlags(h->prof_ev[2 * prof_index + 1], h->stream,
                                            cudaEventRecordExternal));
+    return GBST_OK;
+}
+
+// Enqueue a whole run as one persistent launch (grid-wide barriers between steps).
+gbst_status enqueue_persistent(gbst_handle h, int64_t nsteps, int parity, const float *srcval, bool prof)
+{
+    GBST_CUDA(cudaMemsetAsync(h->dbarrier, 0, sizeof(unsigned int), h->stream));
+    SweepArgs a = sweep_args(h, parity, srcval);
+    a.nsteps = static_cast<int>(nsteps);
+    if (prof)
+        GBST_CUDA(cudaEventRecordWithFlags(h->prof_ev[0], h->stream, cudaEventRecordExternal));
+    const cudaError_t e = launch_stream_sweep(h->plan.var, a, h->plan.ctas, h->plan.smem, h->stream, true);
+    if (e != cudaSuccess)
+        return fail(GBST_ECUDA, "persistent sweep launch: %s", cudaGetErrorString(e));
+    if (prof)
+        GBST_CUDA(cudaEventRecordWithFlags(h->prof_ev[1], h->stream, cudaEventRecordExternal));
     return GBST_OK;
 }
 
@@ -691,42 +720,23 @@ gbst_status ensure_src_capacity(gbst_handle h, int64_t nsteps)
 
 gbst_status read_kappa_at_source(gbst_handle h)
 {
-    if (!h->has_src)
-        return GBST_OK;
-    const Sub &s = h->subs[h->src_sub];
-    const GridDev &g = h->hgrids[h->src_sub];
-    const int64_t k = h->ndim == 3 ? h->src_local[2] : 0;
-    const int64_t idx = s.lk.origin + (k * s.lk.rows + h->src_local[1]) * s.lk.pitch + h->src_local[0];
-    float v = 0.f;
     GBST_CUDA(cudaStreamSynchronize(h->stream));
-    GBST_CUDA(cudaMemcpy(&v, g.kappa + idx, sizeof(float), cudaMemcpyDeviceToHost));
-    h->kappa_src = v;
+    for (size_t i = 0; i < h->subs.size(); ++i) {
+        Sub &s = h->subs[i];
+        if (!s.src_on)
+            continue;
+        const int64_t k = h->ndim == 3 ? s.src_local[2] : 0;
+        const int64_t idx = s.lk.origin + (k * s.lk.rows + s.src_local[1]) * s.lk.pitch + s.src_local[0];
+        float v = 0.f;
+        GBST_CUDA(cudaMemcpy(&v, h->hgrids[i].kappa + idx, sizeof(float), cudaMemcpyDeviceToHost));
+        s.kappa_src = v;
+    }
     return GBST_OK;
 }
 
-}  // namespace
-
-// =========================================================================
-extern "C" {
-
-int gbst_version(void) { return 10000; }
-
-const char *stencil_last_error(void) { return t_err.c_str(); }
-
-gbst_status stencil_fd_weights(int space_order, double *out)
+// Validate one grid description; dims receives the interior sizes (z = 1 in 2D).
+gbst_status validate_desc(const gbst_desc &d, int64_t dims[3], int decomp[3])
 {
-    if (!out || space_order < 2 || space_order > 16 || space_order % 2)
-        return fail(GBST_EINVAL, "space_order must be even in [2, 16]");
-    central_weights(space_order / 2, out);
-    return GBST_OK;
-}
-
-gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
-{
-    if (!desc || !out)
-        return fail(GBST_EINVAL, "null desc or out");
-    *out = nullptr;
-    const gbst_desc &d = *desc;
     if (d.ndim != 2 && d.ndim != 3)
         return fail(GBST_EINVAL, "ndim must be 2 or 3");
     if (d.space_order != 2 && d.space_order != 4 && d.space_order != 8)
@@ -740,11 +750,12 @@ gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
     if (d.kernel < GBST_KERNEL_AUTO || d.kernel > GBST_KERNEL_SIMPLE)
         return fail(GBST_EINVAL, "kernel must be GBST_KERNEL_AUTO, _STREAM or _SIMPLE");
     const int R = d.space_order / 2;
-    int64_t dims[3] = {d.dims[0], d.dims[1], d.ndim == 3 ? d.dims[2] : 1};
+    dims[0] = d.dims[0];
+    dims[1] = d.dims[1];
+    dims[2] = d.ndim == 3 ? d.dims[2] : 1;
     for (int a = 0; a < d.ndim; ++a)
         if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
             return fail(GBST_EINVAL, "dims[%d] = %lld out of range", a, static_cast<long long>(dims[a]));
-    int decomp[3];
     for (int a = 0; a < 3; ++a) {
         decomp[a] = d.decomp[a] <= 0 ? 1 : d.decomp[a];
         if (a >= d.ndim && decomp[a] != 1)
@@ -761,6 +772,47 @@ gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
                 return fail(GBST_EINVAL, "periodic boundaries need at least r points per axis");
     if (d.h <= 0.0 || d.dt <= 0.0)
         return fail(GBST_EINVAL, "h and dt must be positive");
+    return GBST_OK;
+}
+
+gbst_status destroy_handle(gbst_handle h);
+
+// Create a handle from n descriptions: n == 1 is a single (possibly decomposed)
+// grid; n > 1 a batch of independent grids sharing dimensionality, order,
+// equation, storage and weights (each with its own sizes, step and spacing).
+gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle *out)
+{
+    if (!descs || !out || n < 1)
+        return fail(GBST_EINVAL, "null descriptions or handle, or n < 1");
+    *out = nullptr;
+    const gbst_desc &d = descs[0];
+    int64_t dims0[3];
+    int decomp[3];
+    gbst_status st = validate_desc(d, dims0, decomp);
+    if (st != GBST_OK)
+        return st;
+    const int R = d.space_order / 2;
+    for (int i = 1; i < n; ++i) {
+        int64_t di[3];
+        int dc[3];
+        st = validate_desc(descs[i], di, dc);
+        if (st != GBST_OK)
+            return st;
+        const gbst_desc &e = descs[i];
+        if (e.ndim != d.ndim || e.space_order != d.space_order || e.eq != d.eq || e.storage != d.storage ||
+            e.bc != d.bc || e.kernel != d.kernel)
+            return fail(GBST_EINVAL, "batch member %d differs in ndim/order/equation/storage/bc/kernel", i);
+    }
+    if (batch) {
+        for (int i = 0; i < n; ++i) {
+            const gbst_desc &e = descs[i];
+            if (e.bc != GBST_BC_ZERO)
+                return fail(GBST_ENOTSUP, "batch members need zero (Dirichlet) halos");
+            for (int a = 0; a < 3; ++a)
+                if (e.decomp[a] > 1)
+                    return fail(GBST_ENOTSUP, "batch members cannot be decomposed");
+        }
+    }
 
     gbst_handle h = new (std::nothrow) gbst_grid_s;
     if (!h)
@@ -770,17 +822,16 @@ gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
     h->ndim = d.ndim;
     h->R = R;
     h->es = d.storage == GBST_BF16 ? 2 : 4;
-    for (int a = 0; a < 3; ++a) {
-        h->dims[a] = dims[a];
-        h->decomp[a] = decomp[a];
-    }
+    h->batch = batch;
+    h->members = n;
+    for (int a = 0; a < 3; ++a)
+        h->decomp[a] = batch ? 1 : decomp[a];
     if (d.coeffs)
         for (int m = 0; m <= R; ++m)
             h->w[m] = d.coeffs[m];
     else
         central_weights(R, h->w);
     h->S = symbol_max(R, h->w);
-    h->a = d.alpha * d.dt / (d.h * d.h);
     h->stream = static_cast<cudaStream_t>(d.stream);
     h->mem.s = h->stream;
     if (d.allocator) {
@@ -791,40 +842,56 @@ gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
         h->mem.a = *d.allocator;
         h->mem.custom = true;
     }
-    if (d.eq == GBST_HEAT && !d.allow_unstable && h->a * h->ndim * h->S > 2.0 * (1.0 + 1e-12)) {
-        delete h;
-        return fail(GBST_EUNSTABLE, "heat step a*ndim*S = %g exceeds 2 (von Neumann limit)",
-                    h->a * d.ndim * h->S);
+    for (int i = 0; i < n; ++i) {
+        const gbst_desc &e = descs[i];
+        const double a = e.alpha * e.dt / (e.h * e.h);
+        if (e.eq == GBST_HEAT && !e.allow_unstable && a * h->ndim * h->S > 2.0 * (1.0 + 1e-12)) {
+            delete h;
+            return fail(GBST_EUNSTABLE, "heat step a*ndim*S = %g exceeds 2 (von Neumann limit)", a * d.ndim * h->S);
+        }
     }
 
-    auto bail = [&](gbst_status st) {
-        stencil_destroy(h);
-        return st;
+    auto bail = [&](gbst_status code) {
+        destroy_handle(h);
+        return code;
     };
 
     // subdomains: equal slicing, the first n mod D parts one larger
-    auto split = [](int64_t n, int parts, int i, int64_t *start) {
-        const int64_t base = n / parts, rem = n % parts;
+    auto split = [](int64_t len, int parts, int i, int64_t *start) {
+        const int64_t base = len / parts, rem = len % parts;
         *start = i * base + std::min<int64_t>(i, rem);
         return base + (i < rem ? 1 : 0);
     };
     const int px = px_of(d.storage);
-    for (int cz = 0; cz < decomp[2]; ++cz)
-        for (int cy = 0; cy < decomp[1]; ++cy)
-            for (int cx = 0; cx < decomp[0]; ++cx) {
-                Sub s{};
-                s.c[0] = cx;
-                s.c[1] = cy;
-                s.c[2] = cz;
-                int64_t n[3];
-                n[0] = split(dims[0], decomp[0], cx, &s.g0[0]);
-                n[1] = split(dims[1], decomp[1], cy, &s.g0[1]);
-                n[2] = split(dims[2], decomp[2], cz, &s.g0[2]);
-                s.lu = make_layout(d.ndim, n[0], n[1], n[2], R, h->es, 16 / h->es);
-                s.lk = make_layout(d.ndim, n[0], n[1], n[2], R, 4, px);
-                h->subs.push_back(s);
-                h->max_points = std::max(h->max_points, n[0] * n[1] * n[2]);
-            }
+    for (int mi = 0; mi < n; ++mi) {
+        const gbst_desc &e = descs[mi];
+        int64_t dims[3];
+        int dc[3];
+        validate_desc(e, dims, dc);
+        const int *dd = h->decomp;  // all ones for a batch
+        for (int cz = 0; cz < dd[2]; ++cz)
+            for (int cy = 0; cy < dd[1]; ++cy)
+                for (int cx = 0; cx < dd[0]; ++cx) {
+                    Sub s{};
+                    s.c[0] = cx;
+                    s.c[1] = cy;
+                    s.c[2] = cz;
+                    s.member = mi;
+                    s.dt = e.dt;
+                    s.h = e.h;
+                    s.alpha = e.alpha;
+                    for (int a = 0; a < 3; ++a)
+                        s.dense[a] = dims[a];
+                    int64_t nn[3];
+                    nn[0] = split(dims[0], dd[0], cx, &s.g0[0]);
+                    nn[1] = split(dims[1], dd[1], cy, &s.g0[1]);
+                    nn[2] = split(dims[2], dd[2], cz, &s.g0[2]);
+                    s.lu = make_layout(d.ndim, nn[0], nn[1], nn[2], R, h->es, 16 / h->es);
+                    s.lk = make_layout(d.ndim, nn[0], nn[1], nn[2], R, 4, px);
+                    h->subs.push_back(s);
+                    h->max_points = std::max(h->max_points, nn[0] * nn[1] * nn[2]);
+                }
+    }
     const size_t ns = h->subs.size();
     h->hgrids.assign(ns, GridDev{});
     for (size_t i = 0; i < ns; ++i) {
@@ -861,22 +928,25 @@ gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
         g.kpitch = s.lk.pitch;
         g.krows = s.lk.rows;
         g.korigin = s.lk.origin;
+        g.heat_a = static_cast<float>(s.alpha * s.dt / (s.h * s.h));
     }
     h->dgrids = static_cast<GridDev *>(dalloc(h, ns * sizeof(GridDev)));
     h->derr = static_cast<int *>(dalloc(h, 256));
-    h->red_blocks_per_grid = std::max(1, reduce_blocks_for(h->max_points) / static_cast<int>(ns));
+    h->dbarrier = static_cast<unsigned int *>(dalloc(h, 256));
+    h->red_blocks_per_grid = std::max(1, reduce_blocks_for(h->max_points) / static_cast<int>(std::min<size_t>(ns, 8)));
     h->dpartials = static_cast<double *>(dalloc(h, ns * h->red_blocks_per_grid * sizeof(double)));
     h->dred_out = static_cast<double *>(dalloc(h, 256));
     h->dred_grids = static_cast<ReduceGrid *>(dalloc(h, ns * sizeof(ReduceGrid)));
-    if (!h->dgrids || !h->derr || !h->dpartials || !h->dred_out || !h->dred_grids) {
+    if (!h->dgrids || !h->derr || !h->dbarrier || !h->dpartials || !h->dred_out || !h->dred_grids) {
         fail(GBST_ENOMEM, "metadata allocation");
         return bail(GBST_ENOMEM);
     }
-    if (cudaMemsetAsync(h->derr, 0, 256, h->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(h->derr, 0, 256, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->dbarrier, 0, 256, h->stream) != cudaSuccess) {
         fail(GBST_ECUDA, "memset of the error word");
         return bail(GBST_ECUDA);
     }
-    gbst_status st = build_copies(h);
+    st = build_copies(h);
     if (st != GBST_OK)
         return bail(st);
     TunedPlan tp{};
@@ -890,7 +960,7 @@ gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
     return GBST_OK;
 }
 
-gbst_status stencil_destroy(gbst_handle h)
+gbst_status destroy_handle(gbst_handle h)
 {
     if (!h)
         return GBST_OK;
@@ -909,13 +979,16 @@ gbst_status stencil_destroy(gbst_handle h)
     return GBST_OK;
 }
 
-static gbst_status transfer(gbst_handle h, int field, void *user, int dtype, int on_device, bool to_dev)
+// Copy one member's dense field in (to_dev) or out.
+gbst_status transfer(gbst_handle h, int member, int field, void *user, int dtype, int on_device, bool to_dev)
 {
     gbst_status st = check_handle(h);
     if (st != GBST_OK)
         return st;
     if (!user)
         return fail(GBST_EINVAL, "null buffer");
+    if (member < 0 || member >= h->members)
+        return fail(GBST_EINVAL, "grid index %d out of range [0, %d)", member, h->members);
     if (dtype != GBST_F32 && dtype != GBST_F64 && dtype != GBST_BF16)
         return fail(GBST_EINVAL, "dtype must be GBST_F32, GBST_F64 or GBST_BF16");
     if (field != GBST_U && field != GBST_U_PREV && field != GBST_VEL)
@@ -923,7 +996,12 @@ static gbst_status transfer(gbst_handle h, int field, void *user, int dtype, int
     if (h->d.eq == GBST_HEAT && field != GBST_U)
         return fail(GBST_EINVAL, "heat grids have only the field GBST_U");
     const size_t esz = dtype == GBST_F64 ? 8 : dtype == GBST_F32 ? 4 : 2;
-    const size_t n = static_cast<size_t>(h->dims[0] * h->dims[1] * h->dims[2]);
+    size_t n = 0;
+    for (const Sub &s : h->subs)
+        if (s.member == member) {
+            n = static_cast<size_t>(s.dense[0] * s.dense[1] * s.dense[2]);
+            break;
+        }
     void *dense = user;
     void *staging = nullptr;
     if (!on_device) {
@@ -941,6 +1019,8 @@ static gbst_status transfer(gbst_handle h, int field, void *user, int dtype, int
     }
     for (size_t i = 0; i < h->subs.size(); ++i) {
         const Sub &s = h->subs[i];
+        if (s.member != member)
+            continue;
         const GridDev &g = h->hgrids[i];
         XferArgs x{};
         const bool kap = field == GBST_VEL;
@@ -956,11 +1036,11 @@ static gbst_status transfer(gbst_handle h, int field, void *user, int dtype, int
         x.gx = s.g0[0];
         x.gy = s.g0[1];
         x.gz = s.g0[2];
-        x.gnx = h->dims[0];
-        x.gny = h->dims[1];
+        x.gnx = s.dense[0];
+        x.gny = s.dense[1];
         x.dense = dense;
         x.dense_dtype = dtype;
-        x.scale_sq = (kap && to_dev) ? (h->d.dt * h->d.dt) / (h->d.h * h->d.h) : 0.0;
+        x.scale_sq = (kap && to_dev) ? (s.dt * s.dt) / (s.h * s.h) : 0.0;
         cudaError_t e = to_dev ? launch_scatter(x, h->stream) : launch_gather(x, h->stream);
         if (e != cudaSuccess) {
             if (staging)
@@ -981,94 +1061,208 @@ static gbst_status transfer(gbst_handle h, int field, void *user, int dtype, int
     return st;
 }
 
-gbst_status stencil_reduce_f64(gbst_handle h, int kind, double *out);
-
-gbst_status stencil_set_field(gbst_handle h, int field, const void *src, int src_dtype, int src_on_device)
+// FP64 reduction over the subdomains of one member (member < 0: all of them).
+gbst_status reduce_member(gbst_handle h, int member, int kind, int field_is_kappa, double *out)
 {
-    gbst_status st = transfer(h, field, const_cast<void *>(src), src_dtype, src_on_device, true);
+    std::vector<ReduceGrid> rg;
+    int64_t maxp = 0;
+    for (size_t i = 0; i < h->subs.size(); ++i) {
+        const Sub &s = h->subs[i];
+        if (member >= 0 && s.member != member)
+            continue;
+        const GridDev &g = h->hgrids[i];
+        if (field_is_kappa)
+            rg.push_back(ReduceGrid{g.kappa, nullptr, nullptr, s.lk.pitch, s.lk.rows, s.lk.origin, 0, 0, 0, s.lk.nx,
+                                    s.lk.ny, s.lk.nz});
+        else
+            rg.push_back(ReduceGrid{g.buf[h->parity], g.buf[1 - h->parity], g.kappa, s.lu.pitch, s.lu.rows,
+                                    s.lu.origin, s.lk.pitch, s.lk.rows, s.lk.origin, s.lu.nx, s.lu.ny, s.lu.nz});
+        maxp = std::max(maxp, s.lu.nx * s.lu.ny * s.lu.nz);
+    }
+    const int ng = static_cast<int>(rg.size());
+    GBST_CUDA(cudaMemcpyAsync(h->dred_grids, rg.data(), rg.size() * sizeof(ReduceGrid), cudaMemcpyHostToDevice,
+                              h->stream));
+    const int nb = h->red_blocks_per_grid * ng;
+    GBST_CUDA(launch_reduce_partials(kind, field_is_kappa ? GBST_F32 : h->d.storage, h->ndim, h->R, h->w,
+                                     h->dred_grids, ng, maxp, h->dpartials, nb, h->stream));
+    GBST_CUDA(launch_reduce_final(kind, h->dpartials, nb, h->dred_out, h->stream));
+    double v = 0.0;
+    GBST_CUDA(cudaMemcpyAsync(&v, h->dred_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    gbst_status st = poll_device_error(h);
+    if (st != GBST_OK)
+        return st;
+    *out = v;
+    return GBST_OK;
+}
+
+gbst_status set_field_member(gbst_handle h, int member, int field, const void *src, int dtype, int on_device)
+{
+    gbst_status st = transfer(h, member, field, const_cast<void *>(src), dtype, on_device, true);
     if (st != GBST_OK || field != GBST_VEL)
         return st;
-    h->kappa_set = true;
     st = read_kappa_at_source(h);
     if (st != GBST_OK)
         return st;
     // stability of the leapfrog scheme: kappa_max * ndim * S <= 4
     double kmax = 0.0;
-    {
-        // max |kappa| through the FP64 reduction kernel (kappa stored as FP32)
-        std::vector<ReduceGrid> rg(h->subs.size());
-        for (size_t i = 0; i < h->subs.size(); ++i) {
-            const Sub &s = h->subs[i];
-            rg[i] = ReduceGrid{h->hgrids[i].kappa, nullptr, nullptr, s.lk.pitch, s.lk.rows, s.lk.origin,
-                               0, 0, 0, s.lk.nx, s.lk.ny, s.lk.nz};
-        }
-        GBST_CUDA(cudaMemcpyAsync(h->dred_grids, rg.data(), rg.size() * sizeof(ReduceGrid), cudaMemcpyHostToDevice,
-                                  h->stream));
-        const int nb = h->red_blocks_per_grid * static_cast<int>(h->subs.size());
-        GBST_CUDA(launch_reduce_partials(GBST_RED_MAXABS, GBST_F32, h->ndim, h->R, h->w, h->dred_grids,
-                                         static_cast<int>(h->subs.size()), h->max_points, h->dpartials, nb,
-                                         h->stream));
-        GBST_CUDA(launch_reduce_final(GBST_RED_MAXABS, h->dpartials, nb, h->dred_out, h->stream));
-        GBST_CUDA(cudaMemcpyAsync(&kmax, h->dred_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        GBST_CUDA(cudaStreamSynchronize(h->stream));
-    }
-    h->unstable = kmax * h->ndim * h->S > 4.0 * (1.0 + 1e-9);
-    if (h->unstable && !h->d.allow_unstable)
+    st = reduce_member(h, member, GBST_RED_MAXABS, 1, &kmax);
+    if (st != GBST_OK)
+        return st;
+    const bool unstable = kmax * h->ndim * h->S > 4.0 * (1.0 + 1e-9);
+    for (Sub &s : h->subs)
+        if (s.member == member)
+            s.unstable = unstable;
+    if (unstable && !h->d.allow_unstable)
         return fail(GBST_EUNSTABLE, "wave step: kappa_max*ndim*S = %g exceeds 4 (CFL limit)", kmax * h->ndim * h->S);
     return GBST_OK;
 }
 
-gbst_status stencil_get_field(gbst_handle h, int field, void *dst, int dst_dtype, int dst_on_device)
-{
-    return transfer(h, field, dst, dst_dtype, dst_on_device, false);
-}
-
-gbst_status stencil_set_source(gbst_handle h, const int64_t idx[3], double f0_hz, double t0_s, double amp)
+gbst_status set_source_member(gbst_handle h, int member, const int64_t idx[3], double f0_hz, double t0_s,
+                              double amp)
 {
     gbst_status st = check_handle(h);
     if (st != GBST_OK)
         return st;
     if (h->d.eq != GBST_WAVE)
         return fail(GBST_EINVAL, "sources are only defined for the wave equation");
-    for (GridDev &g : h->hgrids)
-        g.has_src = 0;
-    h->has_src = false;
-    h->src_sub = -1;
+    if (member < 0 || member >= h->members)
+        return fail(GBST_EINVAL, "grid index %d out of range", member);
+    for (size_t i = 0; i < h->subs.size(); ++i)
+        if (h->subs[i].member == member) {
+            h->subs[i].src_on = false;
+            h->hgrids[i].has_src = 0;
+        }
     if (f0_hz > 0.0) {
         if (!idx)
             return fail(GBST_EINVAL, "null source index");
-        const int64_t k = h->ndim == 3 ? idx[2] : 0;
-        const int64_t p[3] = {idx[0], idx[1], k};
-        for (int a = 0; a < 3; ++a)
-            if (p[a] < 0 || p[a] >= h->dims[a])
-                return fail(GBST_EINVAL, "source index outside the grid");
+        bool placed = false;
         for (size_t i = 0; i < h->subs.size(); ++i) {
-            const Sub &s = h->subs[i];
+            Sub &s = h->subs[i];
+            if (s.member != member)
+                continue;
+            const int64_t p[3] = {idx[0], idx[1], h->ndim == 3 ? idx[2] : 0};
             bool in = true;
-            for (int a = 0; a < 3; ++a)
-                in = in && p[a] >= s.g0[a] &&
-                     p[a] < s.g0[a] + (a == 0 ? s.lu.nx : a == 1 ? s.lu.ny : s.lu.nz);
-            if (in) {
-                h->src_sub = static_cast<int>(i);
-                for (int a = 0; a < 3; ++a)
-                    h->src_local[a] = p[a] - s.g0[a];
-                GridDev &g = h->hgrids[i];
-                g.has_src = 1;
-                g.src_x = static_cast<int>(h->src_local[0]);
-                g.src_y = static_cast<int>(h->src_local[1]);
-                g.src_z = static_cast<int>(h->src_local[2]);
+            for (int a = 0; a < 3; ++a) {
+                if (p[a] < 0 || p[a] >= s.dense[a])
+                    return fail(GBST_EINVAL, "source index outside the grid");
+                const int64_t n = a == 0 ? s.lu.nx : a == 1 ? s.lu.ny : s.lu.nz;
+                in = in && p[a] >= s.g0[a] && p[a] < s.g0[a] + n;
             }
+            if (!in)
+                continue;
+            s.src_on = true;
+            for (int a = 0; a < 3; ++a)
+                s.src_local[a] = p[a] - s.g0[a];
+            s.f0 = f0_hz;
+            s.t0 = t0_s;
+            s.amp = amp;
+            GridDev &g = h->hgrids[i];
+            g.has_src = 1;
+            g.src_x = static_cast<int>(s.src_local[0]);
+            g.src_y = static_cast<int>(s.src_local[1]);
+            g.src_z = static_cast<int>(s.src_local[2]);
+            placed = true;
         }
-        h->has_src = true;
-        h->f0 = f0_hz;
-        h->t0 = t0_s;
-        h->amp = amp;
+        if (!placed)
+            return fail(GBST_EINVAL, "source index outside the grid");
     }
     GBST_CUDA(cudaMemcpyAsync(h->dgrids, h->hgrids.data(), h->hgrids.size() * sizeof(GridDev),
                               cudaMemcpyHostToDevice, h->stream));
     st = read_kappa_at_source(h);
     destroy_graphs(h);
     return st;
+}
+
+}  // namespace
+
+// =========}  // namespace
+
+// =========================================================================
+extern "C" {
+
+int gbst_version(void) { return 10000; }
+
+const char *stencil_last_error(void) { return t_err.c_str(); }
+
+gbst_status stencil_fd_weights(int space_order, double *out)
+{
+    if (!out || space_order < 2 || space_order > 16 || space_order % 2)
+        return fail(GBST_EINVAL, "space_order must be even in [2, 16]");
+    central_weights(space_order / 2, out);
+    return GBST_OK;
+}
+
+gbst_status stencil_create(const gbst_desc *desc, gbst_handle *out)
+{
+    return create_handle(desc, 1, false, out);
+}
+
+gbst_status stencil_batch_create(const gbst_desc *descs, int n, gbst_handle *out)
+{
+    return create_handle(descs, n, true, out);
+}
+
+gbst_status stencil_batch_size(gbst_handle h, int *n)
+{
+    if (!h || !n)
+        return fail(GBST_EINVAL, "null argument");
+    *n = h->members;
+    return GBST_OK;
+}
+
+gbst_status stencil_destroy(gbst_handle h) { return destroy_handle(h); }
+
+gbst_status stencil_set_field(gbst_handle h, int field, const void *src, int src_dtype, int src_on_device)
+{
+    return set_field_member(h, 0, field, src, src_dtype, src_on_device);
+}
+
+gbst_status stencil_batch_set_field(gbst_handle h, int grid, int field, const void *src, int src_dtype,
+                                    int src_on_device)
+{
+    return set_field_member(h, grid, field, src, src_dtype, src_on_device);
+}
+
+gbst_status stencil_get_field(gbst_handle h, int field, void *dst, int dst_dtype, int dst_on_device)
+{
+    return transfer(h, 0, field, dst, dst_dtype, dst_on_device, false);
+}
+
+gbst_status stencil_batch_get_field(gbst_handle h, int grid, int field, void *dst, int dst_dtype, int dst_on_device)
+{
+    return transfer(h, grid, field, dst, dst_dtype, dst_on_device, false);
+}
+
+gbst_status stencil_set_source(gbst_handle h, const int64_t idx[3], double f0_hz, double t0_s, double amp)
+{
+    return set_source_member(h, 0, idx, f0_hz, t0_s, amp);
+}
+
+gbst_status stencil_batch_set_source(gbst_handle h, int grid, const int64_t idx[3], double f0_hz, double t0_s,
+                                     double amp)
+{
+    return set_source_member(h, grid, idx, f0_hz, t0_s, amp);
+}
+
+gbst_status stencil_set_persistent(gbst_handle h, int enable)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (enable && (!h->plan.stream || h->nboxes > 0))
+        return fail(GBST_ENOTSUP, "persistent runs need the streaming kernel and no halo exchanges");
+    h->persistent = enable != 0;
+    destroy_graphs(h);
+    return GBST_OK;
+}
+
+gbst_status stencil_debug_barrier_extra(gbst_handle h, unsigned int extra)
+{
+    if (!h)
+        return fail(GBST_EINVAL, "null handle");
+    h->barrier_extra = extra;
+    destroy_graphs(h);
+    return GBST_OK;
 }
 
 gbst_status stencil_run(gbst_handle h, int64_t nsteps)
@@ -1080,10 +1274,15 @@ gbst_status stencil_run(gbst_handle h, int64_t nsteps)
         return fail(GBST_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0)
         return GBST_OK;
-    if (h->unstable && !h->d.allow_unstable)
-        return fail(GBST_EUNSTABLE, "velocity model exceeds the stability limit");
+    if (nsteps > (int64_t(1) << 30))
+        return fail(GBST_EINVAL, "nsteps too large for one call");
+    for (const Sub &s : h->subs)
+        if (s.unstable && !h->d.allow_unstable)
+            return fail(GBST_EUNSTABLE, "velocity model exceeds the stability limit");
     const int64_t ns = static_cast<int64_t>(h->subs.size());
-    const bool src = h->d.eq == GBST_WAVE && h->has_src;
+    bool src = false;
+    for (const Sub &s : h->subs)
+        src = src || (h->d.eq == GBST_WAVE && s.src_on);
     if (src) {
         st = ensure_src_capacity(h, nsteps);
         if (st != GBST_OK)
@@ -1092,42 +1291,55 @@ gbst_status stencil_run(gbst_handle h, int64_t nsteps)
             GBST_CUDA(cudaEventSynchronize(h->src_ev));  // previous upload finished reading hsrc
         else
             GBST_CUDA(cudaEventCreateWithFlags(&h->src_ev, cudaEventDisableTiming));
-        const double scale = h->amp * h->kappa_src * h->d.h * h->d.h;
-        for (int64_t k = 0; k < nsteps; ++k)
-            for (int64_t i = 0; i < ns; ++i)
+        for (int64_t i = 0; i < ns; ++i) {
+            const Sub &s = h->subs[i];
+            const double scale = s.src_on ? s.amp * s.kappa_src * s.h * s.h : 0.0;
+            for (int64_t k = 0; k < nsteps; ++k)
                 h->hsrc[k * ns + i] =
-                    i == h->src_sub ? static_cast<float>(scale * ricker((h->step + k) * h->d.dt, h->f0, h->t0)) : 0.f;
+                    s.src_on ? static_cast<float>(scale * ricker((h->step + k) * s.dt, s.f0, s.t0)) : 0.f;
+        }
         GBST_CUDA(cudaMemcpyAsync(h->dsrc, h->hsrc, nsteps * ns * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         GBST_CUDA(cudaEventRecord(h->src_ev, h->stream));
     }
+    const bool persistent = h->persistent && h->plan.stream && h->nboxes == 0;
     if (h->profile) {
-        while (static_cast<int64_t>(h->prof_ev.size()) < 2 * nsteps) {
+        const int64_t need = persistent ? 2 : 2 * nsteps;
+        while (static_cast<int64_t>(h->prof_ev.size()) < need) {
             cudaEvent_t e;
             GBST_CUDA(cudaEventCreate(&e));
             h->prof_ev.push_back(e);
         }
-        h->prof_launches = nsteps;
+        h->prof_launches = persistent ? 1 : nsteps;
     }
+    auto enqueue_all = [&]() -> gbst_status {
+        if (persistent)
+            return enqueue_persistent(h, nsteps, h->parity, src ? h->dsrc : nullptr, h->profile);
+        int par = h->parity;
+        for (int64_t k = 0; k < nsteps; ++k) {
+            gbst_status s2 =
+                enqueue_step(h, par, src ? h->dsrc + k * ns : nullptr, h->profile ? static_cast<int>(k) : -1);
+            if (s2 != GBST_OK)
+                return s2;
+            par ^= 1;
+        }
+        return GBST_OK;
+    };
     const bool graph = h->d.use_graph && h->stream != nullptr;
     if (graph) {
-        const auto key = std::make_pair(nsteps, h->parity + (h->profile ? 2 : 0));
+        const auto key = std::make_pair(nsteps, h->parity + (h->profile ? 2 : 0) + (persistent ? 4 : 0));
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             GBST_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            int par = h->parity;
-            for (int64_t k = 0; k < nsteps; ++k) {
-                st = enqueue_step(h, par, src ? h->dsrc + k * ns : nullptr, h->profile ? static_cast<int>(k) : -1);
-                if (st != GBST_OK) {
-                    cudaGraph_t g;
-                    cudaStreamEndCapture(h->stream, &g);
-                    if (g)
-                        cudaGraphDestroy(g);
-                    return st;
-                }
-                par ^= 1;
-            }
+            st = enqueue_all();
             cudaGraph_t g = nullptr;
-            GBST_CUDA(cudaStreamEndCapture(h->stream, &g));
+            const cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+            if (st != GBST_OK) {
+                if (g)
+                    cudaGraphDestroy(g);
+                return st;
+            }
+            if (ec != cudaSuccess)
+                return fail(GBST_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
             cudaGraphExec_t ge = nullptr;
             cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
             cudaGraphDestroy(g);
@@ -1137,13 +1349,9 @@ gbst_status stencil_run(gbst_handle h, int64_t nsteps)
         }
         GBST_CUDA(cudaGraphLaunch(it->second, h->stream));
     } else {
-        int par = h->parity;
-        for (int64_t k = 0; k < nsteps; ++k) {
-            st = enqueue_step(h, par, src ? h->dsrc + k * ns : nullptr, h->profile ? static_cast<int>(k) : -1);
-            if (st != GBST_OK)
-                return st;
-            par ^= 1;
-        }
+        st = enqueue_all();
+        if (st != GBST_OK)
+            return st;
     }
     h->parity ^= static_cast<int>(nsteps & 1);
     h->step += nsteps;
@@ -1174,7 +1382,7 @@ gbst_status stencil_set_step(gbst_handle h, int64_t step)
     return GBST_OK;
 }
 
-gbst_status stencil_reduce_f64(gbst_handle h, int kind, double *out)
+static gbst_status reduce_api(gbst_handle h, int member, int kind, double *out)
 {
     gbst_status st = check_handle(h);
     if (st != GBST_OK)
@@ -1183,6 +1391,8 @@ gbst_status stencil_reduce_f64(gbst_handle h, int kind, double *out)
         return fail(GBST_EINVAL, "null out");
     if (kind < GBST_RED_SUM || kind > GBST_RED_ENERGY)
         return fail(GBST_EINVAL, "unknown reduction %d", kind);
+    if (member >= h->members)
+        return fail(GBST_EINVAL, "grid index %d out of range", member);
     if (kind == GBST_RED_ENERGY && h->d.eq != GBST_WAVE)
         return fail(GBST_EINVAL, "the energy reduction is defined for the wave equation only");
     if (kind == GBST_RED_ENERGY && h->nboxes > 0) {
@@ -1192,28 +1402,21 @@ gbst_status stencil_reduce_f64(gbst_handle h, int kind, double *out)
         if (e != cudaSuccess)
             return fail(GBST_ECUDA, "halo copies: %s", cudaGetErrorString(e));
     }
-    std::vector<ReduceGrid> rg(h->subs.size());
-    for (size_t i = 0; i < h->subs.size(); ++i) {
-        const Sub &s = h->subs[i];
-        const GridDev &g = h->hgrids[i];
-        rg[i] = ReduceGrid{g.buf[h->parity], g.buf[1 - h->parity], g.kappa, s.lu.pitch, s.lu.rows, s.lu.origin,
-                           s.lk.pitch, s.lk.rows, s.lk.origin, s.lu.nx, s.lu.ny, s.lu.nz};
-    }
-    GBST_CUDA(cudaMemcpyAsync(h->dred_grids, rg.data(), rg.size() * sizeof(ReduceGrid), cudaMemcpyHostToDevice,
-                              h->stream));
-    const int nb = h->red_blocks_per_grid * static_cast<int>(h->subs.size());
-    GBST_CUDA(launch_reduce_partials(kind, h->d.storage, h->ndim, h->R, h->w, h->dred_grids,
-                                     static_cast<int>(h->subs.size()), h->max_points, h->dpartials, nb, h->stream));
-    GBST_CUDA(launch_reduce_final(kind, h->dpartials, nb, h->dred_out, h->stream));
     double v = 0.0;
-    GBST_CUDA(cudaMemcpyAsync(&v, h->dred_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    st = poll_device_error(h);
+    st = reduce_member(h, member, kind, 0, &v);
     if (st != GBST_OK)
         return st;
     *out = v;
     if (!std::isfinite(v))
         return fail(GBST_EUNSTABLE, "reduction result is not finite");
     return GBST_OK;
+}
+
+gbst_status stencil_reduce_f64(gbst_handle h, int kind, double *out) { return reduce_api(h, -1, kind, out); }
+
+gbst_status stencil_batch_reduce_f64(gbst_handle h, int grid, int kind, double *out)
+{
+    return reduce_api(h, grid, kind, out);
 }
 
 gbst_status stencil_describe(gbst_handle h, char *buf, size_t len)

@@ -56,7 +56,8 @@ struct alignas(128) GridDev {
     int txt;               // threads along x per tile (tile width = txt * PX)
     int box_bytes;         // bytes of one TMA box (tile + halo)
     int src_x, src_y, src_z, has_src;  // source position (interior coordinates)
-    int pad_[2];
+    float heat_a;          // heat: alpha dt / h^2 of this grid
+    int pad_;
 };
 
 // A unit of sweep work: one tile of one grid over planes [z0, z1).
@@ -73,9 +74,12 @@ struct SweepArgs {
     int ndim;
     float wc;              // ndim * w_0
     float w[kMaxRadius + 1];  // w_1..w_r at w[1..r]
-    float a;               // heat: alpha dt / h^2
-    const float *srcval;   // wave: per-grid source value for this step (already scaled), or null
+    const float *srcval;   // wave: per-grid source values, [step][grid] (already scaled), or null
     int *err;              // device error word
+    int nsteps;            // steps in this launch (> 1: persistent launch with grid barriers)
+    int ngrids;            // grids (row length of srcval)
+    unsigned int *barrier; // grid-barrier counter (zeroed before a persistent launch)
+    unsigned int barrier_extra;  // test hook: extra arrivals a barrier waits for (0 in normal use)
 };
 
 // Host-side entry points of the kernel translation units.
@@ -98,7 +102,7 @@ inline int px_of(int storage) { return storage == GBST_BF16 ? 8 : 4; }
 size_t stream_smem_bytes(const StreamVariant &v, int max_box_bytes);
 // Launch the streaming (TMA, 2.5D) sweep.  Returns cudaSuccess or the launch error.
 cudaError_t launch_stream_sweep(const StreamVariant &v, const SweepArgs &a, int ctas, size_t smem,
-                                cudaStream_t s);
+                                cudaStream_t s, bool cooperative = false);
 // Max resident CTAs per SM of the variant at the given shared memory size (0 = unsupported).
 int stream_occupancy(const StreamVariant &v, size_t smem);
 bool stream_variant_exists(const StreamVariant &v);

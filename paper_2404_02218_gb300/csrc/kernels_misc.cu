@@ -55,7 +55,7 @@ __global__ void k_simple(const SweepArgs a)
         }
         float o;
         if (EQ == GBST_HEAT) {
-            o = fmaf(a.a, s, c);
+            o = fmaf(g.heat_a, s, c);
         } else {
             const float kap = g.kappa[g.korigin + z * g.kpitch * g.krows + y * g.kpitch + x];
             const float um = E::ld(out + idx);

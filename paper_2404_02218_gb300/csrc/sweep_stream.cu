@@ -98,7 +98,8 @@ int stream_occupancy(const StreamVariant &v, size_t smem)
     return n;
 }
 
-cudaError_t launch_stream_sweep(const StreamVariant &v, const SweepArgs &a, int ctas, size_t smem, cudaStream_t s)
+cudaError_t launch_stream_sweep(const StreamVariant &v, const SweepArgs &a, int ctas, size_t smem, cudaStream_t s,
+                                bool cooperative)
 {
     const Entry *e = find(v);
     if (!e)
@@ -106,8 +107,22 @@ cudaError_t launch_stream_sweep(const StreamVariant &v, const SweepArgs &a, int 
     const int rz = v.has_z ? v.R : 0;
     const int slots = rz + 1 + v.depth;
     const int slot_bytes = static_cast<int>((smem - 256) / slots);
-    e->fn<<<ctas, v.nthreads + 32, smem, s>>>(a, slot_bytes);
-    return cudaGetLastError();
+    if (!cooperative) {
+        e->fn<<<ctas, v.nthreads + 32, smem, s>>>(a, slot_bytes);
+        return cudaGetLastError();
+    }
+    // persistent launch: every CTA must be resident for the grid barrier
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(v.nthreads + 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, e->fn, a, slot_bytes);
 }
 
 }  // namespace gbst

@@ -204,6 +204,38 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
     return true;
 }
 
+// Grid-wide barrier of a persistent launch (all CTAs co-resident).  Thread 0
+// publishes the CTA's stores (fence, and a proxy fence because the next step
+// reads them through TMA), arrives on the counter and spins, bounded by
+// kWaitLimitNs; on expiry the CTA's abort flag and the error word are set.  A
+// CTA that has already aborted does not arrive, so the others time out too.
+__device__ __forceinline__ bool grid_barrier(unsigned int *counter, unsigned int target, volatile int *abort_flag,
+                                             int *err)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && !*abort_flag) {
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        atomicAdd(counter, 1u);
+        const unsigned long long t0 = global_ns();
+        while (true) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+            if (v >= target)
+                break;
+            if (global_ns() - t0 > kWaitLimitNs) {
+                *abort_flag = 1;
+                atomicExch(err, static_cast<int>(kDevTimeoutBarrier));
+                break;
+            }
+            __nanosleep(256);
+        }
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __syncthreads();
+    return *abort_flag == 0;
+}
+
 // Warp-specialised streaming sweep.  Warp NC is the TMA producer (one lane
 // issues a plane load per iteration into ring slot it % S, completing on
 // full[it % NB]); warps 0..NC-1 consume.  A consumer warp arrives on
@@ -235,8 +267,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NB);
     unsigned char *slots = smem + 256;
 
-    if (blockIdx.x >= a.nunits)
-        return;
+    // (a CTA without units still joins the grid barriers of a persistent launch)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -250,38 +281,29 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
     __syncthreads();
 
     // ------------------------------------------------------------ producer
-    if (warp == NC) {
-        if (lane != 0)
-            return;
-        int it = 0;
-        bool ok = true;
-        for (int ui = blockIdx.x; ok && ui < a.nunits; ui += gridDim.x) {
+    // One step's plane loads for this CTA's units; `it` counts iterations over
+    // the whole launch (all steps), like the consumers' ring position.
+    int it = 0;
+    auto produce = [&](int parity) -> bool {
+        // order the previous step's generic-proxy stores (made visible by the
+        // grid barrier) before this thread's async-proxy (TMA) reads
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
             const Unit u = a.units[ui];
             const GridDev &g = a.grids[u.grid];
             const int bx = (u.tile % g.tiles_x) * TX, by = (u.tile / g.tiles_x) * TY;
-            const CUtensorMap *map = &g.tmap[a.parity];
+            const CUtensorMap *map = &g.tmap[parity];
             const uint32_t bytes = static_cast<uint32_t>(g.box_bytes);
             const int L = (u.z1 - u.z0) + 2 * RZ;
             for (int l = 0; l < L; ++l, ++it) {
-                if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag)) {
-                    ok = false;
-                    break;
-                }
+                if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
+                    return false;
                 mbar_arrive_expect_tx(&full[it % NB], bytes);
                 tma_load_plane(slots + (it % S) * slot_bytes, map, &full[it % NB], bx, by, u.z0 + l);
             }
         }
-        if (!ok) {
-            atomicExch(a.err, kDevTimeoutTma);
-            // let the loads already issued land before the CTA can exit (short bound)
-            for (int k = it - NB < 0 ? 0 : it - NB; k < it; ++k) {
-                const unsigned long long t0 = global_ns();
-                while (!mbar_try_wait(&full[k % NB], (k / NB) & 1) && global_ns() - t0 < 50000000ull) {
-                }
-            }
-        }
-        return;
-    }
+        return true;
+    };
 
     // ----------------------------------------------------------- consumers
     const int tid = threadIdx.x;
@@ -299,215 +321,246 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
         }
     };
     const float2 wc2 = make_float2(a.wc, a.wc);
-    const float2 a2 = make_float2(a.a, a.a);
     float2 w2[R + 1];
 #pragma unroll
     for (int m = 0; m <= R; ++m)
         w2[m] = make_float2(a.w[m], a.w[m]);
 
-    for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
-        const Unit u = a.units[ui];
-        // Copy the grid's descriptor into registers: the output stores below could
-        // alias it, which would otherwise force a reload after every store.
-        const GridDev *gp = a.grids + u.grid;
-        const int tiles_x = gp->tiles_x;
-        const int64_t nx = gp->nx, ny = gp->ny;
-        const int64_t pitch = gp->pitch, rows = gp->rows, origin = gp->origin;
-        const int64_t kpitch = gp->kpitch, krows = gp->krows, korigin = gp->korigin;
-        const float *__restrict__ kappa = gp->kappa;
-        unsigned char *__restrict__ outbase = static_cast<unsigned char *>(gp->buf[1 - a.parity]);
-        const bool src_unit = (EQ == GBST_WAVE) && gp->has_src;
-        const int src_x = gp->src_x, src_y = gp->src_y, src_z = gp->src_z;
-        const float srcv = (EQ == GBST_WAVE && a.srcval) ? a.srcval[u.grid] : 0.0f;
-        const int tx = tid % TXT, ty = tid / TXT;
-        const int x0 = (u.tile % tiles_x) * TX + tx * PX;
-        const int y0 = (u.tile / tiles_x) * TY + ty * PY;
-        constexpr int row_bytes = ROW_BYTES;
-        const int own_off = (R + ty * PY) * row_bytes + (G + tx * PX) * ES;
-        const bool xfull = x0 + PX <= nx;
-        bool row_ok[PY];
-#pragma unroll
-        for (int r_ = 0; r_ < PY; ++r_)
-            row_ok[r_] = y0 + r_ < ny && x0 < nx;
-        // running pointers to the thread's first row of the current output plane
-        const int64_t plane_elems = rows * pitch, kplane = krows * kpitch;
-        unsigned char *optr = outbase + (origin + (static_cast<int64_t>(u.z0) * rows + y0) * pitch + x0) * ES;
-        const float *kptr = kappa + korigin + (static_cast<int64_t>(u.z0) * krows + y0) * kpitch + x0;
-        const int64_t row_stride = pitch * ES;
+    auto consume = [&](int parity, const float *srcval) -> bool {
+        for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
+            const Unit u = a.units[ui];
+            // Copy the grid's descriptor into registers: the output stores below could
+            // alias it, which would otherwise force a reload after every store.
+            const GridDev *gp = a.grids + u.grid;
+            const int tiles_x = gp->tiles_x;
+            const int64_t nx = gp->nx, ny = gp->ny;
+            const int64_t pitch = gp->pitch, rows = gp->rows, origin = gp->origin;
+            const int64_t kpitch = gp->kpitch, krows = gp->krows, korigin = gp->korigin;
+            const float *__restrict__ kappa = gp->kappa;
+            unsigned char *__restrict__ outbase = static_cast<unsigned char *>(gp->buf[1 - parity]);
+            const bool src_unit = (EQ == GBST_WAVE) && gp->has_src;
+            const int src_x = gp->src_x, src_y = gp->src_y, src_z = gp->src_z;
+            const float srcv = (EQ == GBST_WAVE && srcval) ? srcval[u.grid] : 0.0f;
+            const float2 a2 = make_float2(gp->heat_a, gp->heat_a);
+            const int tx = tid % TXT, ty = tid / TXT;
+            const int x0 = (u.tile % tiles_x) * TX + tx * PX;
+            const int y0 = (u.tile / tiles_x) * TY + ty * PY;
+            constexpr int row_bytes = ROW_BYTES;
+            const int own_off = (R + ty * PY) * row_bytes + (G + tx * PX) * ES;
+            const bool xfull = x0 + PX <= nx;
+            bool row_ok[PY];
+    #pragma unroll
+            for (int r_ = 0; r_ < PY; ++r_)
+                row_ok[r_] = y0 + r_ < ny && x0 < nx;
+            // running pointers to the thread's first row of the current output plane
+            const int64_t plane_elems = rows * pitch, kplane = krows * kpitch;
+            unsigned char *optr = outbase + (origin + (static_cast<int64_t>(u.z0) * rows + y0) * pitch + x0) * ES;
+            const float *kptr = kappa + korigin + (static_cast<int64_t>(u.z0) * krows + y0) * kpitch + x0;
+            const int64_t row_stride = pitch * ES;
 
-        // prologue: the 2*rz planes below the first output plane fill the queue
-#pragma unroll
-        for (int k = 0; k < 2 * RZ; ++k) {
-            if (!wait_or_abort(&full[bar_i], par, reinterpret_cast<volatile int *>(abort_flag)))
-                return;
-            const unsigned char *nb = slots + slot_n * slot_bytes + own_off;
-#pragma unroll
-            for (int r_ = 0; r_ < PY; ++r_) {
-                const uint4 v = lds128(nb + r_ * row_bytes);
-#pragma unroll
-                for (int pp = 0; pp < PP; ++pp)
-                    q[k][r_][pp] = St::pair(v, pp);
-            }
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(&empty[bar_i]);
-            advance();
-        }
-
-        const int nout = u.z1 - u.z0;
-        for (int c0 = 0; c0 < nout; c0 += QN) {
-#pragma unroll
-            for (int k = 0; k < QN; ++k) {
-                const int c = c0 + k;
-                if (c < nout) {
-                    const int qn = (k + 2 * RZ) % QN;  // slot of the newest plane (constant after unrolling)
-                    const int qc = (k + RZ) % QN;      // slot of the centre plane
-                    const int zc = u.z0 + c;
-
-                    // Wave: kappa and u- of the centre plane, issued before waiting on the TMA.
-                    float kap[PY][PX], um[PY][PX];
-                    if (EQ == GBST_WAVE) {
-#pragma unroll
-                        for (int r_ = 0; r_ < PY; ++r_) {
-                            const float *kp = kptr + r_ * kpitch;
-                            const unsigned char *up = optr + r_ * row_stride;
-#pragma unroll
-                            for (int v = 0; v < PX / 4; ++v) {
-                                const float4 kv = row_ok[r_] ? ldg_f4_nc(kp + 4 * v) : make_float4(0, 0, 0, 0);
-                                kap[r_][4 * v + 0] = kv.x;
-                                kap[r_][4 * v + 1] = kv.y;
-                                kap[r_][4 * v + 2] = kv.z;
-                                kap[r_][4 * v + 3] = kv.w;
-                            }
-                            const uint4 uv =
-                                row_ok[r_] ? __ldcs(reinterpret_cast<const uint4 *>(up)) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-                            for (int i = 0; i < PX; ++i)
-                                um[r_][i] = St::get(uv, i);
-                        }
-                    }
-
-                    if (!wait_or_abort(&full[bar_i], par, reinterpret_cast<volatile int *>(abort_flag)))
-                        return;
-                    {
-                        const unsigned char *nb = slots + slot_n * slot_bytes + own_off;
-#pragma unroll
-                        for (int r_ = 0; r_ < PY; ++r_) {
-                            const uint4 v = lds128(nb + r_ * row_bytes);
-#pragma unroll
-                            for (int pp = 0; pp < PP; ++pp)
-                                q[qn][r_][pp] = St::pair(v, pp);
-                        }
-                    }
-
-                    const int slot_c = slot_n >= RZ ? slot_n - RZ : slot_n - RZ + S;
-                    const unsigned char *cb = slots + slot_c * slot_bytes + own_off;
-                    uint4 ylo[R], yhi[R], xl[PY], xr[PY];
-#pragma unroll
-                    for (int m = 1; m <= R; ++m) {
-                        ylo[m - 1] = lds128(cb - m * row_bytes);
-                        yhi[m - 1] = lds128(cb + (PY - 1 + m) * row_bytes);
-                    }
-#pragma unroll
-                    for (int r_ = 0; r_ < PY; ++r_) {
-                        xl[r_] = load_left<ST, R>(cb + r_ * row_bytes - 16);
-                        xr[r_] = load_right<ST, R>(cb + r_ * row_bytes + 16);
-                    }
-
-                    // element e in [-G, PX+G) of centre row r_: own points or the x-halo chunks
-                    auto xel = [&](int r_, int e) -> float {
-                        if (e < 0)
-                            return St::get(xl[r_], PX + e);
-                        if (e >= PX)
-                            return St::get(xr[r_], e - PX);
-                        return (e & 1) ? q[qc][r_][e >> 1].y : q[qc][r_][e >> 1].x;
-                    };
-                    // pair pp of centre-plane row `row` (relative to the thread's first row)
-                    auto yrow = [&](int row, int pp) -> float2 {
-                        if (row < 0)
-                            return St::pair(ylo[-row - 1], pp);
-                        if (row >= PY)
-                            return St::pair(yhi[row - PY], pp);
-                        return q[qc][row][pp];
-                    };
-                    // Per point: t_m = ((x-m + x+m) + (y-m + y+m)) + (z-m + z+m) for every m
-                    // (independent of each other), then s = w0*ndim*c, s = fma(w_m, t_m, s)
-                    // for m = 1..r.  The dependent chain is r + 3 deep instead of 3r + 1.
-                    float2 sv[PY][PP];
-#pragma unroll
-                    for (int r_ = 0; r_ < PY; ++r_)
-#pragma unroll
-                        for (int pp = 0; pp < PP; ++pp)
-                            sv[r_][pp] = __fmul2_rn(wc2, q[qc][r_][pp]);
-#pragma unroll
-                    for (int m = 1; m <= R; ++m) {
-#pragma unroll
-                        for (int r_ = 0; r_ < PY; ++r_) {
-#pragma unroll
-                            for (int pp = 0; pp < PP; ++pp) {
-                                const int e = 2 * pp;
-                                const float2 xm = make_float2(xel(r_, e - m), xel(r_, e + 1 - m));
-                                const float2 xp = make_float2(xel(r_, e + m), xel(r_, e + 1 + m));
-                                float2 t = __fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
-                                if (HAS_Z)
-                                    t = __fadd2_rn(t, __fadd2_rn(q[(qc - m + 2 * QN) % QN][r_][pp], q[(qc + m) % QN][r_][pp]));
-                                sv[r_][pp] = __ffma2_rn(w2[m], t, sv[r_][pp]);
-                            }
-                        }
-                    }
-                    float o[PY][PX];
-#pragma unroll
-                    for (int r_ = 0; r_ < PY; ++r_) {
-#pragma unroll
-                        for (int pp = 0; pp < PP; ++pp) {
-                            const float2 cv = q[qc][r_][pp];
-                            float2 ov;
-                            if (EQ == GBST_HEAT) {
-                                ov = __ffma2_rn(a2, sv[r_][pp], cv);
-                            } else {
-                                const float2 k2 = make_float2(kap[r_][2 * pp], kap[r_][2 * pp + 1]);
-                                const float2 t2 = __fadd2_rn(__fadd2_rn(cv, cv),
-                                                             make_float2(-um[r_][2 * pp], -um[r_][2 * pp + 1]));
-                                ov = __ffma2_rn(k2, sv[r_][pp], t2);
-                            }
-                            o[r_][2 * pp] = ov.x;
-                            o[r_][2 * pp + 1] = ov.y;
-                        }
-                    }
-                    // all shared-memory reads of this iteration are done: release the planes
-                    __syncwarp();
-                    if (lane == 0)
-                        mbar_arrive(&empty[bar_i]);
-                    advance();
-
-                    if (src_unit && zc == src_z) {
-                        const int sr = src_y - y0, si = src_x - x0;
-                        if (sr >= 0 && sr < PY && si >= 0 && si < PX) {
-#pragma unroll
-                            for (int r_ = 0; r_ < PY; ++r_)
-#pragma unroll
-                                for (int i = 0; i < PX; ++i)
-                                    if (r_ == sr && i == si)
-                                        o[r_][i] += srcv;
-                        }
-                    }
-#pragma unroll
-                    for (int r_ = 0; r_ < PY; ++r_) {
-                        if (row_ok[r_]) {
-                            unsigned char *op = optr + r_ * row_stride;
-                            if (xfull) {
-                                *reinterpret_cast<uint4 *>(op) = St::pack(o[r_]);
-                            } else {
-#pragma unroll
-                                for (int i = 0; i < PX; ++i)
-                                    if (x0 + i < nx)
-                                        St::store1(op + i * ES, o[r_][i]);
-                            }
-                        }
-                    }
-                    optr += plane_elems * ES;
-                    kptr += kplane;
+            // prologue: the 2*rz planes below the first output plane fill the queue
+    #pragma unroll
+            for (int k = 0; k < 2 * RZ; ++k) {
+                if (!wait_or_abort(&full[bar_i], par, abort_flag))
+                    return false;
+                const unsigned char *nb = slots + slot_n * slot_bytes + own_off;
+    #pragma unroll
+                for (int r_ = 0; r_ < PY; ++r_) {
+                    const uint4 v = lds128(nb + r_ * row_bytes);
+    #pragma unroll
+                    for (int pp = 0; pp < PP; ++pp)
+                        q[k][r_][pp] = St::pair(v, pp);
                 }
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&empty[bar_i]);
+                advance();
+            }
+
+            const int nout = u.z1 - u.z0;
+            for (int c0 = 0; c0 < nout; c0 += QN) {
+    #pragma unroll
+                for (int k = 0; k < QN; ++k) {
+                    const int c = c0 + k;
+                    if (c < nout) {
+                        const int qn = (k + 2 * RZ) % QN;  // slot of the newest plane (constant after unrolling)
+                        const int qc = (k + RZ) % QN;      // slot of the centre plane
+                        const int zc = u.z0 + c;
+
+                        // Wave: kappa and u- of the centre plane, issued before waiting on the TMA.
+                        float kap[PY][PX], um[PY][PX];
+                        if (EQ == GBST_WAVE) {
+    #pragma unroll
+                            for (int r_ = 0; r_ < PY; ++r_) {
+                                const float *kp = kptr + r_ * kpitch;
+                                const unsigned char *up = optr + r_ * row_stride;
+    #pragma unroll
+                                for (int v = 0; v < PX / 4; ++v) {
+                                    const float4 kv = row_ok[r_] ? ldg_f4_nc(kp + 4 * v) : make_float4(0, 0, 0, 0);
+                                    kap[r_][4 * v + 0] = kv.x;
+                                    kap[r_][4 * v + 1] = kv.y;
+                                    kap[r_][4 * v + 2] = kv.z;
+                                    kap[r_][4 * v + 3] = kv.w;
+                                }
+                                const uint4 uv =
+                                    row_ok[r_] ? __ldcs(reinterpret_cast<const uint4 *>(up)) : make_uint4(0, 0, 0, 0);
+    #pragma unroll
+                                for (int i = 0; i < PX; ++i)
+                                    um[r_][i] = St::get(uv, i);
+                            }
+                        }
+
+                        if (!wait_or_abort(&full[bar_i], par, abort_flag))
+                            return false;
+                        {
+                            const unsigned char *nb = slots + slot_n * slot_bytes + own_off;
+    #pragma unroll
+                            for (int r_ = 0; r_ < PY; ++r_) {
+                                const uint4 v = lds128(nb + r_ * row_bytes);
+    #pragma unroll
+                                for (int pp = 0; pp < PP; ++pp)
+                                    q[qn][r_][pp] = St::pair(v, pp);
+                            }
+                        }
+
+                        const int slot_c = slot_n >= RZ ? slot_n - RZ : slot_n - RZ + S;
+                        const unsigned char *cb = slots + slot_c * slot_bytes + own_off;
+                        uint4 ylo[R], yhi[R], xl[PY], xr[PY];
+    #pragma unroll
+                        for (int m = 1; m <= R; ++m) {
+                            ylo[m - 1] = lds128(cb - m * row_bytes);
+                            yhi[m - 1] = lds128(cb + (PY - 1 + m) * row_bytes);
+                        }
+    #pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_) {
+                            xl[r_] = load_left<ST, R>(cb + r_ * row_bytes - 16);
+                            xr[r_] = load_right<ST, R>(cb + r_ * row_bytes + 16);
+                        }
+
+                        // element e in [-G, PX+G) of centre row r_: own points or the x-halo chunks
+                        auto xel = [&](int r_, int e) -> float {
+                            if (e < 0)
+                                return St::get(xl[r_], PX + e);
+                            if (e >= PX)
+                                return St::get(xr[r_], e - PX);
+                            return (e & 1) ? q[qc][r_][e >> 1].y : q[qc][r_][e >> 1].x;
+                        };
+                        // pair pp of centre-plane row `row` (relative to the thread's first row)
+                        auto yrow = [&](int row, int pp) -> float2 {
+                            if (row < 0)
+                                return St::pair(ylo[-row - 1], pp);
+                            if (row >= PY)
+                                return St::pair(yhi[row - PY], pp);
+                            return q[qc][row][pp];
+                        };
+                        // Per point: t_m = ((x-m + x+m) + (y-m + y+m)) + (z-m + z+m) for every m
+                        // (independent of each other), then s = w0*ndim*c, s = fma(w_m, t_m, s)
+                        // for m = 1..r.  The dependent chain is r + 3 deep instead of 3r + 1.
+                        float2 sv[PY][PP];
+    #pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_)
+    #pragma unroll
+                            for (int pp = 0; pp < PP; ++pp)
+                                sv[r_][pp] = __fmul2_rn(wc2, q[qc][r_][pp]);
+    #pragma unroll
+                        for (int m = 1; m <= R; ++m) {
+    #pragma unroll
+                            for (int r_ = 0; r_ < PY; ++r_) {
+    #pragma unroll
+                                for (int pp = 0; pp < PP; ++pp) {
+                                    const int e = 2 * pp;
+                                    const float2 xm = make_float2(xel(r_, e - m), xel(r_, e + 1 - m));
+                                    const float2 xp = make_float2(xel(r_, e + m), xel(r_, e + 1 + m));
+                                    float2 t = __fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
+                                    if (HAS_Z)
+                                        t = __fadd2_rn(t, __fadd2_rn(q[(qc - m + 2 * QN) % QN][r_][pp], q[(qc + m) % QN][r_][pp]));
+                                    sv[r_][pp] = __ffma2_rn(w2[m], t, sv[r_][pp]);
+                                }
+                            }
+                        }
+                        float o[PY][PX];
+    #pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_) {
+    #pragma unroll
+                            for (int pp = 0; pp < PP; ++pp) {
+                                const float2 cv = q[qc][r_][pp];
+                                float2 ov;
+                                if (EQ == GBST_HEAT) {
+                                    ov = __ffma2_rn(a2, sv[r_][pp], cv);
+                                } else {
+                                    const float2 k2 = make_float2(kap[r_][2 * pp], kap[r_][2 * pp + 1]);
+                                    const float2 t2 = __fadd2_rn(__fadd2_rn(cv, cv),
+                                                                 make_float2(-um[r_][2 * pp], -um[r_][2 * pp + 1]));
+                                    ov = __ffma2_rn(k2, sv[r_][pp], t2);
+                                }
+                                o[r_][2 * pp] = ov.x;
+                                o[r_][2 * pp + 1] = ov.y;
+                            }
+                        }
+                        // all shared-memory reads of this iteration are done: release the planes
+                        __syncwarp();
+                        if (lane == 0)
+                            mbar_arrive(&empty[bar_i]);
+                        advance();
+
+                        if (src_unit && zc == src_z) {
+                            const int sr = src_y - y0, si = src_x - x0;
+                            if (sr >= 0 && sr < PY && si >= 0 && si < PX) {
+    #pragma unroll
+                                for (int r_ = 0; r_ < PY; ++r_)
+    #pragma unroll
+                                    for (int i = 0; i < PX; ++i)
+                                        if (r_ == sr && i == si)
+                                            o[r_][i] += srcv;
+                            }
+                        }
+    #pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_) {
+                            if (row_ok[r_]) {
+                                unsigned char *op = optr + r_ * row_stride;
+                                if (xfull) {
+                                    *reinterpret_cast<uint4 *>(op) = St::pack(o[r_]);
+                                } else {
+    #pragma unroll
+                                    for (int i = 0; i < PX; ++i)
+                                        if (x0 + i < nx)
+                                            St::store1(op + i * ES, o[r_][i]);
+                                }
+                            }
+                        }
+                        optr += plane_elems * ES;
+                        kptr += kplane;
+                    }
+                }
+            }
+        }
+        return true;
+    };
+
+    // --------------------------------------------------------------- steps
+    // nsteps == 1: one sweep.  nsteps > 1 (persistent launch, all CTAs
+    // co-resident): a grid-wide barrier separates the steps, the parity flips.
+    bool ok = true;
+    for (int step = 0; step < a.nsteps; ++step) {
+        const int parity = a.parity ^ (step & 1);
+        const float *srcval = a.srcval ? a.srcval + static_cast<int64_t>(step) * a.ngrids : nullptr;
+        if (warp == NC) {
+            if (lane == 0 && ok)
+                ok = produce(parity);
+        } else if (ok) {
+            ok = consume(parity, srcval);
+        }
+        if (step + 1 < a.nsteps &&
+            !grid_barrier(a.barrier, static_cast<unsigned int>(step + 1) * gridDim.x + a.barrier_extra, abort_flag,
+                          a.err))
+            break;
+    }
+    if (warp == NC && lane == 0 && *abort_flag) {
+        atomicCAS(a.err, 0, static_cast<int>(kDevTimeoutTma));
+        // let the loads already issued land before the CTA can exit (short bound)
+        for (int k = it - NB < 0 ? 0 : it - NB; k < it; ++k) {
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try_wait(&full[k % NB], (k / NB) & 1) && global_ns() - t0 < 50000000ull) {
             }
         }
     }

@@ -169,8 +169,125 @@ class Grid:
     def set_profile(self, on: bool):
         N.stencil_set_profile(self.h, on)
 
+    def set_persistent(self, on: bool):
+        N.stencil_set_persistent(self.h, on)
+
     def last_kernel_time(self):
         return N.stencil_last_kernel_time(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.stencil_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent grids advanced together (see ``stencil_batch_create``).
+
+    ``members`` is a list of dicts with keys ``dims`` and optionally ``h``,
+    ``dt``, ``alpha``; the remaining settings are shared.
+    """
+
+    def __init__(self, ndim: int, members, space_order: int, eq: str = "wave", *, storage: str = "f32",
+                 kernel: str = "auto", tile: int = 0, use_graph: bool = True, stream=None,
+                 torch_allocator: bool = True, allow_unstable: bool = False):
+        import torch
+        self._torch = torch
+        self.ndim = ndim
+        dev = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self._alloc = TorchAllocator(dev) if torch_allocator else None
+        self.dims = []
+        descs = []
+        for m in members:
+            d = N.gbst_desc()
+            d.ndim = ndim
+            dims = tuple(int(x) for x in m["dims"])[:ndim]
+            self.dims.append(dims)
+            full = list(dims) + [1] * (3 - ndim)
+            for i in range(3):
+                d.dims[i] = full[i]
+                d.decomp[i] = 1
+            d.space_order = space_order
+            d.eq = _EQ[eq]
+            d.bc = N.GBST_BC_ZERO
+            d.storage = _ST[storage]
+            d.h = float(m.get("h", 1.0))
+            d.dt = float(m.get("dt", 1.0))
+            d.alpha = float(m.get("alpha", 1.0))
+            d.allow_unstable = int(allow_unstable)
+            d.kernel = _KER[kernel]
+            d.tile = int(tile)
+            d.use_graph = int(use_graph)
+            d.stream = ctypes.c_void_p(self.stream.cuda_stream)
+            d.allocator = ctypes.pointer(self._alloc.struct) if self._alloc else None
+            descs.append(d)
+        self._descs = descs
+        self.h = N.stencil_batch_create(descs)
+
+    def __len__(self):
+        return len(self.dims)
+
+    def shape(self, i: int):
+        return tuple(reversed(self.dims[i]))
+
+    def set_field(self, i: int, field: str, data):
+        f = _FIELD[field]
+        if isinstance(data, np.ndarray):
+            a = np.ascontiguousarray(data)
+            assert a.shape == self.shape(i), (a.shape, self.shape(i))
+            N.stencil_batch_set_field(self.h, i, f, a.ctypes.data, _np_dtype_code(a.dtype), False)
+        else:
+            t = data.contiguous()
+            if t.is_cuda:
+                self.stream.wait_stream(self._torch.cuda.current_stream())
+            N.stencil_batch_set_field(self.h, i, f, t.data_ptr(), _torch_dtype_code(t), t.is_cuda)
+
+    def get_field(self, i: int, field: str = "u", dtype=np.float64):
+        out = np.empty(self.shape(i), dtype=dtype)
+        N.stencil_batch_get_field(self.h, i, _FIELD[field], out.ctypes.data, _np_dtype_code(out.dtype), False)
+        return out
+
+    def set_source(self, i: int, idx, f0: float, t0: float, amp: float = 1.0):
+        N.stencil_batch_set_source(self.h, i, idx, f0, t0, amp)
+
+    def run(self, nsteps: int):
+        N.stencil_run(self.h, nsteps)
+
+    def sync(self):
+        N.stencil_sync(self.h)
+
+    def reduce(self, kind: str, grid: int = -1) -> float:
+        return N.stencil_batch_reduce_f64(self.h, grid, _RED[kind])
+
+    def set_persistent(self, on: bool):
+        N.stencil_set_persistent(self.h, on)
+
+    def set_plan(self, variant: int = -1, txt: int = 0, zchunks: int = 0, ctas: int = 0):
+        N.stencil_set_plan(self.h, variant, txt, zchunks, ctas)
+
+    def tune(self, reps: int = 5) -> dict:
+        import json
+        return json.loads(N.stencil_tune(self.h, reps))
+
+    def describe(self) -> str:
+        return N.stencil_describe(self.h)
+
+    def set_profile(self, on: bool):
+        N.stencil_set_profile(self.h, on)
+
+    def last_kernel_time(self):
+        return N.stencil_last_kernel_time(self.h)
+
+    @property
+    def step(self) -> int:
+        return N.stencil_get_step(self.h)
 
     def close(self):
         if getattr(self, "h", None):

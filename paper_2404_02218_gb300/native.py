@@ -102,6 +102,14 @@ def lib() -> ctypes.CDLL:
                 "stencil_variant_count": ([], i32),
                 "stencil_variant_info": ([i32, ctypes.c_char_p, ctypes.c_size_t], i32),
                 "gbst_reduce_dense_f64_noalloc": ([vp, i32, i64, i32, vp, vp], i32),
+                "stencil_batch_create": ([ctypes.POINTER(gbst_desc), i32, ctypes.POINTER(H)], i32),
+                "stencil_batch_size": ([H, ctypes.POINTER(i32)], i32),
+                "stencil_batch_set_field": ([H, i32, i32, vp, i32, i32], i32),
+                "stencil_batch_get_field": ([H, i32, i32, vp, i32, i32], i32),
+                "stencil_batch_set_source": ([H, i32, ctypes.POINTER(i64), dbl, dbl, dbl], i32),
+                "stencil_batch_reduce_f64": ([H, i32, i32, ctypes.POINTER(dbl)], i32),
+                "stencil_set_persistent": ([H, i32], i32),
+                "stencil_debug_barrier_extra": ([H, ctypes.c_uint], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -221,3 +229,46 @@ def gbst_reduce_dense_f64_noalloc(x_ptr: int, dtype: int, n: int, kind: int, out
     _check(lib().gbst_reduce_dense_f64_noalloc(ctypes.c_void_p(x_ptr), dtype, int(n), kind,
                                                ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)),
            "gbst_reduce_dense_f64_noalloc")
+
+
+def stencil_batch_create(descs) -> ctypes.c_void_p:
+    arr = (gbst_desc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    _check(lib().stencil_batch_create(arr, len(descs), ctypes.byref(h)), "stencil_batch_create")
+    return h
+
+
+def stencil_batch_size(h) -> int:
+    n = ctypes.c_int()
+    _check(lib().stencil_batch_size(h, ctypes.byref(n)), "stencil_batch_size")
+    return n.value
+
+
+def stencil_batch_set_field(h, grid: int, field: int, ptr: int, dtype: int, on_device: bool):
+    _check(lib().stencil_batch_set_field(h, grid, field, ctypes.c_void_p(ptr), dtype, int(on_device)),
+           "stencil_batch_set_field")
+
+
+def stencil_batch_get_field(h, grid: int, field: int, ptr: int, dtype: int, on_device: bool):
+    _check(lib().stencil_batch_get_field(h, grid, field, ctypes.c_void_p(ptr), dtype, int(on_device)),
+           "stencil_batch_get_field")
+
+
+def stencil_batch_set_source(h, grid: int, idx, f0: float, t0: float, amp: float):
+    arr = (ctypes.c_int64 * 3)(*(list(idx) + [0] * (3 - len(idx))))
+    _check(lib().stencil_batch_set_source(h, grid, arr, float(f0), float(t0), float(amp)),
+           "stencil_batch_set_source")
+
+
+def stencil_batch_reduce_f64(h, grid: int, kind: int) -> float:
+    v = ctypes.c_double()
+    _check(lib().stencil_batch_reduce_f64(h, grid, kind, ctypes.byref(v)), "stencil_batch_reduce_f64")
+    return v.value
+
+
+def stencil_set_persistent(h, enable: bool):
+    _check(lib().stencil_set_persistent(h, int(enable)), "stencil_set_persistent")
+
+
+def stencil_debug_barrier_extra(h, extra: int):
+    _check(lib().stencil_debug_barrier_extra(h, int(extra)), "stencil_debug_barrier_extra")
