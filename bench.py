@@ -24,6 +24,8 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+
+import numpy as np
 import json
 import os
 import statistics
@@ -55,6 +57,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the secondary measurements (decomposition, wave FP32/BF16, batch)")
     p.add_argument("--n", type=int, default=1024, help="grid edge (profiling runs use a smaller cube)")
     p.add_argument("--sos", default="2,4,8", help="space orders to run (profiling runs use one)")
     p.add_argument("--tune", default="on", choices=["on", "cache", "off"],
@@ -172,6 +176,116 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
     return 0
 
+
+
+# ------------------------------------------------------- secondary lines ---
+def timed_runs(torch, stream, fn, reps=1):
+    """CUDA-event time (ms) of fn() on `stream`, after one untimed call."""
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extras(torch, hbm: float, tune: bool):
+    """Decomposition, 768^3 wave FP32 vs BF16, and the 64-grid batch (not in the timed region)."""
+    import synthetic
+    from paper_2404_02218_gb300.grid import Grid, Batch
+    out = {}
+    stream = torch.cuda.Stream()
+
+    # heat 1024^3 order 4 on a 2x2x2 decomposition vs the undecomposed grid
+    case = synthetic.heat3d(1024, 4)
+    u0 = synthetic.uniform_field_torch(case.seed, (1024,) * 3, "cuda")
+    res = {}
+    for name, dec in (("undecomposed", (1, 1, 1)), ("decomp_2x2x2", (2, 2, 2))):
+        g = Grid(3, case.dims, 4, "heat", dt=case.a, decomp=dec, stream=stream)
+        g.set_field("u", u0)
+        if tune:
+            g.tune(reps=2)
+        g.set_field("u", u0)
+        ms = timed_runs(torch, stream, lambda: g.run(STEPS_PER_RUN))
+        pts = STEPS_PER_RUN * 1024 ** 3
+        o = torch.empty_like(u0)
+        g.get_field("u", out=o)
+        res[name] = o
+        out[f"heat3d_so4_{name}"] = {"gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6,
+                                     "frac": 8 * pts / ms / 1e6 / hbm, "steps": STEPS_PER_RUN}
+        g.close()
+    out["heat3d_so4_decomp_2x2x2"]["bitwise_equal_to_undecomposed"] = bool(
+        torch.equal(res["undecomposed"], res["decomp_2x2x2"]))
+    del res, u0, o
+
+    # acoustic wave 768^3, order 8, five layers, Ricker 10 Hz: FP32 vs BF16 storage
+    wc = synthetic.wave3d()
+    c = torch.from_numpy(synthetic.layered_velocity(tuple(reversed(wc.dims)), wc.speeds)).cuda()
+    nsteps = 100
+    for st, bpp in (("f32", 16), ("bf16", 10)):
+        g = Grid(3, wc.dims, 8, "wave", h=wc.h, dt=wc.dt, storage=st, stream=stream)
+        g.set_field("vel", c)
+        g.set_source(wc.src, wc.f0, wc.t0, wc.amp)
+        if tune:
+            g.tune(reps=2)
+        ms = timed_runs(torch, stream, lambda: g.run(nsteps))
+        pts = nsteps * 768 ** 3
+        out[f"wave3d_768_so8_{st}"] = {"gpts": pts / ms / 1e6, "gbs": bpp * pts / ms / 1e6,
+                                       "frac": bpp * pts / ms / 1e6 / hbm, "bytes_per_pt": bpp,
+                                       "steps": nsteps, "plan": json.loads(g.describe())}
+        g.close()
+    del c
+
+    # batched wave: 64 grids U[96,256]^3, order 4, 300 steps
+    cases = synthetic.batch_wave_cases()
+    members = [dict(dims=cs.dims, h=cs.h, dt=cs.dt) for cs in cases]
+    pts_step = sum(int(np.prod(cs.dims)) for cs in cases)
+    nsteps = cases[0].nsteps
+
+    def setup(b):
+        for i, cs in enumerate(cases):
+            b.set_field(i, "vel", torch.from_numpy(cs.velocity()).cuda())
+            b.set_source(i, cs.src, cs.f0, cs.t0, cs.amp)
+
+    b = Batch(3, members, 4, "wave", stream=stream)
+    setup(b)
+    if tune:
+        b.tune(reps=2)
+    ms = timed_runs(torch, stream, lambda: b.run(nsteps))
+    out["batch64_wave_so4_graph_per_step"] = {"gpts": nsteps * pts_step / ms / 1e6,
+                                              "gbs": 16 * nsteps * pts_step / ms / 1e6,
+                                              "frac": 16 * nsteps * pts_step / ms / 1e6 / hbm,
+                                              "launches_per_run": nsteps}
+    b.set_persistent(True)
+    ms = timed_runs(torch, stream, lambda: b.run(nsteps))
+    out["batch64_wave_so4_persistent"] = {"gpts": nsteps * pts_step / ms / 1e6,
+                                          "gbs": 16 * nsteps * pts_step / ms / 1e6,
+                                          "frac": 16 * nsteps * pts_step / ms / 1e6 / hbm,
+                                          "launches_per_run": 1, "points": pts_step,
+                                          "plan": json.loads(b.describe())}
+    b.close()
+    singles = []
+    for cs in cases:
+        g = Grid(3, cs.dims, 4, "wave", h=cs.h, dt=cs.dt, stream=stream)
+        g.set_field("vel", torch.from_numpy(cs.velocity()).cuda())
+        g.set_source(cs.src, cs.f0, cs.t0, cs.amp)
+        singles.append(g)
+
+    def run_all():
+        for g in singles:
+            g.run(nsteps)
+    ms = timed_runs(torch, stream, run_all)
+    out["batch64_wave_so4_64_separate_runs"] = {"gpts": nsteps * pts_step / ms / 1e6,
+                                                "gbs": 16 * nsteps * pts_step / ms / 1e6,
+                                                "frac": 16 * nsteps * pts_step / ms / 1e6 / hbm,
+                                                "launches_per_run": 64 * nsteps}
+    for g in singles:
+        g.close()
+    return out
 
 # -------------------------------------------------------------- our path ---
 def kernel_source_sha() -> str:
@@ -310,6 +424,14 @@ def run_ours(args):
         e2e = {"value": world * args.e2e_steps * pts_per_step / el / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
 
+    extra = None
+    if not args.no_extras:
+        for g in grids.values():
+            g.close()
+        grids = {}
+        torch.cuda.empty_cache()
+        extra = extras(torch, hbm, args.tune == "on")
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
@@ -327,7 +449,7 @@ def run_ours(args):
                            "l2": f"inputs larger than L2 ({4 * N ** 3 / 1e9:.2f} GB per field), no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * len(SOS) * STEPS_PER_RUN, "clocks": clocks,
-                "per_stencil": per, "autotune": tuning or args.tune}
+                "per_stencil": per, "autotune": tuning or args.tune, "secondary": extra}
         print(json.dumps(line), flush=True)
     for g in grids.values():
         g.close()
