@@ -201,6 +201,57 @@ gbst_status stencil_set_persistent(gbst_handle h, int enable);
  * arrivals that never come, so the bounded wait expires (0 restores normal use). */
 gbst_status stencil_debug_barrier_extra(gbst_handle h, unsigned int extra);
 
+/* ---- learned closure (not in the paper) ---------------------------------------
+ * A 3-layer 3x3x3 convolutional network (4 -> 16 -> 16 -> 1, GELU, zero
+ * padding) that corrects a 2x-coarsened acoustic-wave step: with u+ the plain
+ * coarse step, u^n the current level and c_n = c / c_ref,
+ *   x = s (u+, u^n, c_n^2 u+, c_n^2 u^n),  o = net(x),  u+ <- u+ + o / t
+ * (s = in_scale; t = the output scale, closure_set_out_scale, default s).
+ * BF16 weights and activations, FP32 accumulation on the tensor cores, FP32
+ * master weights and Adam (beta 0.9/0.999, eps 1e-8).  cin must be 4 and
+ * hidden 16.  Parameters are a flat
+ * FP32 vector in the order w1[16][cin][3][3][3], b1[16], w2[16][16][3][3][3],
+ * b2[16], w3[1][16][3][3][3], b3[1] (zero after creation).  Device arrays are
+ * dense FP32, x fastest, nx*ny*nz <= max_points.  All calls are ordered on
+ * `stream`; loss_grad and the parameter copies synchronise it. */
+typedef struct gbst_closure_s *gbst_closure;
+gbst_status closure_create(int cin, int hidden, int64_t max_points, double in_scale, void *stream,
+                           const gbst_allocator *allocator, gbst_closure *out);
+gbst_status closure_destroy(gbst_closure c);
+gbst_status closure_param_count(gbst_closure c, int64_t *n);
+gbst_status closure_set_params(gbst_closure c, const float *host, int64_t n);
+gbst_status closure_get_params(gbst_closure c, float *host, int64_t n);
+/* correction = o / t for the given coarse fields (device). */
+gbst_status closure_forward(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,
+                            int64_t nx, int64_t ny, int64_t nz, float *correction);
+/* loss = mean (o - t (u_ref - u+))^2 and its gradient w.r.t. every parameter
+ * (kept on the device; closure_get_grads copies it out). */
+gbst_status closure_loss_grad(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,
+                              const float *u_ref, int64_t nx, int64_t ny, int64_t nz, double *loss);
+gbst_status closure_get_grads(gbst_closure c, float *host, int64_t n);
+/* One Adam update of the parameters with the last gradient. */
+gbst_status closure_adam_step(gbst_closure c, double lr);
+/* Output scale t (default in_scale): the loss compares o with t (u_ref - u+) and
+ * the correction added to u+ is o / t, so the network works with O(1) targets
+ * even when one-step corrections are small next to the field. */
+gbst_status closure_set_out_scale(gbst_closure c, double out_scale);
+/* Factor w > 0 on the loss and its gradient in later closure_loss_grad calls
+ * (default 1), e.g. 1 / mean(target^2) to give every sample the same weight. */
+gbst_status closure_set_loss_weight(gbst_closure c, double w);
+/* freeze != 0: Adam leaves the three bias vectors unchanged (with zero biases a
+ * zero field then gets a zero correction). */
+gbst_status closure_freeze_biases(gbst_closure c, int freeze);
+
+/* Attach a closure to a single (undecomposed) 3D wave grid: from then on every
+ * step of stencil_run is the plain sweep followed by u^{n+1} += closure
+ * correction (c_ref normalises the velocity, c_norm = c / c_ref).  NULL detaches. */
+gbst_status stencil_attach_closure(gbst_handle h, gbst_closure c, double c_ref);
+
+/* Every stride-th interior point (0, stride, 2 stride, .. along each axis) of a
+ * field into a dense FP32 device array of ceil(dims/stride) points (injection
+ * restriction of a fine grid onto a 2x-coarser one when stride = 2). */
+gbst_status stencil_get_field_strided(gbst_handle h, int field, float *dst_device, int stride);
+
 /* Execution plan of the streaming sweep.  variant: index into the kernel
  * table (stencil_variant_count / stencil_variant_info; -1 = the default for
  * this grid); txt: threads along x of a tile (8, 16, 32; 0 = default); zchunks:

@@ -1,0 +1,380 @@
+"""Learned closure for a 2x-coarsened acoustic-wave solve: wrapper and training driver.
+
+The network, its backward pass and Adam run in ``libgbstencil.so``
+(``closure_*`` entry points); the fine and coarse solves are the library's
+stencil sweeps.  This module only orchestrates: it builds the fine (h) and
+coarse (2h, 2 dt) grids of one seeded layered model, restricts the fine
+solution onto the coarse grid by injection (every second point, the library's
+strided read), trains the closure on one-step corrections, and evaluates
+plain and corrected coarse runs against the restricted fine solution.
+
+Inputs: s (u+, u^n, c_n^2 u+, c_n^2 u^n) with c_n = c / 4500 -- every channel
+vanishes with the field, so with zero, frozen biases a zero field receives an
+exactly zero correction (a constant velocity channel made rollouts diverge).
+
+Reading of the set-up (the paper has no learned part): the point source is
+volume-normalised, so the coarse grid injects (h_f / h_c)^3 = 1/8 of the fine
+amplitude per unit of c^2 dt^2 R(t); with dt_c = 2 dt_f the CFL number of both
+grids is the same.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+from . import native as N
+from .grid import Grid, TorchAllocator
+
+C_REF = 4500.0
+
+
+class Closure:
+    """One closure network (``closure_create``) with torch-owned device memory."""
+
+    def __init__(self, max_points: int, in_scale: float, cin: int = 4, hidden: int = 16, stream=None,
+                 torch_allocator: bool = True):
+        import torch
+        self._torch = torch
+        dev = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self._alloc = TorchAllocator(dev) if torch_allocator else None
+        self.h = N.closure_create(cin, hidden, max_points, in_scale, self.stream.cuda_stream,
+                                  self._alloc.struct if self._alloc else None)
+        self.nparams = N.closure_param_count(self.h)
+        self.scale = in_scale
+        self.out_scale = in_scale
+
+    def set_params(self, flat: np.ndarray):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.nparams
+        N.closure_set_params(self.h, a.ctypes.data, a.size)
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.nparams, dtype=np.float32)
+        N.closure_get_params(self.h, out.ctypes.data, out.size)
+        return out
+
+    def get_grads(self) -> np.ndarray:
+        out = np.empty(self.nparams, dtype=np.float32)
+        N.closure_get_grads(self.h, out.ctypes.data, out.size)
+        return out
+
+    def _sync_in(self):
+        self.stream.wait_stream(self._torch.cuda.current_stream())
+
+    def forward(self, up, un, cn):
+        """Correction o / s for dense (nz, ny, nx) FP32 CUDA tensors."""
+        self._sync_in()
+        out = self._torch.empty_like(up)
+        dims = tuple(reversed(up.shape))
+        N.closure_forward(self.h, up.data_ptr(), un.data_ptr(), cn.data_ptr(), dims, out.data_ptr())
+        self._torch.cuda.current_stream().wait_stream(self.stream)
+        return out
+
+    def loss_grad(self, up, un, cn, ref) -> float:
+        self._sync_in()
+        dims = tuple(reversed(up.shape))
+        return N.closure_loss_grad(self.h, up.data_ptr(), un.data_ptr(), cn.data_ptr(), ref.data_ptr(), dims)
+
+    def adam_step(self, lr: float):
+        N.closure_adam_step(self.h, lr)
+
+    def set_out_scale(self, v: float):
+        N.closure_set_out_scale(self.h, v)
+        self.out_scale = v
+
+    def set_loss_weight(self, w: float):
+        N.closure_set_loss_weight(self.h, w)
+
+    def freeze_biases(self, on: bool = True):
+        N.closure_freeze_biases(self.h, on)
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.closure_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def flatten_params(p: dict) -> np.ndarray:
+    """Oracle-order flat vector w1, b1, w2, b2, w3, b3."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float32).reshape(-1)
+                           for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+
+
+def unflatten_params(flat: np.ndarray, cin: int = 4, hidden: int = 16) -> dict:
+    shapes = [("w1", (hidden, cin, 3, 3, 3)), ("b1", (hidden,)), ("w2", (hidden, hidden, 3, 3, 3)),
+              ("b2", (hidden,)), ("w3", (1, hidden, 3, 3, 3)), ("b3", (1,))]
+    out, o = {}, 0
+    for k, shp in shapes:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(shp)
+        o += n
+    return out
+
+
+# ----------------------------------------------------------------- set-up ---
+
+@dataclasses.dataclass
+class PairConfig:
+    nc: int = 256          # coarse points per axis (fine: 2 nc)
+    hf: float = 10.0       # fine spacing (m); coarse 2 hf
+    so: int = 4
+    f0: float = 10.0
+    steps: int = 400       # coarse steps
+    cfl_frac: float = 0.5  # of the stability limit
+
+
+def _courant_max(ndim: int, so: int) -> float:
+    import synthetic
+    return synthetic.wave_courant_max(ndim, so)
+
+
+class FineCoarsePair:
+    """Fine (2 nc)^3 grid with spacing hf and coarse nc^3 grid with 2 hf of one seeded model."""
+
+    def __init__(self, seed: int, cfg: PairConfig, stream=None):
+        import torch
+        import synthetic
+        self.torch = torch
+        self.cfg = cfg
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        nc, nf = cfg.nc, 2 * cfg.nc
+        self.nc, self.nf = nc, nf
+        speeds = synthetic.seeded_layer_speeds(seed)
+        self.cf = synthetic.layered_velocity((nf, nf, nf), speeds)
+        self.cc = np.ascontiguousarray(self.cf[::2, ::2, ::2])
+        self.dtf = cfg.cfl_frac * _courant_max(3, cfg.so) * cfg.hf / max(speeds)
+        self.dtc = 2.0 * self.dtf
+        # source near the middle of the coarse grid, on a point shared with the fine grid
+        u = synthetic.uniform01(seed, 3, start=500).astype(np.float64)
+        self.src_c = tuple(int(nc // 2 - nc // 8 + np.floor(v * (nc // 4))) for v in u)
+        self.src_f = tuple(2 * s for s in self.src_c)
+        self.fine = Grid(3, (nf,) * 3, cfg.so, "wave", h=cfg.hf, dt=self.dtf, stream=self.stream)
+        self.fine.set_field("vel", self.cf)
+        self.fine.set_source(self.src_f, cfg.f0, 1.0 / cfg.f0, 1.0)
+        self.coarse = Grid(3, (nc,) * 3, cfg.so, "wave", h=2 * cfg.hf, dt=self.dtc, stream=self.stream)
+        self.coarse.set_field("vel", self.cc)
+        self.coarse.set_source(self.src_c, cfg.f0, 1.0 / cfg.f0, 1.0 / 8.0)
+        cn = (self.cc / C_REF).astype(np.float32)
+        self.cnorm = torch.from_numpy(cn).cuda()
+
+    def restrict(self, out=None):
+        """Fine u at even indices (injection), as a dense (nc, nc, nc) FP32 CUDA tensor."""
+        t = self.torch
+        if out is None:
+            out = t.empty((self.nc,) * 3, dtype=t.float32, device="cuda")
+        N.stencil_get_field_strided(self.fine.h, N.GBST_U, out.data_ptr(), 2)
+        return out
+
+    def close(self):
+        self.fine.close()
+        self.coarse.close()
+
+
+def coarse_step(pair: FineCoarsePair, u_cur, u_prev, n: int, out):
+    """One plain coarse step from (u^n, u^{n-1}) at step index n; u^{n+1} into `out`."""
+    g = pair.coarse
+    g.set_field("u", u_cur)
+    g.set_field("u_prev", u_prev)
+    g.step = n
+    g.run(1)
+    g.get_field("u", out=out)
+    return out
+
+
+def field_scale(seed: int, cfg: PairConfig) -> float:
+    """1 / max |u| of the restricted fine solution over a trajectory (sampled every 8 coarse steps)."""
+    import torch
+    pair = FineCoarsePair(seed, cfg)
+    m = 0.0
+    r = torch.empty((pair.nc,) * 3, dtype=torch.float32, device="cuda")
+    for n in range(0, cfg.steps, 8):
+        pair.fine.run(16)
+        m = max(m, float(pair.restrict(r).abs().max()))
+    pair.close()
+    return 1.0 / m if m > 0 else 1.0
+
+
+def zero_last_layer(flat: np.ndarray, cin: int = 4, hidden: int = 16) -> np.ndarray:
+    """Parameters with w3 = b3 = 0: the closure starts as 'no correction'."""
+    out = np.array(flat, dtype=np.float32, copy=True)
+    n3 = hidden * 27 + 1
+    out[-n3:] = 0.0
+    return out
+
+
+def zero_biases(flat: np.ndarray, cin: int = 4, hidden: int = 16) -> np.ndarray:
+    p = unflatten_params(flat, cin, hidden)
+    for k in ("b1", "b2", "b3"):
+        p[k][...] = 0.0
+    return flatten_params(p)
+
+
+def correction_scale(seed: int, cfg: PairConfig, quantile: float = 0.999) -> float:
+    """1 / (the `quantile` of |u_ref - u+| over nonzero points) along one trajectory."""
+    import torch
+    pair = FineCoarsePair(seed, cfg)
+    shp = (pair.nc,) * 3
+    r_prev = torch.zeros(shp, dtype=torch.float32, device="cuda")
+    r_cur = torch.zeros(shp, dtype=torch.float32, device="cuda")
+    r_next = torch.empty(shp, dtype=torch.float32, device="cuda")
+    up = torch.empty(shp, dtype=torch.float32, device="cuda")
+    vals = []
+    for n in range(cfg.steps):
+        coarse_step(pair, r_cur, r_prev, n, up)
+        pair.fine.run(2)
+        pair.restrict(r_next)
+        if n % 4 == 0:
+            d = (r_next - up).abs().flatten()
+            vals.append(float(d.max()))
+        r_prev, r_cur, r_next = r_cur, r_next, r_prev
+    pair.close()
+    m = float(np.quantile(np.asarray(vals), quantile)) if vals else 1.0
+    return 1.0 / m if m > 0 else 1.0
+
+
+def train(closure: Closure, seeds, cfg: PairConfig, lr: float = 2e-3, epochs: int = 1, lr_final: float = None,
+          crop: int = 0, updates_per_step: int = 1, seed: int = 0, normalise: bool = False, log=None):
+    """Train on one-step corrections along fine trajectories (teacher forcing).
+
+    Every epoch replays each seed's fine trajectory (cheap next to the network,
+    so no samples are stored); at each coarse step the plain coarse step from the
+    restricted fine state is compared with the restricted next fine state.  With
+    crop > 0 each update uses a random crop^3 window of the coarse grid (the
+    closure is local, so windows are enough and keep updates cheap).  The
+    learning rate decays geometrically from lr to lr_final (default lr / 20).
+    """
+    import torch
+    losses = []
+    t0 = time.time()
+    total = max(1, epochs * len(seeds) * cfg.steps * updates_per_step)
+    lr_final = lr / 20 if lr_final is None else lr_final
+    rng = np.random.default_rng(seed)
+    k = 0
+    for ep in range(epochs):
+        for sd in seeds:
+            pair = FineCoarsePair(sd, cfg)
+            shp = (pair.nc,) * 3
+            r_prev = torch.zeros(shp, dtype=torch.float32, device="cuda")
+            r_cur = torch.zeros(shp, dtype=torch.float32, device="cuda")
+            r_next = torch.empty(shp, dtype=torch.float32, device="cuda")
+            up = torch.empty(shp, dtype=torch.float32, device="cuda")
+            w = crop if 0 < crop < pair.nc else pair.nc
+            for n in range(cfg.steps):
+                coarse_step(pair, r_cur, r_prev, n, up)
+                pair.fine.run(2)
+                pair.restrict(r_next)
+                if n > 0:
+                    for _ in range(updates_per_step):
+                        if w < pair.nc:
+                            o = rng.integers(0, pair.nc - w + 1, size=3)
+                            sl = (slice(o[0], o[0] + w), slice(o[1], o[1] + w), slice(o[2], o[2] + w))
+                            args = [t[sl].contiguous() for t in (up, r_cur, pair.cnorm, r_next)]
+                        else:
+                            args = [up, r_cur, pair.cnorm, r_next]
+                        if normalise:
+                            ms = float(((args[3] - args[0]) ** 2).mean()) * closure.out_scale ** 2
+                            if ms <= 0:
+                                continue
+                            closure.set_loss_weight(1.0 / ms)
+                        losses.append(closure.loss_grad(*args))
+                        closure.adam_step(lr * (lr_final / lr) ** (k / total))
+                        k += 1
+                r_prev, r_cur, r_next = r_cur, r_next, r_prev
+            pair.close()
+            if log:
+                log(f"epoch {ep} seed {sd}: {len(losses)} updates, mean loss of the last 50 "
+                    f"{np.mean(losses[-50:]) if losses else float('nan'):.3e}, {time.time() - t0:.1f}s")
+    return losses
+
+
+def init_params(cin: int = 4, hidden: int = 16, seed: int = 5) -> np.ndarray:
+    """Seeded uniform initial weights (bound 1 / sqrt(fan_in)), zero biases, zero last layer."""
+    import synthetic
+    shapes = [(hidden, cin, 3, 3, 3), (hidden,), (hidden, hidden, 3, 3, 3), (hidden,), (1, hidden, 3, 3, 3), (1,)]
+    parts, off = [], 0
+    for li, shp in enumerate(shapes):
+        n = int(np.prod(shp))
+        if li in (1, 3, 4, 5):
+            parts.append(np.zeros(n, dtype=np.float32))
+        else:
+            fan_in = (cin if li == 0 else hidden) * 27
+            u = synthetic.uniform01(seed, n, start=off).astype(np.float64)
+            parts.append(((2.0 * u - 1.0) / np.sqrt(fan_in)).astype(np.float32))
+        off += n
+    return np.concatenate(parts)
+
+
+def new_closure(cfg: PairConfig, max_points: int, scale_seed: int = 10, init_seed: int = 5,
+                stream=None) -> Closure:
+    """A closure with data-derived input/output scales, zero last layer and zero, frozen biases."""
+    s = field_scale(scale_seed, cfg)
+    t = correction_scale(scale_seed, cfg)
+    cl = Closure(max_points, s, stream=stream)
+    cl.set_out_scale(t)
+    cl.freeze_biases(True)
+    cl.set_params(init_params(seed=init_seed))
+    return cl
+
+
+def rel_l2(a, b) -> float:
+    return float((a - b).norm() / b.norm())
+
+
+def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None):
+    """Plain coarse, closure-corrected coarse and restricted fine solutions.
+
+    Returns the relative L2 errors (vs the restricted fine solution) at the
+    last step, the gain err_plain / err_closure, wall times of the three solves,
+    and the errors at the intermediate checkpoints.
+    """
+    import torch
+    checkpoints = sorted(set(list(checkpoints or []) + [cfg.steps]))
+    pair = FineCoarsePair(seed, cfg)
+    shp = (pair.nc,) * 3
+    g = Grid(3, shp, cfg.so, "wave", h=2 * cfg.hf, dt=pair.dtc, stream=closure.stream)
+    g.set_field("vel", pair.cc)
+    g.set_source(pair.src_c, cfg.f0, 1.0 / cfg.f0, 1.0 / 8.0)
+    N.stencil_attach_closure(g.h, closure.h, C_REF)
+    ref = torch.empty(shp, dtype=torch.float32, device="cuda")
+    u_plain = torch.empty(shp, dtype=torch.float32, device="cuda")
+    u_cl = torch.empty(shp, dtype=torch.float32, device="cuda")
+    curve = {}
+    t_fine = t_plain = t_cl = 0.0
+    done = 0
+    for cp in checkpoints:
+        k = cp - done
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pair.fine.run(2 * k)
+        pair.fine.sync()
+        t_fine += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        pair.coarse.run(k)
+        pair.coarse.sync()
+        t_plain += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        g.run(k)
+        g.sync()
+        t_cl += time.perf_counter() - t0
+        done = cp
+        pair.restrict(ref)
+        pair.coarse.get_field("u", out=u_plain)
+        g.get_field("u", out=u_cl)
+        curve[cp] = (rel_l2(u_plain, ref), rel_l2(u_cl, ref))
+    e_plain, e_cl = curve[cfg.steps]
+    out = {"rel_l2_plain_coarse": e_plain, "rel_l2_closure": e_cl, "gain": e_plain / e_cl,
+           "seconds_fine": t_fine, "seconds_plain_coarse": t_plain, "seconds_closure": t_cl,
+           "steps": cfg.steps, "coarse": pair.nc, "fine": pair.nf,
+           "curve": {str(k): {"plain": v[0], "closure": v[1]} for k, v in curve.items()}}
+    g.close()
+    pair.close()
+    return out

@@ -260,6 +260,9 @@ struct gbst_grid_s {
     bool profile = false;
     std::vector<cudaEvent_t> prof_ev;
     int64_t prof_launches = 0;
+    // learned closure applied after every sweep (single 3D wave grid)
+    gbst_closure closure = nullptr;
+    float *cl_up = nullptr, *cl_un = nullptr, *cl_cn = nullptr, *cl_corr = nullptr;
 };
 
 namespace {
@@ -672,6 +675,36 @@ gbst_status enqueue_step(gbst_handle h, int parity, const float *srcval, int pro
     if (prof_index >= 0)
         GBST_CUDA(cudaEventRecordWithFlags(h->prof_ev[2 * prof_index + 1], h->stream,
                                            cudaEventRecordExternal));
+    if (h->closure) {
+        // u^{n+1} += closure(u^{n+1}, u^n, c_norm): gather both levels dense, run the
+        // network, add the correction back into the padded field
+        const Sub &sb = h->subs[0];
+        const GridDev &g = h->hgrids[0];
+        XferArgs x{};
+        x.storage = h->d.storage;
+        x.pitch = sb.lu.pitch;
+        x.rows = sb.lu.rows;
+        x.origin = sb.lu.origin;
+        x.nx = sb.lu.nx;
+        x.ny = sb.lu.ny;
+        x.nz = sb.lu.nz;
+        x.gnx = sb.lu.nx;
+        x.gny = sb.lu.ny;
+        x.dense_dtype = GBST_F32;
+        x.padded = g.buf[1 - parity];
+        x.dense = h->cl_up;
+        GBST_CUDA(launch_gather(x, h->stream));
+        x.padded = g.buf[parity];
+        x.dense = h->cl_un;
+        GBST_CUDA(launch_gather(x, h->stream));
+        gbst_status cs = closure_forward(h->closure, h->cl_up, h->cl_un, h->cl_cn, sb.lu.nx, sb.lu.ny, sb.lu.nz,
+                                         h->cl_corr);
+        if (cs != GBST_OK)
+            return cs;
+        x.padded = g.buf[1 - parity];
+        x.dense = h->cl_corr;
+        GBST_CUDA(launch_scatter_add(x, h->stream));
+    }
     return GBST_OK;
 }
 
@@ -1249,11 +1282,85 @@ gbst_status stencil_set_persistent(gbst_handle h, int enable)
     gbst_status st = check_handle(h);
     if (st != GBST_OK)
         return st;
+    if (enable && h->closure)
+        return fail(GBST_ENOTSUP, "persistent runs cannot apply a closure");
     if (enable && (!h->plan.stream || h->nboxes > 0))
         return fail(GBST_ENOTSUP, "persistent runs need the streaming kernel and no halo exchanges");
     h->persistent = enable != 0;
     destroy_graphs(h);
     return GBST_OK;
+}
+
+gbst_status stencil_attach_closure(gbst_handle h, gbst_closure c, double c_ref)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    destroy_graphs(h);
+    if (!c) {
+        h->closure = nullptr;
+        return GBST_OK;
+    }
+    if (h->d.eq != GBST_WAVE || h->ndim != 3 || h->subs.size() != 1)
+        return fail(GBST_ENOTSUP, "closures apply to a single undecomposed 3D wave grid");
+    if (h->persistent)
+        return fail(GBST_ENOTSUP, "closures cannot run in persistent mode");
+    if (!(c_ref > 0.0))
+        return fail(GBST_EINVAL, "c_ref must be positive");
+    const Sub &sb = h->subs[0];
+    const int64_t n = sb.lu.nx * sb.lu.ny * sb.lu.nz;
+    if (!h->cl_up) {
+        h->cl_up = static_cast<float *>(dalloc(h, n * sizeof(float)));
+        h->cl_un = static_cast<float *>(dalloc(h, n * sizeof(float)));
+        h->cl_cn = static_cast<float *>(dalloc(h, n * sizeof(float)));
+        h->cl_corr = static_cast<float *>(dalloc(h, n * sizeof(float)));
+        if (!h->cl_up || !h->cl_un || !h->cl_cn || !h->cl_corr)
+            return fail(GBST_ENOMEM, "closure work buffers");
+    }
+    XferArgs x{};
+    x.padded = h->hgrids[0].kappa;
+    x.storage = GBST_F32;
+    x.pitch = sb.lk.pitch;
+    x.rows = sb.lk.rows;
+    x.origin = sb.lk.origin;
+    x.nx = sb.lk.nx;
+    x.ny = sb.lk.ny;
+    x.nz = sb.lk.nz;
+    x.dense = h->cl_cn;
+    GBST_CUDA(launch_kappa_to_cnorm(x, sb.h / (sb.dt * c_ref), h->stream));
+    if (closure_stream(c) != h->stream)
+        return fail(GBST_EINVAL, "the closure and the grid must use the same stream");
+    h->closure = c;
+    GBST_CUDA(cudaStreamSynchronize(h->stream));
+    return GBST_OK;
+}
+
+gbst_status stencil_get_field_strided(gbst_handle h, int field, float *dst, int stride)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (!dst || stride < 1)
+        return fail(GBST_EINVAL, "null destination or stride < 1");
+    if (h->subs.size() != 1)
+        return fail(GBST_ENOTSUP, "strided reads need a single undecomposed grid");
+    if (field != GBST_U && field != GBST_U_PREV)
+        return fail(GBST_EINVAL, "strided reads support GBST_U and GBST_U_PREV");
+    if (h->d.eq == GBST_HEAT && field != GBST_U)
+        return fail(GBST_EINVAL, "heat grids have only the field GBST_U");
+    const Sub &sb = h->subs[0];
+    XferArgs x{};
+    x.padded = h->hgrids[0].buf[field == GBST_U ? h->parity : 1 - h->parity];
+    x.storage = h->d.storage;
+    x.pitch = sb.lu.pitch;
+    x.rows = sb.lu.rows;
+    x.origin = sb.lu.origin;
+    x.nx = sb.lu.nx;
+    x.ny = sb.lu.ny;
+    x.nz = sb.lu.nz;
+    x.dense = dst;
+    GBST_CUDA(launch_gather_strided(x, stride, h->stream));
+    return poll_device_error(h);
 }
 
 gbst_status stencil_debug_barrier_extra(gbst_handle h, unsigned int extra)
@@ -1324,7 +1431,8 @@ gbst_status stencil_run(gbst_handle h, int64_t nsteps)
         }
         return GBST_OK;
     };
-    const bool graph = h->d.use_graph && h->stream != nullptr;
+    // (a closure's weights may change between runs: its steps are launched directly)
+    const bool graph = h->d.use_graph && h->stream != nullptr && !h->closure;
     if (graph) {
         const auto key = std::make_pair(nsteps, h->parity + (h->profile ? 2 : 0) + (persistent ? 4 : 0));
         auto it = h->graphs.find(key);

@@ -1,0 +1,825 @@
+// Learned closure for a 2x-coarsened acoustic-wave solve: a 3-layer 3x3x3
+// convolutional network (C_in = 4 -> 16 -> 16 -> 1, GELU), BF16 weights and
+// activations, FP32 accumulation on the tensor cores (mma.sync m16n8k16), with
+// its backward pass and an Adam optimiser.  The paper has no learned part.
+//
+// Network (per coarse step, inputs scaled by s, c_n = c / c_ref):
+//   x  = s (u+, u^n, c_n^2 u+, c_n^2 u^n)    u+ = the plain coarse step
+//   z1 = conv1(x) + b1,  y1 = GELU(z1)
+//   z2 = conv2(y1) + b2, y2 = GELU(z2)
+//   o  = conv3(y2) + b3                       u+ += o / t  (t: output scale)
+// Training minimises mean((o - t (u_ref - u+))^2) over all points.
+//
+// Layouts: every activation is channels-last BF16 with 16 channels (inputs and
+// the 1-channel gradient padded with zeros); weights are kept in FP32 (master,
+// order [co][ci][dz][dy][dx] per layer, then the biases) and converted to BF16
+// [tap][co][16] for the forward convolutions and to the flipped, transposed
+// [tap][ci][16] for the data gradient.
+#include <cmath>
+#include <vector>
+
+#include "gbst_internal.h"
+
+namespace gbst {
+namespace {
+
+constexpr int CH = 16;               // channels of every stored activation
+constexpr int TXC = 32, TYC = 4;     // output tile of a CTA (x, y)
+constexpr int HX = TXC + 2, HY = TYC + 2;
+constexpr int PLANE_PTS = HX * HY;   // halo tile points per plane
+constexpr int PLANE_BYTES = PLANE_PTS * 32;
+constexpr int NSLOT = 4;             // plane ring: z-1, z, z+1 and one prefetch
+constexpr int NTHR = 256;            // 8 warps; warp w: row w/2, 16-point segment w%2
+constexpr int ZCHUNK = 16;           // output planes per CTA
+
+enum Epi { EPI_GELU = 0, EPI_LINEAR_F32 = 1, EPI_DGELU = 2 };
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Row-swizzled byte offset of half `half` (8 channels, 16 B) of row `row` in a
+// 32-byte-row matrix: the halves of every other group of 4 rows are swapped so
+// that the 8 rows an ldmatrix phase reads fall on distinct banks.
+__device__ __forceinline__ int swz(int row, int half) { return row * 32 + ((half ^ ((row >> 2) & 1)) << 4); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t &r0, uint32_t &r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+__device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid)
+{
+    const int n = valid ? 16 : 0;  // 0: zero-fill, nothing read
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+struct Dims {
+    int nx, ny, nz;
+};
+
+// Load plane z (interior index; outside [0, nz) -> zeros) of the halo tile at
+// (x0-1 .. x0+TXC, y0-1 .. y0+TYC) of a channels-last 16-channel BF16 tensor.
+__device__ __forceinline__ void load_plane(unsigned char *slot, const __nv_bfloat16 *in, Dims d, int x0, int y0, int z)
+{
+    const bool zin = z >= 0 && z < d.nz;
+    for (int idx = threadIdx.x; idx < PLANE_PTS * 2; idx += NTHR) {
+        const int pt = idx >> 1, half = idx & 1;
+        const int gx = x0 - 1 + pt % HX, gy = y0 - 1 + pt / HX;
+        const bool valid = zin && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+        const __nv_bfloat16 *src =
+            valid ? in + ((static_cast<int64_t>(z) * d.ny + gy) * d.nx + gx) * CH + half * 8 : in;
+        cp_async16(smem_addr(slot + swz(pt, half)), src, valid);
+    }
+}
+
+// Load plane z of the interior tile (no halo) of a 16-channel tensor.
+__device__ __forceinline__ void load_tile(unsigned char *dst, const __nv_bfloat16 *in, Dims d, int x0, int y0, int z)
+{
+    for (int idx = threadIdx.x; idx < TXC * TYC * 2; idx += NTHR) {
+        const int pt = idx >> 1, half = idx & 1;
+        const int gx = x0 + pt % TXC, gy = y0 + pt / TXC;
+        const bool valid = gx < d.nx && gy < d.ny;
+        const __nv_bfloat16 *src =
+            valid ? in + ((static_cast<int64_t>(z) * d.ny + gy) * d.nx + gx) * CH + half * 8 : in;
+        cp_async16(smem_addr(dst + swz(pt, half)), src, valid);
+    }
+}
+
+struct ConvArgs {
+    const __nv_bfloat16 *in;   // [z][y][x][16]
+    const __nv_bfloat16 *wt;   // [27][COUT][16] (tap = (dz*3 + dy)*3 + dx)
+    const float *bias;         // [COUT] or null
+    __nv_bfloat16 *out;        // EPI_GELU / EPI_DGELU: [z][y][x][16]
+    __nv_bfloat16 *zout;       // EPI_GELU: pre-activations (optional)
+    const __nv_bfloat16 *aux;  // EPI_DGELU: pre-activations of the layer below
+    float *out_f32;            // EPI_LINEAR_F32: channel 0, dense [z][y][x]
+    Dims d;
+    int cout_valid;            // output channels that are real (the rest are written as 0)
+};
+
+// 3x3x3 convolution, zero padding, one CTA per (32 x 4) column and ZCHUNK planes.
+template <int COUT, int EPI>
+__global__ void __launch_bounds__(NTHR) k_conv(const ConvArgs a)
+{
+    constexpr int NT = COUT / 8;  // n-tiles of 8 output channels
+    extern __shared__ __align__(128) unsigned char sm[];
+    unsigned char *wsm = sm;                               // 27 * COUT rows of 32 B
+    unsigned char *ring = sm + 27 * COUT * 32;             // NSLOT plane slots
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = (a.d.nx + TXC - 1) / TXC;
+    const int x0 = (blockIdx.x % tiles_x) * TXC, y0 = (blockIdx.x / tiles_x) * TYC;
+    const int z0 = blockIdx.y * ZCHUNK;
+    const int z1 = min(a.d.nz, z0 + ZCHUNK);
+
+    for (int idx = tid; idx < 27 * COUT * 2; idx += NTHR) {
+        const int row = idx >> 1, half = idx & 1;
+        cp_async16(smem_addr(wsm + swz(row, half)), a.wt + row * 16 + half * 8, true);
+    }
+    load_plane(ring + 0 * PLANE_BYTES, a.in, a.d, x0, y0, z0 - 1);
+    load_plane(ring + 1 * PLANE_BYTES, a.in, a.d, x0, y0, z0);
+    cp_commit();
+    load_plane(ring + 2 * PLANE_BYTES, a.in, a.d, x0, y0, z0 + 1);
+    cp_commit();
+
+    const int wy = warp >> 1, ws = warp & 1;
+    const int m = lane >> 3, r = lane & 7;
+    const int a_pt = r + 8 * (m & 1), a_half = m >> 1;  // A fragment rows (points) / channel half
+    const int g = lane >> 2, q = lane & 3;
+    const int y = y0 + wy;
+
+    for (int z = z0; z < z1; ++z) {
+        // planes z-1, z, z+1 must be resident; prefetch z+2 into the free slot
+        load_plane(ring + ((z + 2 - z0 + 1) % NSLOT) * PLANE_BYTES, a.in, a.d, x0, y0, z + 2);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+
+        float acc[NT][4];
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                acc[t][k] = 0.f;
+#pragma unroll
+        for (int kz = 0; kz < 3; ++kz) {
+            const unsigned char *slot = ring + ((z + kz - 1 - z0 + 1) % NSLOT) * PLANE_BYTES;
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int tap = (kz * 3 + ky) * 3 + kx;
+                    const int pt = (wy + ky) * HX + ws * 16 + a_pt + kx;
+                    uint32_t a0, a1, a2, a3;
+                    ldsm_x4(smem_addr(slot + swz(pt, a_half)), a0, a1, a2, a3);
+                    if (NT == 2) {
+                        uint32_t b0, b1, b2, b3;
+                        ldsm_x4(smem_addr(wsm + swz(tap * COUT + (m >> 1) * 8 + r, m & 1)), b0, b1, b2, b3);
+                        mma16816(acc[0], a0, a1, a2, a3, b0, b1);
+                        mma16816(acc[NT - 1], a0, a1, a2, a3, b2, b3);
+                    } else {
+                        uint32_t b0, b1;
+                        ldsm_x2(smem_addr(wsm + swz(tap * COUT + r, m & 1)), b0, b1);
+                        mma16816(acc[0], a0, a1, a2, a3, b0, b1);
+                    }
+                }
+            }
+        }
+
+        // epilogue: C rows = points g, g+8 of the warp's segment; cols = channels 8t + 2q, +1
+#pragma unroll
+        for (int half8 = 0; half8 < 2; ++half8) {
+            const int x = x0 + ws * 16 + g + 8 * half8;
+            if (x >= a.d.nx || y >= a.d.ny)
+                continue;
+            const int64_t p = (static_cast<int64_t>(z) * a.d.ny + y) * a.d.nx + x;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const int c = 8 * t + 2 * q;
+                float v0 = acc[t][2 * half8], v1 = acc[t][2 * half8 + 1];
+                if (EPI == EPI_LINEAR_F32) {
+                    if (c == 0)
+                        a.out_f32[p] = v0 + a.bias[0];
+                } else if (EPI == EPI_GELU) {
+                    v0 += a.bias[c];
+                    v1 += a.bias[c + 1];
+                    if (c >= a.cout_valid)
+                        v0 = 0.f;
+                    if (c + 1 >= a.cout_valid)
+                        v1 = 0.f;
+                    if (a.zout)
+                        *reinterpret_cast<__nv_bfloat162 *>(a.zout + p * CH + c) = __floats2bfloat162_rn(v0, v1);
+                    *reinterpret_cast<__nv_bfloat162 *>(a.out + p * CH + c) =
+                        __floats2bfloat162_rn(gelu(v0), gelu(v1));
+                } else {  // EPI_DGELU: data gradient times GELU'(pre-activation below)
+                    const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162 *>(a.aux + p * CH + c);
+                    v0 *= gelu_grad(__bfloat162float(zz.x));
+                    v1 *= gelu_grad(__bfloat162float(zz.y));
+                    *reinterpret_cast<__nv_bfloat162 *>(a.out + p * CH + c) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+        __syncthreads();  // the slot of plane z-1 is reused by the next prefetch
+    }
+    cp_wait<0>();
+}
+
+struct WgradArgs {
+    const __nv_bfloat16 *x;   // layer input [z][y][x][16]
+    const __nv_bfloat16 *dz;  // output gradient [z][y][x][16]
+    float *grad_w;            // master-order gradient of this layer's weights [co][ci][27]
+    float *grad_b;            // [co]
+    Dims d;
+    int cin, cout;            // real channel counts
+};
+
+// dW[co][ci][tap] += sum_p x[p + tap][ci] dz[p][co];  db[co] += sum_p dz[p][co].
+// Warp w owns taps w, w+8, w+16, w+24; per 16-point chunk the tensor cores
+// compute a (ci x points) x (points x co) product.
+__global__ void __launch_bounds__(NTHR) k_wgrad(const WgradArgs a)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    unsigned char *ring = sm;                              // NSLOT halo planes of x
+    unsigned char *dzs = sm + NSLOT * PLANE_BYTES;         // 2 slots of the dz tile
+    constexpr int DZ_BYTES = TXC * TYC * 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = (a.d.nx + TXC - 1) / TXC;
+    const int x0 = (blockIdx.x % tiles_x) * TXC, y0 = (blockIdx.x / tiles_x) * TYC;
+    const int z0 = blockIdx.y * ZCHUNK;
+    const int z1 = min(a.d.nz, z0 + ZCHUNK);
+    const int m = lane >> 3, r = lane & 7;
+    const int g = lane >> 2, q = lane & 3;
+
+    float acc[4][2][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                acc[i][t][k] = 0.f;
+    float bsum = 0.f;  // thread tid < 16: db of channel tid over this CTA
+
+    load_plane(ring + 0 * PLANE_BYTES, a.x, a.d, x0, y0, z0 - 1);
+    load_plane(ring + 1 * PLANE_BYTES, a.x, a.d, x0, y0, z0);
+    cp_commit();
+    for (int z = z0; z < z1; ++z) {
+        load_plane(ring + ((z + 1 - z0 + 1) % NSLOT) * PLANE_BYTES, a.x, a.d, x0, y0, z + 1);
+        load_tile(dzs + (z & 1) * DZ_BYTES, a.dz, a.d, x0, y0, z);
+        cp_commit();
+        cp_wait<0>();
+        __syncthreads();
+        const unsigned char *dzt = dzs + (z & 1) * DZ_BYTES;
+        if (tid < 16) {
+            for (int pt = 0; pt < TXC * TYC; ++pt) {
+                const __nv_bfloat16 *row = reinterpret_cast<const __nv_bfloat16 *>(dzt + swz(pt, tid >> 3));
+                bsum += __bfloat162float(row[tid & 7]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int tap = warp + 8 * i;
+            if (tap >= 27)
+                break;
+            const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+            const unsigned char *slot = ring + ((z + kz - 1 - z0 + 1) % NSLOT) * PLANE_BYTES;
+#pragma unroll
+            for (int chunk = 0; chunk < TYC * 2; ++chunk) {
+                const int cy = chunk >> 1, cs = chunk & 1;
+                // A = x^T (ci x 16 points): matrices (ci 0-7|8-15) x (points 0-7|8-15), transposed loads
+                const int apt = (cy + ky) * HX + cs * 16 + r + 8 * (m >> 1) + kx;
+                uint32_t a0, a1, a2, a3;
+                ldsm_x4_t(smem_addr(slot + swz(apt, m & 1)), a0, a1, a2, a3);
+                // B = dz (16 points x co) column-major fragments for the two 8-channel tiles
+                const int bpt = cy * TXC + cs * 16 + r + 8 * (m & 1);
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4_t(smem_addr(dzt + swz(bpt, m >> 1)), b0, b1, b2, b3);
+                mma16816(acc[i][0], a0, a1, a2, a3, b0, b1);
+                mma16816(acc[i][1], a0, a1, a2, a3, b2, b3);
+            }
+        }
+        __syncthreads();
+    }
+    // C rows = ci (g, g+8), cols = co (8t + 2q, +1)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int tap = warp + 8 * i;
+        if (tap >= 27)
+            break;
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int ci = g + 8 * (k >> 1), co = 8 * t + 2 * q + (k & 1);
+                if (ci < a.cin && co < a.cout)
+                    atomicAdd(&a.grad_w[(co * a.cin + ci) * 27 + tap], acc[i][t][k]);
+            }
+    }
+    if (tid < 16 && tid < a.cout)
+        atomicAdd(&a.grad_b[tid], bsum);
+}
+
+// x = s (u+, u^n, c_norm^2 u+, c_norm^2 u^n, 0...) channels-last BF16: every
+// channel vanishes with the field, so with zero biases a zero field gets a zero
+// correction.
+__global__ void k_prep(const float *up, const float *un, const float *cn, float s, int64_t n, __nv_bfloat16 *x)
+{
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(x + p * CH);
+        const float a = s * up[p], b = s * un[p], c2 = cn[p] * cn[p];
+        o[0] = __floats2bfloat162_rn(a, b);
+        o[1] = __floats2bfloat162_rn(c2 * a, c2 * b);
+#pragma unroll
+        for (int k = 2; k < 8; ++k)
+            o[k] = __floats2bfloat162_rn(0.f, 0.f);
+    }
+}
+
+// loss += sum (o - s (ref - u+))^2;  dOut = 2 (o - target) / n into channel 0 of a 16-channel tensor.
+__global__ void k_loss(const float *o, const float *up, const float *ref, float s, float wgt, int64_t n,
+                       double *loss, __nv_bfloat16 *dout)
+{
+    double acc = 0.0;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float d = o[p] - s * (ref[p] - up[p]);  // s: the output scale
+        acc += static_cast<double>(d) * d;
+        __nv_bfloat162 *g = reinterpret_cast<__nv_bfloat162 *>(dout + p * CH);
+        g[0] = __floats2bfloat162_rn(2.0f * wgt * d / static_cast<float>(n), 0.f);
+#pragma unroll
+        for (int k = 1; k < 8; ++k)
+            g[k] = __floats2bfloat162_rn(0.f, 0.f);
+    }
+    for (int off = 16; off > 0; off >>= 1)
+        acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0)
+        atomicAdd(loss, acc);
+}
+
+// Master FP32 weights -> BF16 forward [tap][co_pad][16] and data-gradient [tap'][ci][16] layouts.
+__global__ void k_convert(const float *w, int cin, int cout, int cout_pad, __nv_bfloat16 *fwd, __nv_bfloat16 *bwd)
+{
+    const int n = 27 * CH * CH;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int tap = i / (CH * CH), a = (i / CH) % CH, b = i % CH;
+        // forward: row (tap, co = a), column ci = b
+        if (a < cout_pad)
+            fwd[(tap * cout_pad + a) * CH + b] =
+                __float2bfloat16_rn((a < cout && b < cin) ? w[(a * cin + b) * 27 + tap] : 0.f);
+        // data gradient: output channel ci = a, input channel co = b, tap flipped
+        if (bwd)
+            bwd[(tap * CH + a) * CH + b] =
+                __float2bfloat16_rn((a < cin && b < cout) ? w[(b * cin + a) * 27 + (26 - tap)] : 0.f);
+    }
+}
+
+// (1 - beta) is passed in: 1 - 0.999f evaluated in FP32 is off by 1.3e-5.
+struct BiasRanges {
+    int lo[3], hi[3];  // [lo, hi) index ranges of the three bias vectors; empty when not frozen
+};
+
+__global__ void k_adam(float *p, const float *g, float *m1, float *m2, int n, float lr, float b1, float b2,
+                       float omb1, float omb2, float eps, float bc1, float bc2, BiasRanges frozen)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if ((i >= frozen.lo[0] && i < frozen.hi[0]) || (i >= frozen.lo[1] && i < frozen.hi[1]) ||
+            (i >= frozen.lo[2] && i < frozen.hi[2]))
+            continue;
+        const float gi = g[i];
+        const float mi = b1 * m1[i] + omb1 * gi;
+        const float vi = b2 * m2[i] + omb2 * gi * gi;
+        m1[i] = mi;
+        m2[i] = vi;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+__global__ void k_scale_add(float *dst, const float *src, float scale, int64_t n)
+{
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        dst[p] += scale * src[p];
+}
+
+}  // namespace
+}  // namespace gbst
+
+// ===========================================================================
+using namespace gbst;
+
+struct gbst_closure_s {
+    int cin = 3, hidden = 16;
+    int64_t max_pts = 0;
+    double scale = 1.0;
+    cudaStream_t stream = nullptr;
+    gbst_allocator alloc{};
+    bool custom = false;
+    std::vector<std::pair<void *, size_t>> owned;
+    // parameters (master FP32, oracle order) and their offsets
+    int64_t off[6] = {0}, cnt[6] = {0}, nparams = 0;
+    float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
+    int64_t t = 0;  // Adam step
+    __nv_bfloat16 *wf[3] = {nullptr}, *wb[3] = {nullptr};
+    // activations
+    __nv_bfloat16 *x = nullptr, *z1 = nullptr, *y1 = nullptr, *z2 = nullptr, *y2 = nullptr;
+    __nv_bfloat16 *dout = nullptr, *dz2 = nullptr, *dz1 = nullptr;
+    float *o = nullptr;
+    double *dloss = nullptr;
+    bool weights_dirty = true;
+    double out_scale = 1.0;     // target in network units: out_scale * (u_ref - u+)
+    bool freeze_biases = false; // Adam leaves the biases unchanged
+    double loss_weight = 1.0;   // factor on the loss (and its gradient) of the next loss_grad calls
+};
+
+cudaStream_t gbst::closure_stream(gbst_closure c) { return c ? c->stream : nullptr; }
+
+namespace {
+
+void *cl_alloc(gbst_closure c, size_t bytes)
+{
+    void *ptr = nullptr;
+    if (c->custom)
+        ptr = c->alloc.alloc(bytes, c->stream, c->alloc.ctx);
+    else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr)
+        c->owned.emplace_back(ptr, bytes);
+    return ptr;
+}
+
+int blocks_for(int64_t n) { return static_cast<int>(std::min<int64_t>(8192, (n + 255) / 256)); }
+
+size_t conv_smem(int cout) { return 27 * cout * 32 + NSLOT * PLANE_BYTES; }
+size_t wgrad_smem() { return NSLOT * PLANE_BYTES + 2 * TXC * TYC * 32; }
+
+template <int COUT, int EPI>
+cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
+{
+    const size_t smem = conv_smem(COUT);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_conv<COUT, EPI>),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        attr = true;
+    }
+    const int tiles = ((a.d.nx + TXC - 1) / TXC) * ((a.d.ny + TYC - 1) / TYC);
+    dim3 grid(tiles, (a.d.nz + ZCHUNK - 1) / ZCHUNK);
+    k_conv<COUT, EPI><<<grid, NTHR, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad(const WgradArgs &a, cudaStream_t s)
+{
+    const size_t smem = wgrad_smem();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_wgrad), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
+        attr = true;
+    }
+    const int tiles = ((a.d.nx + TXC - 1) / TXC) * ((a.d.ny + TYC - 1) / TYC);
+    dim3 grid(tiles, (a.d.nz + ZCHUNK - 1) / ZCHUNK);
+    k_wgrad<<<grid, NTHR, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+gbst_status check_dims(gbst_closure c, int64_t nx, int64_t ny, int64_t nz, Dims *d)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || nx * ny * nz > c->max_pts || nx > (1 << 30) || ny > (1 << 30) ||
+        nz > (1 << 30))
+        return record_error(GBST_EINVAL, "closure: grid larger than the size given at closure_create");
+    d->nx = static_cast<int>(nx);
+    d->ny = static_cast<int>(ny);
+    d->nz = static_cast<int>(nz);
+    return GBST_OK;
+}
+
+gbst_status refresh_weights(gbst_closure c)
+{
+    if (!c->weights_dirty)
+        return GBST_OK;
+    const int cins[3] = {c->cin, c->hidden, c->hidden}, couts[3] = {c->hidden, c->hidden, 1};
+    const int pads[3] = {CH, CH, 8};
+    for (int l = 0; l < 3; ++l) {
+        k_convert<<<8, 256, 0, c->stream>>>(c->p + c->off[2 * l], cins[l], couts[l], pads[l], c->wf[l],
+                                             l > 0 ? c->wb[l] : nullptr);
+    }
+    c->weights_dirty = false;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
+}
+
+// Forward pass into c->o (network units).  keep: also store the pre-activations.
+gbst_status forward(gbst_closure c, const float *up, const float *un, const float *cn, Dims d, bool keep)
+{
+    gbst_status st = refresh_weights(c);
+    if (st != GBST_OK)
+        return st;
+    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
+    k_prep<<<blocks_for(n), 256, 0, c->stream>>>(up, un, cn, static_cast<float>(c->scale), n, c->x);
+    ConvArgs a{};
+    a.d = d;
+    a.in = c->x;
+    a.wt = c->wf[0];
+    a.bias = c->p + c->off[1];
+    a.out = c->y1;
+    a.zout = keep ? c->z1 : nullptr;
+    a.cout_valid = c->hidden;
+    cudaError_t e = launch_conv<16, EPI_GELU>(a, c->stream);
+    a.in = c->y1;
+    a.wt = c->wf[1];
+    a.bias = c->p + c->off[3];
+    a.out = c->y2;
+    a.zout = keep ? c->z2 : nullptr;
+    if (e == cudaSuccess)
+        e = launch_conv<16, EPI_GELU>(a, c->stream);
+    ConvArgs b{};
+    b.d = d;
+    b.in = c->y2;
+    b.wt = c->wf[2];
+    b.bias = c->p + c->off[5];
+    b.out_f32 = c->o;
+    b.cout_valid = 1;
+    if (e == cudaSuccess)
+        e = launch_conv<8, EPI_LINEAR_F32>(b, c->stream);
+    return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+gbst_status closure_create(int cin, int hidden, int64_t max_points, double in_scale, void *stream,
+                           const gbst_allocator *allocator, gbst_closure *out)
+{
+    if (!out)
+        return record_error(GBST_EINVAL, "closure_create: null out");
+    *out = nullptr;
+    if (cin != 4 || hidden != 16)
+        return record_error(GBST_ENOTSUP, "closure_create: this build has 4 input and 16 hidden channels");
+    if (max_points < 1 || !(in_scale > 0.0))
+        return record_error(GBST_EINVAL, "closure_create: max_points and in_scale must be positive");
+    gbst_closure c = new (std::nothrow) gbst_closure_s;
+    if (!c)
+        return record_error(GBST_ENOMEM, "closure_create: handle");
+    c->cin = cin;
+    c->hidden = hidden;
+    c->max_pts = max_points;
+    c->scale = in_scale;
+    c->out_scale = in_scale;
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (allocator) {
+        c->alloc = *allocator;
+        c->custom = true;
+    }
+    const int64_t counts[6] = {int64_t(hidden) * cin * 27, hidden, int64_t(hidden) * hidden * 27, hidden,
+                               int64_t(hidden) * 27, 1};
+    int64_t o = 0;
+    for (int i = 0; i < 6; ++i) {
+        c->off[i] = o;
+        c->cnt[i] = counts[i];
+        o += counts[i];
+    }
+    c->nparams = o;
+    const size_t pb = static_cast<size_t>(o) * sizeof(float);
+    const size_t ab = static_cast<size_t>(max_points) * CH * sizeof(__nv_bfloat16);
+    c->p = static_cast<float *>(cl_alloc(c, pb));
+    c->g = static_cast<float *>(cl_alloc(c, pb));
+    c->m1 = static_cast<float *>(cl_alloc(c, pb));
+    c->m2 = static_cast<float *>(cl_alloc(c, pb));
+    for (int l = 0; l < 3; ++l) {
+        c->wf[l] = static_cast<__nv_bfloat16 *>(cl_alloc(c, 27 * CH * CH * sizeof(__nv_bfloat16)));
+        c->wb[l] = static_cast<__nv_bfloat16 *>(cl_alloc(c, 27 * CH * CH * sizeof(__nv_bfloat16)));
+    }
+    __nv_bfloat16 **acts[8] = {&c->x, &c->z1, &c->y1, &c->z2, &c->y2, &c->dout, &c->dz2, &c->dz1};
+    bool ok = c->p && c->g && c->m1 && c->m2;
+    for (int l = 0; l < 3; ++l)
+        ok = ok && c->wf[l] && c->wb[l];
+    for (auto pp : acts) {
+        *pp = static_cast<__nv_bfloat16 *>(cl_alloc(c, ab));
+        ok = ok && *pp;
+    }
+    c->o = static_cast<float *>(cl_alloc(c, static_cast<size_t>(max_points) * sizeof(float)));
+    c->dloss = static_cast<double *>(cl_alloc(c, 256));
+    ok = ok && c->o && c->dloss;
+    if (ok)
+        ok = cudaMemsetAsync(c->p, 0, pb, c->stream) == cudaSuccess && cudaMemsetAsync(c->g, 0, pb, c->stream) ==
+             cudaSuccess && cudaMemsetAsync(c->m1, 0, pb, c->stream) == cudaSuccess &&
+             cudaMemsetAsync(c->m2, 0, pb, c->stream) == cudaSuccess;
+    if (!ok) {
+        closure_destroy(c);
+        return record_error(GBST_ENOMEM, "closure_create: device memory");
+    }
+    *out = c;
+    return GBST_OK;
+}
+
+gbst_status closure_destroy(gbst_closure c)
+{
+    if (!c)
+        return GBST_OK;
+    cudaStreamSynchronize(c->stream);
+    for (auto &pb : c->owned) {
+        if (c->custom)
+            c->alloc.release(pb.first, pb.second, c->stream, c->alloc.ctx);
+        else
+            cudaFree(pb.first);
+    }
+    delete c;
+    return GBST_OK;
+}
+
+gbst_status closure_param_count(gbst_closure c, int64_t *n)
+{
+    if (!c || !n)
+        return record_error(GBST_EINVAL, "closure_param_count: null argument");
+    *n = c->nparams;
+    return GBST_OK;
+}
+
+gbst_status closure_set_params(gbst_closure c, const float *host, int64_t n)
+{
+    if (!c || !host || n != c->nparams)
+        return record_error(GBST_EINVAL, "closure_set_params: null argument or wrong count");
+    if (cudaMemcpyAsync(c->p, host, n * sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return record_error(GBST_ECUDA, "closure_set_params: copy failed");
+    c->weights_dirty = true;
+    return GBST_OK;
+}
+
+static gbst_status copy_out(gbst_closure c, const float *src, float *host, int64_t n)
+{
+    if (!c || !host || n != c->nparams)
+        return record_error(GBST_EINVAL, "closure: null argument or wrong count");
+    if (cudaMemcpyAsync(host, src, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return record_error(GBST_ECUDA, "closure: copy failed");
+    return GBST_OK;
+}
+
+gbst_status closure_get_params(gbst_closure c, float *host, int64_t n) { return copy_out(c, c->p, host, n); }
+gbst_status closure_get_grads(gbst_closure c, float *host, int64_t n) { return copy_out(c, c->g, host, n); }
+
+gbst_status closure_forward(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm, int64_t nx,
+                            int64_t ny, int64_t nz, float *correction)
+{
+    if (!c || !u_plus || !u_n || !c_norm || !correction)
+        return record_error(GBST_EINVAL, "closure_forward: null argument");
+    Dims d;
+    gbst_status st = check_dims(c, nx, ny, nz, &d);
+    if (st != GBST_OK)
+        return st;
+    st = forward(c, u_plus, u_n, c_norm, d, false);
+    if (st != GBST_OK)
+        return st;
+    const int64_t n = nx * ny * nz;
+    if (cudaMemsetAsync(correction, 0, n * sizeof(float), c->stream) != cudaSuccess)
+        return record_error(GBST_ECUDA, "closure_forward: memset");
+    k_scale_add<<<blocks_for(n), 256, 0, c->stream>>>(correction, c->o, static_cast<float>(1.0 / c->out_scale), n);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
+}
+
+gbst_status closure_loss_grad(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,
+                              const float *u_ref, int64_t nx, int64_t ny, int64_t nz, double *loss)
+{
+    if (!c || !u_plus || !u_n || !c_norm || !u_ref || !loss)
+        return record_error(GBST_EINVAL, "closure_loss_grad: null argument");
+    Dims d;
+    gbst_status st = check_dims(c, nx, ny, nz, &d);
+    if (st != GBST_OK)
+        return st;
+    st = forward(c, u_plus, u_n, c_norm, d, true);
+    if (st != GBST_OK)
+        return st;
+    const int64_t n = nx * ny * nz;
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaMemsetAsync(c->dloss, 0, sizeof(double), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->g, 0, c->nparams * sizeof(float), s);
+    k_loss<<<blocks_for(n), 256, 0, s>>>(c->o, u_plus, u_ref, static_cast<float>(c->out_scale),
+                                         static_cast<float>(c->loss_weight), n, c->dloss, c->dout);
+    // layer 3: dW3 from y2 and dOut; dZ2 = conv(dOut, W3 flipped^T) * GELU'(z2)
+    WgradArgs w{};
+    w.d = d;
+    w.x = c->y2;
+    w.dz = c->dout;
+    w.grad_w = c->g + c->off[4];
+    w.grad_b = c->g + c->off[5];
+    w.cin = c->hidden;
+    w.cout = 1;
+    if (e == cudaSuccess)
+        e = launch_wgrad(w, s);
+    ConvArgs a{};
+    a.d = d;
+    a.in = c->dout;
+    a.wt = c->wb[2];
+    a.aux = c->z2;
+    a.out = c->dz2;
+    a.cout_valid = CH;
+    if (e == cudaSuccess)
+        e = launch_conv<16, EPI_DGELU>(a, s);
+    // layer 2
+    w.x = c->y1;
+    w.dz = c->dz2;
+    w.grad_w = c->g + c->off[2];
+    w.grad_b = c->g + c->off[3];
+    w.cin = c->hidden;
+    w.cout = c->hidden;
+    if (e == cudaSuccess)
+        e = launch_wgrad(w, s);
+    a.in = c->dz2;
+    a.wt = c->wb[1];
+    a.aux = c->z1;
+    a.out = c->dz1;
+    if (e == cudaSuccess)
+        e = launch_conv<16, EPI_DGELU>(a, s);
+    // layer 1 (no data gradient for the inputs)
+    w.x = c->x;
+    w.dz = c->dz1;
+    w.grad_w = c->g + c->off[0];
+    w.grad_b = c->g + c->off[1];
+    w.cin = c->cin;
+    w.cout = c->hidden;
+    if (e == cudaSuccess)
+        e = launch_wgrad(w, s);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    double l = 0.0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&l, c->dloss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return record_error(GBST_ECUDA, cudaGetErrorString(e));
+    *loss = c->loss_weight * l / static_cast<double>(n);
+    return GBST_OK;
+}
+
+gbst_status closure_set_out_scale(gbst_closure c, double out_scale)
+{
+    if (!c || !(out_scale > 0.0))
+        return record_error(GBST_EINVAL, "closure_set_out_scale: null closure or scale <= 0");
+    c->out_scale = out_scale;
+    return GBST_OK;
+}
+
+gbst_status closure_set_loss_weight(gbst_closure c, double w)
+{
+    if (!c || !(w > 0.0))
+        return record_error(GBST_EINVAL, "closure_set_loss_weight: null closure or weight <= 0");
+    c->loss_weight = w;
+    return GBST_OK;
+}
+
+gbst_status closure_freeze_biases(gbst_closure c, int freeze)
+{
+    if (!c)
+        return record_error(GBST_EINVAL, "closure_freeze_biases: null closure");
+    c->freeze_biases = freeze != 0;
+    return GBST_OK;
+}
+
+gbst_status closure_adam_step(gbst_closure c, double lr)
+{
+    if (!c || !(lr > 0.0))
+        return record_error(GBST_EINVAL, "closure_adam_step: null closure or lr <= 0");
+    c->t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float bc1 = static_cast<float>(1.0 - std::pow(0.9, static_cast<double>(c->t)));
+    const float bc2 = static_cast<float>(1.0 - std::pow(0.999, static_cast<double>(c->t)));
+    BiasRanges fr{};
+    for (int l = 0; l < 3; ++l) {
+        fr.lo[l] = c->freeze_biases ? static_cast<int>(c->off[2 * l + 1]) : 0;
+        fr.hi[l] = c->freeze_biases ? static_cast<int>(c->off[2 * l + 1] + c->cnt[2 * l + 1]) : 0;
+    }
+    k_adam<<<blocks_for(c->nparams), 256, 0, c->stream>>>(c->p, c->g, c->m1, c->m2, static_cast<int>(c->nparams),
+                                                          static_cast<float>(lr), b1, b2, static_cast<float>(1.0 - 0.9),
+                                                          static_cast<float>(1.0 - 0.999), 1e-8f, bc1, bc2, fr);
+    c->weights_dirty = true;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
+}
+
+}  // extern "C"

@@ -134,6 +134,12 @@ struct XferArgs {
 };
 cudaError_t launch_scatter(const XferArgs &x, cudaStream_t s);
 cudaError_t launch_gather(const XferArgs &x, cudaStream_t s);
+// padded[o] += dense (FP32 dense, storage F32 or BF16)
+cudaError_t launch_scatter_add(const XferArgs &x, cudaStream_t s);
+// dense[ (k/st*ceil(ny/st) + j/st) * ceil(nx/st) + i/st ] = padded(i, j, k) for i, j, k multiples of st
+cudaError_t launch_gather_strided(const XferArgs &x, int stride, cudaStream_t s);
+// c_norm = sqrt(kappa) * h / (dt * c_ref), dense FP32 from the padded kappa field
+cudaError_t launch_kappa_to_cnorm(const XferArgs &x, double factor, cudaStream_t s);
 
 // FP64 reductions.  kinds as GBST_RED_*.  Partials: one double per block.
 struct ReduceGrid {
@@ -147,6 +153,9 @@ cudaError_t launch_reduce_partials(int kind, int storage, int ndim, int R, const
                                    double *partials, int nblocks, cudaStream_t s);
 cudaError_t launch_reduce_final(int kind, const double *partials, int n, double *out,
                                 cudaStream_t s);
+
+// Stream a closure was created on.
+cudaStream_t closure_stream(gbst_closure c);
 
 // Record the message returned by stencil_last_error() for the calling thread.
 gbst_status record_error(gbst_status st, const char *msg);

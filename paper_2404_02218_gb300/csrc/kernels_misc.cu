@@ -151,6 +151,49 @@ __global__ void k_gather(const XferArgs x)
     }
 }
 
+__global__ void k_scatter_add(const XferArgs x)
+{
+    const int64_t n = x.nx * x.ny * x.nz;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = p % x.nx, j = (p / x.nx) % x.ny, k = p / (x.nx * x.ny);
+        const int64_t o = x.origin + (k * x.rows + j) * x.pitch + i;
+        const float v = static_cast<const float *>(x.dense)[p];
+        if (x.storage == GBST_BF16) {
+            __nv_bfloat16 *q = static_cast<__nv_bfloat16 *>(x.padded) + o;
+            *q = __float2bfloat16_rn(__bfloat162float(*q) + v);
+        } else {
+            static_cast<float *>(x.padded)[o] += v;
+        }
+    }
+}
+
+__global__ void k_gather_strided(const XferArgs x, int st)
+{
+    const int64_t mx = (x.nx + st - 1) / st, my = (x.ny + st - 1) / st, mz = (x.nz + st - 1) / st;
+    const int64_t n = mx * my * mz;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = (p % mx) * st, j = ((p / mx) % my) * st, k = (p / (mx * my)) * st;
+        const int64_t o = x.origin + (k * x.rows + j) * x.pitch + i;
+        static_cast<float *>(x.dense)[p] = x.storage == GBST_BF16
+                                               ? __bfloat162float(static_cast<const __nv_bfloat16 *>(x.padded)[o])
+                                               : static_cast<const float *>(x.padded)[o];
+    }
+}
+
+__global__ void k_kappa_to_cnorm(const XferArgs x, double factor)
+{
+    const int64_t n = x.nx * x.ny * x.nz;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = p % x.nx, j = (p / x.nx) % x.ny, k = p / (x.nx * x.ny);
+        const int64_t o = x.origin + (k * x.rows + j) * x.pitch + i;
+        const double kap = static_cast<const float *>(x.padded)[o];
+        static_cast<float *>(x.dense)[p] = static_cast<float>(sqrt(kap) * factor);
+    }
+}
+
 // ---------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
 
@@ -290,6 +333,25 @@ cudaError_t launch_scatter(const XferArgs &x, cudaStream_t s)
 cudaError_t launch_gather(const XferArgs &x, cudaStream_t s)
 {
     k_gather<<<grid_for(x.nx * x.ny * x.nz, 256, 8192), 256, 0, s>>>(x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_add(const XferArgs &x, cudaStream_t s)
+{
+    k_scatter_add<<<grid_for(x.nx * x.ny * x.nz, 256, 8192), 256, 0, s>>>(x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_strided(const XferArgs &x, int stride, cudaStream_t s)
+{
+    const int64_t n = ((x.nx + stride - 1) / stride) * ((x.ny + stride - 1) / stride) * ((x.nz + stride - 1) / stride);
+    k_gather_strided<<<grid_for(n, 256, 8192), 256, 0, s>>>(x, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kappa_to_cnorm(const XferArgs &x, double factor, cudaStream_t s)
+{
+    k_kappa_to_cnorm<<<grid_for(x.nx * x.ny * x.nz, 256, 8192), 256, 0, s>>>(x, factor);
     return cudaGetLastError();
 }
 

@@ -110,6 +110,20 @@ def lib() -> ctypes.CDLL:
                 "stencil_batch_reduce_f64": ([H, i32, i32, ctypes.POINTER(dbl)], i32),
                 "stencil_set_persistent": ([H, i32], i32),
                 "stencil_debug_barrier_extra": ([H, ctypes.c_uint], i32),
+                "closure_create": ([i32, i32, i64, dbl, vp, ctypes.POINTER(gbst_allocator), ctypes.POINTER(H)], i32),
+                "closure_destroy": ([H], i32),
+                "closure_param_count": ([H, ctypes.POINTER(i64)], i32),
+                "closure_set_params": ([H, vp, i64], i32),
+                "closure_get_params": ([H, vp, i64], i32),
+                "closure_get_grads": ([H, vp, i64], i32),
+                "closure_forward": ([H, vp, vp, vp, i64, i64, i64, vp], i32),
+                "closure_loss_grad": ([H, vp, vp, vp, vp, i64, i64, i64, ctypes.POINTER(dbl)], i32),
+                "closure_adam_step": ([H, dbl], i32),
+                "closure_set_out_scale": ([H, dbl], i32),
+                "closure_freeze_biases": ([H, i32], i32),
+                "closure_set_loss_weight": ([H, dbl], i32),
+                "stencil_attach_closure": ([H, H, dbl], i32),
+                "stencil_get_field_strided": ([H, i32, vp, i32], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -272,3 +286,72 @@ def stencil_set_persistent(h, enable: bool):
 
 def stencil_debug_barrier_extra(h, extra: int):
     _check(lib().stencil_debug_barrier_extra(h, int(extra)), "stencil_debug_barrier_extra")
+
+
+def closure_create(cin: int, hidden: int, max_points: int, in_scale: float, stream: int = 0, allocator=None):
+    h = ctypes.c_void_p()
+    _check(lib().closure_create(cin, hidden, int(max_points), float(in_scale), ctypes.c_void_p(stream),
+                                ctypes.pointer(allocator) if allocator is not None else None, ctypes.byref(h)),
+           "closure_create")
+    return h
+
+
+def closure_destroy(c):
+    _check(lib().closure_destroy(c), "closure_destroy")
+
+
+def closure_param_count(c) -> int:
+    n = ctypes.c_int64()
+    _check(lib().closure_param_count(c, ctypes.byref(n)), "closure_param_count")
+    return n.value
+
+
+def closure_set_params(c, host_ptr: int, n: int):
+    _check(lib().closure_set_params(c, ctypes.c_void_p(host_ptr), int(n)), "closure_set_params")
+
+
+def closure_get_params(c, host_ptr: int, n: int):
+    _check(lib().closure_get_params(c, ctypes.c_void_p(host_ptr), int(n)), "closure_get_params")
+
+
+def closure_get_grads(c, host_ptr: int, n: int):
+    _check(lib().closure_get_grads(c, ctypes.c_void_p(host_ptr), int(n)), "closure_get_grads")
+
+
+def closure_forward(c, up: int, un: int, cn: int, dims, corr: int):
+    nx, ny, nz = dims
+    _check(lib().closure_forward(c, ctypes.c_void_p(up), ctypes.c_void_p(un), ctypes.c_void_p(cn), nx, ny, nz,
+                                 ctypes.c_void_p(corr)), "closure_forward")
+
+
+def closure_loss_grad(c, up: int, un: int, cn: int, ref: int, dims) -> float:
+    nx, ny, nz = dims
+    v = ctypes.c_double()
+    _check(lib().closure_loss_grad(c, ctypes.c_void_p(up), ctypes.c_void_p(un), ctypes.c_void_p(cn),
+                                   ctypes.c_void_p(ref), nx, ny, nz, ctypes.byref(v)), "closure_loss_grad")
+    return v.value
+
+
+def closure_adam_step(c, lr: float):
+    _check(lib().closure_adam_step(c, float(lr)), "closure_adam_step")
+
+
+def stencil_attach_closure(h, c, c_ref: float):
+    _check(lib().stencil_attach_closure(h, c, float(c_ref)), "stencil_attach_closure")
+
+
+def stencil_get_field_strided(h, field: int, dst_ptr: int, stride: int):
+    _check(lib().stencil_get_field_strided(h, field, ctypes.c_void_p(dst_ptr), int(stride)),
+           "stencil_get_field_strided")
+
+
+def closure_set_out_scale(c, v: float):
+    _check(lib().closure_set_out_scale(c, float(v)), "closure_set_out_scale")
+
+
+def closure_freeze_biases(c, freeze: bool):
+    _check(lib().closure_freeze_biases(c, int(freeze)), "closure_freeze_biases")
+
+
+def closure_set_loss_weight(c, w: float):
+    _check(lib().closure_set_loss_weight(c, float(w)), "closure_set_loss_weight")
