@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true",
-                   help="skip the secondary measurements (decomposition, wave FP32/BF16, batch)")
+                   help="skip the secondary measurements (decomposition, wave FP32/BF16, batch, closure)")
     p.add_argument("--n", type=int, default=1024, help="grid edge (profiling runs use a smaller cube)")
     p.add_argument("--sos", default="2,4,8", help="space orders to run (profiling runs use one)")
     p.add_argument("--tune", default="on", choices=["on", "cache", "off"],
@@ -285,6 +285,32 @@ def extras(torch, hbm: float, tune: bool):
                                                 "launches_per_run": 64 * nsteps}
     for g in singles:
         g.close()
+    del singles
+
+    # learned closure: 256^3 coarse / 512^3 fine, order 4, trained on four seeded models,
+    # evaluated on a fifth against the restricted fine solution up to step 400
+    from paper_2404_02218_gb300.closure import PairConfig, evaluate, new_closure, train
+    cfg = PairConfig(nc=256, steps=400)
+    t0 = time.time()
+    cl = new_closure(cfg, cfg.nc ** 3)
+    losses = train(cl, (10, 11, 12, 13), cfg, lr=2e-3, epochs=1)
+    t_train = time.time() - t0
+    res = evaluate(cl, 99, cfg, checkpoints=(50, 100, 150, 200, 300))
+    # forward throughput of the three convolutions at 256^3 (padded and useful FLOPs)
+    n3 = cfg.nc ** 3
+    up = torch.randn((cfg.nc,) * 3, device="cuda") * 0.1
+    cn = torch.full((cfg.nc,) * 3, 0.6, device="cuda")
+    torch.cuda.synchronize()
+    ms = timed_runs(torch, cl.stream, lambda: cl.forward(up, up, cn), reps=10)
+    padded = 27 * 2 * (16 * 16 + 16 * 16 + 16 * 8)
+    useful = 27 * 2 * (4 * 16 + 16 * 16 + 16 * 1)
+    bf16 = measured_peaks()[0].get("bf16_tflops", 1900.0)
+    res.update({"train_seconds": t_train, "updates": len(losses), "forward_ms_256": ms,
+                "forward_tflops_padded": padded * n3 / ms / 1e9, "forward_tflops_useful": useful * n3 / ms / 1e9,
+                "forward_frac_of_bf16_peak": padded * n3 / ms / 1e9 / bf16,
+                "kernel": "mma.sync m16n8k16 BF16 (FP32 accumulate)"})
+    out["closure_256_so4"] = res
+    cl.close()
     return out
 
 # -------------------------------------------------------------- our path ---

@@ -380,7 +380,7 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
     for (size_t i = 0; i < h->subs.size(); ++i) {
         GridDev &g = h->hgrids[i];
         const Sub &s = h->subs[i];
-        g.txt = txt;
+        g.txt = p.txt;
         g.tiles_x = static_cast<int>((s.lu.nx + TX - 1) / TX);
         g.tiles_y = static_cast<int>((s.lu.ny + TY - 1) / TY);
         g.box_bytes = p.max_box_bytes;
@@ -390,6 +390,13 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
             for (int b = 0; b < 2; ++b)
                 if (!encode_tmap(&g.tmap[b], g.buf[b], s.lu, st, box_w, box_h, &err))
                     return fail(GBST_ECUDA, "%s", err.c_str());
+            if (h->d.eq == GBST_WAVE) {
+                for (int b = 0; b < 2; ++b)
+                    if (!encode_tmap(&g.tmap_c[b], g.buf[b], s.lu, st, TX, TY, &err))
+                        return fail(GBST_ECUDA, "%s", err.c_str());
+                if (!encode_tmap(&g.tmap_k, g.kappa, s.lk, GBST_F32, TX, TY, &err))
+                    return fail(GBST_ECUDA, "%s", err.c_str());
+            }
         }
     }
     if (p.stream) {

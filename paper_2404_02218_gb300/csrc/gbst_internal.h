@@ -46,6 +46,8 @@ Layout make_layout(int ndim, int64_t nx, int64_t ny, int64_t nz, int r, int elem
 // the tensor maps must be 64-byte aligned.
 struct alignas(128) GridDev {
     CUtensorMap tmap[2];   // TMA descriptors of u buffers 0 and 1 (box = tile + halo)
+    CUtensorMap tmap_c[2]; // wave: u buffers 0 and 1, interior boxes (tile only)
+    CUtensorMap tmap_k;    // wave: kappa, interior boxes
     void *buf[2];          // u buffers (padded, storage type)
     float *kappa;          // wave: kappa (padded FP32 layout `klay`), else null
     int64_t nx, ny, nz;    // interior
@@ -100,6 +102,8 @@ inline int px_of(int storage) { return storage == GBST_BF16 ? 8 : 4; }
 
 // Shared-memory bytes of the streaming kernel for the given variant and max box size.
 size_t stream_smem_bytes(const StreamVariant &v, int max_box_bytes);
+// Plane-slot bytes of a launch with `smem` bytes of shared memory.
+int stream_slot_bytes(const StreamVariant &v, size_t smem);
 // Launch the streaming (TMA, 2.5D) sweep.  Returns cudaSuccess or the launch error.
 cudaError_t launch_stream_sweep(const StreamVariant &v, const SweepArgs &a, int ctas, size_t smem,
                                 cudaStream_t s, bool cooperative = false);

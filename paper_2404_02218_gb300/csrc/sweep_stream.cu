@@ -79,12 +79,30 @@ bool stream_variant_get(int i, StreamVariant *v)
     return true;
 }
 
+// Wave: per barrier pair, kappa (FP32) and u^{n-1} of the centre plane (tile only).
+static size_t centre_bytes(const StreamVariant &v)
+{
+    if (v.eq != GBST_WAVE)
+        return 0;
+    const int px = px_of(v.storage), es = v.storage == GBST_BF16 ? 2 : 4;
+    const size_t tx = static_cast<size_t>(v.txt) * px, ty = static_cast<size_t>(v.nthreads / v.txt) * v.py;
+    const size_t slot = (tx * ty * (4 + es) + 127) / 128 * 128;
+    return slot * (v.depth + 1);
+}
+
 size_t stream_smem_bytes(const StreamVariant &v, int max_box_bytes)
 {
     const int rz = v.has_z ? v.R : 0;
     const int slots = rz + 1 + v.depth;
     const size_t slot = (static_cast<size_t>(max_box_bytes) + 127) / 128 * 128;
-    return 256 + slots * slot;
+    return 256 + slots * slot + centre_bytes(v);
+}
+
+int stream_slot_bytes(const StreamVariant &v, size_t smem)
+{
+    const int rz = v.has_z ? v.R : 0;
+    const int slots = rz + 1 + v.depth;
+    return static_cast<int>((smem - 256 - centre_bytes(v)) / slots);
 }
 
 int stream_occupancy(const StreamVariant &v, size_t smem)
@@ -104,9 +122,7 @@ cudaError_t launch_stream_sweep(const StreamVariant &v, const SweepArgs &a, int 
     const Entry *e = find(v);
     if (!e)
         return cudaErrorInvalidDeviceFunction;
-    const int rz = v.has_z ? v.R : 0;
-    const int slots = rz + 1 + v.depth;
-    const int slot_bytes = static_cast<int>((smem - 256) / slots);
+    const int slot_bytes = stream_slot_bytes(v, smem);
     if (!cooperative) {
         e->fn<<<ctas, v.nthreads + 32, smem, s>>>(a, slot_bytes);
         return cudaGetLastError();

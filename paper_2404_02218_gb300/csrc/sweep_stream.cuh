@@ -141,11 +141,6 @@ struct Storage<GBST_BF16> {
     }
 };
 
-__device__ __forceinline__ float4 ldg_f4_nc(const float *p)
-{
-    return __ldg(reinterpret_cast<const float4 *>(p));
-}
-
 // x-halo loads narrowed to the r elements next to the thread's column: the
 // returned 16-byte chunk holds them at their natural positions (zero elsewhere).
 template <int ST, int R>
@@ -257,6 +252,10 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
     constexpr int TX = TXT * PX;                 // tile width (points)
     constexpr int TY = (NT / TXT) * PY;          // tile height (rows)
     constexpr int ROW_BYTES = (TX + 2 * G) * ES; // one row of a plane slot
+    // wave: kappa (FP32) and u^{n-1} of the centre plane, TX x TY each, per barrier pair
+    constexpr int CK = TX * TY * 4;
+    constexpr int CBYTES = CK + TX * TY * ES;
+    constexpr int CSLOT = EQ == GBST_WAVE ? (CBYTES + 127) / 128 * 128 : 0;
     static_assert(R <= G, "x halo must cover the radius");
     static_assert(2 * NB * 8 + 16 <= 256, "barrier header");
     static_assert(NT % TXT == 0, "tile shape");
@@ -266,6 +265,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
     uint64_t *empty = full + NB;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NB);
     unsigned char *slots = smem + 256;
+    unsigned char *cslots = slots + S * slot_bytes;  // wave centre-plane slots (NB of CSLOT bytes)
 
     // (a CTA without units still joins the grid barriers of a persistent launch)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -293,13 +293,24 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
             const GridDev &g = a.grids[u.grid];
             const int bx = (u.tile % g.tiles_x) * TX, by = (u.tile / g.tiles_x) * TY;
             const CUtensorMap *map = &g.tmap[parity];
+            const CUtensorMap *umap = &g.tmap_c[1 - parity];  // u^{n-1}, interior boxes
+            const CUtensorMap *kmap = &g.tmap_k;              // kappa, interior boxes
             const uint32_t bytes = static_cast<uint32_t>(g.box_bytes);
             const int L = (u.z1 - u.z0) + 2 * RZ;
             for (int l = 0; l < L; ++l, ++it) {
                 if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
                     return false;
-                mbar_arrive_expect_tx(&full[it % NB], bytes);
-                tma_load_plane(slots + (it % S) * slot_bytes, map, &full[it % NB], bx, by, u.z0 + l);
+                const bool centre = EQ == GBST_WAVE && l >= 2 * RZ;
+                uint64_t *bar = &full[it % NB];
+                mbar_arrive_expect_tx(bar, bytes + (centre ? CBYTES : 0));
+                tma_load_plane(slots + (it % S) * slot_bytes, map, bar, bx, by, u.z0 + l);
+                if (centre) {
+                    // centre plane of this iteration: interior z = z0 + l - 2rz, padded + rz
+                    unsigned char *cs = cslots + (it % NB) * CSLOT;
+                    const int zp = u.z0 + l - RZ;
+                    tma_load_plane(cs, kmap, bar, bx + G, by + R, zp);
+                    tma_load_plane(cs + CK, umap, bar, bx + G, by + R, zp);
+                }
             }
         }
         return true;
@@ -335,8 +346,6 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
             const int tiles_x = gp->tiles_x;
             const int64_t nx = gp->nx, ny = gp->ny;
             const int64_t pitch = gp->pitch, rows = gp->rows, origin = gp->origin;
-            const int64_t kpitch = gp->kpitch, krows = gp->krows, korigin = gp->korigin;
-            const float *__restrict__ kappa = gp->kappa;
             unsigned char *__restrict__ outbase = static_cast<unsigned char *>(gp->buf[1 - parity]);
             const bool src_unit = (EQ == GBST_WAVE) && gp->has_src;
             const int src_x = gp->src_x, src_y = gp->src_y, src_z = gp->src_z;
@@ -353,9 +362,8 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
             for (int r_ = 0; r_ < PY; ++r_)
                 row_ok[r_] = y0 + r_ < ny && x0 < nx;
             // running pointers to the thread's first row of the current output plane
-            const int64_t plane_elems = rows * pitch, kplane = krows * kpitch;
+            const int64_t plane_elems = rows * pitch;
             unsigned char *optr = outbase + (origin + (static_cast<int64_t>(u.z0) * rows + y0) * pitch + x0) * ES;
-            const float *kptr = kappa + korigin + (static_cast<int64_t>(u.z0) * krows + y0) * kpitch + x0;
             const int64_t row_stride = pitch * ES;
 
             // prologue: the 2*rz planes below the first output plane fill the queue
@@ -387,31 +395,29 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                         const int qc = (k + RZ) % QN;      // slot of the centre plane
                         const int zc = u.z0 + c;
 
-                        // Wave: kappa and u- of the centre plane, issued before waiting on the TMA.
                         float kap[PY][PX], um[PY][PX];
+                        if (!wait_or_abort(&full[bar_i], par, abort_flag))
+                            return false;
                         if (EQ == GBST_WAVE) {
+                            // kappa and u^{n-1} of the centre plane, landed with this iteration's TMA
+                            const unsigned char *cs = cslots + bar_i * CSLOT;
     #pragma unroll
                             for (int r_ = 0; r_ < PY; ++r_) {
-                                const float *kp = kptr + r_ * kpitch;
-                                const unsigned char *up = optr + r_ * row_stride;
+                                const int e = (ty * PY + r_) * TX + tx * PX;
     #pragma unroll
                                 for (int v = 0; v < PX / 4; ++v) {
-                                    const float4 kv = row_ok[r_] ? ldg_f4_nc(kp + 4 * v) : make_float4(0, 0, 0, 0);
-                                    kap[r_][4 * v + 0] = kv.x;
-                                    kap[r_][4 * v + 1] = kv.y;
-                                    kap[r_][4 * v + 2] = kv.z;
-                                    kap[r_][4 * v + 3] = kv.w;
+                                    const uint4 kv = lds128(cs + (e + 4 * v) * 4);
+                                    kap[r_][4 * v + 0] = __uint_as_float(kv.x);
+                                    kap[r_][4 * v + 1] = __uint_as_float(kv.y);
+                                    kap[r_][4 * v + 2] = __uint_as_float(kv.z);
+                                    kap[r_][4 * v + 3] = __uint_as_float(kv.w);
                                 }
-                                const uint4 uv =
-                                    row_ok[r_] ? __ldcs(reinterpret_cast<const uint4 *>(up)) : make_uint4(0, 0, 0, 0);
+                                const uint4 uv = lds128(cs + CK + e * ES);
     #pragma unroll
                                 for (int i = 0; i < PX; ++i)
                                     um[r_][i] = St::get(uv, i);
                             }
                         }
-
-                        if (!wait_or_abort(&full[bar_i], par, abort_flag))
-                            return false;
                         {
                             const unsigned char *nb = slots + slot_n * slot_bytes + own_off;
     #pragma unroll
@@ -529,7 +535,6 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                             }
                         }
                         optr += plane_elems * ES;
-                        kptr += kplane;
                     }
                 }
             }
