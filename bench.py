@@ -61,6 +61,10 @@ def parse():
                    help="skip the secondary measurements (decomposition, wave FP32/BF16, batch, closure)")
     p.add_argument("--n", type=int, default=1024, help="grid edge (profiling runs use a smaller cube)")
     p.add_argument("--sos", default="2,4,8", help="space orders to run (profiling runs use one)")
+    p.add_argument("--case", default=None, choices=["wave3d_f32", "wave3d_bf16", "closure"],
+                   help="run one small named case instead of the bench (for profiler captures): "
+                        "the order-8 layered wave at --n^3 in FP32 or BF16 storage, or the closure "
+                        "network's forward pass at --n^3; prints one timing line")
     p.add_argument("--tune", default="on", choices=["on", "cache", "off"],
                    help="on: autotune each kernel before timing; cache: use plans cached in "
                         "GBST_TUNE_CACHE (no tuning launches); off: default plans")
@@ -313,25 +317,71 @@ def extras(torch, hbm: float, tune: bool):
     cl.close()
     return out
 
+def run_case(args):
+    """One small named case, for profiler captures (not a bench line)."""
+    import torch
+    import synthetic
+    from paper_2404_02218_gb300.grid import Grid
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    n = N
+    if args.case.startswith("wave3d"):
+        st = args.case.split("_")[1]
+        wc = synthetic.wave3d(n)
+        c = torch.from_numpy(synthetic.layered_velocity((n, n, n), wc.speeds)).cuda()
+        g = Grid(3, wc.dims, 8, "wave", h=wc.h, dt=wc.dt, storage=st, stream=stream)
+        g.set_field("vel", c)
+        g.set_source(wc.src, wc.f0, wc.t0, wc.amp)
+        if args.tune == "on":
+            g.tune(reps=2)
+        fn, pts = (lambda: g.run(10)), 10 * n ** 3
+    else:
+        from paper_2404_02218_gb300.closure import Closure, init_params
+        cl = Closure(n ** 3, 1.0)
+        cl.set_params(init_params(seed=5))
+        up = synthetic.uniform_field_torch(5, (n, n, n), "cuda") - 0.5
+        cn = torch.full((n, n, n), 0.6, device="cuda")
+        fn, pts = (lambda: cl.forward(up, up, cn)), n ** 3
+        stream = cl.stream
+    for _ in range(max(3, args.warmup)):
+        fn()
+    ms = timed_runs(torch, stream, fn, reps=max(1, args.steps))
+    print(json.dumps({"case": args.case, "n": n, "ms_per_run": ms, "gpts": pts / ms / 1e6}), flush=True)
+    return 0
+
+
 # -------------------------------------------------------------- our path ---
+KERNEL_SOURCES = ("sweep_stream.cuh", "sweep_r1.cu", "sweep_r2.cu", "sweep_r4.cu", "gbst_internal.h")
+
+
 def kernel_source_sha() -> str:
+    """Hash of the sweep kernel's sources; a traffic figure is used only for this exact source."""
     h = hashlib.sha256()
-    for f in ("sweep_stream.cu", "gbst_internal.h"):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2404_02218_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+def ncu_traffic(kernel_key: str, plan: dict):
+    """DRAM bytes per launch from the committed ncu traffic summary, if it was taken on the
+    current kernel source with the same plan (variant and z-chunking).
+
+    The summary's table rows read ``| key | source sha | dram bytes per launch | variant | zchunks | ...``."""
+    path = os.path.join(ROOT, "profiles", "sweep_dram_traffic.md")
     try:
-        d = json.load(open(path))
-    except (OSError, ValueError):
+        lines = open(path).read().splitlines()
+    except OSError:
         return None
-    e = d.get(kernel_key)
-    if not e or e.get("source_sha") != kernel_source_sha():
-        return None
-    return e.get("dram_bytes_per_launch")
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) >= 5 and cells[0] == kernel_key and cells[1] == kernel_source_sha():
+            try:
+                if int(cells[3]) != plan.get("variant") or int(cells[4]) != plan.get("zchunks"):
+                    return None
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
 
 
 def measured_peaks():
@@ -413,7 +463,7 @@ def run_ours(args):
         per[f"heat3d_so{so}"] = {"gpts": N ** 3 / avg / 1e9, "gbs": gbs, "frac": gbs / hbm,
                                  "avg_launch_ms": avg * 1e3, "plan": json.loads(g.describe())}
     dom = max(per, key=lambda k: per[k]["avg_launch_ms"])
-    traffic = ncu_traffic(dom)
+    traffic = ncu_traffic(dom, per[dom]["plan"])
     roofline = {"bound": "hbm", "achieved": per[dom]["gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": per[dom]["gbs"] / hbm, "traffic": traffic, "kernel": dom,
                 "algorithmic_bytes_per_launch": BYTES_PER_PT * N ** 3, "peak_source": peak_kind}
@@ -488,6 +538,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
     return run_ours(args)
 
 

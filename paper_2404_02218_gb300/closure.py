@@ -218,8 +218,8 @@ def zero_biases(flat: np.ndarray, cin: int = 4, hidden: int = 16) -> np.ndarray:
     return flatten_params(p)
 
 
-def correction_scale(seed: int, cfg: PairConfig, quantile: float = 0.999) -> float:
-    """1 / (the `quantile` of |u_ref - u+| over nonzero points) along one trajectory."""
+def correction_scale(seed: int, cfg: PairConfig, quantile: float = 0.999, n_start: int = 0) -> float:
+    """1 / (the `quantile` of the per-step max |u_ref - u+|) over steps >= n_start of one trajectory."""
     import torch
     pair = FineCoarsePair(seed, cfg)
     shp = (pair.nc,) * 3
@@ -232,7 +232,7 @@ def correction_scale(seed: int, cfg: PairConfig, quantile: float = 0.999) -> flo
         coarse_step(pair, r_cur, r_prev, n, up)
         pair.fine.run(2)
         pair.restrict(r_next)
-        if n % 4 == 0:
+        if n % 4 == 0 and n >= n_start:
             d = (r_next - up).abs().flatten()
             vals.append(float(d.max()))
         r_prev, r_cur, r_next = r_cur, r_next, r_prev
@@ -242,9 +242,12 @@ def correction_scale(seed: int, cfg: PairConfig, quantile: float = 0.999) -> flo
 
 
 def train(closure: Closure, seeds, cfg: PairConfig, lr: float = 2e-3, epochs: int = 1, lr_final: float = None,
-          crop: int = 0, updates_per_step: int = 1, seed: int = 0, normalise: bool = False, log=None):
+          crop: int = 0, updates_per_step: int = 1, seed: int = 0, normalise: bool = False, n_start: int = 1,
+          log=None):
     """Train on one-step corrections along fine trajectories (teacher forcing).
 
+    Updates use coarse steps n >= max(1, n_start) (the trajectory before is
+    replayed without updates).
     Every epoch replays each seed's fine trajectory (cheap next to the network,
     so no samples are stored); at each coarse step the plain coarse step from the
     restricted fine state is compared with the restricted next fine state.  With
@@ -255,7 +258,8 @@ def train(closure: Closure, seeds, cfg: PairConfig, lr: float = 2e-3, epochs: in
     import torch
     losses = []
     t0 = time.time()
-    total = max(1, epochs * len(seeds) * cfg.steps * updates_per_step)
+    n_start = max(1, n_start)
+    total = max(1, epochs * len(seeds) * (cfg.steps - n_start) * updates_per_step)
     lr_final = lr / 20 if lr_final is None else lr_final
     rng = np.random.default_rng(seed)
     k = 0
@@ -272,7 +276,7 @@ def train(closure: Closure, seeds, cfg: PairConfig, lr: float = 2e-3, epochs: in
                 coarse_step(pair, r_cur, r_prev, n, up)
                 pair.fine.run(2)
                 pair.restrict(r_next)
-                if n > 0:
+                if n >= n_start:
                     for _ in range(updates_per_step):
                         if w < pair.nc:
                             o = rng.integers(0, pair.nc - w + 1, size=3)
@@ -314,10 +318,12 @@ def init_params(cin: int = 4, hidden: int = 16, seed: int = 5) -> np.ndarray:
 
 
 def new_closure(cfg: PairConfig, max_points: int, scale_seed: int = 10, init_seed: int = 5,
-                stream=None) -> Closure:
-    """A closure with data-derived input/output scales, zero last layer and zero, frozen biases."""
+                stream=None, n_start: int = 0) -> Closure:
+    """A closure with data-derived input/output scales, zero last layer and zero, frozen biases.
+
+    The output scale comes from the one-step corrections of steps >= n_start."""
     s = field_scale(scale_seed, cfg)
-    t = correction_scale(scale_seed, cfg)
+    t = correction_scale(scale_seed, cfg, n_start=n_start)
     cl = Closure(max_points, s, stream=stream)
     cl.set_out_scale(t)
     cl.freeze_biases(True)
@@ -329,21 +335,23 @@ def rel_l2(a, b) -> float:
     return float((a - b).norm() / b.norm())
 
 
-def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None):
+def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, attach_at: int = 0):
     """Plain coarse, closure-corrected coarse and restricted fine solutions.
 
     Returns the relative L2 errors (vs the restricted fine solution) at the
     last step, the gain err_plain / err_closure, wall times of the three solves,
-    and the errors at the intermediate checkpoints.
+    and the errors at the intermediate checkpoints.  The closure corrects steps
+    n >= attach_at (before, the corrected run is the plain coarse run).
     """
     import torch
-    checkpoints = sorted(set(list(checkpoints or []) + [cfg.steps]))
+    checkpoints = sorted(set(list(checkpoints or []) + [cfg.steps] + ([attach_at] if attach_at > 0 else [])))
     pair = FineCoarsePair(seed, cfg)
     shp = (pair.nc,) * 3
     g = Grid(3, shp, cfg.so, "wave", h=2 * cfg.hf, dt=pair.dtc, stream=closure.stream)
     g.set_field("vel", pair.cc)
     g.set_source(pair.src_c, cfg.f0, 1.0 / cfg.f0, 1.0 / 8.0)
-    N.stencil_attach_closure(g.h, closure.h, C_REF)
+    if attach_at <= 0:
+        N.stencil_attach_closure(g.h, closure.h, C_REF)
     ref = torch.empty(shp, dtype=torch.float32, device="cuda")
     u_plain = torch.empty(shp, dtype=torch.float32, device="cuda")
     u_cl = torch.empty(shp, dtype=torch.float32, device="cuda")
@@ -366,6 +374,8 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None):
         g.sync()
         t_cl += time.perf_counter() - t0
         done = cp
+        if cp == attach_at:
+            N.stencil_attach_closure(g.h, closure.h, C_REF)
         pair.restrict(ref)
         pair.coarse.get_field("u", out=u_plain)
         g.get_field("u", out=u_cl)
@@ -373,7 +383,7 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None):
     e_plain, e_cl = curve[cfg.steps]
     out = {"rel_l2_plain_coarse": e_plain, "rel_l2_closure": e_cl, "gain": e_plain / e_cl,
            "seconds_fine": t_fine, "seconds_plain_coarse": t_plain, "seconds_closure": t_cl,
-           "steps": cfg.steps, "coarse": pair.nc, "fine": pair.nf,
+           "steps": cfg.steps, "coarse": pair.nc, "fine": pair.nf, "attach_at": attach_at,
            "curve": {str(k): {"plain": v[0], "closure": v[1]} for k, v in curve.items()}}
     g.close()
     pair.close()
