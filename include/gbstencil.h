@@ -87,6 +87,11 @@ typedef struct gbst_desc {
     int use_graph;         /* 0: direct launches; 1: capture the step loop as a CUDA graph */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
     const gbst_allocator *allocator; /* NULL = cudaMalloc / cudaFree */
+    int temporal_block;    /* heat, FP32, 3D, zero ghosts, no decomposition only:
+                              0 = automatic (single steps by default; stencil_tune may pick
+                              two-step blocking), 1 = off, 2 = two time steps per pass over
+                              memory (overlapped temporal blocking; results are bit-identical to
+                              single steps; afterwards GBST_U_PREV does not hold u^{n-1}) */
 } gbst_desc;
 
 typedef struct gbst_grid_s *gbst_handle;

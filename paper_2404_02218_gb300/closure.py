@@ -335,16 +335,19 @@ def rel_l2(a, b) -> float:
     return float((a - b).norm() / b.norm())
 
 
-def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, attach_at: int = 0):
+def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, attach_at: int = 0,
+             detach_at: int | None = None):
     """Plain coarse, closure-corrected coarse and restricted fine solutions.
 
     Returns the relative L2 errors (vs the restricted fine solution) at the
     last step, the gain err_plain / err_closure, wall times of the three solves,
     and the errors at the intermediate checkpoints.  The closure corrects steps
-    n >= attach_at (before, the corrected run is the plain coarse run).
+    attach_at <= n < detach_at (outside that window the corrected run takes plain
+    coarse steps).
     """
     import torch
-    checkpoints = sorted(set(list(checkpoints or []) + [cfg.steps] + ([attach_at] if attach_at > 0 else [])))
+    extra = ([attach_at] if attach_at > 0 else []) + ([detach_at] if detach_at else [])
+    checkpoints = sorted(set(list(checkpoints or []) + [cfg.steps] + extra))
     pair = FineCoarsePair(seed, cfg)
     shp = (pair.nc,) * 3
     g = Grid(3, shp, cfg.so, "wave", h=2 * cfg.hf, dt=pair.dtc, stream=closure.stream)
@@ -376,6 +379,8 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, att
         done = cp
         if cp == attach_at:
             N.stencil_attach_closure(g.h, closure.h, C_REF)
+        if detach_at and cp == detach_at:
+            N.stencil_attach_closure(g.h, None, C_REF)
         pair.restrict(ref)
         pair.coarse.get_field("u", out=u_plain)
         g.get_field("u", out=u_cl)
@@ -383,7 +388,7 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, att
     e_plain, e_cl = curve[cfg.steps]
     out = {"rel_l2_plain_coarse": e_plain, "rel_l2_closure": e_cl, "gain": e_plain / e_cl,
            "seconds_fine": t_fine, "seconds_plain_coarse": t_plain, "seconds_closure": t_cl,
-           "steps": cfg.steps, "coarse": pair.nc, "fine": pair.nf, "attach_at": attach_at,
+           "steps": cfg.steps, "coarse": pair.nc, "fine": pair.nf, "attach_at": attach_at, "detach_at": detach_at,
            "curve": {str(k): {"plain": v[0], "closure": v[1]} for k, v in curve.items()}}
     g.close()
     pair.close()

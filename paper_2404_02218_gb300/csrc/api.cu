@@ -335,11 +335,27 @@ void destroy_graphs(gbst_handle h)
 
 // ---- plan: tiles, TMA boxes, work units ----------------------------------
 // Index of the first streaming variant matching the handle (the default), or -1.
+// Two-step (temporally blocked) sweeps need a heat grid in FP32, 3D, with zero
+// ghosts and no halo exchange between steps.
+bool tb_allowed(gbst_handle h)
+{
+    return h->d.temporal_block != 1 && h->d.eq == GBST_HEAT && h->d.storage == GBST_F32 && h->ndim == 3 &&
+           h->d.bc == GBST_BC_ZERO && h->nboxes == 0 && h->d.kernel != GBST_KERNEL_SIMPLE;
+}
+
+bool variant_matches(gbst_handle h, const StreamVariant &v)
+{
+    if (v.R != h->R || v.eq != h->d.eq || v.storage != h->d.storage || v.has_z != (h->ndim == 3))
+        return false;
+    return v.tb == 1 || tb_allowed(h);
+}
+
 int default_variant(gbst_handle h)
 {
     StreamVariant v;
+    const int want_tb = h->d.temporal_block == 2 && tb_allowed(h) ? 2 : 1;
     for (int i = 0; stream_variant_get(i, &v); ++i)
-        if (v.R == h->R && v.eq == h->d.eq && v.storage == h->d.storage && v.has_z == (h->ndim == 3))
+        if (variant_matches(h, v) && v.tb == want_tb)
             return i;
     return -1;
 }
@@ -358,7 +374,7 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
     if (p.stream) {
         if (!stream_variant_get(variant, &p.var))
             return fail(GBST_EINVAL, "unknown kernel variant %d", variant);
-        if (p.var.R != h->R || p.var.eq != h->d.eq || p.var.storage != st || p.var.has_z != (h->ndim == 3))
+        if (!variant_matches(h, p.var))
             return fail(GBST_EINVAL, "kernel variant %d does not match this grid", variant);
         p.variant = variant;
     } else {
@@ -370,8 +386,10 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
         p.var.txt = 8;
     (void)txt;
     p.txt = p.var.txt;
-    const int TX = p.txt * px, TY = (nt / p.txt) * p.var.py;
-    const int box_w = TX + 2 * G, box_h = TY + 2 * h->R;
+    (void)nt;
+    const int TX = tile_w(p.var, px), TY = tile_h(p.var);
+    // two-step variants read the tile plus 2 chunks in x and 2r rows in y per side
+    const int box_w = TX + 2 * G * p.var.tb, box_h = TY + 2 * h->R * p.var.tb;
     if (box_w > 256 || box_h > 256)
         return fail(GBST_EINVAL, "tile %dx%d too large for a TMA box", TX, TY);
     p.max_box_bytes = box_w * box_h * h->es;
@@ -416,7 +434,7 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
                 for (int c = 1; c <= 64 && nz / c >= 2 * h->R + 1; ++c) {
                     const int64_t units = T * c;
                     const int64_t waves = (units + cmax - 1) / cmax;
-                    const double cost = static_cast<double>(waves) * ((nz + c - 1) / c + 2 * h->R);
+                    const double cost = static_cast<double>(waves) * ((nz + c - 1) / c + 2 * h->R * p.var.tb);
                     if (cost < best * 0.999) {
                         best = cost;
                         zc = c;
@@ -658,8 +676,9 @@ SweepArgs sweep_args(gbst_handle h, int parity, const float *srcval)
     return a;
 }
 
-// Enqueue one time step (halo copies + sweep) at the given parity.
-gbst_status enqueue_step(gbst_handle h, int parity, const float *srcval, int prof_index)
+// Enqueue one sweep launch (halo copies + sweep) at the given parity: one time
+// step, or two with a temporally blocked plan unless `single`.
+gbst_status enqueue_step(gbst_handle h, int parity, const float *srcval, int prof_index, bool single = false)
 {
     if (h->nboxes > 0) {
         cudaError_t e =
@@ -667,7 +686,8 @@ gbst_status enqueue_step(gbst_handle h, int parity, const float *srcval, int pro
         if (e != cudaSuccess)
             return fail(GBST_ECUDA, "halo copy launch: %s", cudaGetErrorString(e));
     }
-    const SweepArgs a = sweep_args(h, parity, srcval);
+    SweepArgs a = sweep_args(h, parity, srcval);
+    a.tb_single = single ? 1 : 0;
     if (prof_index >= 0)
         GBST_CUDA(cudaEventRecordWithFlags(h->prof_ev[2 * prof_index], h->stream,
                                            cudaEventRecordExternal));
@@ -789,6 +809,8 @@ gbst_status validate_desc(const gbst_desc &d, int64_t dims[3], int decomp[3])
         return fail(GBST_EINVAL, "storage must be GBST_F32 or GBST_BF16");
     if (d.kernel < GBST_KERNEL_AUTO || d.kernel > GBST_KERNEL_SIMPLE)
         return fail(GBST_EINVAL, "kernel must be GBST_KERNEL_AUTO, _STREAM or _SIMPLE");
+    if (d.temporal_block < 0 || d.temporal_block > 2)
+        return fail(GBST_EINVAL, "temporal_block must be 0 (automatic), 1 (off) or 2");
     const int R = d.space_order / 2;
     dims[0] = d.dims[0];
     dims[1] = d.dims[1];
@@ -990,7 +1012,9 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
     if (st != GBST_OK)
         return bail(st);
     TunedPlan tp{};
-    if (d.tile == 0 && d.kernel != GBST_KERNEL_SIMPLE && tune_cache_find(h, &tp))
+    StreamVariant cv;
+    if (d.tile == 0 && d.kernel != GBST_KERNEL_SIMPLE && tune_cache_find(h, &tp) &&
+        stream_variant_get(tp.variant, &cv) && variant_matches(h, cv))
         st = build_plan(h, tp.variant, tp.txt, tp.zchunks, tp.ctas);
     else
         st = build_plan(h, d.tile > 0 ? d.tile - 1 : -1, 0, 0, 0);
@@ -1415,23 +1439,27 @@ gbst_status stencil_run(gbst_handle h, int64_t nsteps)
         GBST_CUDA(cudaMemcpyAsync(h->dsrc, h->hsrc, nsteps * ns * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         GBST_CUDA(cudaEventRecord(h->src_ev, h->stream));
     }
-    const bool persistent = h->persistent && h->plan.stream && h->nboxes == 0;
+    const bool tb = h->plan.stream && h->plan.var.tb == 2;
+    const bool persistent = h->persistent && h->plan.stream && h->nboxes == 0 && !tb;
+    // sweep launches: one per step, or one per two steps (+ one single step if odd)
+    const int64_t launches = persistent ? 1 : (tb ? (nsteps + 1) / 2 : nsteps);
     if (h->profile) {
-        const int64_t need = persistent ? 2 : 2 * nsteps;
+        const int64_t need = 2 * launches;
         while (static_cast<int64_t>(h->prof_ev.size()) < need) {
             cudaEvent_t e;
             GBST_CUDA(cudaEventCreate(&e));
             h->prof_ev.push_back(e);
         }
-        h->prof_launches = persistent ? 1 : nsteps;
+        h->prof_launches = launches;
     }
     auto enqueue_all = [&]() -> gbst_status {
         if (persistent)
             return enqueue_persistent(h, nsteps, h->parity, src ? h->dsrc : nullptr, h->profile);
         int par = h->parity;
-        for (int64_t k = 0; k < nsteps; ++k) {
-            gbst_status s2 =
-                enqueue_step(h, par, src ? h->dsrc + k * ns : nullptr, h->profile ? static_cast<int>(k) : -1);
+        for (int64_t k = 0; k < launches; ++k) {
+            const bool single = tb && 2 * k + 1 == nsteps;
+            gbst_status s2 = enqueue_step(h, par, src ? h->dsrc + k * ns : nullptr,
+                                          h->profile ? static_cast<int>(k) : -1, single);
             if (s2 != GBST_OK)
                 return s2;
             par ^= 1;
@@ -1468,7 +1496,7 @@ gbst_status stencil_run(gbst_handle h, int64_t nsteps)
         if (st != GBST_OK)
             return st;
     }
-    h->parity ^= static_cast<int>(nsteps & 1);
+    h->parity ^= static_cast<int>((persistent ? nsteps : launches) & 1);
     h->step += nsteps;
     return GBST_OK;
 }
@@ -1543,10 +1571,11 @@ gbst_status stencil_describe(gbst_handle h, char *buf, size_t len)
     snprintf(buf, len,
              "{\"kernel\": \"%s\", \"R\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, \"tile\": [%d, %d], "
              "\"zchunks\": %d, \"units\": %d, \"ctas\": %d, \"occupancy\": %d, \"smem\": %zu, \"subdomains\": %zu, "
-             "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d}",
-             p.stream ? "stream" : "simple", h->R, p.var.nthreads, p.var.py, p.var.depth, p.txt * px,
-             (p.var.nthreads / std::max(1, p.txt)) * p.var.py, p.zchunks, p.nunits, p.ctas, p.occupancy, p.smem,
-             h->subs.size(), h->nboxes, p.variant, p.var.minb);
+             "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d, \"tb\": %d}",
+             p.stream ? "stream" : "simple", h->R, p.var.nthreads, p.var.py, p.var.depth, tile_w(p.var, px),
+             p.stream ? tile_h(p.var) : (p.var.nthreads / std::max(1, p.txt)) * p.var.py, p.zchunks, p.nunits,
+             p.ctas, p.occupancy, p.smem, h->subs.size(), h->nboxes, p.variant, p.var.minb,
+             p.stream ? p.var.tb : 1);
     return GBST_OK;
 }
 
@@ -1597,8 +1626,8 @@ gbst_status stencil_variant_info(int i, char *buf, size_t len)
         return fail(GBST_EINVAL, "bad variant index or buffer");
     snprintf(buf, len,
              "{\"R\": %d, \"eq\": %d, \"storage\": %d, \"has_z\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, "
-             "\"minb\": %d, \"txt\": %d}",
-             v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb, v.txt);
+             "\"minb\": %d, \"txt\": %d, \"tb\": %d}",
+             v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb, v.txt, v.tb);
     return GBST_OK;
 }
 
@@ -1649,7 +1678,7 @@ gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len)
     const int zlist_3d[] = {0, 1, 2, 4, 8, 16};
     const int zlist_2d[] = {0};
     for (int vi = 0; stream_variant_get(vi, &v); ++vi) {
-        if (v.R != h->R || v.eq != h->d.eq || v.storage != h->d.storage || v.has_z != (h->ndim == 3))
+        if (!variant_matches(h, v))
             continue;
         {
             const int txt = v.txt;
@@ -1674,11 +1703,12 @@ gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len)
                 }
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                const double per = ms / reps;
+                const double per = ms / reps / v.tb;  // per time step
                 char b[256];
                 snprintf(b, sizeof b,
-                         "%s{\"variant\": %d, \"txt\": %d, \"zchunks\": %d, \"units\": %d, \"ctas\": %d, \"ms\": %.5f}",
-                         ncand ? ", " : "", vi, txt, h->plan.zchunks, h->plan.nunits, h->plan.ctas, per);
+                         "%s{\"variant\": %d, \"txt\": %d, \"zchunks\": %d, \"units\": %d, \"ctas\": %d, "
+                         "\"tb\": %d, \"ms\": %.5f}",
+                         ncand ? ", " : "", vi, txt, h->plan.zchunks, h->plan.nunits, h->plan.ctas, v.tb, per);
                 rep += b;
                 ++ncand;
                 if (per < best_ms) {

@@ -82,6 +82,7 @@ struct SweepArgs {
     int ngrids;            // grids (row length of srcval)
     unsigned int *barrier; // grid-barrier counter (zeroed before a persistent launch)
     unsigned int barrier_extra;  // test hook: extra arrivals a barrier waits for (0 in normal use)
+    int tb_single;         // temporally blocked kernel: 1 = perform one step only
 };
 
 // Host-side entry points of the kernel translation units.
@@ -95,7 +96,17 @@ struct StreamVariant {
     int depth;      // TMA prefetch depth (planes in flight beyond the current one)
     int minb;       // minimum resident CTAs per SM requested from the compiler (register bound)
     int txt;        // threads along x of a tile (tile width = txt * 16 bytes of storage)
+    int tb = 1;     // time steps per launch: 1, or 2 (temporally blocked heat kernel)
 };
+
+// Tile of a variant: width in points, height in rows (a temporally blocked
+// variant's nthreads counts its main and edge warps; the tile is the grown
+// step-1 region of the main warps less r rows on each side).
+inline int tile_w(const StreamVariant &v, int px) { return v.txt * px; }
+inline int tile_h(const StreamVariant &v)
+{
+    return v.tb == 2 ? (v.nthreads / 32 - 1) * v.py - 2 * v.R : (v.nthreads / v.txt) * v.py;
+}
 
 // Number of element columns a thread owns (16 bytes of storage).
 inline int px_of(int storage) { return storage == GBST_BF16 ? 8 : 4; }

@@ -7,24 +7,27 @@ namespace sweep {
 const Entry *table_r1(int *n);
 const Entry *table_r2(int *n);
 const Entry *table_r4(int *n);
+const Entry *table_tb(int *n);
 }  // namespace sweep
 
 namespace {
 using sweep::Entry;
 
 struct Registry {
-    const Entry *tab[3];
-    int n[3];
+    static constexpr int kTables = 4;
+    const Entry *tab[kTables];
+    int n[kTables];
     Registry()
     {
         tab[0] = sweep::table_r1(&n[0]);
         tab[1] = sweep::table_r2(&n[1]);
         tab[2] = sweep::table_r4(&n[2]);
+        tab[3] = sweep::table_tb(&n[3]);
     }
-    int total() const { return n[0] + n[1] + n[2]; }
+    int total() const { return n[0] + n[1] + n[2] + n[3]; }
     const Entry *at(int i) const
     {
-        for (int t = 0; t < 3; ++t) {
+        for (int t = 0; t < kTables; ++t) {
             if (i < n[t])
                 return &tab[t][i];
             i -= n[t];
@@ -46,7 +49,7 @@ const Entry *find(const StreamVariant &v)
         const Entry *e = r.at(i);
         if (e->v.R == v.R && e->v.eq == v.eq && e->v.storage == v.storage && e->v.has_z == v.has_z &&
             e->v.nthreads == v.nthreads && e->v.py == v.py && e->v.depth == v.depth && e->v.minb == v.minb &&
-            e->v.txt == v.txt)
+            e->v.txt == v.txt && e->v.tb == v.tb)
             return e;
     }
     return nullptr;
@@ -79,9 +82,18 @@ bool stream_variant_get(int i, StreamVariant *v)
     return true;
 }
 
-// Wave: per barrier pair, kappa (FP32) and u^{n-1} of the centre plane (tile only).
+// Shared memory beyond the barrier header and the plane ring.  Wave: per
+// barrier pair, kappa (FP32) and u^{n-1} of the centre plane (tile only).
+// Temporally blocked heat: r + 2 step-1 planes of the grown tile plus r rows of
+// slack (rows a main warp may read past the last plane, results discarded).
 static size_t centre_bytes(const StreamVariant &v)
 {
+    if (v.tb == 2) {
+        const size_t uw = static_cast<size_t>(tile_w(v, 4)) + 8, uh = static_cast<size_t>(tile_h(v)) + 2 * v.R;
+        const size_t plane = (uw * uh * 4 + 127) / 128 * 128;
+        const size_t pad = (static_cast<size_t>(v.R) * uw * 4 + 127) / 128 * 128;
+        return plane * (v.R + 2) + pad;
+    }
     if (v.eq != GBST_WAVE)
         return 0;
     const int px = px_of(v.storage), es = v.storage == GBST_BF16 ? 2 : 4;

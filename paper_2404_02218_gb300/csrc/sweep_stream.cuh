@@ -554,6 +554,8 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                 ok = produce(parity);
         } else if (ok) {
             ok = consume(parity, srcval);
+            if (!ok)  // a wait gave up (the producer may have left already): report it here
+                atomicCAS(a.err, 0, static_cast<int>(kDevTimeoutTma));
         }
         if (step + 1 < a.nsteps &&
             !grid_barrier(a.barrier, static_cast<unsigned int>(step + 1) * gridDim.x + a.barrier_extra, abort_flag,

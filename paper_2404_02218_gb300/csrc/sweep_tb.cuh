@@ -1,0 +1,410 @@
+// Temporally blocked streaming heat sweep (two forward-Euler steps per pass
+// over HBM), FP32 storage, 3D, zero Dirichlet ghosts.
+//
+// The step-1 field u' = u + a L(u) is computed on the output tile grown by r
+// in y and by one 16-byte chunk (4 points >= r) in x, from input planes that
+// carry a 2r halo; u' is kept on chip (a ring of shared-memory planes for its
+// x/y neighbours, a register queue for its z neighbours) and the step-2 field
+// u'' = u' + a L(u') is computed on the tile and stored.  Points of u' outside
+// the interior are zero, as the ghost cells of a stored u' would be, and every
+// point is updated with the same arithmetic, in the same order, as the
+// single-step kernel, so a blocked run equals the same number of single steps
+// bit for bit.  Overlapped tiles recompute the u' halo instead of exchanging
+// it (overlapped temporal blocking; the paper's related work, Section 7).
+//
+// CTA: NW "main" warps (warp w owns rows w*PY .. w*PY+PY-1 of the grown tile,
+// lane l owns x chunk l), one "edge" warp (the two x-halo chunks of every row
+// group, step 1 only) and one TMA producer warp.  Input planes arrive as in the
+// single-step kernel: ring of S = r + 1 + D slots, full/empty mbarrier pairs.
+// One mbarrier phase per plane (every consumer thread arrives; waits are
+// bounded like all others) orders the u' plane writes before the step-2
+// reads.  A launch with a.tb_single = 1 performs only step 1 (the odd step of
+// a run) and stores it.
+#pragma once
+#include <type_traits>
+
+#include "sweep_stream.cuh"
+
+namespace gbst {
+namespace sweep {
+namespace {
+
+__device__ __forceinline__ void sts128(unsigned char *p, const uint4 &v)
+{
+    *reinterpret_cast<uint4 *>(p) = v;
+}
+
+// f(integral_constant<int, 0>), ..., f(integral_constant<int, N-1>) while f returns true.
+template <int N, int I = 0, class F>
+__device__ __forceinline__ bool static_for(F &f)
+{
+    if constexpr (I < N) {
+        if (!f(std::integral_constant<int, I>{}))
+            return false;
+        return static_for<N, I + 1>(f);
+    } else {
+        return true;
+    }
+}
+
+template <int R, int NW, int PY, int D>
+struct TbShape {
+    static constexpr int PX = 4;                     // FP32 points per 16-byte chunk
+    static constexpr int TX = 32 * PX;               // tile width (points)
+    static constexpr int TY = NW * PY - 2 * R;       // tile height (rows)
+    static constexpr int IN_W = TX + 4 * PX;         // input box width: tile + 2 chunks per side
+    static constexpr int IN_H = TY + 4 * R;          // input box height: tile + 2r per side
+    static constexpr int U_W = TX + 2 * PX;          // u' plane width: tile + 1 chunk per side
+    static constexpr int U_H = TY + 2 * R;           // u' plane height
+    static constexpr int U_BYTES = (U_W * U_H * 4 + 127) / 128 * 128;
+    static constexpr int NU = R + 2;                 // u' planes kept
+    static constexpr int QN = 2 * R + 1;             // z-queue length
+    static constexpr int S = R + 1 + D;              // input plane slots
+    static constexpr int NB = D + 1;                 // mbarrier pairs
+    static constexpr int PAD = (R * U_W * 4 + 127) / 128 * 128;  // rows read past the last u' plane
+    static_assert(TY >= 1, "tile height");
+    static_assert(2 * NW <= 32, "the edge warp covers both x-halo chunks of every row group");
+    static_assert(R <= PX, "x halo chunk must cover the radius");
+};
+
+// One star-stencil heat update of PY rows x 4 FP32 points, in the single-step
+// kernel's order: own values from queue slot QC of q, x/y neighbours from
+// shared memory at `cb` (row pitch `row` bytes), z neighbours from queue slots
+// QC -+ m.
+template <int R, int PY, int QC>
+__device__ __forceinline__ void tb_update(const float2 (&q)[2 * R + 1][PY][2], const unsigned char *cb,
+                                          const int row, const float2 wc2, const float2 (&w2)[R + 1],
+                                          const float2 a2, float (&o)[PY][4])
+{
+    using St = Storage<GBST_F32>;
+    constexpr int PX = 4, PP = 2, QN = 2 * R + 1;
+    uint4 ylo[R], yhi[R], xl[PY], xr[PY];
+#pragma unroll
+    for (int m = 1; m <= R; ++m) {
+        ylo[m - 1] = lds128(cb - m * row);
+        yhi[m - 1] = lds128(cb + (PY - 1 + m) * row);
+    }
+#pragma unroll
+    for (int r_ = 0; r_ < PY; ++r_) {
+        xl[r_] = load_left<GBST_F32, R>(cb + r_ * row - 16);
+        xr[r_] = load_right<GBST_F32, R>(cb + r_ * row + 16);
+    }
+    auto xel = [&](int r_, int e) -> float {
+        if (e < 0)
+            return St::get(xl[r_], PX + e);
+        if (e >= PX)
+            return St::get(xr[r_], e - PX);
+        return (e & 1) ? q[QC][r_][e >> 1].y : q[QC][r_][e >> 1].x;
+    };
+    auto yrow = [&](int rr, int pp) -> float2 {
+        if (rr < 0)
+            return St::pair(ylo[-rr - 1], pp);
+        if (rr >= PY)
+            return St::pair(yhi[rr - PY], pp);
+        return q[QC][rr][pp];
+    };
+    float2 sv[PY][PP];
+#pragma unroll
+    for (int r_ = 0; r_ < PY; ++r_)
+#pragma unroll
+        for (int pp = 0; pp < PP; ++pp)
+            sv[r_][pp] = __fmul2_rn(wc2, q[QC][r_][pp]);
+#pragma unroll
+    for (int m = 1; m <= R; ++m) {
+#pragma unroll
+        for (int r_ = 0; r_ < PY; ++r_) {
+#pragma unroll
+            for (int pp = 0; pp < PP; ++pp) {
+                const int e = 2 * pp;
+                const float2 xm = make_float2(xel(r_, e - m), xel(r_, e + 1 - m));
+                const float2 xp = make_float2(xel(r_, e + m), xel(r_, e + 1 + m));
+                float2 t = __fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
+                t = __fadd2_rn(t, __fadd2_rn(q[(QC - m + 2 * QN) % QN][r_][pp], q[(QC + m) % QN][r_][pp]));
+                sv[r_][pp] = __ffma2_rn(w2[m], t, sv[r_][pp]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r_ = 0; r_ < PY; ++r_)
+#pragma unroll
+        for (int pp = 0; pp < PP; ++pp) {
+            const float2 ov = __ffma2_rn(a2, sv[r_][pp], q[QC][r_][pp]);
+            o[r_][2 * pp] = ov.x;
+            o[r_][2 * pp + 1] = ov.y;
+        }
+}
+
+template <int R, int NW, int PY, int D, int MINB>
+__global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, const int slot_bytes)
+{
+    using Sh = TbShape<R, NW, PY, D>;
+    using St = Storage<GBST_F32>;
+    constexpr int PX = Sh::PX, TX = Sh::TX, TY = Sh::TY;
+    constexpr int QN = Sh::QN, S = Sh::S, NB = Sh::NB, NU = Sh::NU;
+    constexpr int IN_ROW = Sh::IN_W * 4, U_ROW = Sh::U_W * 4;
+    constexpr int PP = PX / 2;
+    constexpr int NCONS = (NW + 1) * 32;  // consumer threads (main + edge warps)
+    static_assert((2 * NB + 1) * 8 + 8 <= 256, "barrier header");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + NB;
+    uint64_t *ubar = empty + NB;  // u' plane complete (every consumer thread arrives)
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(ubar + 1);
+    unsigned char *slots = smem + 256;
+    unsigned char *ubuf = slots + S * slot_bytes;  // NU u' planes of Sh::U_BYTES
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], NW + 1);
+        }
+        mbar_init(ubar, NCONS);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int parity = a.parity;
+    const bool single = a.tb_single != 0;
+
+    // ------------------------------------------------------------ producer
+    if (warp == NW + 1) {
+        if (lane != 0)
+            return;
+        int it = 0;
+        for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
+            const Unit u = a.units[ui];
+            const GridDev &g = a.grids[u.grid];
+            const int bx = (u.tile % g.tiles_x) * TX, by = (u.tile / g.tiles_x) * TY;
+            const CUtensorMap *map = &g.tmap[parity];
+            const uint32_t bytes = static_cast<uint32_t>(g.box_bytes);
+            const int L = (u.z1 - u.z0) + 4 * R;
+            for (int l = 0; l < L; ++l, ++it) {
+                if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
+                    goto drain;
+                mbar_arrive_expect_tx(&full[it % NB], bytes);
+                // padded coordinates: x from bx - 2 chunks (ghost G = one chunk), y from
+                // by - 2r (ghost r rows), plane z0 - 2r + l (ghost r planes); outside the
+                // tensor the load fills zeros
+                tma_load_plane(slots + (it % S) * slot_bytes, map, &full[it % NB], bx - PX, by - R,
+                               u.z0 - R + l);
+            }
+        }
+    drain:
+        if (*abort_flag) {
+            atomicCAS(a.err, 0, static_cast<int>(kDevTimeoutTma));
+            for (int k = it - NB < 0 ? 0 : it - NB; k < it; ++k) {
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try_wait(&full[k % NB], (k / NB) & 1) && global_ns() - t0 < 50000000ull) {
+                }
+            }
+        }
+        return;
+    }
+
+    // ----------------------------------------------------------- consumers
+    const bool is_edge = warp == NW;
+    // edge lanes: e < NW left chunk of row group e, NW <= e < 2 NW right chunk of group e - NW
+    const bool active = !is_edge || lane < 2 * NW;
+    const int grp = is_edge ? (lane < NW ? lane : (active ? lane - NW : 0)) : warp;
+    const int cx = is_edge ? (lane < NW || !active ? -PX : TX) : lane * PX;  // chunk x offset in the tile
+    const int rho0 = grp * PY;                                     // first row of the grown tile
+    // step-2 rows of this main warp (grown-tile rows [r, TY + r))
+    bool s2row[PY];
+    bool any_s2 = false;
+#pragma unroll
+    for (int k = 0; k < PY; ++k) {
+        s2row[k] = !is_edge && rho0 + k >= R && rho0 + k < TY + R;
+        any_s2 = any_s2 || s2row[k];
+    }
+    const float2 wc2 = make_float2(a.wc, a.wc);
+    float2 w2[R + 1];
+#pragma unroll
+    for (int m = 1; m <= R; ++m)
+        w2[m] = make_float2(a.w[m], a.w[m]);
+    const int in_off = (rho0 + R) * IN_ROW + (cx + 2 * PX) * 4;
+    const int u_off = rho0 * U_ROW + (cx + PX) * 4;
+
+    float2 q1[QN][PY][PP];  // input u, own points, by plane index mod QN
+    float2 q2[QN][PY][PP];  // u', own points, by u' plane index mod QN
+    int slot_n = 0, bar_i = 0, ub_w = 0;  // ring slot, barrier pair, u' plane being written
+    uint32_t par = 0, upar = 0;          // phase parities of full/empty and of ubar
+    auto advance = [&]() {
+        slot_n = slot_n + 1 == S ? 0 : slot_n + 1;
+        if (++bar_i == NB) {
+            bar_i = 0;
+            par ^= 1;
+        }
+    };
+
+    for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
+        const Unit u = a.units[ui];
+        const GridDev *gp = a.grids + u.grid;
+        const int tiles_x = gp->tiles_x;
+        const int64_t nx = gp->nx, ny = gp->ny, nz = gp->nz;
+        const int64_t pitch = gp->pitch, rows = gp->rows, origin = gp->origin;
+        unsigned char *__restrict__ outbase = static_cast<unsigned char *>(gp->buf[1 - parity]);
+        const float2 a2 = make_float2(gp->heat_a, gp->heat_a);
+        const int bx = (u.tile % tiles_x) * TX, by = (u.tile / tiles_x) * TY;
+        // interior masks of this thread's u' points
+        bool yin[PY];
+#pragma unroll
+        for (int k = 0; k < PY; ++k) {
+            const int64_t y = static_cast<int64_t>(by) - R + rho0 + k;
+            yin[k] = y >= 0 && y < ny;
+        }
+        bool xin[PX];
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            const int64_t x = static_cast<int64_t>(bx) + cx + i;
+            xin[i] = x >= 0 && x < nx;
+        }
+        const bool xfull = bx + cx + PX <= nx;
+        bool st_row[PY];  // rows this thread stores (step-2 rows, or step-1 rows in single mode)
+#pragma unroll
+        for (int k = 0; k < PY; ++k)
+            st_row[k] = s2row[k] && yin[k] && bx + cx < nx;
+        const int64_t plane_elems = rows * pitch;
+        const int64_t row_stride = pitch * 4;
+        // output pointer at plane z0, grown-tile row rho0 (y = by - r + rho0), column bx + cx
+        unsigned char *optr = outbase +
+                              (origin + (static_cast<int64_t>(u.z0) * rows + (by - R + rho0)) * pitch + bx + cx) * 4;
+
+        const int nout = u.z1 - u.z0;
+        const int L = nout + 4 * R;
+        int j0 = 0;
+        // iteration j = j0 + k of the z-march; k is a compile-time constant so every
+        // queue slot index below is one too (false: a wait gave up, leave)
+        auto body = [&](auto kc) -> bool {
+            constexpr int k = decltype(kc)::value;
+            {
+                const int j = j0 + k;
+                if (j < L) {
+                    if (!wait_or_abort(&full[bar_i], par, abort_flag))
+                        return false;
+                    // newest input plane into the z-queue
+                    {
+                        const unsigned char *nb = slots + slot_n * slot_bytes + in_off;
+#pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_) {
+                            const uint4 v = lds128(nb + r_ * IN_ROW);
+#pragma unroll
+                            for (int pp = 0; pp < PP; ++pp)
+                                q1[k][r_][pp] = St::pair(v, pp);
+                        }
+                    }
+                    const bool s1 = j >= 2 * R;  // step 1 on input plane j - r (u' plane j - 2r)
+                    if (s1 && active) {
+                        constexpr int qc1 = (k - R + QN) % QN;
+                        const int slot_c = slot_n >= R ? slot_n - R : slot_n - R + S;
+                        float o[PY][PX];
+                        tb_update<R, PY, qc1>(q1, slots + slot_c * slot_bytes + in_off, IN_ROW, wc2, w2, a2, o);
+                        // u' plane index (interior z) of this result
+                        const int64_t zq = static_cast<int64_t>(u.z0) - 3 * R + j;
+                        const bool zin = zq >= 0 && zq < nz;
+#pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_)
+#pragma unroll
+                            for (int i = 0; i < PX; ++i)
+                                if (!(zin && yin[r_] && xin[i]))
+                                    o[r_][i] = 0.0f;
+                        if (single) {
+                            // one step only: store u' of planes [z0, z1)
+                            if (zq >= u.z0 && zq < u.z1) {
+                                unsigned char *op = optr + (zq - u.z0) * plane_elems * 4;
+#pragma unroll
+                                for (int r_ = 0; r_ < PY; ++r_) {
+                                    if (st_row[r_]) {
+                                        if (xfull) {
+                                            *reinterpret_cast<uint4 *>(op + r_ * row_stride) = St::pack(o[r_]);
+                                        } else {
+#pragma unroll
+                                            for (int i = 0; i < PX; ++i)
+                                                if (xin[i])
+                                                    St::store1(op + r_ * row_stride + i * 4, o[r_][i]);
+                                        }
+                                    }
+                                }
+                            }
+                        } else {
+                            constexpr int qn2 = (k - 2 * R + 2 * QN) % QN;
+                            unsigned char *ub = ubuf + ub_w * Sh::U_BYTES + u_off;
+#pragma unroll
+                            for (int r_ = 0; r_ < PY; ++r_) {
+#pragma unroll
+                                for (int pp = 0; pp < PP; ++pp)
+                                    q2[qn2][r_][pp] = make_float2(o[r_][2 * pp], o[r_][2 * pp + 1]);
+                                sts128(ub + r_ * U_ROW, St::pack(o[r_]));
+                            }
+                        }
+                    }
+                    // the input planes of this iteration are no longer read
+                    __syncwarp();
+                    if (lane == 0)
+                        mbar_arrive(&empty[bar_i]);
+                    advance();
+
+                    if (s1 && !single) {
+                        // u' plane j - 2r is complete in shared memory
+                        mbar_arrive(ubar);
+                        if (!wait_or_abort(ubar, upar, abort_flag))
+                            return false;
+                        upar ^= 1;
+                        const int ub_c = ub_w - R < 0 ? ub_w - R + NU : ub_w - R;  // u' plane j - 3r
+                        ub_w = ub_w + 1 == NU ? 0 : ub_w + 1;
+                        if (j >= 4 * R && any_s2) {
+                            // step 2 on u' plane j - 3r = output plane z0 + (j - 4r)
+                            constexpr int qc2 = (k - 3 * R + 3 * QN) % QN;
+                            float o[PY][PX];
+                            tb_update<R, PY, qc2>(q2, ubuf + ub_c * Sh::U_BYTES + u_off, U_ROW, wc2, w2, a2, o);
+                            unsigned char *op = optr + static_cast<int64_t>(j - 4 * R) * plane_elems * 4;
+#pragma unroll
+                            for (int r_ = 0; r_ < PY; ++r_) {
+                                if (st_row[r_]) {
+                                    if (xfull) {
+                                        *reinterpret_cast<uint4 *>(op + r_ * row_stride) = St::pack(o[r_]);
+                                    } else {
+#pragma unroll
+                                        for (int i = 0; i < PX; ++i)
+                                            if (xin[i])
+                                                St::store1(op + r_ * row_stride + i * 4, o[r_][i]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            return true;
+        };
+        bool ok = true;
+        for (; j0 < L && ok; j0 += QN)
+            ok = static_for<QN>(body);
+        // all u' reads of this unit are done before the next unit overwrites the planes
+        if (ok && !single) {
+            mbar_arrive(ubar);
+            ok = wait_or_abort(ubar, upar, abort_flag);
+            upar ^= 1;
+        }
+        if (!ok) {
+            // a wait gave up (the producer may have left already): report it here
+            atomicCAS(a.err, 0, static_cast<int>(kDevTimeoutTma));
+            return;
+        }
+    }
+}
+
+}  // namespace
+
+template <int R, int NW, int PY, int D, int MINB>
+constexpr Entry tb_entry()
+{
+    return Entry{StreamVariant{R, GBST_HEAT, GBST_F32, true, (NW + 1) * 32, PY, D, MINB, 32, 2},
+                 &k_tb<R, NW, PY, D, MINB>};
+}
+
+}  // namespace sweep
+}  // namespace gbst

@@ -66,7 +66,7 @@ class Grid:
                  bc: str = "zero", storage: str = "f32", h: float = 1.0, dt: float = 1.0,
                  alpha: float = 1.0, coeffs=None, decomp=(1, 1, 1), allow_unstable: bool = False,
                  kernel: str = "auto", tile: int = 0, use_graph: bool = True, stream=None,
-                 torch_allocator: bool = True):
+                 torch_allocator: bool = True, temporal_block: int = 0):
         import torch
         self._torch = torch
         self.ndim = ndim
@@ -96,6 +96,7 @@ class Grid:
         d.kernel = _KER[kernel]
         d.tile = int(tile)
         d.use_graph = int(use_graph)
+        d.temporal_block = int(temporal_block)
         d.stream = ctypes.c_void_p(self.stream.cuda_stream)
         self._alloc = TorchAllocator(dev) if torch_allocator else None
         d.allocator = ctypes.pointer(self._alloc.struct) if self._alloc else None

@@ -60,6 +60,7 @@ class gbst_desc(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("allocator", ctypes.POINTER(gbst_allocator)),
+        ("temporal_block", ctypes.c_int),
     ]
 
 
