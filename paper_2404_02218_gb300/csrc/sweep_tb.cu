@@ -13,6 +13,9 @@ const Entry kTable[] = {
     tb_entry<1, 16, 1, 2, 1>(),
     tb_entry<1, 10, 1, 3, 1>(),
     tb_entry<1, 12, 2, 2, 1>(),
+    tb_entry<1, 8, 2, 2, 2>(),
+    tb_entry<1, 10, 1, 2, 2>(),
+    tb_entry<1, 6, 2, 2, 2>(),
     tb_entry<2, 10, 2, 2, 1>(),
     tb_entry<2, 12, 1, 2, 1>(),
     tb_entry<2, 16, 1, 2, 1>(),

@@ -16,9 +16,9 @@
 // lane l owns x chunk l), one "edge" warp (the two x-halo chunks of every row
 // group, step 1 only) and one TMA producer warp.  Input planes arrive as in the
 // single-step kernel: ring of S = r + 1 + D slots, full/empty mbarrier pairs.
-// One mbarrier phase per plane (every consumer thread arrives; waits are
-// bounded like all others) orders the u' plane writes before the step-2
-// reads.  A launch with a.tb_single = 1 performs only step 1 (the odd step of
+// Per u' plane buffer an mbarrier (one arrival per consumer warp; waits are
+// bounded like all others) orders the plane's writes before its step-2 reads;
+// step 2 runs one plane behind step 1, so that wait is usually already met.  A launch with a.tb_single = 1 performs only step 1 (the odd step of
 // a run) and stores it.
 #pragma once
 #include <type_traits>
@@ -70,7 +70,8 @@ struct TbShape {
 // One star-stencil heat update of PY rows x 4 FP32 points, in the single-step
 // kernel's order: own values from queue slot QC of q, x/y neighbours from
 // shared memory at `cb` (row pitch `row` bytes), z neighbours from queue slots
-// QC -+ m.
+// QC -+ m.  (Taking the x neighbours from adjacent lanes by shuffles, with the
+// tile-edge lanes reading shared memory, measured slower.)
 template <int R, int PY, int QC>
 __device__ __forceinline__ void tb_update(const float2 (&q)[2 * R + 1][PY][2], const unsigned char *cb,
                                           const int row, const float2 wc2, const float2 (&w2)[R + 1],
@@ -143,14 +144,14 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
     constexpr int QN = Sh::QN, S = Sh::S, NB = Sh::NB, NU = Sh::NU;
     constexpr int IN_ROW = Sh::IN_W * 4, U_ROW = Sh::U_W * 4;
     constexpr int PP = PX / 2;
-    constexpr int NCONS = (NW + 1) * 32;  // consumer threads (main + edge warps)
-    static_assert((2 * NB + 1) * 8 + 8 <= 256, "barrier header");
+    static_assert((2 * NB + NU + 1) * 8 + 8 <= 256, "barrier header");
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + NB;
-    uint64_t *ubar = empty + NB;  // u' plane complete (every consumer thread arrives)
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(ubar + 1);
+    uint64_t *ubar = empty + NB;  // per u' plane buffer: plane written (one arrival per consumer warp)
+    uint64_t *uend = ubar + NU;   // end of a unit: every consumer warp is done with the u' planes
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(uend + 1);
     unsigned char *slots = smem + 256;
     unsigned char *ubuf = slots + S * slot_bytes;  // NU u' planes of Sh::U_BYTES
 
@@ -161,7 +162,10 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], NW + 1);
         }
-        mbar_init(ubar, NCONS);
+#pragma unroll
+        for (int b = 0; b < NU; ++b)
+            mbar_init(&ubar[b], NW + 1);
+        mbar_init(uend, NW + 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
             const int bx = (u.tile % g.tiles_x) * TX, by = (u.tile / g.tiles_x) * TY;
             const CUtensorMap *map = &g.tmap[parity];
             const uint32_t bytes = static_cast<uint32_t>(g.box_bytes);
-            const int L = (u.z1 - u.z0) + 4 * R;
+            const int L = (u.z1 - u.z0) + 4 * R + (single ? 0 : 1);
             for (int l = 0; l < L; ++l, ++it) {
                 if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
                     goto drain;
@@ -230,8 +234,9 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
 
     float2 q1[QN][PY][PP];  // input u, own points, by plane index mod QN
     float2 q2[QN][PY][PP];  // u', own points, by u' plane index mod QN
-    int slot_n = 0, bar_i = 0, ub_w = 0;  // ring slot, barrier pair, u' plane being written
-    uint32_t par = 0, upar = 0;          // phase parities of full/empty and of ubar
+    int slot_n = 0, bar_i = 0;  // ring slot, barrier pair
+    int pc = 0;                 // u' planes written so far by this CTA (buffer pc % NU)
+    uint32_t par = 0, upar = 0; // phase parities of full/empty and of uend
     auto advance = [&]() {
         slot_n = slot_n + 1 == S ? 0 : slot_n + 1;
         if (++bar_i == NB) {
@@ -274,110 +279,115 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                               (origin + (static_cast<int64_t>(u.z0) * rows + (by - R + rho0)) * pitch + bx + cx) * 4;
 
         const int nout = u.z1 - u.z0;
-        const int L = nout + 4 * R;
+        // input planes of the unit; two-step mode takes one more so that the last
+        // output plane's step 2 (one plane behind step 1) runs inside the loop
+        const int L = nout + 4 * R + (single ? 0 : 1);
         int j0 = 0;
-        // iteration j = j0 + k of the z-march; k is a compile-time constant so every
-        // queue slot index below is one too (false: a wait gave up, leave)
+        // Iteration j = j0 + k of the z-march (k is a compile-time constant, so every
+        // queue slot below is one too): step 2 on u' plane P - 1 - r, then step 1 on
+        // input plane j - r giving u' plane P = j - 2r.  Step 2 waits for plane P - 1,
+        // which every consumer warp finished one iteration earlier (split-phase
+        // barrier), and reads its u' z-neighbours before step 1 overwrites the
+        // oldest queue slot.  Returns false when a wait gave up.
         auto body = [&](auto kc) -> bool {
             constexpr int k = decltype(kc)::value;
+            const int j = j0 + k;
+            if (j >= L)
+                return true;
+            if (!wait_or_abort(&full[bar_i], par, abort_flag))
+                return false;
+            // newest input plane into the z-queue
             {
-                const int j = j0 + k;
-                if (j < L) {
-                    if (!wait_or_abort(&full[bar_i], par, abort_flag))
-                        return false;
-                    // newest input plane into the z-queue
-                    {
-                        const unsigned char *nb = slots + slot_n * slot_bytes + in_off;
+                const unsigned char *nb = slots + slot_n * slot_bytes + in_off;
 #pragma unroll
-                        for (int r_ = 0; r_ < PY; ++r_) {
-                            const uint4 v = lds128(nb + r_ * IN_ROW);
+                for (int r_ = 0; r_ < PY; ++r_) {
+                    const uint4 v = lds128(nb + r_ * IN_ROW);
 #pragma unroll
-                            for (int pp = 0; pp < PP; ++pp)
-                                q1[k][r_][pp] = St::pair(v, pp);
-                        }
-                    }
-                    const bool s1 = j >= 2 * R;  // step 1 on input plane j - r (u' plane j - 2r)
-                    if (s1 && active) {
-                        constexpr int qc1 = (k - R + QN) % QN;
-                        const int slot_c = slot_n >= R ? slot_n - R : slot_n - R + S;
-                        float o[PY][PX];
-                        tb_update<R, PY, qc1>(q1, slots + slot_c * slot_bytes + in_off, IN_ROW, wc2, w2, a2, o);
-                        // u' plane index (interior z) of this result
-                        const int64_t zq = static_cast<int64_t>(u.z0) - 3 * R + j;
-                        const bool zin = zq >= 0 && zq < nz;
+                    for (int pp = 0; pp < PP; ++pp)
+                        q1[k][r_][pp] = St::pair(v, pp);
+                }
+            }
+            if (!single && j >= 4 * R + 1) {
+                // u' plane P - 1 (global count pc - 1) is complete in shared memory
+                if (!wait_or_abort(&ubar[(pc - 1) % NU], ((pc - 1) / NU) & 1, abort_flag))
+                    return false;
+                if (any_s2) {
+                    // step 2 on u' plane P - 1 - r = output plane z0 + j - 4r - 1
+                    constexpr int qc2 = (k - 3 * R - 1 + 4 * QN) % QN;
+                    float o[PY][PX];
+                    tb_update<R, PY, qc2>(q2, ubuf + ((pc - 1 - R) % NU) * Sh::U_BYTES + u_off, U_ROW, wc2, w2,
+                                          a2, o);
+                    unsigned char *op = optr + static_cast<int64_t>(j - 4 * R - 1) * plane_elems * 4;
 #pragma unroll
-                        for (int r_ = 0; r_ < PY; ++r_)
+                    for (int r_ = 0; r_ < PY; ++r_) {
+                        if (st_row[r_]) {
+                            if (xfull) {
+                                *reinterpret_cast<uint4 *>(op + r_ * row_stride) = St::pack(o[r_]);
+                            } else {
 #pragma unroll
-                            for (int i = 0; i < PX; ++i)
-                                if (!(zin && yin[r_] && xin[i]))
-                                    o[r_][i] = 0.0f;
-                        if (single) {
-                            // one step only: store u' of planes [z0, z1)
-                            if (zq >= u.z0 && zq < u.z1) {
-                                unsigned char *op = optr + (zq - u.z0) * plane_elems * 4;
-#pragma unroll
-                                for (int r_ = 0; r_ < PY; ++r_) {
-                                    if (st_row[r_]) {
-                                        if (xfull) {
-                                            *reinterpret_cast<uint4 *>(op + r_ * row_stride) = St::pack(o[r_]);
-                                        } else {
-#pragma unroll
-                                            for (int i = 0; i < PX; ++i)
-                                                if (xin[i])
-                                                    St::store1(op + r_ * row_stride + i * 4, o[r_][i]);
-                                        }
-                                    }
-                                }
-                            }
-                        } else {
-                            constexpr int qn2 = (k - 2 * R + 2 * QN) % QN;
-                            unsigned char *ub = ubuf + ub_w * Sh::U_BYTES + u_off;
-#pragma unroll
-                            for (int r_ = 0; r_ < PY; ++r_) {
-#pragma unroll
-                                for (int pp = 0; pp < PP; ++pp)
-                                    q2[qn2][r_][pp] = make_float2(o[r_][2 * pp], o[r_][2 * pp + 1]);
-                                sts128(ub + r_ * U_ROW, St::pack(o[r_]));
-                            }
-                        }
-                    }
-                    // the input planes of this iteration are no longer read
-                    __syncwarp();
-                    if (lane == 0)
-                        mbar_arrive(&empty[bar_i]);
-                    advance();
-
-                    if (s1 && !single) {
-                        // u' plane j - 2r is complete in shared memory
-                        mbar_arrive(ubar);
-                        if (!wait_or_abort(ubar, upar, abort_flag))
-                            return false;
-                        upar ^= 1;
-                        const int ub_c = ub_w - R < 0 ? ub_w - R + NU : ub_w - R;  // u' plane j - 3r
-                        ub_w = ub_w + 1 == NU ? 0 : ub_w + 1;
-                        if (j >= 4 * R && any_s2) {
-                            // step 2 on u' plane j - 3r = output plane z0 + (j - 4r)
-                            constexpr int qc2 = (k - 3 * R + 3 * QN) % QN;
-                            float o[PY][PX];
-                            tb_update<R, PY, qc2>(q2, ubuf + ub_c * Sh::U_BYTES + u_off, U_ROW, wc2, w2, a2, o);
-                            unsigned char *op = optr + static_cast<int64_t>(j - 4 * R) * plane_elems * 4;
-#pragma unroll
-                            for (int r_ = 0; r_ < PY; ++r_) {
-                                if (st_row[r_]) {
-                                    if (xfull) {
-                                        *reinterpret_cast<uint4 *>(op + r_ * row_stride) = St::pack(o[r_]);
-                                    } else {
-#pragma unroll
-                                        for (int i = 0; i < PX; ++i)
-                                            if (xin[i])
-                                                St::store1(op + r_ * row_stride + i * 4, o[r_][i]);
-                                    }
-                                }
+                                for (int i = 0; i < PX; ++i)
+                                    if (xin[i])
+                                        St::store1(op + r_ * row_stride + i * 4, o[r_][i]);
                             }
                         }
                     }
                 }
             }
+            const bool s1 = j >= 2 * R;  // step 1 on input plane j - r (u' plane P = j - 2r)
+            if (s1 && active) {
+                constexpr int qc1 = (k - R + QN) % QN;
+                const int slot_c = slot_n >= R ? slot_n - R : slot_n - R + S;
+                float o[PY][PX];
+                tb_update<R, PY, qc1>(q1, slots + slot_c * slot_bytes + in_off, IN_ROW, wc2, w2, a2, o);
+                // u' plane index (interior z) of this result
+                const int64_t zq = static_cast<int64_t>(u.z0) - 3 * R + j;
+                const bool zin = zq >= 0 && zq < nz;
+#pragma unroll
+                for (int r_ = 0; r_ < PY; ++r_)
+#pragma unroll
+                    for (int i = 0; i < PX; ++i)
+                        if (!(zin && yin[r_] && xin[i]))
+                            o[r_][i] = 0.0f;
+                if (single) {
+                    // one step only: store u' of planes [z0, z1)
+                    if (zq >= u.z0 && zq < u.z1) {
+                        unsigned char *op = optr + (zq - u.z0) * plane_elems * 4;
+#pragma unroll
+                        for (int r_ = 0; r_ < PY; ++r_) {
+                            if (st_row[r_]) {
+                                if (xfull) {
+                                    *reinterpret_cast<uint4 *>(op + r_ * row_stride) = St::pack(o[r_]);
+                                } else {
+#pragma unroll
+                                    for (int i = 0; i < PX; ++i)
+                                        if (xin[i])
+                                            St::store1(op + r_ * row_stride + i * 4, o[r_][i]);
+                                }
+                            }
+                        }
+                    }
+                } else {
+                    constexpr int qn2 = (k - 2 * R + 2 * QN) % QN;
+                    unsigned char *ub = ubuf + (pc % NU) * Sh::U_BYTES + u_off;
+#pragma unroll
+                    for (int r_ = 0; r_ < PY; ++r_) {
+#pragma unroll
+                        for (int pp = 0; pp < PP; ++pp)
+                            q2[qn2][r_][pp] = make_float2(o[r_][2 * pp], o[r_][2 * pp + 1]);
+                        sts128(ub + r_ * U_ROW, St::pack(o[r_]));
+                    }
+                }
+            }
+            // the input planes of this iteration are no longer read; u' plane P is written
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[bar_i]);
+                if (s1 && !single)
+                    mbar_arrive(&ubar[pc % NU]);
+            }
+            if (s1 && !single)
+                ++pc;
+            advance();
             return true;
         };
         bool ok = true;
@@ -385,8 +395,10 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
             ok = static_for<QN>(body);
         // all u' reads of this unit are done before the next unit overwrites the planes
         if (ok && !single) {
-            mbar_arrive(ubar);
-            ok = wait_or_abort(ubar, upar, abort_flag);
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(uend);
+            ok = wait_or_abort(uend, upar, abort_flag);
             upar ^= 1;
         }
         if (!ok) {
