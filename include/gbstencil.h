@@ -125,9 +125,26 @@ gbst_status stencil_set_field(gbst_handle h, int field, const void *src, int src
                               int src_on_device);
 
 /* Copy a dense interior field out (same layout rules; GBST_VEL returns kappa).
- * Synchronises the handle's stream and reports any deferred device error. */
+ * Synchronises the handle's stream and reports any deferred device error.
+ * Host buffers move by the copy engines through a device staging buffer
+ * (allocated from the handle's allocator for the duration of the copy). */
 gbst_status stencil_get_field(gbst_handle h, int field, void *dst, int dst_dtype,
                               int dst_on_device);
+
+/* Asynchronous forms of stencil_set_field / stencil_get_field for GBST_U and
+ * GBST_U_PREV: the copy is enqueued on the handle's stream and the call returns
+ * at once.  The buffer must be device memory or page-locked host memory (else
+ * EINVAL), and must stay valid, and unmodified / unread by the caller, until
+ * the stream reaches the copy (e.g. stencil_sync).  The staging buffer of a
+ * host copy is released in stream order, which needs a stream-ordered
+ * allocator (e.g. a framework's caching allocator); with the default
+ * cudaMalloc / cudaFree the release synchronises the device.  Device errors
+ * surface at the next synchronising call.  No counterpart in the paper: lets a
+ * caller overlap one grid's transfers with another grid's sweeps. */
+gbst_status stencil_set_field_async(gbst_handle h, int field, const void *src, int src_dtype,
+                                    int src_on_device);
+gbst_status stencil_get_field_async(gbst_handle h, int field, void *dst, int dst_dtype,
+                                    int dst_on_device);
 
 /* Wave only: a Ricker point source at interior index idx = (i, j, k) (k ignored
  * in 2D).  At the end of step n the value amp * c_s^2 dt^2 * R(n dt) is added to

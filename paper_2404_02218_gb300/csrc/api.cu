@@ -1044,7 +1044,8 @@ gbst_status destroy_handle(gbst_handle h)
 }
 
 // Copy one member's dense field in (to_dev) or out.
-gbst_status transfer(gbst_handle h, int member, int field, void *user, int dtype, int on_device, bool to_dev)
+gbst_status transfer(gbst_handle h, int member, int field, void *user, int dtype, int on_device, bool to_dev,
+                     bool async = false)
 {
     gbst_status st = check_handle(h);
     if (st != GBST_OK)
@@ -1068,6 +1069,17 @@ gbst_status transfer(gbst_handle h, int member, int field, void *user, int dtype
         }
     void *dense = user;
     void *staging = nullptr;
+    if (async && !on_device) {
+        // host memory moves by the copy engines through a device staging buffer (no SMs
+        // held while the host link is busy); only page-locked memory copies asynchronously
+        cudaPointerAttributes pa{};
+        const bool pinned = cudaPointerGetAttributes(&pa, user) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        if (!pinned)
+            return fail(GBST_EINVAL, "asynchronous transfers need device memory or page-locked host memory");
+    }
+    if (async && field == GBST_VEL)
+        return fail(GBST_EINVAL, "GBST_VEL is transferred synchronously (its stability check reads it back)");
     if (!on_device) {
         staging = h->mem.alloc(n * esz);
         if (!staging)
@@ -1118,6 +1130,13 @@ gbst_status transfer(gbst_handle h, int member, int field, void *user, int dtype
             h->mem.release(staging, n * esz);
             return fail(GBST_ECUDA, "device-to-host copy: %s", cudaGetErrorString(e));
         }
+    }
+    if (async) {
+        // the staging buffer returns to the allocator in stream order (the torch
+        // caching allocator reuses it only for later work on the same stream)
+        if (staging)
+            h->mem.release(staging, n * esz);
+        return GBST_OK;  // errors surface at the next synchronising call
     }
     st = poll_device_error(h);
     if (staging)
@@ -1295,6 +1314,16 @@ gbst_status stencil_get_field(gbst_handle h, int field, void *dst, int dst_dtype
 gbst_status stencil_batch_get_field(gbst_handle h, int grid, int field, void *dst, int dst_dtype, int dst_on_device)
 {
     return transfer(h, grid, field, dst, dst_dtype, dst_on_device, false);
+}
+
+gbst_status stencil_set_field_async(gbst_handle h, int field, const void *src, int src_dtype, int src_on_device)
+{
+    return transfer(h, 0, field, const_cast<void *>(src), src_dtype, src_on_device, true, true);
+}
+
+gbst_status stencil_get_field_async(gbst_handle h, int field, void *dst, int dst_dtype, int dst_on_device)
+{
+    return transfer(h, 0, field, dst, dst_dtype, dst_on_device, false, true);
 }
 
 gbst_status stencil_set_source(gbst_handle h, const int64_t idx[3], double f0_hz, double t0_s, double amp)

@@ -1,6 +1,8 @@
 // Supporting kernels: the one-thread-per-point sweep, halo copies (dmp.swap
 // faces and periodic wrap), dense <-> padded field transfers and the FP64
 // reductions.
+#include <algorithm>
+
 #include "gbst_internal.h"
 
 namespace gbst {
@@ -111,43 +113,56 @@ __device__ __forceinline__ double load_dense(const void *p, int dtype, int64_t i
     return static_cast<double>(__bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]));
 }
 
+// Dense <-> padded transfers, one block per x row (grid-stride over the ny*nz
+// rows; one division per row), threads along x: both sides are read and
+// written in contiguous runs, which also suits host memory accessed over the
+// host link.
 __global__ void k_scatter(const XferArgs x)
 {
-    const int64_t n = x.nx * x.ny * x.nz;
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t i = p % x.nx, j = (p / x.nx) % x.ny, k = p / (x.nx * x.ny);
-        const int64_t d = ((x.gz + k) * x.gny + (x.gy + j)) * x.gnx + (x.gx + i);
-        double v = load_dense(x.dense, x.dense_dtype, d);
-        if (x.scale_sq > 0.0)
-            v = v * v * x.scale_sq;
-        const int64_t o = x.origin + (k * x.rows + j) * x.pitch + i;
-        if (x.storage == GBST_BF16)
-            static_cast<__nv_bfloat16 *>(x.padded)[o] = __double2bfloat16(v);
-        else
-            static_cast<float *>(x.padded)[o] = __double2float_rn(v);
+    const int64_t nrows = x.ny * x.nz;
+    for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const int64_t j = row % x.ny, k = row / x.ny;
+        const int64_t d0 = ((x.gz + k) * x.gny + (x.gy + j)) * x.gnx + x.gx;
+        const int64_t o0 = x.origin + (k * x.rows + j) * x.pitch;
+        if (x.storage == GBST_F32 && x.dense_dtype == GBST_F32 && !(x.scale_sq > 0.0)) {
+            const float *src = static_cast<const float *>(x.dense) + d0;
+            float *dst = static_cast<float *>(x.padded) + o0;
+            for (int64_t i = threadIdx.x; i < x.nx; i += blockDim.x)
+                dst[i] = src[i];
+            continue;
+        }
+        for (int64_t i = threadIdx.x; i < x.nx; i += blockDim.x) {
+            double v = load_dense(x.dense, x.dense_dtype, d0 + i);
+            if (x.scale_sq > 0.0)
+                v = v * v * x.scale_sq;
+            if (x.storage == GBST_BF16)
+                static_cast<__nv_bfloat16 *>(x.padded)[o0 + i] = __double2bfloat16(v);
+            else
+                static_cast<float *>(x.padded)[o0 + i] = __double2float_rn(v);
+        }
     }
 }
 
 __global__ void k_gather(const XferArgs x)
 {
-    const int64_t n = x.nx * x.ny * x.nz;
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t i = p % x.nx, j = (p / x.nx) % x.ny, k = p / (x.nx * x.ny);
-        const int64_t d = ((x.gz + k) * x.gny + (x.gy + j)) * x.gnx + (x.gx + i);
-        const int64_t o = x.origin + (k * x.rows + j) * x.pitch + i;
-        float v;
-        if (x.storage == GBST_BF16)
-            v = __bfloat162float(static_cast<const __nv_bfloat16 *>(x.padded)[o]);
-        else
-            v = static_cast<const float *>(x.padded)[o];
-        if (x.dense_dtype == GBST_F64)
-            static_cast<double *>(x.dense)[d] = static_cast<double>(v);
-        else if (x.dense_dtype == GBST_F32)
-            static_cast<float *>(x.dense)[d] = v;
-        else
-            static_cast<__nv_bfloat16 *>(x.dense)[d] = __float2bfloat16_rn(v);
+    const int64_t nrows = x.ny * x.nz;
+    for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const int64_t j = row % x.ny, k = row / x.ny;
+        const int64_t d0 = ((x.gz + k) * x.gny + (x.gy + j)) * x.gnx + x.gx;
+        const int64_t o0 = x.origin + (k * x.rows + j) * x.pitch;
+        for (int64_t i = threadIdx.x; i < x.nx; i += blockDim.x) {
+            float v;
+            if (x.storage == GBST_BF16)
+                v = __bfloat162float(static_cast<const __nv_bfloat16 *>(x.padded)[o0 + i]);
+            else
+                v = static_cast<const float *>(x.padded)[o0 + i];
+            if (x.dense_dtype == GBST_F64)
+                static_cast<double *>(x.dense)[d0 + i] = static_cast<double>(v);
+            else if (x.dense_dtype == GBST_F32)
+                static_cast<float *>(x.dense)[d0 + i] = v;
+            else
+                static_cast<__nv_bfloat16 *>(x.dense)[d0 + i] = __float2bfloat16_rn(v);
+        }
     }
 }
 
@@ -326,13 +341,13 @@ cudaError_t launch_halo_copies(const GridDev *grids, const CopyBox *boxes, int n
 
 cudaError_t launch_scatter(const XferArgs &x, cudaStream_t s)
 {
-    k_scatter<<<grid_for(x.nx * x.ny * x.nz, 256, 8192), 256, 0, s>>>(x);
+    k_scatter<<<static_cast<unsigned>(std::min<int64_t>(x.ny * x.nz, 16384)), 256, 0, s>>>(x);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const XferArgs &x, cudaStream_t s)
 {
-    k_gather<<<grid_for(x.nx * x.ny * x.nz, 256, 8192), 256, 0, s>>>(x);
+    k_gather<<<static_cast<unsigned>(std::min<int64_t>(x.ny * x.nz, 16384)), 256, 0, s>>>(x);
     return cudaGetLastError();
 }
 

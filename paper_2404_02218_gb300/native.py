@@ -125,6 +125,8 @@ def lib() -> ctypes.CDLL:
                 "closure_set_loss_weight": ([H, dbl], i32),
                 "stencil_attach_closure": ([H, H, dbl], i32),
                 "stencil_get_field_strided": ([H, i32, vp, i32], i32),
+                "stencil_set_field_async": ([H, i32, vp, i32, i32], i32),
+                "stencil_get_field_async": ([H, i32, vp, i32, i32], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -167,6 +169,16 @@ def stencil_set_field(h, field: int, ptr: int, dtype: int, on_device: bool):
 
 def stencil_get_field(h, field: int, ptr: int, dtype: int, on_device: bool):
     _check(lib().stencil_get_field(h, field, ctypes.c_void_p(ptr), dtype, int(on_device)), "stencil_get_field")
+
+
+def stencil_set_field_async(h, field: int, ptr: int, dtype: int, on_device: bool):
+    _check(lib().stencil_set_field_async(h, field, ctypes.c_void_p(ptr), dtype, int(on_device)),
+           "stencil_set_field_async")
+
+
+def stencil_get_field_async(h, field: int, ptr: int, dtype: int, on_device: bool):
+    _check(lib().stencil_get_field_async(h, field, ctypes.c_void_p(ptr), dtype, int(on_device)),
+           "stencil_get_field_async")
 
 
 def stencil_set_source(h, idx, f0: float, t0: float, amp: float):
