@@ -263,6 +263,12 @@ gbst_status closure_set_loss_weight(gbst_closure c, double w);
 /* freeze != 0: Adam leaves the three bias vectors unchanged (with zero biases a
  * zero field then gets a zero correction). */
 gbst_status closure_freeze_biases(gbst_closure c, int freeze);
+/* Convolution kernels: impl 0 (default) = tcgen05 MMAs with accumulators in
+ * tensor memory, operands staged by TMA; impl 1 = the mma.sync kernels (kept
+ * as an independent cross-check of the same arithmetic).  A bounded wait that
+ * expires in a tcgen05 kernel is reported as GBST_ETIMEOUT by the next
+ * closure_loss_grad / closure_get_params / closure_get_grads. */
+gbst_status closure_set_conv_impl(gbst_closure c, int impl);
 
 /* Attach a closure to a single (undecomposed) 3D wave grid: from then on every
  * step of stencil_run is the plain sweep followed by u^{n+1} += closure

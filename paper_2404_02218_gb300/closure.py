@@ -91,6 +91,10 @@ class Closure:
     def freeze_biases(self, on: bool = True):
         N.closure_freeze_biases(self.h, on)
 
+    def set_conv_impl(self, impl: int):
+        """0: tcgen05 convolutions (default); 1: mma.sync convolutions."""
+        N.closure_set_conv_impl(self.h, impl)
+
     def close(self):
         if getattr(self, "h", None):
             N.closure_destroy(self.h)

@@ -89,6 +89,32 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
     return fn;
 }
 
+bool encode_tmap_bf16_4d(CUtensorMap *m, const void *base, const uint64_t dims[4], const uint64_t strides[3],
+                         const uint32_t box[4], std::string *err)
+{
+    auto fn = tmap_encoder();
+    if (!fn) {
+        *err = "cuTensorMapEncodeTiled is not available from the driver";
+        return false;
+    }
+    cuuint64_t d[4], st[3];
+    cuuint32_t b[4], es[4] = {1, 1, 1, 1};
+    for (int i = 0; i < 4; ++i) {
+        d[i] = dims[i];
+        b[i] = box[i];
+    }
+    for (int i = 0; i < 3; ++i)
+        st[i] = strides[i];
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), d, st, b, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *err = "cuTensorMapEncodeTiled failed (" + std::to_string(static_cast<int>(r)) + ") for a 4D BF16 tensor";
+        return false;
+    }
+    return true;
+}
+
 bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h, std::string *err)
 {
     auto fn = tmap_encoder();

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <vector>
 
+#include "conv_tc.cuh"
 #include "gbst_internal.h"
 
 namespace gbst {
@@ -241,6 +242,233 @@ __global__ void __launch_bounds__(NTHR) k_conv(const ConvArgs a)
     cp_wait<0>();
 }
 
+// 3x3x3 convolution on tcgen05 (see conv_tc.cuh): same arguments and
+// epilogues as k_conv; the input is read through the tensor map `tmap`
+// (channels-last [z][y][x][16] BF16, boxes of 8 channels x 130 points x 3 rows).
+template <int COUT, int EPI>
+__global__ void __launch_bounds__(convtc::NTHREADS, 2)
+    k_conv_tc(const __grid_constant__ CUtensorMap tmap, const ConvArgs a, const convtc::UnitMap um, const int nunits,
+              int *err)
+{
+    using namespace convtc;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm);  // [NS] input plane landed
+    uint64_t *empty = full + NS;                          // [NS] input plane no longer read
+    uint64_t *tfull = empty + NS;                         // [2] accumulator ready
+    uint64_t *tempty = tfull + 2;                         // [2] accumulator read out
+    uint64_t *fin = tempty + 2;                           // all issued MMAs complete
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(fin + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1) + 1;
+    unsigned char *wsm = sm + HDR;
+    unsigned char *slots = sm + HDR + WBYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // weights [tap][co][16 ci] -> [tap][half][co 0..15][8 ci]; rows co >= COUT stay zero
+    for (int i = threadIdx.x; i < 27 * 2 * 16; i += blockDim.x) {
+        const int tap = i >> 5, half = (i >> 4) & 1, co = i & 15;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (co < COUT)
+            v = *reinterpret_cast<const uint4 *>(a.wt + (tap * COUT + co) * CH + half * 8);
+        *reinterpret_cast<uint4 *>(wsm + ((tap * 2 + half) * 16 + co) * 16) = v;
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&tfull[b], 1);
+            bar_init(&tempty[b], NEPI);
+        }
+        bar_init(fin, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the weight stores (generic proxy) become visible to the tensor cores (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    constexpr int WPROD = NEPI, WMMA = NEPI + 1;
+    if (warp == WMMA) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tmem_slot)),
+                     "n"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = *tmem_slot;
+
+    if (warp == WPROD) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                int y0, x0, z0, z1;
+                um.decode(u, y0, x0, z0, z1);
+                for (int p = z0 - 1; p <= z1; ++p) {
+                    const int s = it % NS;
+                    if (it >= NS && !bar_wait(&empty[s], ((it / NS) - 1) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    bar_expect(&full[s], 2 * BOX_BYTES);
+                    unsigned char *dst = slots + s * SLOT;
+                    tma_load_4d(dst, &tmap, &full[s], 0, x0 - 1, y0 - 1, p);
+                    tma_load_4d(dst + HALF, &tmap, &full[s], 8, x0 - 1, y0 - 1, p);
+                    ++it;
+                }
+            }
+            if (!ok) {
+                // let the loads already issued land before the CTA can exit (short bound)
+                for (int k = it - NS < 0 ? 0 : it - NS; k < it; ++k) {
+                    const unsigned long long t0 = now_ns();
+                    while (!bar_try(&full[k % NS], (k / NS) & 1) && now_ns() - t0 < 50000000ull) {
+                    }
+                }
+                atomicCAS(err, 0, static_cast<int>(kDevTimeoutTma));
+            }
+        }
+    } else if (warp == WMMA) {
+        // ------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int it = 0, waited = 0, ot = 0;
+            bool ok = true;
+            const uint32_t wbase = sa(wsm);
+            for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                int y0, x0, z0, z1;
+                um.decode(u, y0, x0, z0, z1);
+                const int base = it, nout = z1 - z0;
+                for (int k = 0; k < nout && ok; ++k) {
+                    // input planes base+k .. base+k+2 (z-1, z, z+1) resident
+                    while (ok && waited <= base + k + 2) {
+                        ok = bar_wait(&full[waited % NS], (waited / NS) & 1, abort_flag);
+                        ++waited;
+                    }
+                    const int b = ot & 1;
+                    if (ok && ot >= 2)
+                        ok = bar_wait(&tempty[b], ((ot >> 1) - 1) & 1, abort_flag);
+                    if (!ok)
+                        break;
+                    fence_after();
+                    const uint32_t d = tbase + b * (RY * 16);
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz) {
+                        const uint32_t pa = sa(slots + ((base + k + dz) % NS) * SLOT);
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx) {
+                                const int tap = (dz * 3 + dy) * 3 + dx;
+                                const uint64_t bd = sdesc(wbase + tap * 512, 256, 128);
+#pragma unroll
+                                for (int r = 0; r < RY; ++r)
+                                    mma_bf16(d + r * 16, sdesc(pa + (r + dy) * ROWB + dx * 16, HALF, 128), bd,
+                                             tap > 0 ? 1u : 0u);
+                            }
+                    }
+                    mma_commit(&tfull[b]);               // accumulator b holds output plane z0 + k
+                    mma_commit(&empty[(base + k) % NS]);  // input plane z0 + k - 1 is done
+                    ++ot;
+                }
+                if (!ok)
+                    break;
+                mma_commit(&empty[(base + nout) % NS]);  // the unit's last two input planes
+                mma_commit(&empty[(base + nout + 1) % NS]);
+                it = base + nout + 2;
+            }
+            // every issued MMA completes before the tensor memory is released
+            mma_commit(fin);
+            const unsigned long long t0 = now_ns();
+            while (!bar_try(fin, 0) && now_ns() - t0 < 100000000ull) {
+            }
+            if (!ok)
+                atomicCAS(err, 0, static_cast<int>(kDevTimeoutTma));
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int quad = warp & 3, c0 = (warp >> 2) * 8;  // points 32 quad .., channels c0 .. c0 + 7
+        float bias[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            bias[c] = (EPI != EPI_DGELU && a.bias && c0 + c < COUT) ? a.bias[c0 + c] : 0.f;
+        int ot = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            int y0, x0, z0, z1;
+            um.decode(u, y0, x0, z0, z1);
+            const int x = x0 + quad * 32 + lane;
+            for (int z = z0; z < z1; ++z) {
+                const int b = ot & 1;
+                ok = __all_sync(0xffffffffu, bar_wait(&tfull[b], (ot >> 1) & 1, abort_flag));
+                if (!ok)
+                    break;
+                fence_after();
+                float vr[RY][8];
+#pragma unroll
+                for (int r = 0; r < RY; ++r)
+                    tmem_ld8(tbase + (static_cast<uint32_t>(quad * 32) << 16) + b * (RY * 16) + r * 16 + c0, vr[r]);
+                fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    bar_arrive(&tempty[b]);
+                ++ot;
+                if (x >= a.d.nx || (EPI == EPI_LINEAR_F32 && c0 != 0))
+                    continue;
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                const int y = y0 + r;
+                if (y >= a.d.ny)
+                    break;
+                const float (&v)[8] = vr[r];
+                const int64_t p = (static_cast<int64_t>(z) * a.d.ny + y) * a.d.nx + x;
+                if (EPI == EPI_LINEAR_F32) {
+                    a.out_f32[p] = v[0] + bias[0];
+                } else if (EPI == EPI_GELU) {
+                    uint32_t zz[4], yy[4];
+#pragma unroll
+                    for (int c = 0; c < 8; c += 2) {
+                        float v0 = v[c] + bias[c], v1 = v[c + 1] + bias[c + 1];
+                        if (c0 + c >= a.cout_valid)
+                            v0 = 0.f;
+                        if (c0 + c + 1 >= a.cout_valid)
+                            v1 = 0.f;
+                        const __nv_bfloat162 zb = __floats2bfloat162_rn(v0, v1);
+                        const __nv_bfloat162 yb = __floats2bfloat162_rn(gelu(v0), gelu(v1));
+                        zz[c >> 1] = *reinterpret_cast<const uint32_t *>(&zb);
+                        yy[c >> 1] = *reinterpret_cast<const uint32_t *>(&yb);
+                    }
+                    *reinterpret_cast<uint4 *>(a.out + p * CH + c0) = make_uint4(yy[0], yy[1], yy[2], yy[3]);
+                    if (a.zout)
+                        *reinterpret_cast<uint4 *>(a.zout + p * CH + c0) = make_uint4(zz[0], zz[1], zz[2], zz[3]);
+                } else {  // EPI_DGELU: data gradient times GELU'(pre-activation below)
+                    const uint4 q0 = *reinterpret_cast<const uint4 *>(a.aux + p * CH + c0);
+                    const uint32_t aw[4] = {q0.x, q0.y, q0.z, q0.w};
+                    uint32_t oo[4];
+#pragma unroll
+                    for (int c = 0; c < 8; c += 2) {
+                        const __nv_bfloat162 zb = *reinterpret_cast<const __nv_bfloat162 *>(&aw[c >> 1]);
+                        const float v0 = v[c] * gelu_grad(__bfloat162float(zb.x));
+                        const float v1 = v[c + 1] * gelu_grad(__bfloat162float(zb.y));
+                        const __nv_bfloat162 ob = __floats2bfloat162_rn(v0, v1);
+                        oo[c >> 1] = *reinterpret_cast<const uint32_t *>(&ob);
+                    }
+                    *reinterpret_cast<uint4 *>(a.out + p * CH + c0) = make_uint4(oo[0], oo[1], oo[2], oo[3]);
+                }
+                }
+            }
+        }
+        if (!ok && lane == 0)
+            atomicCAS(err, 0, static_cast<int>(kDevTimeoutTma));
+    }
+    // teardown: the MMA issuer has seen its last MMA complete
+    __syncthreads();
+    if (warp == WMMA) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(TCOLS) : "memory");
+    }
+}
+
 struct WgradArgs {
     const __nv_bfloat16 *x;   // layer input [z][y][x][16]
     const __nv_bfloat16 *dz;  // output gradient [z][y][x][16]
@@ -447,6 +675,8 @@ struct gbst_closure_s {
     double out_scale = 1.0;     // target in network units: out_scale * (u_ref - u+)
     bool freeze_biases = false; // Adam leaves the biases unchanged
     double loss_weight = 1.0;   // factor on the loss (and its gradient) of the next loss_grad calls
+    int conv_impl = 0;          // 0: tcgen05 (tensor memory), 1: mma.sync (cross-check)
+    int *derr = nullptr;        // device error word of the tcgen05 convolutions
 };
 
 cudaStream_t gbst::closure_stream(gbst_closure c) { return c ? c->stream : nullptr; }
@@ -486,6 +716,69 @@ cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
     dim3 grid(tiles, (a.d.nz + ZCHUNK - 1) / ZCHUNK);
     k_conv<COUT, EPI><<<grid, NTHR, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+int num_sms_dev()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+template <int COUT, int EPI>
+cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
+{
+    using namespace convtc;
+    static int occ = -1;
+    if (occ < 0) {
+        const void *fn = reinterpret_cast<const void *>(&k_conv_tc<COUT, EPI>);
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NTHREADS, SMEM) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 2;
+        }
+    }
+    // activation [z][y][x][16] BF16: dims (channel, x, y, z), boxes of 8 channels x 130 points x 3 rows
+    CUtensorMap m;
+    const uint64_t dims[4] = {static_cast<uint64_t>(CH), static_cast<uint64_t>(a.d.nx),
+                              static_cast<uint64_t>(a.d.ny), static_cast<uint64_t>(a.d.nz)};
+    const uint64_t strides[3] = {CH * 2ull, static_cast<uint64_t>(a.d.nx) * CH * 2,
+                                 static_cast<uint64_t>(a.d.nx) * a.d.ny * CH * 2};
+    const uint32_t box[4] = {8, BOXX, BOXY, 1};
+    std::string msg;
+    if (!encode_tmap_bf16_4d(&m, a.in, dims, strides, box, &msg))
+        return cudaErrorInvalidValue;
+    UnitMap um{(a.d.nx + TXP - 1) / TXP, (a.d.nz + ZCH - 1) / ZCH, (a.d.ny + RY - 1) / RY, a.d.nz};
+    const int64_t nunits = static_cast<int64_t>(um.nxc) * um.nyc * um.nzc;
+    if (nunits > (1ll << 31) - 1)
+        return cudaErrorInvalidValue;
+    const int ctas = static_cast<int>(std::min<int64_t>(nunits, static_cast<int64_t>(num_sms_dev()) * occ));
+    k_conv_tc<COUT, EPI><<<ctas, NTHREADS, SMEM, s>>>(m, a, um, static_cast<int>(nunits), err);
+    return cudaGetLastError();
+}
+
+// The convolution of the closure's selected implementation.
+template <int COUT, int EPI>
+cudaError_t conv(gbst_closure c, const ConvArgs &a)
+{
+    return c->conv_impl == 0 ? launch_conv_tc<COUT, EPI>(a, c->derr, c->stream) : launch_conv<COUT, EPI>(a, c->stream);
+}
+
+// Device error word of the tcgen05 kernels (a bounded wait expired): reported once, then cleared.
+gbst_status check_device_error(gbst_closure c)
+{
+    int code = 0;
+    cudaError_t e = cudaMemcpyAsync(&code, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return record_error(GBST_ECUDA, cudaGetErrorString(e));
+    if (code != 0) {
+        cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream);
+        return record_error(GBST_ETIMEOUT, "closure: a bounded device-side wait expired");
+    }
+    return GBST_OK;
 }
 
 cudaError_t launch_wgrad(const WgradArgs &a, cudaStream_t s)
@@ -545,14 +838,14 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     a.out = c->y1;
     a.zout = keep ? c->z1 : nullptr;
     a.cout_valid = c->hidden;
-    cudaError_t e = launch_conv<16, EPI_GELU>(a, c->stream);
+    cudaError_t e = conv<16, EPI_GELU>(c, a);
     a.in = c->y1;
     a.wt = c->wf[1];
     a.bias = c->p + c->off[3];
     a.out = c->y2;
     a.zout = keep ? c->z2 : nullptr;
     if (e == cudaSuccess)
-        e = launch_conv<16, EPI_GELU>(a, c->stream);
+        e = conv<16, EPI_GELU>(c, a);
     ConvArgs b{};
     b.d = d;
     b.in = c->y2;
@@ -561,7 +854,7 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     b.out_f32 = c->o;
     b.cout_valid = 1;
     if (e == cudaSuccess)
-        e = launch_conv<8, EPI_LINEAR_F32>(b, c->stream);
+        e = conv<8, EPI_LINEAR_F32>(c, b);
     return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
 }
 
@@ -621,11 +914,13 @@ gbst_status closure_create(int cin, int hidden, int64_t max_points, double in_sc
     }
     c->o = static_cast<float *>(cl_alloc(c, static_cast<size_t>(max_points) * sizeof(float)));
     c->dloss = static_cast<double *>(cl_alloc(c, 256));
-    ok = ok && c->o && c->dloss;
+    c->derr = static_cast<int *>(cl_alloc(c, 256));
+    ok = ok && c->o && c->dloss && c->derr;
     if (ok)
         ok = cudaMemsetAsync(c->p, 0, pb, c->stream) == cudaSuccess && cudaMemsetAsync(c->g, 0, pb, c->stream) ==
              cudaSuccess && cudaMemsetAsync(c->m1, 0, pb, c->stream) == cudaSuccess &&
-             cudaMemsetAsync(c->m2, 0, pb, c->stream) == cudaSuccess;
+             cudaMemsetAsync(c->m2, 0, pb, c->stream) == cudaSuccess &&
+             cudaMemsetAsync(c->derr, 0, 256, c->stream) == cudaSuccess;
     if (!ok) {
         closure_destroy(c);
         return record_error(GBST_ENOMEM, "closure_create: device memory");
@@ -675,7 +970,7 @@ static gbst_status copy_out(gbst_closure c, const float *src, float *host, int64
     if (cudaMemcpyAsync(host, src, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return record_error(GBST_ECUDA, "closure: copy failed");
-    return GBST_OK;
+    return check_device_error(c);
 }
 
 gbst_status closure_get_params(gbst_closure c, float *host, int64_t n) { return copy_out(c, c->p, host, n); }
@@ -739,7 +1034,7 @@ gbst_status closure_loss_grad(gbst_closure c, const float *u_plus, const float *
     a.out = c->dz2;
     a.cout_valid = CH;
     if (e == cudaSuccess)
-        e = launch_conv<16, EPI_DGELU>(a, s);
+        e = conv<16, EPI_DGELU>(c, a);
     // layer 2
     w.x = c->y1;
     w.dz = c->dz2;
@@ -754,7 +1049,7 @@ gbst_status closure_loss_grad(gbst_closure c, const float *u_plus, const float *
     a.aux = c->z1;
     a.out = c->dz1;
     if (e == cudaSuccess)
-        e = launch_conv<16, EPI_DGELU>(a, s);
+        e = conv<16, EPI_DGELU>(c, a);
     // layer 1 (no data gradient for the inputs)
     w.x = c->x;
     w.dz = c->dz1;
@@ -773,6 +1068,9 @@ gbst_status closure_loss_grad(gbst_closure c, const float *u_plus, const float *
         e = cudaStreamSynchronize(s);
     if (e != cudaSuccess)
         return record_error(GBST_ECUDA, cudaGetErrorString(e));
+    st = check_device_error(c);
+    if (st != GBST_OK)
+        return st;
     *loss = c->loss_weight * l / static_cast<double>(n);
     return GBST_OK;
 }
@@ -790,6 +1088,14 @@ gbst_status closure_set_loss_weight(gbst_closure c, double w)
     if (!c || !(w > 0.0))
         return record_error(GBST_EINVAL, "closure_set_loss_weight: null closure or weight <= 0");
     c->loss_weight = w;
+    return GBST_OK;
+}
+
+gbst_status closure_set_conv_impl(gbst_closure c, int impl)
+{
+    if (!c || (impl != 0 && impl != 1))
+        return record_error(GBST_EINVAL, "closure_set_conv_impl: null closure or impl not 0 / 1");
+    c->conv_impl = impl;
     return GBST_OK;
 }
 

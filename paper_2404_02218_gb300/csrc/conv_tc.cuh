@@ -1,0 +1,175 @@
+// 3x3x3 convolution of a channels-last 16-channel BF16 tensor on the 5th-
+// generation tensor cores (tcgen05.mma, accumulators in tensor memory),
+// zero padding, 16 output channels (fewer are zero-padded weights).
+//
+// Implicit GEMM per output row segment: D[128 points x 16 co] = sum over the 27
+// taps of A_tap[128 points x 16 ci] B_tap[16 ci x 16 co].  A CTA owns 128
+// consecutive x points of RY = 4 rows and marches along z.  For every input
+// plane a TMA load brings rows y0-1..y0+RY, x0-1..x0+128 (out of range ->
+// zeros, which is the zero padding) as two boxes of 8 channels, so each box is
+// a K-major, unswizzled tcgen05 operand: 8 points x 16 bytes form a contiguous
+// core matrix.  A_tap of row r is then just a shifted view of the plane slot
+// (start address + (r + dy) * row + dx * 16 bytes), no data movement per tap.
+// The weights of all taps sit in shared memory in the same layout.  The MMAs
+// of a plane are issued tap-major across the RY rows, so consecutive MMAs
+// accumulate into different tensor-memory columns (RY independent chains:
+// an M = 128, N = 16 MMA is short, and a single chain would wait on itself).
+//
+// Warp roles: warps 0-7 epilogue (warp w reads tensor-memory lanes
+// 32 (w & 3) .. +31 = points, channels 8 (w >> 2) .. +7 of each row), warp 8
+// TMA producer, warp 9 allocates 2 RY 16 tensor-memory columns (two
+// accumulator sets) and one lane issues the MMAs.
+// Pipelines: input plane ring (full / empty mbarriers; a tcgen05.commit frees
+// a plane once the MMAs reading it are done) and the accumulator pair
+// (tfull: commit after the 27 MMAs of a plane; tempty: the epilogue warps).
+// Every wait is bounded; on expiry the CTA sets the error word, lets issued
+// work finish (bounded) and releases its tensor memory.
+#pragma once
+
+#include "gbst_internal.h"
+
+namespace gbst {
+namespace convtc {
+
+constexpr int TXP = 128;                 // output points per CTA row segment (MMA M)
+constexpr int RY = 4;                    // output rows per CTA (independent accumulation chains)
+constexpr int BOXX = TXP + 2;            // input points per row (x halo 1 each side)
+constexpr int BOXY = RY + 2;             // input rows per plane (y halo 1 each side)
+constexpr int ROWB = BOXX * 16;          // bytes of one row of 8 channels
+constexpr int HALF = (BOXY * ROWB + 127) / 128 * 128;  // one 8-channel box
+constexpr int SLOT = 2 * HALF;           // one input plane (both channel halves)
+constexpr int NS = 4;                    // plane slots: z-1, z, z+1 and one in flight
+constexpr int TCOLS = 2 * RY * 16;       // tensor-memory columns: two accumulator sets of RY x 16
+constexpr int WBYTES = 27 * 2 * 16 * 16; // weights: [tap][half][co 16][8 ci] BF16
+constexpr int HDR = 256;                 // barriers and flags
+constexpr int SMEM = HDR + WBYTES + NS * SLOT;
+constexpr int NEPI = 8;                  // epilogue warps: lane quadrant w & 3, channels 8 (w >> 2) ..
+constexpr int NTHREADS = (NEPI + 2) * 32;
+constexpr int ZCH = 32;                  // output planes per work unit
+constexpr uint32_t BOX_BYTES = BOXY * BOXX * 16;  // bytes one box delivers
+
+__device__ __forceinline__ uint32_t sa(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(sa(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; gives up when another thread of the CTA has given up.
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag)
+{
+    if (bar_try(b, parity))
+        return true;
+    const unsigned long long t0 = now_ns();
+    while (!bar_try(b, parity)) {
+        if (*abort_flag)
+            return false;
+        if (now_ns() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c, int x, int y,
+                                            int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sa(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(z), "r"(sa(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle.  lbo: bytes between
+// core matrices along K, sbo: bytes between 8-row groups along M / N.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = 16.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+                 : "memory");
+}
+
+// 8 consecutive FP32 columns of the warp's 32 lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Work unit u -> (row group y0, x chunk, z chunk); z chunk outermost so that
+// the CTAs of one wave hold neighbouring rows of the same planes (halo rows
+// shared in L2).
+struct UnitMap {
+    int nxc, nzc, nyc, nz;
+    __device__ void decode(int u, int &y0, int &x0, int &z0, int &z1) const
+    {
+        const int xc = u % nxc;
+        const int rest = u / nxc;
+        y0 = (rest % nyc) * RY;
+        const int zc = rest / nyc;
+        x0 = xc * TXP;
+        z0 = zc * ZCH;
+        z1 = min(nz, z0 + ZCH);
+    }
+};
+
+}  // namespace convtc
+}  // namespace gbst

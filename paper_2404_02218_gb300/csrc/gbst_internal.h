@@ -176,6 +176,9 @@ cudaStream_t closure_stream(gbst_closure c);
 gbst_status record_error(gbst_status st, const char *msg);
 
 // Tensor-map encoding through the driver entry point.
+// Tiled tensor map of a 4D BF16 tensor (dims innermost first; strides in bytes of dims 1..3).
+bool encode_tmap_bf16_4d(CUtensorMap *m, const void *base, const uint64_t dims[4], const uint64_t strides[3],
+                         const uint32_t box[4], std::string *err);
 bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h,
                  std::string *err);
 

@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
                 "closure_adam_step": ([H, dbl], i32),
                 "closure_set_out_scale": ([H, dbl], i32),
                 "closure_freeze_biases": ([H, i32], i32),
+                "closure_set_conv_impl": ([H, i32], i32),
                 "closure_set_loss_weight": ([H, dbl], i32),
                 "stencil_attach_closure": ([H, H, dbl], i32),
                 "stencil_get_field_strided": ([H, i32, vp, i32], i32),
@@ -347,6 +348,10 @@ def closure_loss_grad(c, up: int, un: int, cn: int, ref: int, dims) -> float:
 
 def closure_adam_step(c, lr: float):
     _check(lib().closure_adam_step(c, float(lr)), "closure_adam_step")
+
+
+def closure_set_conv_impl(c, impl: int):
+    _check(lib().closure_set_conv_impl(c, int(impl)), "closure_set_conv_impl")
 
 
 def stencil_attach_closure(h, c, c_ref: float):

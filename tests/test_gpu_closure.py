@@ -71,6 +71,48 @@ def test_forward_matches_oracle(torch_cuda, dims):
     cl.close()
 
 
+def test_tcgen05_and_mma_sync_convolutions_agree(torch_cuda):
+    """The tcgen05 (tensor memory) and mma.sync convolutions compute the same network."""
+    from paper_2404_02218_gb300.closure import Closure, flatten_params
+    dims = (300, 21, 40)  # several 128-point rows, a ragged row end, two z chunks
+    s = 2.0
+    (up, un, cn, _), (tu, tn, tc, _) = make_inputs(torch_cuda, dims, 45)
+    p = oracle_params()
+    cl = Closure(int(np.prod(dims)), s)
+    cl.set_params(flatten_params(p))
+    a = cl.forward(tu, tn, tc).cpu().numpy()
+    cl.set_conv_impl(1)
+    b = cl.forward(tu, tn, tc).cpu().numpy()
+    assert np.abs(b).max() > 0
+    # FP32 sums of the same BF16 products in another order; a few BF16 roundings of
+    # intermediate activations may differ by one unit
+    assert rel(a, b) <= 2e-3
+    o, _ = ocl.forward(closure_inputs(s, up, un, cn), p)
+    assert rel(a * s, o[0]) <= TOL_NET
+    cl.close()
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+def test_loss_and_gradients_match_oracle_both_impls(torch_cuda, impl):
+    from paper_2404_02218_gb300.closure import Closure, flatten_params, unflatten_params
+    dims = (140, 12, 9)
+    s = 2.0
+    (up, un, cn, ref), (tu, tn, tc, tr) = make_inputs(torch_cuda, dims, 52)
+    p = oracle_params()
+    cl = Closure(int(np.prod(dims)), s)
+    cl.set_conv_impl(impl)
+    cl.set_params(flatten_params(p))
+    loss = cl.loss_grad(tu, tn, tc, tr)
+    g = unflatten_params(cl.get_grads())
+    x = closure_inputs(s, up, un, cn)
+    target = (s * (ref.astype(np.float64) - up))[None]
+    L, gref = ocl.loss_and_grads(x, target, p)
+    assert loss == pytest.approx(L, rel=TOL_NET)
+    for k in ocl.PARAM_ORDER:
+        assert rel(g[k], gref[k]) <= TOL_NET, k
+    cl.close()
+
+
 def test_loss_and_gradients_match_oracle(torch_cuda):
     from paper_2404_02218_gb300.closure import Closure, flatten_params, unflatten_params
     dims = (24, 20, 12)
