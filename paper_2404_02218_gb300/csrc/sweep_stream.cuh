@@ -127,9 +127,9 @@ struct Storage<GBST_BF16> {
     }
     __device__ __forceinline__ static uint32_t pk2(float lo, float hi)
     {
-        const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
-        const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
-        return l | (h << 16);
+        // both halves rounded to nearest even in one conversion (lo in the low 16 bits)
+        const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&b);
     }
     __device__ __forceinline__ static uint4 pack(const float *o)
     {
