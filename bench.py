@@ -198,7 +198,8 @@ def timed_runs(torch, stream, fn, reps=1):
 
 
 def extras(torch, hbm: float, tune: bool):
-    """Decomposition, 768^3 wave FP32 vs BF16, and the 64-grid batch (not in the timed region)."""
+    """Decomposition, 768^3 wave FP32 vs BF16, 2D at 16384^2, the 64-grid batch and the closure
+    (not in the timed region)."""
     import synthetic
     from paper_2404_02218_gb300.grid import Grid, Batch
     out = {}
@@ -243,6 +244,40 @@ def extras(torch, hbm: float, tune: bool):
                                        "steps": nsteps, "plan": json.loads(g.describe())}
         g.close()
     del c
+
+    # 2D at the paper's large size: heat 16384^2, orders 2/4/8, and the order-8 acoustic wave
+    n2 = 16384
+    u2 = synthetic.uniform_field_torch(7, (n2, n2), "cuda")
+    for so in (2, 4, 8):
+        a2 = float(np.float32(0.8 * synthetic.heat_a_max(2, so)))
+        g = Grid(2, (n2, n2), so, "heat", dt=a2, stream=stream)
+        g.set_field("u", u2)
+        if tune:
+            g.tune(reps=2)
+        g.set_field("u", u2)
+        ms = timed_runs(torch, stream, lambda: g.run(STEPS_PER_RUN))
+        pts = STEPS_PER_RUN * n2 * n2
+        out[f"heat2d_{n2}_so{so}"] = {"gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6,
+                                     "frac": 8 * pts / ms / 1e6 / hbm, "steps": STEPS_PER_RUN,
+                                     "plan": json.loads(g.describe())}
+        g.close()
+    del u2
+    speeds = synthetic.five_layer_speeds()
+    c2 = torch.from_numpy(synthetic.layered_velocity((n2, n2), speeds)).cuda()
+    h2 = 10.0
+    dt2 = 0.5 * synthetic.wave_courant_max(2, 8) * h2 / max(speeds)
+    g = Grid(2, (n2, n2), 8, "wave", h=h2, dt=dt2, stream=stream)
+    g.set_field("vel", c2)
+    g.set_source((n2 // 2, n2 // 3), 10.0, 0.1, 1.0)
+    if tune:
+        g.tune(reps=2)
+    ms = timed_runs(torch, stream, lambda: g.run(100))
+    pts = 100 * n2 * n2
+    out[f"wave2d_{n2}_so8_f32"] = {"gpts": pts / ms / 1e6, "gbs": 16 * pts / ms / 1e6,
+                                   "frac": 16 * pts / ms / 1e6 / hbm, "bytes_per_pt": 16, "steps": 100,
+                                   "plan": json.loads(g.describe())}
+    g.close()
+    del c2
 
     # batched wave: 64 grids U[96,256]^3, order 4, 300 steps
     cases = synthetic.batch_wave_cases()
