@@ -24,6 +24,9 @@ const Entry kTable[] = {
     GBST_EQS(4, GBST_F32, false, 4, 2, 3, 1, 32),
     GBST_EQS(4, GBST_F32, false, 4, 2, 5, 2, 32),
     GBST_EQS(4, GBST_F32, false, 4, 2, 3, 1, 8),
+    GBST_EQS(4, GBST_F32, false, 4, 4, 3, 2, 32),
+    GBST_EQS(4, GBST_F32, false, 8, 4, 2, 1, 32),
+    GBST_EQS(4, GBST_F32, false, 4, 8, 2, 1, 32),
     GBST_EQS(4, GBST_BF16, false, 4, 1, 3, 1, 16),
     GBST_EQS(4, GBST_BF16, false, 4, 1, 3, 1, 8),
 };

@@ -121,24 +121,45 @@ def matching_variants(so, eq, storage, ndim):
 
 @pytest.mark.parametrize("so", [2, 4, 8])
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
-def test_every_kernel_variant_bitwise(torch_cuda, so, storage):
+@pytest.mark.parametrize("ndim", [3, 2])
+def test_every_kernel_variant_bitwise(torch_cuda, so, storage, ndim):
     """Every compiled tile shape / depth / register variant gives the same bits as the simple kernel."""
-    dims = (130, 70, 19)
+    dims = (130, 70, 19) if ndim == 3 else (300, 77)
     u0 = synthetic.uniform_field(9, tuple(reversed(dims)))
-    a = float(np.float32(0.8 * synthetic.heat_a_max(3, so)))
-    ref = make_grid(torch_cuda, 3, dims, so, "heat", storage=storage, dt=a, kernel="simple")
+    a = float(np.float32(0.8 * synthetic.heat_a_max(ndim, so)))
+    ref = make_grid(torch_cuda, ndim, dims, so, "heat", storage=storage, dt=a, kernel="simple")
     ref.set_field("u", u0)
     ref.run(4)
     want = ref.get_field("u")
-    variants = matching_variants(so, "heat", storage, 3)
+    variants = matching_variants(so, "heat", storage, ndim)
     assert variants
-    g = make_grid(torch_cuda, 3, dims, so, "heat", storage=storage, dt=a)
+    g = make_grid(torch_cuda, ndim, dims, so, "heat", storage=storage, dt=a)
     for v in variants:
         for zc in (0, 3):
             g.set_field("u", u0)
             g.set_plan(v, 0, zc, 0)
             g.run(4)
             np.testing.assert_array_equal(g.get_field("u"), want, err_msg=f"variant {v} zchunks {zc}")
+
+
+@pytest.mark.parametrize("so", [2, 4, 8])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_every_wave_variant_bitwise(torch_cuda, so, storage):
+    """Wave variants (kappa and u^{n-1} by TMA into the centre slots) == the simple kernel, bit for bit."""
+    dims = (130, 37, 21)
+    ref, *_ = wave_setup(torch_cuda, dims, so, storage=storage, kernel="simple")
+    ref.run(5)
+    want_u, want_p = ref.get_field("u"), ref.get_field("u_prev")
+    variants = matching_variants(so, "wave", storage, 3)
+    assert variants
+    for v in variants:
+        for zc in (0, 2):
+            g, *_ = wave_setup(torch_cuda, dims, so, storage=storage)
+            g.set_plan(v, 0, zc, 0)
+            g.run(5)
+            np.testing.assert_array_equal(g.get_field("u"), want_u, err_msg=f"variant {v} zchunks {zc}")
+            np.testing.assert_array_equal(g.get_field("u_prev"), want_p, err_msg=f"variant {v} zchunks {zc}")
+            g.close()
 
 
 def test_autotuner_keeps_fields_and_picks_a_plan(torch_cuda):
