@@ -390,32 +390,44 @@ def run_case(args):
 
 
 # -------------------------------------------------------------- our path ---
-KERNEL_SOURCES = ("sweep_stream.cuh", "sweep_r1.cu", "sweep_r2.cu", "sweep_r4.cu", "gbst_internal.h")
+KERNEL_SOURCES = ("sweep_stream.cuh", "sweep_tb.cuh", "gbst_internal.h")
 
 
 def kernel_source_sha() -> str:
-    """Hash of the sweep kernel's sources; a traffic figure is used only for this exact source."""
+    """Hash of the sweep kernels' code; a traffic figure is used only for this exact code."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2404_02218_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key: str, plan: dict):
-    """DRAM bytes per launch from the committed ncu traffic summary, if it was taken on the
-    current kernel source with the same plan (variant and z-chunking).
+def kernel_name(plan: dict) -> str:
+    """Template instance of a heat FP32 3D plan, as the profiler names it."""
+    px = 4
+    txt = plan["tile"][0] // px
+    if plan.get("tb", 1) == 2:
+        nw = plan["threads"] // 32 - 1
+        return f"k_tb<{plan['R']}, {nw}, {plan['py']}, {plan['depth']}, {plan['minb']}>"
+    nc = plan["threads"] // 32
+    return f"k_stream<{plan['R']}, 0, 0, 1, {nc}, {plan['py']}, {plan['depth']}, {plan['minb']}, {txt}>"
 
-    The summary's table rows read ``| key | source sha | dram bytes per launch | variant | zchunks | ...``."""
+
+def ncu_traffic(plan: dict):
+    """DRAM bytes per launch from the committed ncu traffic summary, if it was taken on the
+    current kernel code with the same kernel instance and z-chunking.
+
+    The summary's table rows read ``| kernel instance | source sha | dram bytes per launch | zchunks |``."""
     path = os.path.join(ROOT, "profiles", "sweep_dram_traffic.md")
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
+    want = kernel_name(plan)
     for ln in lines:
-        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
-        if len(cells) >= 5 and cells[0] == kernel_key and cells[1] == kernel_source_sha():
+        cells = [c.strip().strip("`") for c in ln.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == want and cells[1] == kernel_source_sha():
             try:
-                if int(cells[3]) != plan.get("variant") or int(cells[4]) != plan.get("zchunks"):
+                if int(cells[3]) != plan.get("zchunks"):
                     return None
                 return float(cells[2])
             except ValueError:
@@ -508,9 +520,10 @@ def run_ours(args):
                                  "steps_per_launch": tb, "avg_launch_ms": avg * 1e3, "plan": plan}
     # dominant kernel: the largest share of the step's device time
     dom = max(per, key=lambda k: per[k]["avg_launch_ms"] * -(-STEPS_PER_RUN // per[k]["steps_per_launch"]))
-    traffic = ncu_traffic(dom, per[dom]["plan"])
+    traffic = ncu_traffic(per[dom]["plan"])
     roofline = {"bound": "hbm", "achieved": per[dom]["gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": per[dom]["gbs"] / hbm, "traffic": traffic, "kernel": dom,
+                "kernel_instance": kernel_name(per[dom]["plan"]),
                 "algorithmic_bytes_per_launch": BYTES_PER_PT * N ** 3, "peak_source": peak_kind}
 
     # End to end through the C ABI with host buffers: every step copies u in from
