@@ -414,8 +414,10 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
     p.txt = p.var.txt;
     (void)nt;
     const int TX = tile_w(p.var, px), TY = tile_h(p.var);
-    // two-step variants read the tile plus 2 chunks in x and 2r rows in y per side
-    const int box_w = TX + 2 * G * p.var.tb, box_h = TY + 2 * h->R * p.var.tb;
+    // two-step variants read the tile plus 2 chunks in x and 2r rows in y per side;
+    // y-streaming (2D) variants read one row per plane
+    const bool ys = p.stream && p.var.ys;
+    const int box_w = TX + 2 * G * p.var.tb, box_h = ys ? 1 : TY + 2 * h->R * p.var.tb;
     if (box_w > 256 || box_h > 256)
         return fail(GBST_EINVAL, "tile %dx%d too large for a TMA box", TX, TY);
     p.max_box_bytes = box_w * box_h * h->es;
@@ -426,7 +428,7 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
         const Sub &s = h->subs[i];
         g.txt = p.txt;
         g.tiles_x = static_cast<int>((s.lu.nx + TX - 1) / TX);
-        g.tiles_y = static_cast<int>((s.lu.ny + TY - 1) / TY);
+        g.tiles_y = ys ? 1 : static_cast<int>((s.lu.ny + TY - 1) / TY);
         g.box_bytes = p.max_box_bytes;
         T += static_cast<int64_t>(g.tiles_x) * g.tiles_y;
         if (p.stream) {
@@ -449,9 +451,10 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
         if (p.occupancy <= 0)
             return fail(GBST_ENOTSUP, "streaming kernel does not fit (smem %zu)", p.smem);
         const int64_t cmax = static_cast<int64_t>(p.occupancy) * num_sms();
-        const int64_t nz = h->subs[0].lu.nz;
+        // extent along the streaming axis: z (3D) or y (2D streamed along y)
+        const int64_t nz = ys ? h->subs[0].lu.ny : h->subs[0].lu.nz;
         int zc = 1;
-        if (h->ndim == 3) {
+        if (h->ndim == 3 || ys) {
             if (zchunks_req > 0) {
                 zc = static_cast<int>(std::min<int64_t>(zchunks_req, nz));
             } else {
@@ -473,7 +476,7 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
         for (int c = 0; c < zc; ++c)
             for (size_t i = 0; i < h->subs.size(); ++i) {
                 const GridDev &g = h->hgrids[i];
-                const int64_t n = h->subs[i].lu.nz;
+                const int64_t n = ys ? h->subs[i].lu.ny : h->subs[i].lu.nz;
                 const int z0 = static_cast<int>(n * c / zc), z1 = static_cast<int>(n * (c + 1) / zc);
                 if (z1 <= z0)
                     continue;
@@ -1626,11 +1629,11 @@ gbst_status stencil_describe(gbst_handle h, char *buf, size_t len)
     snprintf(buf, len,
              "{\"kernel\": \"%s\", \"R\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, \"tile\": [%d, %d], "
              "\"zchunks\": %d, \"units\": %d, \"ctas\": %d, \"occupancy\": %d, \"smem\": %zu, \"subdomains\": %zu, "
-             "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d, \"tb\": %d}",
+             "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d, \"tb\": %d, \"ys\": %d}",
              p.stream ? "stream" : "simple", h->R, p.var.nthreads, p.var.py, p.var.depth, tile_w(p.var, px),
              p.stream ? tile_h(p.var) : (p.var.nthreads / std::max(1, p.txt)) * p.var.py, p.zchunks, p.nunits,
              p.ctas, p.occupancy, p.smem, h->subs.size(), h->nboxes, p.variant, p.var.minb,
-             p.stream ? p.var.tb : 1);
+             p.stream ? p.var.tb : 1, p.stream && p.var.ys ? 1 : 0);
     return GBST_OK;
 }
 
@@ -1681,8 +1684,8 @@ gbst_status stencil_variant_info(int i, char *buf, size_t len)
         return fail(GBST_EINVAL, "bad variant index or buffer");
     snprintf(buf, len,
              "{\"R\": %d, \"eq\": %d, \"storage\": %d, \"has_z\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, "
-             "\"minb\": %d, \"txt\": %d, \"tb\": %d}",
-             v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb, v.txt, v.tb);
+             "\"minb\": %d, \"txt\": %d, \"tb\": %d, \"ys\": %d}",
+             v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb, v.txt, v.tb, v.ys ? 1 : 0);
     return GBST_OK;
 }
 
@@ -1737,8 +1740,9 @@ gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len)
             continue;
         {
             const int txt = v.txt;
-            const int *zl = h->ndim == 3 ? zlist_3d : zlist_2d;
-            const int nz = h->ndim == 3 ? 6 : 1;
+            const bool chunked = h->ndim == 3 || v.ys;
+            const int *zl = chunked ? zlist_3d : zlist_2d;
+            const int nz = chunked ? 6 : 1;
             int last_units = -1;
             for (int zi = 0; zi < nz; ++zi) {
                 if (build_plan(h, vi, txt, zl[zi], 0) != GBST_OK)

@@ -97,6 +97,7 @@ struct StreamVariant {
     int minb;       // minimum resident CTAs per SM requested from the compiler (register bound)
     int txt;        // threads along x of a tile (tile width = txt * 16 bytes of storage)
     int tb = 1;     // time steps per launch: 1, or 2 (temporally blocked heat kernel)
+    bool ys = false; // 2D grid streamed along y (one-row tiles)
 };
 
 // Tile of a variant: width in points, height in rows (a temporally blocked
@@ -105,8 +106,12 @@ struct StreamVariant {
 inline int tile_w(const StreamVariant &v, int px) { return v.txt * px; }
 inline int tile_h(const StreamVariant &v)
 {
+    if (v.ys)
+        return 1;
     return v.tb == 2 ? (v.nthreads / 32 - 1) * v.py - 2 * v.R : (v.nthreads / v.txt) * v.py;
 }
+// Radius along the streaming axis (planes kept below the centre in the ring).
+inline int stream_rz(const StreamVariant &v) { return (v.has_z || v.ys) ? v.R : 0; }
 
 // Number of element columns a thread owns (16 bytes of storage).
 inline int px_of(int storage) { return storage == GBST_BF16 ? 8 : 4; }

@@ -29,6 +29,9 @@ const Entry kTable[] = {
     GBST_EQS(1, GBST_F32, false, 4, 8, 2, 1, 32),
     GBST_EQS(1, GBST_BF16, false, 4, 1, 3, 1, 16),
     GBST_EQS(1, GBST_BF16, false, 4, 1, 3, 1, 8),
+    GBST_EQS_YS(1, GBST_F32, 4, 8),
+    GBST_EQS_YS(1, GBST_F32, 6, 8),
+    GBST_EQS_YS(1, GBST_F32, 3, 12),
 };
 }  // namespace
 

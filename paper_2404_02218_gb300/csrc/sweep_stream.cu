@@ -49,7 +49,7 @@ const Entry *find(const StreamVariant &v)
         const Entry *e = r.at(i);
         if (e->v.R == v.R && e->v.eq == v.eq && e->v.storage == v.storage && e->v.has_z == v.has_z &&
             e->v.nthreads == v.nthreads && e->v.py == v.py && e->v.depth == v.depth && e->v.minb == v.minb &&
-            e->v.txt == v.txt && e->v.tb == v.tb)
+            e->v.txt == v.txt && e->v.tb == v.tb && e->v.ys == v.ys)
             return e;
     }
     return nullptr;
@@ -104,7 +104,7 @@ static size_t centre_bytes(const StreamVariant &v)
 
 size_t stream_smem_bytes(const StreamVariant &v, int max_box_bytes)
 {
-    const int rz = v.has_z ? v.R : 0;
+    const int rz = stream_rz(v);
     const int slots = rz + 1 + v.depth;
     const size_t slot = (static_cast<size_t>(max_box_bytes) + 127) / 128 * 128;
     return 256 + slots * slot + centre_bytes(v);
@@ -112,7 +112,7 @@ size_t stream_smem_bytes(const StreamVariant &v, int max_box_bytes)
 
 int stream_slot_bytes(const StreamVariant &v, size_t smem)
 {
-    const int rz = v.has_z ? v.R : 0;
+    const int rz = stream_rz(v);
     const int slots = rz + 1 + v.depth;
     return static_cast<int>((smem - 256 - centre_bytes(v)) / slots);
 }

@@ -237,7 +237,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *counter, unsigned int
 // empty[j % NB] when it has finished iteration j (its newest plane and its
 // centre plane, slot (j - rz) % S); the producer waits for empty of iteration
 // it - NB before reusing that iteration's slot for iteration it.
-template <int R, int EQ, int ST, bool HAS_Z, int NC, int PY, int D, int MINB, int TXT>
+//
+// YS = true (2D grids): the streaming axis is y.  A plane slot is one row of
+// TX points (plus the x halo), the register queue holds the 2r+1 rows around
+// the output row, and there is no middle axis; the update is the 2D one,
+// ((x- + x+) + (y- + y+)) per offset, bit-identical to the 2D tile mode.
+template <int R, int EQ, int ST, bool HAS_Z, int NC, int PY, int D, int MINB, int TXT, bool YS = false>
 __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs a, const int slot_bytes)
 {
     using St = Storage<ST>;
@@ -245,12 +250,15 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
     constexpr int PX = St::PX;
     constexpr int ES = St::ES;
     constexpr int G = PX;               // x halo in elements (16 bytes)
-    constexpr int RZ = HAS_Z ? R : 0;   // z radius
+    constexpr bool ZQ = HAS_Z || YS;    // a register queue along the streaming axis
+    constexpr bool MID = !YS;           // y neighbours from the plane slot (3D, 2D tiles)
+    constexpr int RZ = ZQ ? R : 0;      // radius along the streaming axis
     constexpr int QN = 2 * RZ + 1;      // register queue length
     constexpr int S = RZ + 1 + D;       // plane slots
     constexpr int NB = D + 1;           // barrier pairs (= loads in flight)
     constexpr int TX = TXT * PX;                 // tile width (points)
-    constexpr int TY = (NT / TXT) * PY;          // tile height (rows)
+    constexpr int TY = (NT / TXT) * PY;          // tile height (rows; 1 when YS)
+    static_assert(!YS || (TY == 1 && !HAS_Z), "y streaming: one-row tiles of a 2D grid");
     constexpr int ROW_BYTES = (TX + 2 * G) * ES; // one row of a plane slot
     // wave: kappa (FP32) and u^{n-1} of the centre plane, TX x TY each, per barrier pair
     constexpr int CK = TX * TY * 4;
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
         for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
             const Unit u = a.units[ui];
             const GridDev &g = a.grids[u.grid];
-            const int bx = (u.tile % g.tiles_x) * TX, by = (u.tile / g.tiles_x) * TY;
+            const int bx = (u.tile % g.tiles_x) * TX, by = YS ? 0 : (u.tile / g.tiles_x) * TY;
             const CUtensorMap *map = &g.tmap[parity];
             const CUtensorMap *umap = &g.tmap_c[1 - parity];  // u^{n-1}, interior boxes
             const CUtensorMap *kmap = &g.tmap_k;              // kappa, interior boxes
@@ -303,13 +311,21 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                 const bool centre = EQ == GBST_WAVE && l >= 2 * RZ;
                 uint64_t *bar = &full[it % NB];
                 mbar_arrive_expect_tx(bar, bytes + (centre ? CBYTES : 0));
-                tma_load_plane(slots + (it % S) * slot_bytes, map, bar, bx, by, u.z0 + l);
+                if (YS)  // row u.z0 - r + l (padded index u.z0 + l)
+                    tma_load_plane(slots + (it % S) * slot_bytes, map, bar, bx, u.z0 + l, 0);
+                else
+                    tma_load_plane(slots + (it % S) * slot_bytes, map, bar, bx, by, u.z0 + l);
                 if (centre) {
                     // centre plane of this iteration: interior z = z0 + l - 2rz, padded + rz
                     unsigned char *cs = cslots + (it % NB) * CSLOT;
                     const int zp = u.z0 + l - RZ;
-                    tma_load_plane(cs, kmap, bar, bx + G, by + R, zp);
-                    tma_load_plane(cs + CK, umap, bar, bx + G, by + R, zp);
+                    if (YS) {
+                        tma_load_plane(cs, kmap, bar, bx + G, zp, 0);
+                        tma_load_plane(cs + CK, umap, bar, bx + G, zp, 0);
+                    } else {
+                        tma_load_plane(cs, kmap, bar, bx + G, by + R, zp);
+                        tma_load_plane(cs + CK, umap, bar, bx + G, by + R, zp);
+                    }
                 }
             }
         }
@@ -353,17 +369,18 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
             const float2 a2 = make_float2(gp->heat_a, gp->heat_a);
             const int tx = tid % TXT, ty = tid / TXT;
             const int x0 = (u.tile % tiles_x) * TX + tx * PX;
-            const int y0 = (u.tile / tiles_x) * TY + ty * PY;
+            const int y0 = YS ? 0 : (u.tile / tiles_x) * TY + ty * PY;
             constexpr int row_bytes = ROW_BYTES;
-            const int own_off = (R + ty * PY) * row_bytes + (G + tx * PX) * ES;
+            const int own_off = ((MID ? R : 0) + ty * PY) * row_bytes + (G + tx * PX) * ES;
             const bool xfull = x0 + PX <= nx;
             bool row_ok[PY];
     #pragma unroll
             for (int r_ = 0; r_ < PY; ++r_)
-                row_ok[r_] = y0 + r_ < ny && x0 < nx;
+                row_ok[r_] = (YS || y0 + r_ < ny) && x0 < nx;
             // running pointers to the thread's first row of the current output plane
-            const int64_t plane_elems = rows * pitch;
-            unsigned char *optr = outbase + (origin + (static_cast<int64_t>(u.z0) * rows + y0) * pitch + x0) * ES;
+            // output "planes" follow the streaming axis: planes (3D, 2D tiles) or rows (YS)
+            const int64_t plane_elems = YS ? pitch : rows * pitch;
+            unsigned char *optr = outbase + (origin + (static_cast<int64_t>(u.z0) * (YS ? 1 : rows) + y0) * pitch + x0) * ES;
             const int64_t row_stride = pitch * ES;
 
             // prologue: the 2*rz planes below the first output plane fill the queue
@@ -432,10 +449,12 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                         const int slot_c = slot_n >= RZ ? slot_n - RZ : slot_n - RZ + S;
                         const unsigned char *cb = slots + slot_c * slot_bytes + own_off;
                         uint4 ylo[R], yhi[R], xl[PY], xr[PY];
+                        if (MID) {
     #pragma unroll
-                        for (int m = 1; m <= R; ++m) {
-                            ylo[m - 1] = lds128(cb - m * row_bytes);
-                            yhi[m - 1] = lds128(cb + (PY - 1 + m) * row_bytes);
+                            for (int m = 1; m <= R; ++m) {
+                                ylo[m - 1] = lds128(cb - m * row_bytes);
+                                yhi[m - 1] = lds128(cb + (PY - 1 + m) * row_bytes);
+                            }
                         }
     #pragma unroll
                         for (int r_ = 0; r_ < PY; ++r_) {
@@ -477,8 +496,10 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                                     const int e = 2 * pp;
                                     const float2 xm = make_float2(xel(r_, e - m), xel(r_, e + 1 - m));
                                     const float2 xp = make_float2(xel(r_, e + m), xel(r_, e + 1 + m));
-                                    float2 t = __fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
-                                    if (HAS_Z)
+                                    float2 t = __fadd2_rn(xm, xp);
+                                    if (MID)
+                                        t = __fadd2_rn(t, __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
+                                    if (ZQ)
                                         t = __fadd2_rn(t, __fadd2_rn(q[(qc - m + 2 * QN) % QN][r_][pp], q[(qc + m) % QN][r_][pp]));
                                     sv[r_][pp] = __ffma2_rn(w2[m], t, sv[r_][pp]);
                                 }
@@ -509,8 +530,8 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                             mbar_arrive(&empty[bar_i]);
                         advance();
 
-                        if (src_unit && zc == src_z) {
-                            const int sr = src_y - y0, si = src_x - x0;
+                        if (src_unit && zc == (YS ? src_y : src_z)) {
+                            const int sr = YS ? 0 : src_y - y0, si = src_x - x0;
                             if (sr >= 0 && sr < PY && si >= 0 && si < PX) {
     #pragma unroll
                                 for (int r_ = 0; r_ < PY; ++r_)
@@ -583,16 +604,20 @@ struct Entry {
     KernelFn fn;
 };
 
-template <int R, int EQ, int ST, bool HZ, int NC, int PY, int D, int MINB, int TXT>
+template <int R, int EQ, int ST, bool HZ, int NC, int PY, int D, int MINB, int TXT, bool YS = false>
 constexpr Entry entry()
 {
-    return Entry{StreamVariant{R, EQ, ST, HZ, NC * 32, PY, D, MINB, TXT},
-                 &k_stream<R, EQ, ST, HZ, NC, PY, D, MINB, TXT>};
+    return Entry{StreamVariant{R, EQ, ST, HZ, NC * 32, PY, D, MINB, TXT, 1, YS},
+                 &k_stream<R, EQ, ST, HZ, NC, PY, D, MINB, TXT, YS>};
 }
 
 // both equations for one radius, storage, dimensionality and shape
 #define GBST_EQS(R, ST, HZ, NC, PY, D, MINB, TXT) \
     entry<R, GBST_HEAT, ST, HZ, NC, PY, D, MINB, TXT>(), entry<R, GBST_WAVE, ST, HZ, NC, PY, D, MINB, TXT>()
+// 2D, streaming along y: one consumer warp, one-row tiles of 32 x 16 bytes
+#define GBST_EQS_YS(R, ST, D, MINB)                                    \
+    entry<R, GBST_HEAT, ST, false, 1, 1, D, MINB, 32, true>(),        \
+        entry<R, GBST_WAVE, ST, false, 1, 1, D, MINB, 32, true>()
 
 }  // namespace sweep
 }  // namespace gbst

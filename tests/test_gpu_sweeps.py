@@ -144,13 +144,15 @@ def test_every_kernel_variant_bitwise(torch_cuda, so, storage, ndim):
 
 @pytest.mark.parametrize("so", [2, 4, 8])
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
-def test_every_wave_variant_bitwise(torch_cuda, so, storage):
-    """Wave variants (kappa and u^{n-1} by TMA into the centre slots) == the simple kernel, bit for bit."""
-    dims = (130, 37, 21)
+@pytest.mark.parametrize("ndim", [3, 2])
+def test_every_wave_variant_bitwise(torch_cuda, so, storage, ndim):
+    """Wave variants (kappa and u^{n-1} by TMA into the centre slots; 2D tiles and
+    2D streamed along y) == the simple kernel, bit for bit."""
+    dims = (130, 37, 21) if ndim == 3 else (300, 77)
     ref, *_ = wave_setup(torch_cuda, dims, so, storage=storage, kernel="simple")
     ref.run(5)
     want_u, want_p = ref.get_field("u"), ref.get_field("u_prev")
-    variants = matching_variants(so, "wave", storage, 3)
+    variants = matching_variants(so, "wave", storage, ndim)
     assert variants
     for v in variants:
         for zc in (0, 2):
