@@ -150,3 +150,68 @@ def test_heat2d_16384_sampled(torch_cuda, so):
         ref = oracle.heat_run(sub, so, a, k)[p[1] - lo[1], p[0] - lo[0]]
         worst = max(worst, abs(float(out[p[1], p[0]].item()) - ref))
     assert worst <= 1e-5
+
+
+def test_wave3d_768_so8_bf16_sampled(torch_cuda):
+    """The 768^3 order-8 wave in BF16 storage, as the benchmark runs it (2e-2 of max |u|:
+    BF16 rounding of the inputs and of every stored step)."""
+    torch = torch_cuda
+    from paper_2404_02218_gb300.grid import Grid
+    case = synthetic.wave3d()
+    so, k = case.so, 4
+    dims = case.dims
+    shape = tuple(reversed(dims))
+    g = Grid(3, dims, so, "wave", h=case.h, dt=case.dt, storage="bf16")
+    c = synthetic.layered_velocity(shape, case.speeds)
+    g.set_field("vel", c)
+    u0 = synthetic.uniform_field_torch(33, shape, "cuda") - 0.5
+    up = synthetic.uniform_field_torch(34, shape, "cuda") - 0.5
+    g.set_field("u", u0)
+    g.set_field("u_prev", up)
+    g.run(k)
+    out = torch.empty_like(u0)
+    g.get_field("u", out=out)
+    g.close()
+    kap = oracle.kappa_from_velocity(c, case.dt, case.h)
+    reach = k * (so // 2)
+    worst = 0.0
+    for p in sample_points(dims, 9):
+        lo, hi = sub_box(dims, p, reach)
+        sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        P, C = oracle.wave_run(up[sl].cpu().numpy().astype(np.float64), u0[sl].cpu().numpy().astype(np.float64),
+                               np.ascontiguousarray(kap[sl]), so, k)
+        ref = C[p[2] - lo[2], p[1] - lo[1], p[0] - lo[0]]
+        worst = max(worst, abs(float(out[p[2], p[1], p[0]].item()) - ref))
+    assert worst <= 2e-2 * 0.5 * 4
+
+
+def test_batch64_full_configuration(torch_cuda):
+    """The 64-grid batch as benchmarked (sizes U[96, 256], order 4, one persistent
+    launch): the three smallest members and the largest, after 20 steps, in full
+    against the oracle."""
+    from paper_2404_02218_gb300.grid import Batch
+    cases = synthetic.batch_wave_cases()
+    k = 20
+    b = Batch(3, [dict(dims=c.dims, h=c.h, dt=c.dt) for c in cases], 4, "wave")
+    for i, c in enumerate(cases):
+        b.set_field(i, "vel", c.velocity())
+        b.set_source(i, c.src, c.f0, c.t0, c.amp)
+    b.set_persistent(True)
+    b.run(k)
+    vol = [int(np.prod(c.dims)) for c in cases]
+    order = np.argsort(vol)
+    for i in order[:3]:
+        c = cases[i]
+        kap = oracle.kappa_from_velocity(c.velocity(), c.dt, c.h)
+        z = np.zeros(kap.shape)
+        _, C = oracle.wave_run(z, z, kap, 4, k, src=c.src, f0=c.f0, t0=c.t0, amp=c.amp, dt=c.dt, h=c.h)
+        got = b.get_field(int(i), "u")
+        assert np.max(np.abs(C)) > 0
+        assert oracle.max_rel_error(got, C) <= 1e-5, int(i)
+    i = int(order[-1])
+    c = cases[i]
+    got = b.get_field(i, "u")
+    kap = oracle.kappa_from_velocity(c.velocity(), c.dt, c.h)
+    z = np.zeros(kap.shape)
+    _, C = oracle.wave_run(z, z, kap, 4, k, src=c.src, f0=c.f0, t0=c.t0, amp=c.amp, dt=c.dt, h=c.h)
+    assert oracle.max_rel_error(got, C) <= 1e-5
