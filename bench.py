@@ -80,6 +80,21 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest of every rank's value (the slowest replica sets the job's time)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest time."""
+    return world * units_per_rank / seconds
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -495,13 +510,9 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     pts_per_step = len(SOS) * STEPS_PER_RUN * N ** 3
-    value = world * args.steps * pts_per_step / (ms / 1e3) / 1e9
+    value = job_throughput(world, args.steps * pts_per_step, ms / 1e3) / 1e9
 
     # per-kernel device time: CUDA events around every sweep launch of the last timed step
     peaks, peak_kind = measured_peaks()
@@ -587,12 +598,9 @@ def run_ours(args):
         e2e_sync()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, dist, "cuda")
         nbytes = len(SOS) * 4 * N ** 3
-        e2e = {"value": world * args.e2e_steps * pts_per_step / el / 1e9, "unit": UNIT,
+        e2e = {"value": job_throughput(world, args.e2e_steps * pts_per_step, el) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
                "overlap": "one stream per order; sweeps in order, copies of the next input and the "
                           "previous result overlap them, also across steps (results double-buffered)"}
