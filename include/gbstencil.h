@@ -282,12 +282,13 @@ gbst_status stencil_get_field_strided(gbst_handle h, int field, float *dst_devic
 
 /* Execution plan of the streaming sweep.  variant: index into the kernel
  * table (stencil_variant_count / stencil_variant_info; -1 = the default for
- * this grid); txt: threads along x of a tile (8, 16, 32; 0 = default); zchunks:
- * z-chunks per tile column (0 = cost model); ctas: CTAs launched (0 = all
- * that are resident).  Synchronises; invalidates captured graphs. */
+ * this grid); txt: 0, or the variant's own threads along x of a tile (the tile
+ * shape is part of the variant; any other value is EINVAL); zchunks: chunks of
+ * the streamed axis per tile column (0 = cost model); ctas: CTAs launched (0 =
+ * all that are resident).  Synchronises; invalidates captured graphs. */
 gbst_status stencil_set_plan(gbst_handle h, int variant, int txt, int zchunks, int ctas);
 
-/* Autotuner: times every applicable (kernel variant, tile width, z-chunking)
+/* Autotuner: times every applicable (kernel variant, z-chunking)
  * on the handle's own fields with `reps` launches each (CUDA events on the
  * handle's stream), keeps the fastest and caches it per shape class -- in the
  * process, and appended to the file named by the environment variable

@@ -410,7 +410,9 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
     // tile: txt threads along x (fixed by the variant), nt / txt along y
     if (!p.stream)
         p.var.txt = 8;
-    (void)txt;
+    if (p.stream && txt != 0 && txt != p.var.txt)
+        return fail(GBST_EINVAL, "txt %d does not match kernel variant %d (tile of %d threads in x)", txt, variant,
+                    p.var.txt);
     p.txt = p.var.txt;
     (void)nt;
     const int TX = tile_w(p.var, px), TY = tile_h(p.var);
