@@ -71,7 +71,8 @@ struct TbShape {
 // kernel's order: own values from queue slot QC of q, x/y neighbours from
 // shared memory at `cb` (row pitch `row` bytes), z neighbours from queue slots
 // QC -+ m.  (Taking the x neighbours from adjacent lanes by shuffles, with the
-// tile-edge lanes reading shared memory, measured slower.)
+// tile-edge lanes reading shared memory -- by a branch or by predicated loads --
+// measured 4-23 % slower for order 2.)
 template <int R, int PY, int QC>
 __device__ __forceinline__ void tb_update(const float2 (&q)[2 * R + 1][PY][2], const unsigned char *cb,
                                           const int row, const float2 wc2, const float2 (&w2)[R + 1],
