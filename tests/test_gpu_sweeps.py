@@ -361,3 +361,42 @@ def test_invalid_arguments(torch_cuda):
     with pytest.raises(GbstError) as e:
         g.set_field("u_prev", np.zeros((16, 16, 16), np.float32))
     assert e.value.status == GBST_EINVAL
+
+
+def test_zero_and_negative_step_counts(torch_cuda):
+    from paper_2404_02218_gb300.native import GbstError, GBST_EINVAL
+    dims = (20, 12, 9)
+    u0 = synthetic.uniform_field(40, tuple(reversed(dims)))
+    g = make_grid(torch_cuda, 3, dims, 4, "heat", dt=0.05)
+    g.set_field("u", u0)
+    g.run(0)
+    assert g.step == 0
+    np.testing.assert_array_equal(g.get_field("u"), u0)
+    with pytest.raises(GbstError) as e:
+        g.run(-1)
+    assert e.value.status == GBST_EINVAL
+
+
+def test_plan_and_descriptor_validation(torch_cuda):
+    import json
+    from paper_2404_02218_gb300.native import GbstError, GBST_EINVAL
+    with pytest.raises(GbstError) as e:
+        make_grid(torch_cuda, 3, (16, 16, 16), 2, "heat", dt=0.05, temporal_block=3)
+    assert e.value.status == GBST_EINVAL
+    g = make_grid(torch_cuda, 3, (40, 30, 20), 2, "heat", dt=0.05)
+    v = json.loads(g.describe())["variant"]
+    with pytest.raises(GbstError) as e:
+        g.set_plan(v, 7, 0, 0)  # a tile width the variant does not have
+    assert e.value.status == GBST_EINVAL
+    with pytest.raises(GbstError) as e:
+        g.set_plan(10 ** 6, 0, 0, 0)
+    assert e.value.status == GBST_EINVAL
+
+
+@pytest.mark.parametrize("dims", [(1 << 20, 3, 2), (3, 1 << 16, 4), (4, 5, 1 << 16)])
+@pytest.mark.parametrize("so", [4, 8])
+def test_extreme_aspect_ratios(torch_cuda, dims, so):
+    """One axis long (a million points in x; 65536 rows; 65536 planes, many z-chunks)."""
+    u0, a, got = heat_case_run(torch_cuda, dims, so, 5)
+    ref = oracle.heat_run(u0, so, a, 5)
+    assert oracle.max_rel_error(got, ref) <= TOL_F32
