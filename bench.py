@@ -432,7 +432,7 @@ def ncu_traffic(plan: dict):
     current kernel code with the same kernel instance and z-chunking.
 
     The summary's table rows read ``| kernel instance | source sha | dram bytes per launch | zchunks |``."""
-    path = os.path.join(ROOT, "profiles", "sweep_dram_traffic.md")
+    path = os.path.join(ROOT, "profiles", "sweep_heat3d_so8_1024_dram_traffic.md")
     try:
         lines = open(path).read().splitlines()
     except OSError:
