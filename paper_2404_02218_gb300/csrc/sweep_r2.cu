@@ -1,5 +1,5 @@
-// Streaming-sweep variants of radius 2 (space order 4).  The first entry
-// matching a grid's (equation, storage, dimensionality) is its default.
+// Streaming-sweep variants of radius 2 (space order 4), 3D grids.  The first
+// entry matching a grid's (equation, storage) is its default.
 #include "sweep_stream.cuh"
 
 namespace gbst {
@@ -14,26 +14,12 @@ const Entry kTable[] = {
     GBST_EQS(2, GBST_F32, true, 8, 1, 3, 2, 32),
     GBST_EQS(2, GBST_F32, true, 4, 2, 3, 1, 16),
     GBST_EQS(2, GBST_F32, true, 4, 2, 3, 1, 8),
-    GBST_EQS(2, GBST_F32, true, 8, 2, 5, 1, 32),
-    GBST_EQS(2, GBST_F32, true, 8, 2, 3, 1, 32),
     GBST_EQS(2, GBST_BF16, true, 4, 1, 3, 1, 16),
     GBST_EQS(2, GBST_BF16, true, 4, 1, 5, 2, 16),
     GBST_EQS(2, GBST_BF16, true, 4, 2, 3, 1, 16),
     GBST_EQS(2, GBST_BF16, true, 4, 1, 3, 1, 8),
     GBST_EQS(2, GBST_BF16, true, 8, 1, 3, 2, 16),
     GBST_EQS(2, GBST_BF16, true, 8, 1, 5, 2, 16),
-    GBST_EQS(2, GBST_F32, false, 4, 2, 3, 1, 16),
-    GBST_EQS(2, GBST_F32, false, 4, 2, 3, 1, 32),
-    GBST_EQS(2, GBST_F32, false, 4, 2, 5, 2, 32),
-    GBST_EQS(2, GBST_F32, false, 4, 2, 3, 1, 8),
-    GBST_EQS(2, GBST_F32, false, 4, 4, 3, 2, 32),
-    GBST_EQS(2, GBST_F32, false, 8, 4, 2, 1, 32),
-    GBST_EQS(2, GBST_F32, false, 4, 8, 2, 1, 32),
-    GBST_EQS(2, GBST_BF16, false, 4, 1, 3, 1, 16),
-    GBST_EQS(2, GBST_BF16, false, 4, 1, 3, 1, 8),
-    GBST_EQS_YS(2, GBST_F32, 4, 8),
-    GBST_EQS_YS(2, GBST_F32, 6, 8),
-    GBST_EQS_YS(2, GBST_F32, 3, 12),
 };
 }  // namespace
 

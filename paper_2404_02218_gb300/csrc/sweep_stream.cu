@@ -8,13 +8,16 @@ const Entry *table_r1(int *n);
 const Entry *table_r2(int *n);
 const Entry *table_r4(int *n);
 const Entry *table_tb(int *n);
+const Entry *table_r1_2d(int *n);
+const Entry *table_r2_2d(int *n);
+const Entry *table_r4_2d(int *n);
 }  // namespace sweep
 
 namespace {
 using sweep::Entry;
 
 struct Registry {
-    static constexpr int kTables = 4;
+    static constexpr int kTables = 7;
     const Entry *tab[kTables];
     int n[kTables];
     Registry()
@@ -23,8 +26,17 @@ struct Registry {
         tab[1] = sweep::table_r2(&n[1]);
         tab[2] = sweep::table_r4(&n[2]);
         tab[3] = sweep::table_tb(&n[3]);
+        tab[4] = sweep::table_r1_2d(&n[4]);
+        tab[5] = sweep::table_r2_2d(&n[5]);
+        tab[6] = sweep::table_r4_2d(&n[6]);
     }
-    int total() const { return n[0] + n[1] + n[2] + n[3]; }
+    int total() const
+    {
+        int t = 0;
+        for (int i = 0; i < kTables; ++i)
+            t += n[i];
+        return t;
+    }
     const Entry *at(int i) const
     {
         for (int t = 0; t < kTables; ++t) {
