@@ -369,6 +369,15 @@ def extras(torch, hbm: float, tune: bool):
                 "forward_ms_256_mma_sync": ms_legacy})
     out["closure_256_so4"] = res
     cl.close()
+    # the same network on the small pair the tests train (96^3 coarse, 100 steps, 20 epochs)
+    cfg96 = PairConfig(nc=96, steps=100)
+    t0 = time.time()
+    cl = new_closure(cfg96, cfg96.nc ** 3)
+    losses = train(cl, (10, 11, 12, 13), cfg96, lr=2e-3, epochs=20)
+    res96 = evaluate(cl, 99, cfg96, checkpoints=(25, 50, 75))
+    res96.update({"train_seconds": time.time() - t0, "updates": len(losses)})
+    out["closure_96_so4_100steps"] = res96
+    cl.close()
     return out
 
 def run_case(args):
