@@ -57,6 +57,8 @@ def lib():
             L.orc_ricker.restype = c_d
             L.orc_heat_run.argtypes = [c_int, i64p, c_int, dp, c_d, c_int, dp, c_i64]
             L.orc_heat_run.restype = c_int
+            L.orc_system_run.argtypes = [c_int, i64p, c_int, dp, c_int, dp, c_int, dp, c_i64]
+            L.orc_system_run.restype = c_int
             L.orc_wave_run.argtypes = [c_int, i64p, c_int, dp, c_int, dp, dp, dp, c_i64, c_i64,
                                        i64p, c_d, c_d, c_d, c_d, c_d]
             L.orc_wave_run.restype = c_int
@@ -106,6 +108,22 @@ def heat_run(u0: np.ndarray, so: int, a: float, nsteps: int, bc: int = BC_ZERO,
     if rc != 0:
         raise MemoryError("oracle heat_run out of memory")
     return u
+
+
+def system_run(fields: Sequence[np.ndarray], so: int, A, nsteps: int, bc: int = BC_ZERO,
+               coeffs=None) -> list:
+    """Coupled system (a synthetic multi-stencil sweep): u_k <- u_k + sum_j A[k][j] L(u_j),
+    nsteps times, for nf = len(fields) fields of one shape."""
+    nf = len(fields)
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(nf, nf))
+    u = np.ascontiguousarray(np.stack([_f64(f) for f in fields]))
+    ndim = u.ndim - 1
+    dims = tuple(reversed(u.shape[1:]))
+    w = weights_array(so, coeffs)
+    rc = lib().orc_system_run(ndim, _dims(dims), so // 2, _dp(w), nf, _dp(A), int(bc), _dp(u), int(nsteps))
+    if rc != 0:
+        raise MemoryError("oracle system_run out of memory")
+    return [u[k] for k in range(nf)]
 
 
 def wave_run(uprev: np.ndarray, u: np.ndarray, kappa: np.ndarray, so: int, nsteps: int,

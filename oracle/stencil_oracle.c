@@ -207,6 +207,62 @@ int orc_heat_run(int ndim, const int64_t n[3], int r, const double *w, double a,
 }
 
 /*
+ * nsteps steps of a coupled system of nf fields (several stencils in one sweep,
+ * a synthetic multi-field workload): for every field k,
+ *     u_k^{n+1} = u_k^n + sum_j A[k][j] L(u_j^n)
+ * with A an nf x nf matrix (row-major).  A = a I is nf independent heat
+ * equations.  u holds the nf dense fields one after another.
+ */
+int orc_system_run(int ndim, const int64_t n[3], int r, const double *w, int nf, const double *A, int bc,
+                   double *u, int64_t nsteps)
+{
+    lay_t L = mk_layout(ndim, n, r);
+    int64_t sz = L.px * L.py * L.pz, s, dn = L.nx * L.ny * L.nz;
+    int f;
+    double *X = calloc((size_t)(sz * nf), sizeof(double));
+    double *Y = calloc((size_t)(sz * nf), sizeof(double));
+    if (!X || !Y) {
+        free(X);
+        free(Y);
+        return -2;
+    }
+    for (f = 0; f < nf; f++)
+        dense_to_padded(&L, u + f * dn, X + f * sz);
+    for (s = 0; s < nsteps; s++) {
+        double *t;
+        int64_t k;
+        for (f = 0; f < nf; f++)
+            orc_fill_ghosts(ndim, n, r, bc, X + f * sz);
+#pragma omp parallel for schedule(static)
+        for (k = 0; k < L.nz; k++) {
+            int64_t i, j;
+            double lap[16];
+            for (j = 0; j < L.ny; j++)
+                for (i = 0; i < L.nx; i++) {
+                    int64_t p = at(&L, i, j, k);
+                    int a, b;
+                    for (b = 0; b < nf; b++)
+                        lap[b] = star(&L, ndim, w, X + b * sz, i, j, k);
+                    for (a = 0; a < nf; a++) {
+                        double acc = 0.0;
+                        for (b = 0; b < nf; b++)
+                            acc += A[a * nf + b] * lap[b];
+                        Y[a * sz + p] = X[a * sz + p] + acc;
+                    }
+                }
+        }
+        t = X;
+        X = Y;
+        Y = t;
+    }
+    for (f = 0; f < nf; f++)
+        padded_to_dense(&L, X + f * sz, u + f * dn);
+    free(X);
+    free(Y);
+    return 0;
+}
+
+/*
  * nsteps wave steps.  uprev = u^{n-1}, u = u^n on entry (dense), u^{n-1+s}, u^{n+s} on exit.
  * step0 is the global index n of the first step (the source time is t_n = n dt).
  * src == NULL: no source; else the value amp * kappa_s * h^2 * R(t_n) = amp c_s^2 dt^2 R(t_n)
