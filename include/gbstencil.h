@@ -203,6 +203,22 @@ gbst_status stencil_last_kernel_time(gbst_handle h, double *ms, int64_t *launche
  * (Not in the paper: the batching of many small problems into one launch.) */
 gbst_status stencil_batch_create(const gbst_desc *descs, int n, gbst_handle *out);
 gbst_status stencil_batch_size(gbst_handle h, int *n);
+
+/* A coupled system of nfields (2..4) FP32 fields on one 3D grid with zero
+ * halos, advanced by fused multi-field sweeps (several stencils in one pass
+ * over memory; a synthetic stand-in for the multi-stencil regions of the
+ * paper's Section 6.2):
+ *     u_k^{n+1} = u_k^n + sum_j A[k][j] L(u_j^n),   A = coupling (row-major).
+ * desc: eq = GBST_HEAT, storage = GBST_F32, ndim = 3, bc = GBST_BC_ZERO, no
+ * decomposition; alpha, dt and h are not used (A holds the coefficients).
+ * The handle is a batch whose members are the fields: stencil_batch_set_field
+ * / _get_field / _reduce_f64 with grid = k address field k (GBST_U); run,
+ * sync, tune, set_plan, describe apply to the whole system.  EUNSTABLE unless
+ * |I + lambda A|_2 <= 1 for every symbol value lambda in [-ndim S, 0] of the
+ * stencil (the exact von Neumann condition for symmetric A) or
+ * allow_unstable.  No temporal blocking, no persistent mode. */
+gbst_status stencil_system_create(const gbst_desc *desc, int nfields, const double *coupling,
+                                  gbst_handle *out);
 gbst_status stencil_batch_set_field(gbst_handle h, int grid, int field, const void *src, int src_dtype,
                                     int src_on_device);
 gbst_status stencil_batch_get_field(gbst_handle h, int grid, int field, void *dst, int dst_dtype,

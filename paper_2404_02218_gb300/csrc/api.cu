@@ -254,6 +254,8 @@ struct gbst_grid_s {
     int decomp[3] = {1, 1, 1};
     bool batch = false;
     int members = 1;
+    int nf = 1;               // fused multi-field system: the members are its fields
+    float coupling[16] = {0}; // system coupling matrix A[k][j] (k * nf + j)
     cudaStream_t stream = nullptr;
     Allocator mem;
     std::vector<DevMem> owned;
@@ -365,13 +367,13 @@ void destroy_graphs(gbst_handle h)
 // ghosts and no halo exchange between steps.
 bool tb_allowed(gbst_handle h)
 {
-    return h->d.temporal_block != 1 && h->d.eq == GBST_HEAT && h->d.storage == GBST_F32 && h->ndim == 3 &&
+    return h->nf == 1 && h->d.temporal_block != 1 && h->d.eq == GBST_HEAT && h->d.storage == GBST_F32 && h->ndim == 3 &&
            h->d.bc == GBST_BC_ZERO && h->nboxes == 0 && h->d.kernel != GBST_KERNEL_SIMPLE;
 }
 
 bool variant_matches(gbst_handle h, const StreamVariant &v)
 {
-    if (v.R != h->R || v.eq != h->d.eq || v.storage != h->d.storage || v.has_z != (h->ndim == 3))
+    if (v.R != h->R || v.eq != h->d.eq || v.storage != h->d.storage || v.has_z != (h->ndim == 3) || v.nf != h->nf)
         return false;
     return v.tb == 1 || tb_allowed(h);
 }
@@ -395,8 +397,9 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
     if (variant < 0)
         variant = default_variant(h);
     p.stream = h->d.kernel != GBST_KERNEL_SIMPLE && variant >= 0;
-    if (h->d.kernel == GBST_KERNEL_STREAM && !p.stream)
-        return fail(GBST_ENOTSUP, "no streaming kernel for radius %d", h->R);
+    if ((h->d.kernel == GBST_KERNEL_STREAM || h->nf > 1) && !p.stream)
+        return fail(GBST_ENOTSUP, "no streaming kernel for radius %d%s", h->R,
+                    h->nf > 1 ? " and this number of fields" : "");
     if (p.stream) {
         if (!stream_variant_get(variant, &p.var))
             return fail(GBST_EINVAL, "unknown kernel variant %d", variant);
@@ -432,7 +435,8 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
         g.tiles_x = static_cast<int>((s.lu.nx + TX - 1) / TX);
         g.tiles_y = ys ? 1 : static_cast<int>((s.lu.ny + TY - 1) / TY);
         g.box_bytes = p.max_box_bytes;
-        T += static_cast<int64_t>(g.tiles_x) * g.tiles_y;
+        if (h->nf == 1 || i == 0)  // a system sweeps the tiles of field 0 only
+            T += static_cast<int64_t>(g.tiles_x) * g.tiles_y;
         if (p.stream) {
             std::string err;
             for (int b = 0; b < 2; ++b)
@@ -477,6 +481,8 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
         std::vector<Unit> units;
         for (int c = 0; c < zc; ++c)
             for (size_t i = 0; i < h->subs.size(); ++i) {
+                if (h->nf > 1 && i > 0)
+                    break;  // a system sweep reads and writes all its fields from the units of field 0
                 const GridDev &g = h->hgrids[i];
                 const int64_t n = ys ? h->subs[i].lu.ny : h->subs[i].lu.nz;
                 const int z0 = static_cast<int>(n * c / zc), z1 = static_cast<int>(n * (c + 1) / zc);
@@ -704,6 +710,8 @@ SweepArgs sweep_args(gbst_handle h, int parity, const float *srcval)
     a.ngrids = static_cast<int>(h->subs.size());
     a.barrier = h->dbarrier;
     a.barrier_extra = h->barrier_extra;
+    for (int k = 0; k < 16; ++k)
+        a.coupling[k] = h->coupling[k];
     return a;
 }
 
@@ -873,7 +881,63 @@ gbst_status destroy_handle(gbst_handle h);
 // Create a handle from n descriptions: n == 1 is a single (possibly decomposed)
 // grid; n > 1 a batch of independent grids sharing dimensionality, order,
 // equation, storage and weights (each with its own sizes, step and spacing).
-gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle *out)
+// Largest singular value of a small square matrix (n <= 4): Jacobi sweeps on B^T B.
+double max_singular_value(const double *B, int n)
+{
+    double M[4][4] = {{0}};
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k)
+                M[i][j] += B[k * n + i] * B[k * n + j];
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q)
+                off += M[p][q] * M[p][q];
+        if (off < 1e-30)
+            break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (std::fabs(M[p][q]) < 1e-300)
+                    continue;
+                const double th = 0.5 * std::atan2(2.0 * M[p][q], M[q][q] - M[p][p]);
+                const double c = std::cos(th), sn = std::sin(th);
+                for (int k = 0; k < n; ++k) {  // rotate columns p, q
+                    const double mkp = M[k][p], mkq = M[k][q];
+                    M[k][p] = c * mkp - sn * mkq;
+                    M[k][q] = sn * mkp + c * mkq;
+                }
+                for (int k = 0; k < n; ++k) {  // rotate rows p, q
+                    const double mpk = M[p][k], mqk = M[q][k];
+                    M[p][k] = c * mpk - sn * mqk;
+                    M[q][k] = sn * mpk + c * mqk;
+                }
+            }
+    }
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i)
+        mx = std::max(mx, M[i][i]);
+    return std::sqrt(std::max(mx, 0.0));
+}
+
+// Stability of u <- u + A L(u) (sufficient): |I + lambda A|_2 <= 1 for every
+// symbol value lambda in [-ndim S, 0] (exact for symmetric A and for A = a I).
+bool system_stable(const double *A, int n, int ndim, double S)
+{
+    double B[16];
+    for (int t = 0; t <= 512; ++t) {
+        const double lam = -ndim * S * t / 512.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                B[i * n + j] = (i == j ? 1.0 : 0.0) + lam * A[i * n + j];
+        if (max_singular_value(B, n) > 1.0 + 1e-9)
+            return false;
+    }
+    return true;
+}
+
+gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle *out, int nfields = 0,
+                          const double *coupling = nullptr)
 {
     if (!descs || !out || n < 1)
         return fail(GBST_EINVAL, "null descriptions or handle, or n < 1");
@@ -935,12 +999,23 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
         h->mem.a = *d.allocator;
         h->mem.custom = true;
     }
-    for (int i = 0; i < n; ++i) {
-        const gbst_desc &e = descs[i];
-        const double a = e.alpha * e.dt / (e.h * e.h);
-        if (e.eq == GBST_HEAT && !e.allow_unstable && a * h->ndim * h->S > 2.0 * (1.0 + 1e-12)) {
+    if (nfields > 0) {
+        h->nf = nfields;
+        for (int k = 0; k < nfields * nfields; ++k)
+            h->coupling[k] = static_cast<float>(coupling[k]);
+        if (!d.allow_unstable && !system_stable(coupling, nfields, h->ndim, h->S)) {
             delete h;
-            return fail(GBST_EUNSTABLE, "heat step a*ndim*S = %g exceeds 2 (von Neumann limit)", a * d.ndim * h->S);
+            return fail(GBST_EUNSTABLE, "coupling matrix: |I + lambda A| > 1 for a symbol value lambda of the stencil");
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            const gbst_desc &e = descs[i];
+            const double a = e.alpha * e.dt / (e.h * e.h);
+            if (e.eq == GBST_HEAT && !e.allow_unstable && a * h->ndim * h->S > 2.0 * (1.0 + 1e-12)) {
+                delete h;
+                return fail(GBST_EUNSTABLE, "heat step a*ndim*S = %g exceeds 2 (von Neumann limit)",
+                            a * d.ndim * h->S);
+            }
         }
     }
 
@@ -1316,6 +1391,24 @@ gbst_status stencil_batch_create(const gbst_desc *descs, int n, gbst_handle *out
     return create_handle(descs, n, true, out);
 }
 
+gbst_status stencil_system_create(const gbst_desc *desc, int nfields, const double *coupling, gbst_handle *out)
+{
+    if (!desc || !out || !coupling)
+        return fail(GBST_EINVAL, "null argument");
+    if (nfields < 2 || nfields > 4)
+        return fail(GBST_EINVAL, "nfields must be 2, 3 or 4");
+    for (int k = 0; k < nfields * nfields; ++k)
+        if (!std::isfinite(coupling[k]))
+            return fail(GBST_EINVAL, "coupling matrix entry %d is not finite", k);
+    if (desc->eq != GBST_HEAT || desc->storage != GBST_F32 || desc->ndim != 3 || desc->bc != GBST_BC_ZERO ||
+        desc->kernel == GBST_KERNEL_SIMPLE)
+        return fail(GBST_ENOTSUP, "systems: heat-type, FP32, 3D, zero halos, streaming kernel");
+    std::vector<gbst_desc> ds(nfields, *desc);
+    for (auto &e : ds)
+        e.temporal_block = 1;
+    return create_handle(ds.data(), nfields, true, out, nfields, coupling);
+}
+
 gbst_status stencil_batch_size(gbst_handle h, int *n)
 {
     if (!h || !n)
@@ -1500,7 +1593,7 @@ gbst_status stencil_run(gbst_handle h, int64_t nsteps)
         GBST_CUDA(cudaEventRecord(h->src_ev, h->stream));
     }
     const bool tb = h->plan.stream && h->plan.var.tb == 2;
-    const bool persistent = h->persistent && h->plan.stream && h->nboxes == 0 && !tb;
+    const bool persistent = h->persistent && h->plan.stream && h->nboxes == 0 && !tb && h->nf == 1;
     // sweep launches: one per step, or one per two steps (+ one single step if odd)
     const int64_t launches = persistent ? 1 : (tb ? (nsteps + 1) / 2 : nsteps);
     if (h->profile) {
@@ -1631,11 +1724,11 @@ gbst_status stencil_describe(gbst_handle h, char *buf, size_t len)
     snprintf(buf, len,
              "{\"kernel\": \"%s\", \"R\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, \"tile\": [%d, %d], "
              "\"zchunks\": %d, \"units\": %d, \"ctas\": %d, \"occupancy\": %d, \"smem\": %zu, \"subdomains\": %zu, "
-             "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d, \"tb\": %d, \"ys\": %d}",
+             "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d, \"tb\": %d, \"ys\": %d, \"nf\": %d}",
              p.stream ? "stream" : "simple", h->R, p.var.nthreads, p.var.py, p.var.depth, tile_w(p.var, px),
              p.stream ? tile_h(p.var) : (p.var.nthreads / std::max(1, p.txt)) * p.var.py, p.zchunks, p.nunits,
              p.ctas, p.occupancy, p.smem, h->subs.size(), h->nboxes, p.variant, p.var.minb,
-             p.stream ? p.var.tb : 1, p.stream && p.var.ys ? 1 : 0);
+             p.stream ? p.var.tb : 1, p.stream && p.var.ys ? 1 : 0, h->nf);
     return GBST_OK;
 }
 
@@ -1686,8 +1779,9 @@ gbst_status stencil_variant_info(int i, char *buf, size_t len)
         return fail(GBST_EINVAL, "bad variant index or buffer");
     snprintf(buf, len,
              "{\"R\": %d, \"eq\": %d, \"storage\": %d, \"has_z\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, "
-             "\"minb\": %d, \"txt\": %d, \"tb\": %d, \"ys\": %d}",
-             v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb, v.txt, v.tb, v.ys ? 1 : 0);
+             "\"minb\": %d, \"txt\": %d, \"tb\": %d, \"ys\": %d, \"nf\": %d}",
+             v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb, v.txt, v.tb, v.ys ? 1 : 0,
+             v.nf);
     return GBST_OK;
 }
 

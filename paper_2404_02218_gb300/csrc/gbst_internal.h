@@ -83,6 +83,7 @@ struct SweepArgs {
     unsigned int *barrier; // grid-barrier counter (zeroed before a persistent launch)
     unsigned int barrier_extra;  // test hook: extra arrivals a barrier waits for (0 in normal use)
     int tb_single;         // temporally blocked kernel: 1 = perform one step only
+    float coupling[16];    // fused multi-field system: A[k][j] at k * nfields + j
 };
 
 // Host-side entry points of the kernel translation units.
@@ -98,6 +99,7 @@ struct StreamVariant {
     int txt;        // threads along x of a tile (tile width = txt * 16 bytes of storage)
     int tb = 1;     // time steps per launch: 1, or 2 (temporally blocked heat kernel)
     bool ys = false; // 2D grid streamed along y (one-row tiles)
+    int nf = 1;      // fields of a fused multi-field system sweep (1: a single field)
 };
 
 // Tile of a variant: width in points, height in rows (a temporally blocked

@@ -11,13 +11,14 @@ const Entry *table_tb(int *n);
 const Entry *table_r1_2d(int *n);
 const Entry *table_r2_2d(int *n);
 const Entry *table_r4_2d(int *n);
+const Entry *table_sys(int *n);
 }  // namespace sweep
 
 namespace {
 using sweep::Entry;
 
 struct Registry {
-    static constexpr int kTables = 7;
+    static constexpr int kTables = 8;
     const Entry *tab[kTables];
     int n[kTables];
     Registry()
@@ -29,6 +30,7 @@ struct Registry {
         tab[4] = sweep::table_r1_2d(&n[4]);
         tab[5] = sweep::table_r2_2d(&n[5]);
         tab[6] = sweep::table_r4_2d(&n[6]);
+        tab[7] = sweep::table_sys(&n[7]);
     }
     int total() const
     {
@@ -61,7 +63,7 @@ const Entry *find(const StreamVariant &v)
         const Entry *e = r.at(i);
         if (e->v.R == v.R && e->v.eq == v.eq && e->v.storage == v.storage && e->v.has_z == v.has_z &&
             e->v.nthreads == v.nthreads && e->v.py == v.py && e->v.depth == v.depth && e->v.minb == v.minb &&
-            e->v.txt == v.txt && e->v.tb == v.tb && e->v.ys == v.ys)
+            e->v.txt == v.txt && e->v.tb == v.tb && e->v.ys == v.ys && e->v.nf == v.nf)
             return e;
     }
     return nullptr;
@@ -117,7 +119,7 @@ static size_t centre_bytes(const StreamVariant &v)
 size_t stream_smem_bytes(const StreamVariant &v, int max_box_bytes)
 {
     const int rz = stream_rz(v);
-    const int slots = rz + 1 + v.depth;
+    const int slots = (rz + 1 + v.depth) * v.nf;  // a multi-field sweep holds nf boxes per plane
     const size_t slot = (static_cast<size_t>(max_box_bytes) + 127) / 128 * 128;
     return 256 + slots * slot + centre_bytes(v);
 }
@@ -125,7 +127,7 @@ size_t stream_smem_bytes(const StreamVariant &v, int max_box_bytes)
 int stream_slot_bytes(const StreamVariant &v, size_t smem)
 {
     const int rz = stream_rz(v);
-    const int slots = rz + 1 + v.depth;
+    const int slots = (rz + 1 + v.depth) * v.nf;
     return static_cast<int>((smem - 256 - centre_bytes(v)) / slots);
 }
 

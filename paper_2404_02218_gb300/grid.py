@@ -300,3 +300,42 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class System(Batch):
+    """A coupled system of fields on one 3D grid advanced by fused multi-field
+    sweeps (see ``stencil_system_create``): u_k <- u_k + sum_j A[k][j] L(u_j).
+    Field k is batch member k."""
+
+    def __init__(self, dims: Sequence[int], space_order: int, coupling, *, kernel: str = "auto", tile: int = 0,
+                 use_graph: bool = True, stream=None, torch_allocator: bool = True, allow_unstable: bool = False):
+        import torch
+        self._torch = torch
+        self.ndim = 3
+        A = np.asarray(coupling, dtype=np.float64)
+        nf = A.shape[0]
+        assert A.shape == (nf, nf)
+        dev = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self._alloc = TorchAllocator(dev) if torch_allocator else None
+        dims = tuple(int(x) for x in dims)
+        self.dims = [dims] * nf
+        d = N.gbst_desc()
+        d.ndim = 3
+        for i in range(3):
+            d.dims[i] = dims[i]
+            d.decomp[i] = 1
+        d.space_order = space_order
+        d.eq = N.GBST_HEAT
+        d.bc = N.GBST_BC_ZERO
+        d.storage = N.GBST_F32
+        d.h = d.dt = d.alpha = 1.0
+        d.allow_unstable = int(allow_unstable)
+        d.kernel = _KER[kernel]
+        d.tile = int(tile)
+        d.use_graph = int(use_graph)
+        d.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        d.allocator = ctypes.pointer(self._alloc.struct) if self._alloc else None
+        self._descs = [d]
+        self.coupling = A
+        self.h = N.stencil_system_create(d, nf, A.reshape(-1))

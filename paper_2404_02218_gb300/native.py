@@ -105,6 +105,8 @@ def lib() -> ctypes.CDLL:
                 "gbst_reduce_dense_f64_noalloc": ([vp, i32, i64, i32, vp, vp], i32),
                 "stencil_batch_create": ([ctypes.POINTER(gbst_desc), i32, ctypes.POINTER(H)], i32),
                 "stencil_batch_size": ([H, ctypes.POINTER(i32)], i32),
+                "stencil_system_create": ([ctypes.POINTER(gbst_desc), i32, ctypes.POINTER(dbl), ctypes.POINTER(H)],
+                                          i32),
                 "stencil_batch_set_field": ([H, i32, i32, vp, i32, i32], i32),
                 "stencil_batch_get_field": ([H, i32, i32, vp, i32, i32], i32),
                 "stencil_batch_set_source": ([H, i32, ctypes.POINTER(i64), dbl, dbl, dbl], i32),
@@ -263,6 +265,14 @@ def stencil_batch_create(descs) -> ctypes.c_void_p:
     arr = (gbst_desc * len(descs))(*descs)
     h = ctypes.c_void_p()
     _check(lib().stencil_batch_create(arr, len(descs), ctypes.byref(h)), "stencil_batch_create")
+    return h
+
+
+def stencil_system_create(desc: gbst_desc, nfields: int, coupling):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_double * (nfields * nfields))(*[float(x) for x in coupling])
+    _check(lib().stencil_system_create(ctypes.byref(desc), int(nfields), arr, ctypes.byref(h)),
+           "stencil_system_create")
     return h
 
 
