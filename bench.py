@@ -294,6 +294,24 @@ def extras(torch, hbm: float, tune: bool):
     g.close()
     del c2
 
+    # fused multi-field sweep: three coupled fields on 768^3, order 4 (several stencils in one pass)
+    from paper_2404_02218_gb300.grid import System
+    ns3 = 768
+    A = np.array([[0.030, 0.012, -0.004], [0.007, 0.025, 0.009], [0.002, -0.006, 0.020]])
+    sysg = System((ns3, ns3, ns3), 4, A, stream=stream)
+    for k in range(3):
+        sysg.set_field(k, "u", synthetic.uniform_field_torch(50 + k, (ns3, ns3, ns3), "cuda"))
+    if tune:
+        sysg.tune(reps=2)
+    ms = timed_runs(torch, stream, lambda: sysg.run(STEPS_PER_RUN))
+    pts = 3 * STEPS_PER_RUN * ns3 ** 3  # field-point updates
+    out["system3_768_so4_fused"] = {"gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6,
+                                    "frac": 8 * pts / ms / 1e6 / hbm, "steps": STEPS_PER_RUN,
+                                    "bytes_per_field_pt": 8,
+                                    "unfused_bytes_per_field_pt": 16,
+                                    "plan": json.loads(sysg.describe())}
+    sysg.close()
+
     # batched wave: 64 grids U[96,256]^3, order 4, 300 steps
     cases = synthetic.batch_wave_cases()
     members = [dict(dims=cs.dims, h=cs.h, dt=cs.dt) for cs in cases]

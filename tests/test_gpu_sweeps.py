@@ -114,7 +114,8 @@ def matching_variants(so, eq, storage, ndim):
     out = []
     for i in range(N.stencil_variant_count()):
         v = json.loads(N.stencil_variant_info(i))
-        if (v["R"], v["eq"], v["storage"], v["has_z"]) == (so // 2, codes[eq], codes[storage], int(ndim == 3)):
+        if (v["R"], v["eq"], v["storage"], v["has_z"], v["nf"]) == (so // 2, codes[eq], codes[storage],
+                                                                     int(ndim == 3), 1):
             out.append(i)
     return out
 
