@@ -61,10 +61,11 @@ def parse():
                    help="skip the secondary measurements (decomposition, wave FP32/BF16, batch, closure)")
     p.add_argument("--n", type=int, default=1024, help="grid edge (profiling runs use a smaller cube)")
     p.add_argument("--sos", default="2,4,8", help="space orders to run (profiling runs use one)")
-    p.add_argument("--case", default=None, choices=["wave3d_f32", "wave3d_bf16", "closure"],
+    p.add_argument("--case", default=None, choices=["wave3d_f32", "wave3d_bf16", "closure", "system3"],
                    help="run one small named case instead of the bench (for profiler captures): "
-                        "the order-8 layered wave at --n^3 in FP32 or BF16 storage, or the closure "
-                        "network's forward pass at --n^3; prints one timing line")
+                        "the order-8 layered wave at --n^3 in FP32 or BF16 storage, the closure "
+                        "network's forward pass at --n^3, or the fused three-field order-4 system at "
+                        "--n^3; prints one timing line")
     p.add_argument("--tune", default="on", choices=["on", "cache", "off"],
                    help="on: autotune each kernel before timing; cache: use plans cached in "
                         "GBST_TUNE_CACHE (no tuning launches); off: default plans")
@@ -308,7 +309,7 @@ def extras(torch, hbm: float, tune: bool):
     out["system3_768_so4_fused"] = {"gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6,
                                     "frac": 8 * pts / ms / 1e6 / hbm, "steps": STEPS_PER_RUN,
                                     "bytes_per_field_pt": 8,
-                                    "unfused_bytes_per_field_pt": 16,
+                                    "unfused_bytes_per_field_pt": 20,
                                     "plan": json.loads(sysg.describe())}
     sysg.close()
 
@@ -416,6 +417,15 @@ def run_case(args):
         if args.tune == "on":
             g.tune(reps=2)
         fn, pts = (lambda: g.run(10)), 10 * n ** 3
+    elif args.case == "system3":
+        from paper_2404_02218_gb300.grid import System
+        A = np.array([[0.030, 0.012, -0.004], [0.007, 0.025, 0.009], [0.002, -0.006, 0.020]])
+        g = System((n, n, n), 4, A, stream=stream)
+        for k in range(3):
+            g.set_field(k, "u", synthetic.uniform_field_torch(50 + k, (n, n, n), "cuda"))
+        if args.tune == "on":
+            g.tune(reps=2)
+        fn, pts = (lambda: g.run(10)), 3 * 10 * n ** 3
     else:
         from paper_2404_02218_gb300.closure import Closure, init_params
         cl = Closure(n ** 3, 1.0)
@@ -451,7 +461,7 @@ def kernel_name(plan: dict) -> str:
         nw = plan["threads"] // 32 - 1
         return f"k_tb<{plan['R']}, {nw}, {plan['py']}, {plan['depth']}, {plan['minb']}>"
     nc = plan["threads"] // 32
-    return f"k_stream<{plan['R']}, 0, 0, 1, {nc}, {plan['py']}, {plan['depth']}, {plan['minb']}, {txt}>"
+    return f"k_stream<{plan['R']}, 0, 0, 1, {nc}, {plan['py']}, {plan['depth']}, {plan['minb']}, {txt}, 0>"
 
 
 def ncu_traffic(plan: dict):
