@@ -442,13 +442,18 @@ def run_case(args):
 
 
 # -------------------------------------------------------------- our path ---
-KERNEL_SOURCES = ("sweep_stream.cuh", "sweep_tb.cuh", "gbst_internal.h")
+# Sources that define each sweep kernel's code (the temporally blocked kernel
+# includes the single-step kernel's header).
+KERNEL_SOURCES = {
+    "k_stream": ("sweep_stream.cuh", "gbst_internal.h"),
+    "k_tb": ("sweep_stream.cuh", "sweep_tb.cuh", "gbst_internal.h"),
+}
 
 
-def kernel_source_sha() -> str:
-    """Hash of the sweep kernels' code; a traffic figure is used only for this exact code."""
+def kernel_source_sha(kernel: str = "k_stream") -> str:
+    """Hash of a sweep kernel's code; a traffic figure is used only for this exact code."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2404_02218_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -477,7 +482,7 @@ def ncu_traffic(plan: dict):
     want = kernel_name(plan)
     for ln in lines:
         cells = [c.strip().strip("`") for c in ln.strip().strip("|").split("|")]
-        if len(cells) >= 4 and cells[0] == want and cells[1] == kernel_source_sha():
+        if len(cells) >= 4 and cells[0] == want and cells[1] == kernel_source_sha(want.split("<")[0]):
             try:
                 if int(cells[3]) != plan.get("zchunks"):
                     return None

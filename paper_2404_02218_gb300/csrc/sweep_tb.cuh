@@ -236,8 +236,11 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
     float2 q1[QN][PY][PP];  // input u, own points, by plane index mod QN
     float2 q2[QN][PY][PP];  // u', own points, by u' plane index mod QN
     int slot_n = 0, bar_i = 0;  // ring slot, barrier pair
-    int pc = 0;                 // u' planes written so far by this CTA (buffer pc % NU)
     uint32_t par = 0, upar = 0; // phase parities of full/empty and of uend
+    // u' planes written so far by this CTA, pc, kept as its buffer uw = pc mod NU
+    // and the phase parity uwp = (pc / NU) & 1 of that buffer's barrier
+    int uw = 0;
+    uint32_t uwp = 0;
     auto advance = [&]() {
         slot_n = slot_n + 1 == S ? 0 : slot_n + 1;
         if (++bar_i == NB) {
@@ -268,6 +271,15 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
             const int64_t x = static_cast<int64_t>(bx) + cx + i;
             xin[i] = x >= 0 && x < nx;
         }
+        // every u' point of this thread lies inside the grid in x and y (the usual
+        // case): only planes outside [0, nz) need zeroing
+        bool inner = true;
+#pragma unroll
+        for (int k = 0; k < PY; ++k)
+            inner = inner && yin[k];
+#pragma unroll
+        for (int i = 0; i < PX; ++i)
+            inner = inner && xin[i];
         const bool xfull = bx + cx + PX <= nx;
         bool st_row[PY];  // rows this thread stores (step-2 rows, or step-1 rows in single mode)
 #pragma unroll
@@ -275,9 +287,11 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
             st_row[k] = s2row[k] && yin[k] && bx + cx < nx;
         const int64_t plane_elems = rows * pitch;
         const int64_t row_stride = pitch * 4;
+        const int64_t plane_bytes = plane_elems * 4;
         // output pointer at plane z0, grown-tile row rho0 (y = by - r + rho0), column bx + cx
         unsigned char *optr = outbase +
                               (origin + (static_cast<int64_t>(u.z0) * rows + (by - R + rho0)) * pitch + bx + cx) * 4;
+        int64_t o2off = 0;  // byte offset of the next step-2 output plane from optr
 
         const int nout = u.z1 - u.z0;
         // input planes of the unit; two-step mode takes one more so that the last
@@ -309,16 +323,20 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                 }
             }
             if (!single && j >= 4 * R + 1) {
-                // u' plane P - 1 (global count pc - 1) is complete in shared memory
-                if (!wait_or_abort(&ubar[(pc - 1) % NU], ((pc - 1) / NU) & 1, abort_flag))
+                // u' plane P - 1 (count pc - 1: buffer uw - 1 mod NU) is complete in shared memory
+                const int up = uw == 0 ? NU - 1 : uw - 1;
+                if (!wait_or_abort(&ubar[up], uw == 0 ? uwp ^ 1u : uwp, abort_flag))
                     return false;
+                unsigned char *op = optr + o2off;
+                o2off += plane_bytes;
                 if (any_s2) {
-                    // step 2 on u' plane P - 1 - r = output plane z0 + j - 4r - 1
+                    // step 2 on u' plane P - 1 - r = output plane z0 + j - 4r - 1, in
+                    // buffer (pc - 1 - r) mod NU = (uw + 1) mod NU since NU = r + 2
+                    static_assert(NU == R + 2, "u' ring length");
                     constexpr int qc2 = (k - 3 * R - 1 + 4 * QN) % QN;
                     float o[PY][PX];
-                    tb_update<R, PY, qc2>(q2, ubuf + ((pc - 1 - R) % NU) * Sh::U_BYTES + u_off, U_ROW, wc2, w2,
-                                          a2, o);
-                    unsigned char *op = optr + static_cast<int64_t>(j - 4 * R - 1) * plane_elems * 4;
+                    tb_update<R, PY, qc2>(q2, ubuf + (uw + 1 == NU ? 0 : uw + 1) * Sh::U_BYTES + u_off, U_ROW,
+                                          wc2, w2, a2, o);
 #pragma unroll
                     for (int r_ = 0; r_ < PY; ++r_) {
                         if (st_row[r_]) {
@@ -340,19 +358,26 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                 const int slot_c = slot_n >= R ? slot_n - R : slot_n - R + S;
                 float o[PY][PX];
                 tb_update<R, PY, qc1>(q1, slots + slot_c * slot_bytes + in_off, IN_ROW, wc2, w2, a2, o);
-                // u' plane index (interior z) of this result
-                const int64_t zq = static_cast<int64_t>(u.z0) - 3 * R + j;
-                const bool zin = zq >= 0 && zq < nz;
+                // u' plane index (interior z) of this result; u' is zero outside the interior
+                const int zq = u.z0 - 3 * R + j;
+                if (static_cast<unsigned>(zq) >= static_cast<unsigned>(nz)) {
 #pragma unroll
-                for (int r_ = 0; r_ < PY; ++r_)
+                    for (int r_ = 0; r_ < PY; ++r_)
 #pragma unroll
-                    for (int i = 0; i < PX; ++i)
-                        if (!(zin && yin[r_] && xin[i]))
+                        for (int i = 0; i < PX; ++i)
                             o[r_][i] = 0.0f;
+                } else if (!inner) {
+#pragma unroll
+                    for (int r_ = 0; r_ < PY; ++r_)
+#pragma unroll
+                        for (int i = 0; i < PX; ++i)
+                            if (!(yin[r_] && xin[i]))
+                                o[r_][i] = 0.0f;
+                }
                 if (single) {
                     // one step only: store u' of planes [z0, z1)
                     if (zq >= u.z0 && zq < u.z1) {
-                        unsigned char *op = optr + (zq - u.z0) * plane_elems * 4;
+                        unsigned char *op = optr + static_cast<int64_t>(zq - u.z0) * plane_bytes;
 #pragma unroll
                         for (int r_ = 0; r_ < PY; ++r_) {
                             if (st_row[r_]) {
@@ -369,7 +394,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                     }
                 } else {
                     constexpr int qn2 = (k - 2 * R + 2 * QN) % QN;
-                    unsigned char *ub = ubuf + (pc % NU) * Sh::U_BYTES + u_off;
+                    unsigned char *ub = ubuf + uw * Sh::U_BYTES + u_off;
 #pragma unroll
                     for (int r_ = 0; r_ < PY; ++r_) {
 #pragma unroll
@@ -384,10 +409,12 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
             if (lane == 0) {
                 mbar_arrive(&empty[bar_i]);
                 if (s1 && !single)
-                    mbar_arrive(&ubar[pc % NU]);
+                    mbar_arrive(&ubar[uw]);
             }
-            if (s1 && !single)
-                ++pc;
+            if (s1 && !single && ++uw == NU) {
+                uw = 0;
+                uwp ^= 1u;
+            }
             advance();
             return true;
         };
