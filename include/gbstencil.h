@@ -304,6 +304,17 @@ gbst_status stencil_get_field_strided(gbst_handle h, int field, float *dst_devic
  * all that are resident).  Synchronises; invalidates captured graphs. */
 gbst_status stencil_set_plan(gbst_handle h, int variant, int txt, int zchunks, int ctas);
 
+/* Work assignment of the streaming sweep's launches (the plan's work units
+ * are (tile, z-range) pieces in list order).  dynamic = 0: unit i goes to CTA
+ * i mod grid size; 1: every CTA draws its next unit from a global counter of
+ * the handle, so that the units in flight stay a contiguous window of the list
+ * (neighbouring tiles share their halo planes in L2, and the load balances
+ * itself); -1: the library's default (dynamic).  Results do not depend on it:
+ * each unit writes its own output points.  Persistent launches always assign
+ * statically.  EINVAL for other values.  Synchronises; invalidates captured
+ * graphs.  The autotuner tries both. */
+gbst_status stencil_set_schedule(gbst_handle h, int dynamic);
+
 /* Autotuner: times every applicable (kernel variant, z-chunking)
  * on the handle's own fields with `reps` launches each (CUDA events on the
  * handle's stream), keeps the fastest and caches it per shape class -- in the

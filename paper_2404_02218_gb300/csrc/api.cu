@@ -232,6 +232,10 @@ struct Sub {
     bool unstable = false;  // kappa above the stability limit
 };
 
+// Default unit assignment of streaming launches: dynamic (measured equal or
+// faster for every streaming variant; fewer DRAM re-reads of halo planes).
+constexpr bool kDynDefault = true;
+
 struct Plan {
     StreamVariant var{};
     int variant = -1;
@@ -244,6 +248,7 @@ struct Plan {
     int occupancy = 0;
     int nunits = 0;
     int max_box_bytes = 0;
+    bool dyn = false;  // launches draw their work units from a global counter
 };
 
 struct gbst_grid_s {
@@ -274,6 +279,7 @@ struct gbst_grid_s {
     int *derr = nullptr;
     unsigned int *dbarrier = nullptr;
     unsigned int barrier_extra = 0;
+    int dyn_pref = -1;  // unit assignment of streaming launches: -1 default, 0 static, 1 dynamic
     bool persistent = false;
     double *dpartials = nullptr;
     int red_blocks_per_grid = 0;
@@ -477,6 +483,8 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
                 }
             }
         }
+        // dynamic unit assignment (single launches; persistent launches assign statically)
+        p.dyn = h->dyn_pref == 1 || (h->dyn_pref < 0 && kDynDefault);
         p.zchunks = zc;
         std::vector<Unit> units;
         for (int c = 0; c < zc; ++c)
@@ -517,7 +525,7 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
 
 // ---- autotuner cache --------------------------------------------------------
 struct TunedPlan {
-    int variant, txt, zchunks, ctas;
+    int variant, txt, zchunks, ctas, dyn;
 };
 
 std::mutex g_tune_mu;
@@ -540,7 +548,7 @@ std::string tune_key(gbst_handle h)
     return b;
 }
 
-// Cache file (GBST_TUNE_CACHE): one "key variant txt zchunks ctas" line per entry.
+// Cache file (GBST_TUNE_CACHE): one "key variant txt zchunks ctas dyn" line per entry.
 void tune_cache_load()
 {
     if (g_tune_loaded)
@@ -552,10 +560,12 @@ void tune_cache_load()
     FILE *f = fopen(path, "r");
     if (!f)
         return;
-    char key[256];
-    TunedPlan t;
-    while (fscanf(f, "%255s %d %d %d %d", key, &t.variant, &t.txt, &t.zchunks, &t.ctas) == 5)
-        g_tune_cache[key] = t;
+    char line[512], key[256];
+    while (fgets(line, sizeof line, f)) {
+        TunedPlan t{0, 0, 0, 0, -1};
+        if (sscanf(line, "%255s %d %d %d %d %d", key, &t.variant, &t.txt, &t.zchunks, &t.ctas, &t.dyn) >= 5)
+            g_tune_cache[key] = t;
+    }
     fclose(f);
 }
 
@@ -568,7 +578,7 @@ void tune_cache_store(const std::string &key, const TunedPlan &t)
     FILE *f = fopen(path, "a");
     if (!f)
         return;
-    fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.variant, t.txt, t.zchunks, t.ctas);
+    fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), t.variant, t.txt, t.zchunks, t.ctas, t.dyn);
     fclose(f);
 }
 
@@ -710,6 +720,8 @@ SweepArgs sweep_args(gbst_handle h, int parity, const float *srcval)
     a.ngrids = static_cast<int>(h->subs.size());
     a.barrier = h->dbarrier;
     a.barrier_extra = h->barrier_extra;
+    // the dynamic-assignment counters share the grid-barrier buffer (zeroed at creation)
+    a.dyn = h->plan.dyn ? h->dbarrier + kDynCounterOffset : nullptr;
     for (int k = 0; k < 16; ++k)
         a.coupling[k] = h->coupling[k];
     return a;
@@ -780,6 +792,7 @@ gbst_status enqueue_persistent(gbst_handle h, int64_t nsteps, int parity, const 
     GBST_CUDA(cudaMemsetAsync(h->dbarrier, 0, sizeof(unsigned int), h->stream));
     SweepArgs a = sweep_args(h, parity, srcval);
     a.nsteps = static_cast<int>(nsteps);
+    a.dyn = nullptr;  // a persistent launch assigns units statically
     if (prof)
         GBST_CUDA(cudaEventRecordWithFlags(h->prof_ev[0], h->stream, cudaEventRecordExternal));
     const cudaError_t e = launch_stream_sweep(h->plan.var, a, h->plan.ctas, h->plan.smem, h->stream, true);
@@ -1120,10 +1133,12 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
     TunedPlan tp{};
     StreamVariant cv;
     if (d.tile == 0 && d.kernel != GBST_KERNEL_SIMPLE && tune_cache_find(h, &tp) &&
-        stream_variant_get(tp.variant, &cv) && variant_matches(h, cv))
+        stream_variant_get(tp.variant, &cv) && variant_matches(h, cv)) {
+        h->dyn_pref = tp.dyn;
         st = build_plan(h, tp.variant, tp.txt, tp.zchunks, tp.ctas);
-    else
+    } else {
         st = build_plan(h, d.tile > 0 ? d.tile - 1 : -1, 0, 0, 0);
+    }
     if (st != GBST_OK)
         return bail(st);
     *out = h;
@@ -1724,11 +1739,11 @@ gbst_status stencil_describe(gbst_handle h, char *buf, size_t len)
     snprintf(buf, len,
              "{\"kernel\": \"%s\", \"R\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, \"tile\": [%d, %d], "
              "\"zchunks\": %d, \"units\": %d, \"ctas\": %d, \"occupancy\": %d, \"smem\": %zu, \"subdomains\": %zu, "
-             "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d, \"tb\": %d, \"ys\": %d, \"nf\": %d}",
+             "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d, \"tb\": %d, \"ys\": %d, \"nf\": %d, \"dyn\": %d}",
              p.stream ? "stream" : "simple", h->R, p.var.nthreads, p.var.py, p.var.depth, tile_w(p.var, px),
              p.stream ? tile_h(p.var) : (p.var.nthreads / std::max(1, p.txt)) * p.var.py, p.zchunks, p.nunits,
              p.ctas, p.occupancy, p.smem, h->subs.size(), h->nboxes, p.variant, p.var.minb,
-             p.stream ? p.var.tb : 1, p.stream && p.var.ys ? 1 : 0, h->nf);
+             p.stream ? p.var.tb : 1, p.stream && p.var.ys ? 1 : 0, h->nf, p.dyn ? 1 : 0);
     return GBST_OK;
 }
 
@@ -1768,6 +1783,18 @@ gbst_status stencil_set_plan(gbst_handle h, int variant, int txt, int zchunks, i
         return st;
     GBST_CUDA(cudaStreamSynchronize(h->stream));
     return build_plan(h, variant, txt, zchunks, ctas);
+}
+
+gbst_status stencil_set_schedule(gbst_handle h, int dynamic)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (dynamic < -1 || dynamic > 1)
+        return fail(GBST_EINVAL, "schedule must be -1 (default), 0 (static) or 1 (dynamic)");
+    GBST_CUDA(cudaStreamSynchronize(h->stream));
+    h->dyn_pref = dynamic;
+    return build_plan(h, h->plan.variant, h->plan.req_txt, h->plan.req_zchunks, h->plan.req_ctas);
 }
 
 int stencil_variant_count(void) { return stream_variant_count(); }
@@ -1825,7 +1852,8 @@ gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len)
     GBST_CUDA(cudaEventCreate(&e1));
     const Plan before = h->plan;
     double best_ms = 1e300;
-    TunedPlan best{before.variant, before.req_txt, before.req_zchunks, before.req_ctas};
+    const int pref_before = h->dyn_pref;
+    TunedPlan best{before.variant, before.req_txt, before.req_zchunks, before.req_ctas, pref_before};
     std::string rep = "{\"candidates\": [";
     int ncand = 0;
     StreamVariant v;
@@ -1840,11 +1868,17 @@ gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len)
             const int *zl = chunked ? zlist_3d : zlist_2d;
             const int nz = chunked ? 6 : 1;
             int last_units = -1;
-            for (int zi = 0; zi < nz; ++zi) {
-                if (build_plan(h, vi, txt, zl[zi], 0) != GBST_OK)
+            // static and dynamic unit assignment
+            const int ndyn = 2;
+            for (int zi = 0; zi < nz * ndyn; ++zi) {
+                const int dv = zi % ndyn;
+                h->dyn_pref = dv;
+                if (build_plan(h, vi, txt, zl[zi / ndyn], 0) != GBST_OK)
                     continue;
-                if (h->plan.nunits == last_units)
+                if (dv == 0 && h->plan.nunits == last_units) {
+                    zi += ndyn - 1;  // same units as the previous z-chunking: skip it
                     continue;
+                }
                 last_units = h->plan.nunits;
                 const SweepArgs a = sweep_args(h, h->parity, nullptr);
                 cudaError_t e = launch_stream_sweep(h->plan.var, a, h->plan.ctas, h->plan.smem, h->stream);
@@ -1862,19 +1896,21 @@ gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len)
                 char b[256];
                 snprintf(b, sizeof b,
                          "%s{\"variant\": %d, \"txt\": %d, \"zchunks\": %d, \"units\": %d, \"ctas\": %d, "
-                         "\"tb\": %d, \"ms\": %.5f}",
-                         ncand ? ", " : "", vi, txt, h->plan.zchunks, h->plan.nunits, h->plan.ctas, v.tb, per);
+                         "\"tb\": %d, \"dyn\": %d, \"ms\": %.5f}",
+                         ncand ? ", " : "", vi, txt, h->plan.zchunks, h->plan.nunits, h->plan.ctas, v.tb,
+                         h->plan.dyn ? 1 : 0, per);
                 rep += b;
                 ++ncand;
                 if (per < best_ms) {
                     best_ms = per;
-                    best = TunedPlan{vi, txt, h->plan.zchunks, 0};
+                    best = TunedPlan{vi, txt, h->plan.zchunks, 0, h->plan.dyn ? 1 : 0};
                 }
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    h->dyn_pref = best.dyn;
     st = build_plan(h, best.variant, best.txt, best.zchunks, best.ctas);
     restore();
     gbst_status pe = poll_device_error(h);
@@ -1888,8 +1924,8 @@ gbst_status stencil_tune(gbst_handle h, int reps, char *report, size_t len)
         tune_cache_store(tune_key(h), best);
     }
     char b[256];
-    snprintf(b, sizeof b, "], \"best\": {\"variant\": %d, \"txt\": %d, \"zchunks\": %d, \"ms\": %.5f}}", best.variant,
-             best.txt, best.zchunks, best_ms);
+    snprintf(b, sizeof b, "], \"best\": {\"variant\": %d, \"txt\": %d, \"zchunks\": %d, \"dyn\": %d, \"ms\": %.5f}}",
+             best.variant, best.txt, best.zchunks, h->plan.dyn ? 1 : 0, best_ms);
     rep += b;
     if (report && len) {
         strncpy(report, rep.c_str(), len - 1);

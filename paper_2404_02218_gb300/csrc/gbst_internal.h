@@ -24,6 +24,9 @@ enum DevErr : int {
 
 // Wall-clock limit of every device-side spin wait (nanoseconds, %globaltimer).
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+// Offset (in unsigned ints) of the dynamic-assignment counters in a handle's
+// 256-byte grid-barrier buffer.
+constexpr int kDynCounterOffset = 16;
 
 // Padded storage of one field of one (sub)domain.
 //   element (i, j, k) of the interior lives at  origin + (k*rows + j)*pitch + i
@@ -84,6 +87,10 @@ struct SweepArgs {
     unsigned int barrier_extra;  // test hook: extra arrivals a barrier waits for (0 in normal use)
     int tb_single;         // temporally blocked kernel: 1 = perform one step only
     float coupling[16];    // fused multi-field system: A[k][j] at k * nfields + j
+    // Dynamic work assignment of a single-step streaming launch: [0] next unit,
+    // [1] CTAs done (the last CTA zeroes both for the next launch); null: unit
+    // ui goes to CTA ui mod gridDim.
+    unsigned int *dyn;
 };
 
 // Host-side entry points of the kernel translation units.

@@ -182,6 +182,33 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Work-unit source of a streaming launch: unit ui to CTA ui mod gridDim, or,
+// with a.dyn, the next index of a global counter (units then start in list
+// order across the whole grid).
+__device__ __forceinline__ int first_unit(const SweepArgs &a)
+{
+    return a.dyn ? static_cast<int>(atomicAdd(a.dyn, 1u)) : static_cast<int>(blockIdx.x);
+}
+
+__device__ __forceinline__ int next_unit(const SweepArgs &a, int prev)
+{
+    return a.dyn ? static_cast<int>(atomicAdd(a.dyn, 1u)) : prev + static_cast<int>(gridDim.x);
+}
+
+// A CTA's producer draws no more units: the last CTA of the launch to get here
+// zeroes the counters for the next launch (every other CTA has drawn its last
+// index by then; kernel completion publishes the reset).
+__device__ __forceinline__ void units_done(const SweepArgs &a)
+{
+    if (!a.dyn)
+        return;
+    __threadfence();
+    if (atomicAdd(a.dyn + 1, 1u) == gridDim.x - 1) {
+        atomicExch(a.dyn, 0u);
+        atomicExch(a.dyn + 1, 0u);
+    }
+}
+
 // Bounded wait that also gives up as soon as another warp of the CTA has.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
 {
@@ -238,6 +265,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *counter, unsigned int
 // centre plane, slot (j - rz) % S); the producer waits for empty of iteration
 // it - NB before reusing that iteration's slot for iteration it.
 //
+// Work units come in list order, either statically (unit ui to CTA ui mod
+// gridDim) or, with a.dyn, from a global counter that the producer draws from
+// when it starts a unit, so that the units in flight stay a contiguous window
+// of the list (neighbouring tiles at nearly the same planes: their shared halo
+// rows are read from L2).  The producer records each unit's index for the
+// consumers in uidx[] of its first iteration's barrier pair and ends a step
+// with a sentinel iteration (index -1, a plain arrive, no load).
+//
 // YS = true (2D grids): the streaming axis is y.  A plane slot is one row of
 // TX points (plus the x halo), the register queue holds the 2r+1 rows around
 // the output row, and there is no middle axis; the update is the 2D one,
@@ -265,13 +300,14 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
     constexpr int CBYTES = CK + TX * TY * ES;
     constexpr int CSLOT = EQ == GBST_WAVE ? (CBYTES + 127) / 128 * 128 : 0;
     static_assert(R <= G, "x halo must cover the radius");
-    static_assert(2 * NB * 8 + 16 <= 256, "barrier header");
+    static_assert(2 * NB * 8 + 16 + 4 * NB <= 256, "barrier header");
     static_assert(NT % TXT == 0, "tile shape");
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + NB;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NB);
+    volatile int *uidx = reinterpret_cast<volatile int *>(smem + 2 * NB * 8 + 16);  // unit of a unit's first iteration
     unsigned char *slots = smem + 256;
     unsigned char *cslots = slots + S * slot_bytes;  // wave centre-plane slots (NB of CSLOT bytes)
 
@@ -296,7 +332,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
         // order the previous step's generic-proxy stores (made visible by the
         // grid barrier) before this thread's async-proxy (TMA) reads
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
+        for (int ui = first_unit(a); ui < a.nunits; ui = next_unit(a, ui)) {
             const Unit u = a.units[ui];
             const GridDev &g = a.grids[u.grid];
             const int bx = (u.tile % g.tiles_x) * TX, by = YS ? 0 : (u.tile / g.tiles_x) * TY;
@@ -308,6 +344,8 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
             for (int l = 0; l < L; ++l, ++it) {
                 if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
                     return false;
+                if (l == 0)
+                    uidx[it % NB] = ui;  // published by the arrive below (release)
                 const bool centre = EQ == GBST_WAVE && l >= 2 * RZ;
                 uint64_t *bar = &full[it % NB];
                 mbar_arrive_expect_tx(bar, bytes + (centre ? CBYTES : 0));
@@ -329,6 +367,13 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                 }
             }
         }
+        // sentinel iteration: no more units in this step
+        if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
+            return false;
+        uidx[it % NB] = -1;
+        mbar_arrive(&full[it % NB]);
+        ++it;
+        units_done(a);
         return true;
     };
 
@@ -354,7 +399,18 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
         w2[m] = make_float2(a.w[m], a.w[m]);
 
     auto consume = [&](int parity, const float *srcval) -> bool {
-        for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
+        for (;;) {
+            // the first iteration of the next unit, or the step's sentinel
+            if (!wait_or_abort(&full[bar_i], par, abort_flag))
+                return false;
+            const int ui = uidx[bar_i];
+            if (ui < 0) {
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&empty[bar_i]);
+                advance();
+                return true;
+            }
             const Unit u = a.units[ui];
             // Copy the grid's descriptor into registers: the output stores below could
             // alias it, which would otherwise force a reload after every store.

@@ -32,13 +32,14 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_system(const SweepArgs 
     constexpr int TY = (NT / TXT) * PY;
     constexpr int ROW_BYTES = (TX + 2 * G) * ES;
     static_assert(R <= G, "x halo must cover the radius");
-    static_assert(2 * NB * 8 + 16 <= 256, "barrier header");
+    static_assert(2 * NB * 8 + 16 + 4 * NB <= 256, "barrier header");
     static_assert(NF >= 2 && NF <= 4, "2 to 4 fields");
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + NB;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NB);
+    volatile int *uidx = reinterpret_cast<volatile int *>(smem + 2 * NB * 8 + 16);  // as in k_stream
     unsigned char *slots = smem + 256;  // slot s, field f: slots + (s * NF + f) * slot_bytes
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_system(const SweepArgs 
             return;
         int it = 0;
         bool ok = true;
-        for (int ui = blockIdx.x; ui < a.nunits && ok; ui += gridDim.x) {
+        for (int ui = first_unit(a); ui < a.nunits && ok; ui = next_unit(a, ui)) {
             const Unit u = a.units[ui];
             const GridDev &g0 = a.grids[u.grid];
             const int bx = (u.tile % g0.tiles_x) * TX, by = (u.tile / g0.tiles_x) * TY;
@@ -71,6 +72,8 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_system(const SweepArgs 
                     ok = false;
                     break;
                 }
+                if (l == 0)
+                    uidx[it % NB] = ui;  // published by the arrive below
                 uint64_t *bar = &full[it % NB];
                 mbar_arrive_expect_tx(bar, bytes * NF);
 #pragma unroll
@@ -78,6 +81,15 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_system(const SweepArgs 
                     tma_load_plane(slots + ((it % S) * NF + f) * slot_bytes, &a.grids[u.grid + f].tmap[parity], bar,
                                    bx, by, u.z0 + l);
             }
+        }
+        // sentinel iteration: no more units
+        if (ok && it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
+            ok = false;
+        if (ok) {
+            uidx[it % NB] = -1;
+            mbar_arrive(&full[it % NB]);
+            ++it;
+            units_done(a);
         }
         if (!ok) {
             atomicCAS(a.err, 0, static_cast<int>(kDevTimeoutTma));
@@ -115,7 +127,20 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_system(const SweepArgs 
             A2[k][j] = make_float2(a.coupling[k * NF + j], a.coupling[k * NF + j]);
 
     bool ok = true;
-    for (int ui = blockIdx.x; ui < a.nunits && ok; ui += gridDim.x) {
+    while (ok) {
+        // the first iteration of the next unit, or the sentinel
+        if (!wait_or_abort(&full[bar_i], par, abort_flag)) {
+            ok = false;
+            break;
+        }
+        const int ui = uidx[bar_i];
+        if (ui < 0) {
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&empty[bar_i]);
+            advance();
+            break;
+        }
         const Unit u = a.units[ui];
         const GridDev *gp = a.grids + u.grid;
         const int tiles_x = gp->tiles_x;

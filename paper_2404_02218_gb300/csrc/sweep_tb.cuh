@@ -145,7 +145,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
     constexpr int QN = Sh::QN, S = Sh::S, NB = Sh::NB, NU = Sh::NU;
     constexpr int IN_ROW = Sh::IN_W * 4, U_ROW = Sh::U_W * 4;
     constexpr int PP = PX / 2;
-    static_assert((2 * NB + NU + 1) * 8 + 8 <= 256, "barrier header");
+    static_assert((2 * NB + NU + 1) * 8 + 8 + 4 * NB <= 256, "barrier header");
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -153,6 +153,8 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
     uint64_t *ubar = empty + NB;  // per u' plane buffer: plane written (one arrival per consumer warp)
     uint64_t *uend = ubar + NU;   // end of a unit: every consumer warp is done with the u' planes
     volatile int *abort_flag = reinterpret_cast<volatile int *>(uend + 1);
+    // unit of a unit's first iteration, by barrier pair (-1: no more units), as in k_stream
+    volatile int *uidx = reinterpret_cast<volatile int *>(smem + (2 * NB + NU + 1) * 8 + 8);
     unsigned char *slots = smem + 256;
     unsigned char *ubuf = slots + S * slot_bytes;  // NU u' planes of Sh::U_BYTES
 
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
         if (lane != 0)
             return;
         int it = 0;
-        for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
+        for (int ui = first_unit(a); ui < a.nunits; ui = next_unit(a, ui)) {
             const Unit u = a.units[ui];
             const GridDev &g = a.grids[u.grid];
             const int bx = (u.tile % g.tiles_x) * TX, by = (u.tile / g.tiles_x) * TY;
@@ -190,6 +192,8 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
             for (int l = 0; l < L; ++l, ++it) {
                 if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
                     goto drain;
+                if (l == 0)
+                    uidx[it % NB] = ui;  // published by the arrive below
                 mbar_arrive_expect_tx(&full[it % NB], bytes);
                 // padded coordinates: x from bx - 2 chunks (ghost G = one chunk), y from
                 // by - 2r (ghost r rows), plane z0 - 2r + l (ghost r planes); outside the
@@ -198,6 +202,13 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                                u.z0 - R + l);
             }
         }
+        // sentinel iteration: no more units
+        if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
+            goto drain;
+        uidx[it % NB] = -1;
+        mbar_arrive(&full[it % NB]);
+        ++it;
+        units_done(a);
     drain:
         if (*abort_flag) {
             atomicCAS(a.err, 0, static_cast<int>(kDevTimeoutTma));
@@ -249,7 +260,19 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
         }
     };
 
-    for (int ui = blockIdx.x; ui < a.nunits; ui += gridDim.x) {
+    for (;;) {
+        // the first iteration of the next unit, or the sentinel
+        if (!wait_or_abort(&full[bar_i], par, abort_flag)) {
+            atomicCAS(a.err, 0, static_cast<int>(kDevTimeoutTma));
+            return;
+        }
+        const int ui = uidx[bar_i];
+        if (ui < 0) {
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&empty[bar_i]);
+            return;
+        }
         const Unit u = a.units[ui];
         const GridDev *gp = a.grids + u.grid;
         const int tiles_x = gp->tiles_x;

@@ -163,6 +163,10 @@ class Grid:
     def set_plan(self, variant: int = -1, txt: int = 0, zchunks: int = 0, ctas: int = 0):
         N.stencil_set_plan(self.h, variant, txt, zchunks, ctas)
 
+    def set_schedule(self, dynamic: int = -1):
+        """Static (0), dynamic (1) or default (-1) work-unit assignment."""
+        N.stencil_set_schedule(self.h, dynamic)
+
     def tune(self, reps: int = 5) -> dict:
         import json
         return json.loads(N.stencil_tune(self.h, reps))
@@ -272,6 +276,10 @@ class Batch:
 
     def set_plan(self, variant: int = -1, txt: int = 0, zchunks: int = 0, ctas: int = 0):
         N.stencil_set_plan(self.h, variant, txt, zchunks, ctas)
+
+    def set_schedule(self, dynamic: int = -1):
+        """Static (0), dynamic (1) or default (-1) work-unit assignment."""
+        N.stencil_set_schedule(self.h, dynamic)
 
     def tune(self, reps: int = 5) -> dict:
         import json

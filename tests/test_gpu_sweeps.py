@@ -135,12 +135,15 @@ def test_every_kernel_variant_bitwise(torch_cuda, so, storage, ndim):
     variants = matching_variants(so, "heat", storage, ndim)
     assert variants
     g = make_grid(torch_cuda, ndim, dims, so, "heat", storage=storage, dt=a)
-    for v in variants:
-        for zc in (0, 3):
-            g.set_field("u", u0)
-            g.set_plan(v, 0, zc, 0)
-            g.run(4)
-            np.testing.assert_array_equal(g.get_field("u"), want, err_msg=f"variant {v} zchunks {zc}")
+    for sched in (0, 1):  # static and dynamic work-unit assignment
+        g.set_schedule(sched)
+        for v in variants:
+            for zc in (0, 3):
+                g.set_field("u", u0)
+                g.set_plan(v, 0, zc, 0)
+                g.run(4)
+                np.testing.assert_array_equal(g.get_field("u"), want,
+                                              err_msg=f"variant {v} zchunks {zc} schedule {sched}")
 
 
 @pytest.mark.parametrize("so", [2, 4, 8])
@@ -156,12 +159,14 @@ def test_every_wave_variant_bitwise(torch_cuda, so, storage, ndim):
     variants = matching_variants(so, "wave", storage, ndim)
     assert variants
     for v in variants:
-        for zc in (0, 2):
+        for zc, sched in ((0, 1), (2, 1), (2, 0)):
             g, *_ = wave_setup(torch_cuda, dims, so, storage=storage)
+            g.set_schedule(sched)
             g.set_plan(v, 0, zc, 0)
             g.run(5)
-            np.testing.assert_array_equal(g.get_field("u"), want_u, err_msg=f"variant {v} zchunks {zc}")
-            np.testing.assert_array_equal(g.get_field("u_prev"), want_p, err_msg=f"variant {v} zchunks {zc}")
+            msg = f"variant {v} zchunks {zc} schedule {sched}"
+            np.testing.assert_array_equal(g.get_field("u"), want_u, err_msg=msg)
+            np.testing.assert_array_equal(g.get_field("u_prev"), want_p, err_msg=msg)
             g.close()
 
 

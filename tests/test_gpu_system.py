@@ -78,12 +78,14 @@ def test_every_system_variant_bitwise(torch_cuda):
                     if (lambda v: v["nf"] == 3 and v["R"] == so // 2)(json.loads(N.stencil_variant_info(i)))]
         assert variants
         for v in variants:
-            for zc in (0, 3):
+            for zc, sched in ((0, 1), (3, 1), (3, 0)):
                 t, _ = make_system(dims, so, A3, (31, 32, 33))
+                t.set_schedule(sched)
                 t.set_plan(v, 0, zc, 0)
                 t.run(4)
                 for k in range(3):
-                    np.testing.assert_array_equal(t.get_field(k, "u"), want[k], err_msg=f"variant {v} zc {zc}")
+                    np.testing.assert_array_equal(t.get_field(k, "u"), want[k],
+                                                  err_msg=f"variant {v} zc {zc} schedule {sched}")
                 t.close()
         s.close()
 

@@ -65,13 +65,15 @@ def test_blocked_equals_single_steps_bitwise(torch_cuda, so, dims):
     want = {n: single_steps(dims, so, u0, n) for n in (1, 2, 5)}
     g, _ = heat(dims, so, 2)
     for v in tb_variants(so):
-        for zc in (0, 1, 3):
+        for zc, sched in ((0, 1), (1, 1), (3, 1), (3, 0)):
+            g.set_schedule(sched)
             for n in (1, 2, 5):
                 g.set_field("u", u0)
                 g.set_plan(v, 0, zc, 0)
                 assert json.loads(g.describe())["tb"] == 2
                 g.run(n)
-                np.testing.assert_array_equal(g.get_field("u"), want[n], err_msg=f"variant {v} zchunks {zc} n {n}")
+                np.testing.assert_array_equal(g.get_field("u"), want[n],
+                                              err_msg=f"variant {v} zchunks {zc} schedule {sched} n {n}")
     g.close()
 
 
