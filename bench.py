@@ -471,24 +471,25 @@ def kernel_name(plan: dict) -> str:
 
 def ncu_traffic(plan: dict):
     """DRAM bytes per launch from the committed ncu traffic summary, if it was taken on the
-    current kernel code with the same kernel instance and z-chunking.
+    current kernel code with the same kernel instance, z-chunking and work assignment.
 
-    The summary's table rows read ``| kernel instance | source sha | dram bytes per launch | zchunks |``."""
+    The summary's table rows read
+    ``| kernel instance | source sha | dram bytes per launch | zchunks | dyn |``."""
     path = os.path.join(ROOT, "profiles", "sweep_heat3d_so8_1024_dram_traffic.md")
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
     want = kernel_name(plan)
+    sha = kernel_source_sha(want.split("<")[0])
     for ln in lines:
         cells = [c.strip().strip("`") for c in ln.strip().strip("|").split("|")]
-        if len(cells) >= 4 and cells[0] == want and cells[1] == kernel_source_sha(want.split("<")[0]):
+        if len(cells) >= 5 and cells[0] == want and cells[1] == sha:
             try:
-                if int(cells[3]) != plan.get("zchunks"):
-                    return None
-                return float(cells[2])
+                if int(cells[3]) == plan.get("zchunks") and int(cells[4]) == plan.get("dyn", 0):
+                    return float(cells[2])
             except ValueError:
-                return None
+                continue
     return None
 
 

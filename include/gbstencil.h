@@ -310,9 +310,8 @@ gbst_status stencil_set_plan(gbst_handle h, int variant, int txt, int zchunks, i
  * the handle, so that the units in flight stay a contiguous window of the list
  * (neighbouring tiles share their halo planes in L2, and the load balances
  * itself); -1: the library's default (dynamic).  Results do not depend on it:
- * each unit writes its own output points.  Persistent launches always assign
- * statically.  EINVAL for other values.  Synchronises; invalidates captured
- * graphs.  The autotuner tries both. */
+ * each unit writes its own output points.  EINVAL for other values.
+ * Synchronises; invalidates captured graphs.  The autotuner tries both. */
 gbst_status stencil_set_schedule(gbst_handle h, int dynamic);
 
 /* Autotuner: times every applicable (kernel variant, z-chunking)

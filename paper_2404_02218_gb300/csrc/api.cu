@@ -115,14 +115,22 @@ bool encode_tmap_bf16_4d(CUtensorMap *m, const void *base, const uint64_t dims[4
     return true;
 }
 
-bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h, std::string *err)
+// Tensor map of a padded field.  The kernels address x from `lead` elements
+// before the interior (one 16-byte chunk of the storage type), so the map
+// starts L.G - lead elements into each row (L.G >= lead) and covers the
+// interior and `lead` ghosts on each side: boxes that reach further read
+// zeros without touching the row padding.
+bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h, int lead,
+                 std::string *err)
 {
     auto fn = tmap_encoder();
     if (!fn) {
         *err = "cuTensorMapEncodeTiled is not available from the driver";
         return false;
     }
-    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(L.pitch), static_cast<cuuint64_t>(L.rows),
+    const int64_t shift = L.G - lead;
+    base = static_cast<unsigned char *>(base) + shift * L.es;
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(L.nx + 2 * lead), static_cast<cuuint64_t>(L.rows),
                                 static_cast<cuuint64_t>(L.planes)};
     const cuuint64_t strides[2] = {static_cast<cuuint64_t>(L.pitch) * L.es,
                                    static_cast<cuuint64_t>(L.pitch) * L.rows * L.es};
@@ -446,13 +454,13 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
         if (p.stream) {
             std::string err;
             for (int b = 0; b < 2; ++b)
-                if (!encode_tmap(&g.tmap[b], g.buf[b], s.lu, st, box_w, box_h, &err))
+                if (!encode_tmap(&g.tmap[b], g.buf[b], s.lu, st, box_w, box_h, px, &err))
                     return fail(GBST_ECUDA, "%s", err.c_str());
             if (h->d.eq == GBST_WAVE) {
                 for (int b = 0; b < 2; ++b)
-                    if (!encode_tmap(&g.tmap_c[b], g.buf[b], s.lu, st, TX, TY, &err))
+                    if (!encode_tmap(&g.tmap_c[b], g.buf[b], s.lu, st, TX, TY, px, &err))
                         return fail(GBST_ECUDA, "%s", err.c_str());
-                if (!encode_tmap(&g.tmap_k, g.kappa, s.lk, GBST_F32, TX, TY, &err))
+                if (!encode_tmap(&g.tmap_k, g.kappa, s.lk, GBST_F32, TX, TY, px, &err))
                     return fail(GBST_ECUDA, "%s", err.c_str());
             }
         }
@@ -483,7 +491,7 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
                 }
             }
         }
-        // dynamic unit assignment (single launches; persistent launches assign statically)
+        // dynamic unit assignment
         p.dyn = h->dyn_pref == 1 || (h->dyn_pref < 0 && kDynDefault);
         p.zchunks = zc;
         std::vector<Unit> units;
@@ -792,7 +800,6 @@ gbst_status enqueue_persistent(gbst_handle h, int64_t nsteps, int parity, const 
     GBST_CUDA(cudaMemsetAsync(h->dbarrier, 0, sizeof(unsigned int), h->stream));
     SweepArgs a = sweep_args(h, parity, srcval);
     a.nsteps = static_cast<int>(nsteps);
-    a.dyn = nullptr;  // a persistent launch assigns units statically
     if (prof)
         GBST_CUDA(cudaEventRecordWithFlags(h->prof_ev[0], h->stream, cudaEventRecordExternal));
     const cudaError_t e = launch_stream_sweep(h->plan.var, a, h->plan.ctas, h->plan.smem, h->stream, true);
@@ -1067,8 +1074,11 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
                     nn[0] = split(dims[0], dd[0], cx, &s.g0[0]);
                     nn[1] = split(dims[1], dd[1], cy, &s.g0[1]);
                     nn[2] = split(dims[2], dd[2], cz, &s.g0[2]);
-                    s.lu = make_layout(d.ndim, nn[0], nn[1], nn[2], R, h->es, 16 / h->es);
-                    s.lk = make_layout(d.ndim, nn[0], nn[1], nn[2], R, 4, px);
+                    // x ghosts of 128 bytes: interior rows start on a 128-byte line, so
+                    // the row pieces of neighbouring tiles never share a sector
+                    // (partial-sector writes would make L2 fetch the sector first)
+                    s.lu = make_layout(d.ndim, nn[0], nn[1], nn[2], R, h->es, kGhostBytesX / h->es);
+                    s.lk = make_layout(d.ndim, nn[0], nn[1], nn[2], R, 4, kGhostBytesX / 4);
                     h->subs.push_back(s);
                     h->max_points = std::max(h->max_points, nn[0] * nn[1] * nn[2]);
                 }

@@ -28,9 +28,13 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 // 256-byte grid-barrier buffer.
 constexpr int kDynCounterOffset = 16;
 
+// x ghost width of the stored fields in bytes (each side): interior rows start
+// on a 128-byte boundary (the row pitch is a multiple of 128 bytes too).
+constexpr int kGhostBytesX = 128;
+
 // Padded storage of one field of one (sub)domain.
 //   element (i, j, k) of the interior lives at  origin + (k*rows + j)*pitch + i
-//   x ghosts: G = 16 bytes / element size (>= r) on each side,
+//   x ghosts: G = kGhostBytesX / element size (>= r) on each side,
 //   y ghosts: r rows, z ghosts: rz = r (3D) or 0 (2D) planes.
 //   pitch = round_up(nx + 2G, 128 bytes / element size) elements.
 struct Layout {
@@ -42,7 +46,7 @@ struct Layout {
     size_t bytes = 0;    // total bytes, rounded up to 256
 };
 
-// G: x ghost width in elements (16 bytes of the field, or more for fields read with wider vectors).
+// G: x ghost width in elements.
 Layout make_layout(int ndim, int64_t nx, int64_t ny, int64_t nz, int r, int elem_size, int G);
 
 // One (sub)domain as the sweep kernels see it.  Lives in device global memory;
@@ -87,9 +91,9 @@ struct SweepArgs {
     unsigned int barrier_extra;  // test hook: extra arrivals a barrier waits for (0 in normal use)
     int tb_single;         // temporally blocked kernel: 1 = perform one step only
     float coupling[16];    // fused multi-field system: A[k][j] at k * nfields + j
-    // Dynamic work assignment of a single-step streaming launch: [0] next unit,
-    // [1] CTAs done (the last CTA zeroes both for the next launch); null: unit
-    // ui goes to CTA ui mod gridDim.
+    // Dynamic work assignment of a streaming launch: [0] units drawn beyond the
+    // first gridDim, [1] CTAs done (the last CTA of a launch or step zeroes both);
+    // null: unit ui goes to CTA ui mod gridDim.
     unsigned int *dyn;
 };
 

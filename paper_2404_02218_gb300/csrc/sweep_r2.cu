@@ -14,6 +14,7 @@ const Entry kTable[] = {
     GBST_EQS(2, GBST_F32, true, 8, 1, 3, 2, 32),
     GBST_EQS(2, GBST_F32, true, 4, 2, 3, 1, 16),
     GBST_EQS(2, GBST_F32, true, 4, 2, 3, 1, 8),
+    GBST_EQS(2, GBST_F32, true, 8, 2, 6, 1, 32),
     GBST_EQS(2, GBST_BF16, true, 4, 1, 3, 1, 16),
     GBST_EQS(2, GBST_BF16, true, 4, 1, 5, 2, 16),
     GBST_EQS(2, GBST_BF16, true, 4, 2, 3, 1, 16),

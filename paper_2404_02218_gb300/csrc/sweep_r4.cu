@@ -14,6 +14,9 @@ const Entry kTable[] = {
     GBST_EQS(4, GBST_F32, true, 8, 1, 3, 2, 32),
     GBST_EQS(4, GBST_F32, true, 4, 2, 3, 1, 16),
     GBST_EQS(4, GBST_F32, true, 4, 2, 3, 1, 8),
+    // 128 x 16 tiles, one CTA per SM (heat only: the wave's centre slots do not fit)
+    entry<4, GBST_HEAT, GBST_F32, true, 8, 2, 7, 1, 32>(),
+    entry<4, GBST_HEAT, GBST_F32, true, 8, 2, 9, 1, 32>(),
     GBST_EQS(4, GBST_BF16, true, 4, 1, 3, 1, 16),
     GBST_EQS(4, GBST_BF16, true, 4, 1, 5, 2, 16),
     GBST_EQS(4, GBST_BF16, true, 4, 2, 3, 1, 16),

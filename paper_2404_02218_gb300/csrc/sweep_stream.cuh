@@ -183,21 +183,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Work-unit source of a streaming launch: unit ui to CTA ui mod gridDim, or,
-// with a.dyn, the next index of a global counter (units then start in list
-// order across the whole grid).
-__device__ __forceinline__ int first_unit(const SweepArgs &a)
-{
-    return a.dyn ? static_cast<int>(atomicAdd(a.dyn, 1u)) : static_cast<int>(blockIdx.x);
-}
+// with a.dyn, CTA b starts with unit b and then draws gridDim + the next index
+// of a global counter (units then start in list order across the whole grid;
+// the first unit costs no atomic round trip).
+__device__ __forceinline__ int first_unit(const SweepArgs &) { return static_cast<int>(blockIdx.x); }
 
 __device__ __forceinline__ int next_unit(const SweepArgs &a, int prev)
 {
-    return a.dyn ? static_cast<int>(atomicAdd(a.dyn, 1u)) : prev + static_cast<int>(gridDim.x);
+    return a.dyn ? static_cast<int>(gridDim.x + atomicAdd(a.dyn, 1u)) : prev + static_cast<int>(gridDim.x);
 }
 
-// A CTA's producer draws no more units: the last CTA of the launch to get here
-// zeroes the counters for the next launch (every other CTA has drawn its last
-// index by then; kernel completion publishes the reset).
+// A CTA's producer draws no more units: the last CTA of the launch (or of the
+// step, in a persistent launch) to get here zeroes the counters for the next
+// one (every other CTA has drawn its last index by then; kernel completion or
+// the grid barrier publishes the reset).
 __device__ __forceinline__ void units_done(const SweepArgs &a)
 {
     if (!a.dyn)
@@ -267,7 +266,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *counter, unsigned int
 //
 // Work units come in list order, either statically (unit ui to CTA ui mod
 // gridDim) or, with a.dyn, from a global counter that the producer draws from
-// when it starts a unit, so that the units in flight stay a contiguous window
+// when it has issued the loads of its current unit (the first unit of CTA b is
+// unit b), so that the units in flight stay a contiguous window
 // of the list (neighbouring tiles at nearly the same planes: their shared halo
 // rows are read from L2).  The producer records each unit's index for the
 // consumers in uidx[] of its first iteration's barrier pair and ends a step
