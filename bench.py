@@ -261,6 +261,20 @@ def extras(torch, hbm: float, tune: bool):
         g.close()
     del c
 
+    # heat 2D 256^2, order 2, a = 0.2, Gaussian bump, 100 steps: 256 KB per field, L2-resident, so
+    # launch/latency bound; the run as one captured graph against one launch per step
+    c1 = synthetic.heat2d_256()
+    lat = {}
+    for use_graph in (True, False):
+        g = Grid(2, c1.dims, c1.so, "heat", dt=c1.a, stream=stream, use_graph=use_graph)
+        g.set_field("u", c1.initial())
+        lat[use_graph] = timed_runs(torch, stream, lambda: g.run(c1.nsteps), reps=5)
+        g.close()
+    out["heat2d_256_so2_100steps"] = {"us_per_step_graph": 1e3 * lat[True] / c1.nsteps,
+                                      "us_per_step_no_graph": 1e3 * lat[False] / c1.nsteps,
+                                      "gpts_graph": c1.nsteps * 256 * 256 / lat[True] / 1e6,
+                                      "bound": "launch / latency (fits L2)"}
+
     # 2D at the paper's large size: heat 16384^2, orders 2/4/8, and the order-8 acoustic wave
     n2 = 16384
     u2 = synthetic.uniform_field_torch(7, (n2, n2), "cuda")

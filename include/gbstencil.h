@@ -135,10 +135,13 @@ gbst_status stencil_get_field(gbst_handle h, int field, void *dst, int dst_dtype
  * GBST_U_PREV: the copy is enqueued on the handle's stream and the call returns
  * at once.  The buffer must be device memory or page-locked host memory (else
  * EINVAL), and must stay valid, and unmodified / unread by the caller, until
- * the stream reaches the copy (e.g. stencil_sync).  The staging buffer of a
- * host copy is released in stream order, which needs a stream-ordered
- * allocator (e.g. a framework's caching allocator); with the default
- * cudaMalloc / cudaFree the release synchronises the device.  Device errors
+ * the stream reaches the copy (e.g. stencil_sync).  Host data in the storage
+ * type of a grid (or batch member) without decomposition moves by one pitched
+ * copy straight between the dense host array and the padded field; otherwise
+ * through a staging buffer and a conversion kernel, the buffer released in
+ * stream order, which needs a stream-ordered allocator (e.g. a framework's
+ * caching allocator; with the default cudaMalloc / cudaFree the release
+ * synchronises the device).  Device errors
  * surface at the next synchronising call.  No counterpart in the paper: lets a
  * caller overlap one grid's transfers with another grid's sweeps. */
 gbst_status stencil_set_field_async(gbst_handle h, int field, const void *src, int src_dtype,
