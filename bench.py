@@ -597,8 +597,8 @@ def run_ours(args):
     # End to end through the C ABI with host buffers: every step copies u in from
     # pinned host memory and the result out, for each order.  The three orders are
     # independent grids, each on its own stream, so one grid's transfers overlap
-    # another's sweeps (stencil_set_field_async / stencil_get_field_async; the
-    # transfer kernels read and write the page-locked host buffers directly).
+    # another's sweeps (stencil_set_field_async / stencil_get_field_async: the copy
+    # engines move each field between the page-locked buffer and the padded field).
     e2e = None
     if not args.no_e2e:
         from paper_2404_02218_gb300 import native as NN
