@@ -221,12 +221,15 @@ def extras(torch, hbm: float, tune: bool):
     out = {}
     stream = torch.cuda.Stream()
 
-    # heat 1024^3 order 4 on a 2x2x2 decomposition vs the undecomposed grid
+    # heat 1024^3 order 4 on a 2x2x2 decomposition (halo exchange overlapped with the
+    # sweep, and not) vs the undecomposed grid
     case = synthetic.heat3d(1024, 4)
     u0 = synthetic.uniform_field_torch(case.seed, (1024,) * 3, "cuda")
     res = {}
-    for name, dec in (("undecomposed", (1, 1, 1)), ("decomp_2x2x2", (2, 2, 2))):
+    for name, dec, ov in (("undecomposed", (1, 1, 1), -1), ("decomp_2x2x2", (2, 2, 2), 1),
+                          ("decomp_2x2x2_no_overlap", (2, 2, 2), 0)):
         g = Grid(3, case.dims, 4, "heat", dt=case.a, decomp=dec, stream=stream)
+        g.set_overlap(ov)
         g.set_field("u", u0)
         if tune:
             g.tune(reps=2)
@@ -236,11 +239,15 @@ def extras(torch, hbm: float, tune: bool):
         o = torch.empty_like(u0)
         g.get_field("u", out=o)
         res[name] = o
+        plan = json.loads(g.describe())
         out[f"heat3d_so4_{name}"] = {"gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6,
-                                     "frac": 8 * pts / ms / 1e6 / hbm, "steps": STEPS_PER_RUN}
+                                     "frac": 8 * pts / ms / 1e6 / hbm, "steps": STEPS_PER_RUN,
+                                     "overlap": plan["overlap"], "interior_units": plan["interior_units"],
+                                     "units": plan["units"]}
         g.close()
-    out["heat3d_so4_decomp_2x2x2"]["bitwise_equal_to_undecomposed"] = bool(
-        torch.equal(res["undecomposed"], res["decomp_2x2x2"]))
+    for name in ("decomp_2x2x2", "decomp_2x2x2_no_overlap"):
+        out[f"heat3d_so4_{name}"]["bitwise_equal_to_undecomposed"] = bool(
+            torch.equal(res["undecomposed"], res[name]))
     del res, u0, o
 
     # acoustic wave 768^3, order 8, five layers, Ricker 10 Hz: FP32 vs BF16 storage

@@ -317,6 +317,18 @@ gbst_status stencil_set_plan(gbst_handle h, int variant, int txt, int zchunks, i
  * Synchronises; invalidates captured graphs.  The autotuner tries both. */
 gbst_status stencil_set_schedule(gbst_handle h, int dynamic);
 
+/* Overlap of the halo exchange with the sweep (decomposition mode, Section 4.2's
+ * dmp.swap; and the periodic wrap): each step copies the faces on a second
+ * stream while the work units whose boxes read no exchanged ghost cell sweep,
+ * then sweeps the remaining units (the paper names this overlap as future
+ * work).  enable = 1 on, 0 off (copies, then one sweep), -1 the library's
+ * default (off: on one device the copies are a small part of a step and the
+ * split sweep costs more than it hides).  Single-step streaming plans only;
+ * results are the same bits either way; with the overlap on, the autotuner
+ * keeps to plans that can split.  EINVAL for other values.  Synchronises;
+ * invalidates captured graphs. */
+gbst_status stencil_set_overlap(gbst_handle h, int enable);
+
 /* Autotuner: times every applicable (kernel variant, z-chunking)
  * on the handle's own fields with `reps` launches each (CUDA events on the
  * handle's stream), keeps the fastest and caches it per shape class -- in the

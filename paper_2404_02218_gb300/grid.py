@@ -167,6 +167,10 @@ class Grid:
         """Static (0), dynamic (1) or default (-1) work-unit assignment."""
         N.stencil_set_schedule(self.h, dynamic)
 
+    def set_overlap(self, enable: int = -1):
+        """Halo exchange overlapped with the sweep: on (1), off (0) or default (-1)."""
+        N.stencil_set_overlap(self.h, enable)
+
     def tune(self, reps: int = 5) -> dict:
         import json
         return json.loads(N.stencil_tune(self.h, reps))
@@ -280,6 +284,10 @@ class Batch:
     def set_schedule(self, dynamic: int = -1):
         """Static (0), dynamic (1) or default (-1) work-unit assignment."""
         N.stencil_set_schedule(self.h, dynamic)
+
+    def set_overlap(self, enable: int = -1):
+        """Halo exchange overlapped with the sweep: on (1), off (0) or default (-1)."""
+        N.stencil_set_overlap(self.h, enable)
 
     def tune(self, reps: int = 5) -> dict:
         import json

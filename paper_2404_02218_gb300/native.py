@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
                 "stencil_last_kernel_time": ([H, ctypes.POINTER(dbl), ctypes.POINTER(i64)], i32),
                 "stencil_set_plan": ([H, i32, i32, i32, i32], i32),
                 "stencil_set_schedule": ([H, i32], i32),
+                "stencil_set_overlap": ([H, i32], i32),
                 "stencil_tune": ([H, i32, ctypes.c_char_p, ctypes.c_size_t], i32),
                 "stencil_variant_count": ([], i32),
                 "stencil_variant_info": ([i32, ctypes.c_char_p, ctypes.c_size_t], i32),
@@ -241,6 +242,10 @@ def stencil_set_plan(h, variant: int = -1, txt: int = 0, zchunks: int = 0, ctas:
 
 def stencil_set_schedule(h, dynamic: int = -1):
     _check(lib().stencil_set_schedule(h, dynamic), "stencil_set_schedule")
+
+
+def stencil_set_overlap(h, enable: int = -1):
+    _check(lib().stencil_set_overlap(h, enable), "stencil_set_overlap")
 
 
 def stencil_tune(h, reps: int = 5) -> str:
