@@ -48,7 +48,7 @@ typedef enum {
     GBST_ETIMEOUT = -4,   /* a bounded device-side wait expired; the handle is poisoned */
     GBST_EUNSTABLE = -5,  /* time step above the von Neumann limit, or NaN/Inf detected */
     GBST_ESTATE = -6,     /* call not valid in the handle's current state */
-    GBST_ENOTSUP = -7     /* combination not supported by this build */
+    GBST_ENOTSUP = -7     /* combination not supported by the library */
 } gbst_status;
 
 enum { GBST_HEAT = 0, GBST_WAVE = 1 };                    /* gbst_desc.eq */

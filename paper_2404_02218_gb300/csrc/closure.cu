@@ -869,7 +869,7 @@ gbst_status closure_create(int cin, int hidden, int64_t max_points, double in_sc
         return record_error(GBST_EINVAL, "closure_create: null out");
     *out = nullptr;
     if (cin != 4 || hidden != 16)
-        return record_error(GBST_ENOTSUP, "closure_create: this build has 4 input and 16 hidden channels");
+        return record_error(GBST_ENOTSUP, "closure_create: the network has 4 input and 16 hidden channels");
     if (max_points < 1 || !(in_scale > 0.0))
         return record_error(GBST_EINVAL, "closure_create: max_points and in_scale must be positive");
     gbst_closure c = new (std::nothrow) gbst_closure_s;
