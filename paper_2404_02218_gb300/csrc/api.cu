@@ -240,6 +240,10 @@ struct Sub {
     bool unstable = false;  // kappa above the stability limit
 };
 
+// Rows of at least this many bytes get kGhostBytesX-wide x ghosts; narrower rows
+// keep one 16-byte chunk (measured below, where the layouts are made).
+constexpr int64_t kWideRowBytes = 2048;
+
 // Default unit assignment of streaming launches: dynamic (measured equal or
 // faster for every streaming variant; fewer DRAM re-reads of halo planes).
 constexpr bool kDynDefault = true;
@@ -1152,11 +1156,14 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
                     nn[0] = split(dims[0], dd[0], cx, &s.g0[0]);
                     nn[1] = split(dims[1], dd[1], cy, &s.g0[1]);
                     nn[2] = split(dims[2], dd[2], cz, &s.g0[2]);
-                    // x ghosts of 128 bytes: interior rows start on a 128-byte line, so
-                    // the row pieces of neighbouring tiles never share a sector
-                    // (partial-sector writes would make L2 fetch the sector first)
-                    s.lu = make_layout(d.ndim, nn[0], nn[1], nn[2], R, h->es, kGhostBytesX / h->es);
-                    s.lk = make_layout(d.ndim, nn[0], nn[1], nn[2], R, 4, kGhostBytesX / 4);
+                    // x ghosts of 128 bytes for wide rows (interior rows start on a
+                    // 128-byte line: 1.47 against 1.50 ms per order-8 sweep at 1024^3);
+                    // one 16-byte chunk for narrow rows, where the wider row pitch cost
+                    // more than it saved (64 grids of 96-256 points per axis: 353
+                    // against 388 GPoints/s)
+                    const bool wide = nn[0] * h->es >= kWideRowBytes;
+                    s.lu = make_layout(d.ndim, nn[0], nn[1], nn[2], R, h->es, (wide ? kGhostBytesX : 16) / h->es);
+                    s.lk = make_layout(d.ndim, nn[0], nn[1], nn[2], R, 4, wide ? kGhostBytesX / 4 : px);
                     h->subs.push_back(s);
                     h->max_points = std::max(h->max_points, nn[0] * nn[1] * nn[2]);
                 }

@@ -28,13 +28,14 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 // 256-byte grid-barrier buffer.
 constexpr int kDynCounterOffset = 16;
 
-// x ghost width of the stored fields in bytes (each side): interior rows start
-// on a 128-byte boundary (the row pitch is a multiple of 128 bytes too).
+// x ghost width in bytes (each side) of the stored fields of wide grids:
+// interior rows start on a 128-byte boundary (the row pitch is a multiple of
+// 128 bytes too).  Narrow grids keep one 16-byte chunk.
 constexpr int kGhostBytesX = 128;
 
 // Padded storage of one field of one (sub)domain.
 //   element (i, j, k) of the interior lives at  origin + (k*rows + j)*pitch + i
-//   x ghosts: G = kGhostBytesX / element size (>= r) on each side,
+//   x ghosts: G = kGhostBytesX or 16 bytes, / element size (>= r), each side,
 //   y ghosts: r rows, z ghosts: rz = r (3D) or 0 (2D) planes.
 //   pitch = round_up(nx + 2G, 128 bytes / element size) elements.
 struct Layout {
