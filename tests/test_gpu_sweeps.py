@@ -406,3 +406,33 @@ def test_extreme_aspect_ratios(torch_cuda, dims, so):
     u0, a, got = heat_case_run(torch_cuda, dims, so, 5)
     ref = oracle.heat_run(u0, so, a, 5)
     assert oracle.max_rel_error(got, ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("eq", ["heat", "wave"])
+def test_wide_rows_layout(torch_cuda, eq):
+    """Rows of at least 2 KB use 128-byte x ghosts (tensor maps shifted to the
+    kernels' 16-byte halo): ragged wide grids, decomposed or not, match the
+    simple kernel bit for bit and the oracle."""
+    so = 8 if eq == "wave" else 4
+    dims = (1030, 19, 11)
+    if eq == "heat":
+        u0 = synthetic.uniform_field(41, tuple(reversed(dims)))
+        a = float(np.float32(0.8 * synthetic.heat_a_max(3, so)))
+        outs = []
+        for kw in (dict(kernel="simple"), {}, dict(decomp=(2, 1, 1))):
+            g = make_grid(torch_cuda, 3, dims, so, "heat", h=1.0, dt=a, alpha=1.0, **kw)
+            g.set_field("u", u0)
+            g.run(5)
+            outs.append(g.get_field("u", np.float64))
+            g.close()
+        for o in outs[1:]:
+            np.testing.assert_array_equal(o, outs[0])
+        assert oracle.max_rel_error(outs[1], oracle.heat_run(u0, so, a, 5)) <= TOL_F32
+    else:
+        ref, *_ = wave_setup(torch_cuda, dims, so, kernel="simple")
+        ref.run(9)
+        for kw in ({}, dict(decomp=(2, 1, 1))):
+            g, *_ = wave_setup(torch_cuda, dims, so, **kw)
+            g.run(9)
+            np.testing.assert_array_equal(g.get_field("u"), ref.get_field("u"))
+            np.testing.assert_array_equal(g.get_field("u_prev"), ref.get_field("u_prev"))
