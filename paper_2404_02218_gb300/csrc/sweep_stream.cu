@@ -12,13 +12,14 @@ const Entry *table_r1_2d(int *n);
 const Entry *table_r2_2d(int *n);
 const Entry *table_r4_2d(int *n);
 const Entry *table_sys(int *n);
+const Entry *table_r2_rows4(int *n);
 }  // namespace sweep
 
 namespace {
 using sweep::Entry;
 
 struct Registry {
-    static constexpr int kTables = 8;
+    static constexpr int kTables = 9;
     const Entry *tab[kTables];
     int n[kTables];
     Registry()
@@ -31,6 +32,7 @@ struct Registry {
         tab[5] = sweep::table_r2_2d(&n[5]);
         tab[6] = sweep::table_r4_2d(&n[6]);
         tab[7] = sweep::table_sys(&n[7]);
+        tab[8] = sweep::table_r2_rows4(&n[8]);
     }
     int total() const
     {
