@@ -320,8 +320,8 @@ gbst_status stencil_set_schedule(gbst_handle h, int dynamic);
 /* Overlap of the halo exchange with the sweep (decomposition mode, Section 4.2's
  * dmp.swap; and the periodic wrap): each step copies the faces on a second
  * stream while the work units whose boxes read no exchanged ghost cell sweep,
- * then sweeps the remaining units (the paper names this overlap as future
- * work).  enable = 1 on, 0 off (copies, then one sweep), -1 the library's
+ * then sweeps the remaining units (communication-computation overlap, which
+ * Section 4.2 lists as a limitation of its dmp design).  enable = 1 on, 0 off (copies, then one sweep), -1 the library's
  * default (off: on one device the copies are a small part of a step and the
  * split sweep costs more than it hides).  Single-step streaming plans only;
  * results are the same bits either way; with the overlap on, the autotuner
