@@ -353,9 +353,12 @@ gbst_status stencil_variant_info(int i, char *buf, size_t len);
  * The per-block partial sums go to a fixed 128 KB array inside the library's
  * device image (16384 doubles, 256-byte aligned), which every GPU that loads the
  * library keeps until the process exits.  n may be at most 2^30 (16384 blocks of
- * 65536 values); larger n returns GBST_EINVAL.  The first call on each device
- * looks up the array's device address with that device current (make that first
- * call outside any stream capture).  All calls share the one array and it keeps
+ * 65536 values); larger n returns GBST_EINVAL.  The first call in each CUDA
+ * context (the current device's primary context, unless the caller made another
+ * one current) looks up the array's device address with that context current and
+ * caches it for that context; make that first call outside any stream capture.
+ * Errors are reported with the entry point's name; an error left pending by an
+ * earlier, unrelated launch is cleared, not reported.  All calls share the one array and it keeps
  * the last call's contents; every call writes all the partials it reads, so no
  * clearing is needed, but calls that overlap on the GPU (different streams,
  * no ordering between them) race on it.  No cudaMalloc, cudaFree or allocating

@@ -8,6 +8,9 @@
 // caller passes the input array and a device location for the result, and the
 // per-block partial sums go to a fixed-size array that lives in this library's
 // own device image (a file-scope __device__ array), not in allocated memory.
+#include <cuda.h>
+
+#include <cstdio>
 #include <mutex>
 
 #include "gbst_internal.h"
@@ -26,9 +29,55 @@ constexpr int64_t kMaxElems = kChunk * kMaxPartials;     // 2^30 elements
 // passes the device address obtained from cudaGetSymbolAddress instead.
 static __device__ __align__(256) double g_partials[kMaxPartials];
 
-constexpr int kMaxDevices = 64;
+// Device address of g_partials per CUDA context.  The address belongs to one
+// context's load of this module, so the cache is keyed on the context's
+// process-unique id (cuCtxGetId): a context created after cudaDeviceReset, or a
+// non-primary context made current by the caller, gets its own look-up.
+constexpr int kMaxContexts = 64;
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    double *addr;
+};
 std::mutex g_mu;
-double *g_partials_addr[kMaxDevices] = {};
+ScratchAddr g_addr[kMaxContexts] = {};
+int g_naddr = 0;
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context (created by the runtime if none is current yet).
+bool current_context_id(unsigned long long *id)
+{
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *p = nullptr, *q = nullptr;
+        cudaDriverEntryPointQueryResult r1{}, r2{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &r1) != cudaSuccess ||
+            r1 != cudaDriverEntryPointSuccess || !p ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &q, 12000, cudaEnableDefault, &r2) != cudaSuccess ||
+            r2 != cudaDriverEntryPointSuccess || !q) {
+            cudaGetLastError();
+            return false;
+        }
+        get_current = reinterpret_cast<PfnCtxGetCurrent>(p);
+        get_id = reinterpret_cast<PfnCtxGetId>(q);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS)
+        return false;
+    if (!ctx) {
+        // No context is current on this thread yet: make the current device's
+        // primary context current (cudaSetDevice initialises it; nothing is allocated).
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess ||
+            get_current(&ctx) != CUDA_SUCCESS || !ctx) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 __device__ __forceinline__ double load_elem(const void *p, int dtype, int64_t i)
 {
@@ -95,6 +144,8 @@ using namespace gbst;
 extern "C" gbst_status gbst_reduce_dense_f64_noalloc(const void *x, int dtype, int64_t n, int kind, double *out,
                                                      void *stream)
 {
+    static const char *kName = "gbst_reduce_dense_f64_noalloc";
+    char msg[256];
     if (!out || (n > 0 && !x))
         return record_error(GBST_EINVAL, "gbst_reduce_dense_f64_noalloc: null input or output");
     if (dtype != GBST_F32 && dtype != GBST_F64 && dtype != GBST_BF16)
@@ -105,30 +156,42 @@ extern "C" gbst_status gbst_reduce_dense_f64_noalloc(const void *x, int dtype, i
         return record_error(
             GBST_EINVAL, "gbst_reduce_dense_f64_noalloc: n must be in [0, 2^30] (the fixed scratch holds 16384 "
                          "block partials of 65536 elements each)");
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return record_error(GBST_ECUDA, "gbst_reduce_dense_f64_noalloc: no current CUDA device");
+    unsigned long long ctx_id = 0;
+    if (!current_context_id(&ctx_id))
+        return record_error(GBST_ECUDA, "gbst_reduce_dense_f64_noalloc: no current CUDA context");
     double *partials = nullptr;
     {
-        // One-time set-up per device, with that device current: the device
-        // address of the scratch array.
+        // One-time set-up per device context, with that context current: the
+        // device address of the scratch array.
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_partials_addr[dev]) {
+        for (int i = 0; i < g_naddr; ++i)
+            if (g_addr[i].ctx_id == ctx_id)
+                partials = g_addr[i].addr;
+        if (!partials) {
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
-            if (e != cudaSuccess || !p)
-                return record_error(GBST_ECUDA, "gbst_reduce_dense_f64_noalloc: cudaGetSymbolAddress failed");
-            g_partials_addr[dev] = static_cast<double *>(p);
+            if (e != cudaSuccess || !p) {
+                snprintf(msg, sizeof msg, "%s: cudaGetSymbolAddress failed (%s)", kName, cudaGetErrorString(e));
+                return record_error(GBST_ECUDA, msg);
+            }
+            partials = static_cast<double *>(p);
+            ScratchAddr &slot = g_addr[g_naddr < kMaxContexts ? g_naddr++ : kMaxContexts - 1];
+            slot.ctx_id = ctx_id;
+            slot.addr = partials;
         }
-        partials = g_partials_addr[dev];
     }
+    // An error left pending by an earlier, unrelated launch would otherwise be
+    // reported as this call's failure.
+    cudaGetLastError();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nparts = static_cast<int>((n + kChunk - 1) / kChunk);
     if (nparts > 0)
         k_partials<<<nparts, kThreads, 0, s>>>(x, dtype, n, kind, partials);
     k_final<<<1, kThreads, 0, s>>>(partials, nparts, kind, out);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return record_error(GBST_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof msg, "%s: kernel launch failed (%s)", kName, cudaGetErrorString(e));
+        return record_error(GBST_ECUDA, msg);
+    }
     return GBST_OK;
 }
