@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=8)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-accuracy", action="store_true",
+                   help="skip the comparison of the configured runs with the FP64 oracle")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the secondary measurements (decomposition, wave FP32/BF16, batch, closure)")
     p.add_argument("--n", type=int, default=1024, help="grid edge (profiling runs use a smaller cube)")
@@ -172,6 +174,105 @@ def oracle_sample(nz_sample: int = 128, steps: int = 3):
     return pts / dt / 1e9, f"heat3d slab {N}x{N}x{nz_sample}, {steps} steps per space order 2/4/8, FP64 oracle", dt
 
 
+# Accuracy at the configured run lengths.  The GPU results are captured off the
+# timed region; the oracle side runs in the cpu_baseline leg below (rank 0, N = 1).
+WAVE_BOX_RADIUS = 96  # cells around the 768^3 wave's source that the oracle advances
+
+
+def heat_boxes(n: int, edge: int = 16):
+    """Output boxes (slow axis first) compared after the full 50-step heat runs: the centre, a
+    corner and a far face across a 128-wide tile seam."""
+    m = n // 2 - edge // 2
+    return [((m, m, m), (m + edge, m + edge, m + edge)),
+            ((0, 0, 0), (edge // 2, edge // 2, edge)),
+            ((n - 4, m, min(120, n - 16)), (n, m + 8, min(136, n)))]
+
+
+def heat_accuracy_gpu(torch, grids, u0):
+    """Each order's grid advanced STEPS_PER_RUN steps from u0; the output boxes, on the host."""
+    out = {}
+    buf = torch.empty_like(u0)
+    for so, g in grids.items():
+        g.set_field("u", u0)
+        g.run(STEPS_PER_RUN)
+        g.get_field("u", out=buf)
+        out[so] = [(lo, hi, buf[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]].cpu().numpy()) for lo, hi in heat_boxes(N)]
+    del buf
+    return out
+
+
+def wave_box(src_xyz, shape_zyx, radius):
+    lo = [max(0, src_xyz[2 - a] - radius) for a in range(3)]
+    hi = [min(shape_zyx[a], src_xyz[2 - a] + radius + 1) for a in range(3)]
+    return lo, hi
+
+
+def wave_accuracy_gpu(torch, g, wc, radius):
+    """A fresh source-driven run of wc.nsteps steps on grid g (fields zero, step 0): the box of
+    the given radius around the source on the host, and the largest |u| outside it."""
+    shape = tuple(reversed(wc.dims))
+    zero = torch.zeros(shape, dtype=torch.float32, device="cuda")
+    g.set_field("u", zero)
+    g.set_field("u_prev", zero)
+    g.step = 0
+    g.run(wc.nsteps)
+    u = torch.empty_like(zero)
+    g.get_field("u", out=u)
+    lo, hi = wave_box(wc.src, shape, radius)
+    box = u[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]].cpu().numpy()
+    u[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] = 0
+    out_max = float(u.abs().max())
+    out_l2sq = float((u.double() ** 2).sum())
+    del u, zero
+    return {"lo": lo, "hi": hi, "box": box, "outside_maxabs": out_max, "outside_l2sq": out_l2sq}
+
+
+def accuracy_vs_oracle(heat_gpu, wave_gpu, wc):
+    """The FP64 oracle on the captured samples: heat boxes from their dependency cones, the wave
+    box whole.  Returns the errors and the oracle's point-updates and seconds."""
+    import oracle
+    import synthetic
+    from oracle.cones import heat_on_box
+    res, pts, secs = {}, 0, 0.0
+    shape = (N, N, N)
+    for so, boxes in (heat_gpu or {}).items():
+        case = synthetic.heat3d(N, so)
+        num = den = 0.0
+        for lo, hi, got in boxes:
+            t0 = time.perf_counter()
+            ref = heat_on_box(lambda l, h: synthetic.uniform_box(case.seed, shape, l, h), shape, lo, hi, so,
+                              case.a, STEPS_PER_RUN)
+            secs += time.perf_counter() - t0
+            num = max(num, float(np.max(np.abs(got.astype(np.float64) - ref))))
+            den = max(den, float(np.max(np.abs(ref))))
+        res[f"heat3d_{N}_so{so}_{STEPS_PER_RUN}steps"] = {
+            "max_rel": num / den, "sample": f"{len(boxes)} output boxes (centre, corner, face), exact by "
+                                            "dependency cone"}
+    if wave_gpu:
+        lo, hi = wave_gpu["f32"]["lo"], wave_gpu["f32"]["hi"]
+        c = synthetic.layered_velocity((wc.dims[2], 1, 1), wc.speeds)[lo[0]:hi[0]]
+        c = np.ascontiguousarray(np.broadcast_to(c, tuple(h - l for l, h in zip(lo, hi))))
+        kap = oracle.kappa_from_velocity(c, wc.dt, wc.h)
+        z = np.zeros(c.shape)
+        src = tuple(wc.src[a] - lo[2 - a] for a in range(3))
+        t0 = time.perf_counter()
+        _, ref = oracle.wave_run(z, z, kap, wc.so, wc.nsteps, src=src, f0=wc.f0, t0=wc.t0, amp=wc.amp, dt=wc.dt,
+                                 h=wc.h)
+        secs += time.perf_counter() - t0
+        pts += c.size * wc.nsteps
+        den = float(np.max(np.abs(ref)))
+        for st, w in wave_gpu.items():
+            d = w["box"].astype(np.float64) - ref
+            res[f"wave3d_{wc.dims[0]}_so{wc.so}_{wc.nsteps}steps_{st}"] = {
+                "max_rel": max(float(np.max(np.abs(d))), w["outside_maxabs"]) / den,
+                "rel_l2": float(np.sqrt((np.sum(d * d) + w["outside_l2sq"]) / np.sum(ref * ref))),
+                "outside_box_maxabs_rel": w["outside_maxabs"] / den,
+                "sample": f"oracle on the {'x'.join(str(h - l) for l, h in zip(lo, hi))} box around the source "
+                          f"(all {wc.nsteps} steps); outside it the GPU field is compared with 0",
+                "energy_drift_source_free": w.get("energy_drift")}
+    return res, secs
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -213,9 +314,10 @@ def timed_runs(torch, stream, fn, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
-def extras(torch, hbm: float, tune: bool):
+def extras(torch, hbm: float, tune: bool, acc: dict | None = None):
     """Decomposition, 768^3 wave FP32 vs BF16, 2D at 16384^2, the 64-grid batch and the closure
-    (not in the timed region)."""
+    (not in the timed region).  With acc given, the 768^3 wave runs are also captured for the
+    accuracy comparison (acc["wave"]) after their timing."""
     import synthetic
     from paper_2404_02218_gb300.grid import Grid, Batch
     out = {}
@@ -265,6 +367,26 @@ def extras(torch, hbm: float, tune: bool):
         out[f"wave3d_768_so8_{st}"] = {"gpts": pts / ms / 1e6, "gbs": bpp * pts / ms / 1e6,
                                        "frac": bpp * pts / ms / 1e6 / hbm, "bytes_per_pt": bpp,
                                        "steps": nsteps, "plan": json.loads(g.describe())}
+        if acc is not None:
+            # the configured run (500 steps from rest) for the oracle comparison, then a
+            # source-free continuation of 500 steps from its final state: FP64 energy drift
+            w = wave_accuracy_gpu(torch, g, wc, WAVE_BOX_RADIUS)
+            shape = tuple(reversed(wc.dims))
+            un = torch.empty(shape, dtype=torch.float32, device="cuda")
+            up = torch.empty_like(un)
+            g.get_field("u", out=un)
+            g.get_field("u_prev", out=up)
+            g.close()
+            g = Grid(3, wc.dims, 8, "wave", h=wc.h, dt=wc.dt, storage=st, stream=stream)
+            g.set_field("vel", c)
+            g.set_field("u", un)
+            g.set_field("u_prev", up)
+            del un, up
+            e0 = g.reduce("energy")
+            g.run(wc.nsteps)
+            e1 = g.reduce("energy")
+            w["energy_drift"] = {"steps": wc.nsteps, "e0": e0, "e1": e1, "rel": (e1 - e0) / e0}
+            acc.setdefault("wave", {})[st] = w
         g.close()
     del c
 
@@ -601,6 +723,11 @@ def run_ours(args):
                 "kernel_instance": kernel_name(per[dom]["plan"]),
                 "algorithmic_bytes_per_launch": BYTES_PER_PT * N ** 3, "peak_source": peak_kind}
 
+    # accuracy: each order's full 50-step run, output boxes kept for the oracle comparison
+    acc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_accuracy:
+        acc = {"heat": heat_accuracy_gpu(torch, grids, u0)}
+
     # End to end through the C ABI with host buffers: every step copies u in from
     # pinned host memory and the result out, for each order.  The three orders are
     # independent grids, each on its own stream, so one grid's transfers overlap
@@ -678,15 +805,21 @@ def run_ours(args):
             g.close()
         grids = {}
         torch.cuda.empty_cache()
-        extra = extras(torch, hbm, args.tune == "on")
+        extra = extras(torch, hbm, args.tune == "on", acc)
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
         os.environ.setdefault("OMP_NUM_THREADS", str(cores))
         v, desc, _ = oracle_sample()
         cpu = {"value": v, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
                "kind": "oracle", "sample": desc}
+        if acc is not None:
+            import synthetic
+            accuracy, acc_secs = accuracy_vs_oracle(acc.get("heat"), acc.get("wave"), synthetic.wave3d())
+            accuracy["oracle_seconds"] = acc_secs
+            accuracy["tolerance"] = {"f32": 1e-5, "bf16": 2e-2, "measure": "max |gpu - oracle| / max |oracle|"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -697,7 +830,8 @@ def run_ours(args):
                            "l2": f"inputs larger than L2 ({4 * N ** 3 / 1e9:.2f} GB per field), no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * launches_per_step, "clocks": clocks,
-                "per_stencil": per, "autotune": tuning or args.tune, "secondary": extra}
+                "per_stencil": per, "autotune": tuning or args.tune, "accuracy": accuracy,
+                "secondary": extra}
         print(json.dumps(line), flush=True)
     for g in grids.values():
         g.close()

@@ -64,6 +64,8 @@ def lib():
             L.orc_wave_run.restype = c_int
             L.orc_energy.argtypes = [c_int, i64p, c_int, dp, c_int, dp, dp, dp, dp]
             L.orc_energy.restype = c_int
+            L.orc_wave_adjoint.argtypes = [c_int, i64p, c_int, dp, dp, dp, dp, dp]
+            L.orc_wave_adjoint.restype = c_int
             L.orc_conv3d_fwd.argtypes = [c_int, c_int, i64p, dp, dp, dp, dp]
             L.orc_conv3d_bwd_data.argtypes = [c_int, c_int, i64p, dp, dp, dp]
             L.orc_conv3d_bwd_weight.argtypes = [c_int, c_int, i64p, dp, dp, dp, dp]
@@ -168,6 +170,27 @@ def sweep_heat_padded(u_pad: np.ndarray, ndim: int, dims, so: int, a: float, coe
     out = np.zeros_like(u_pad)
     lib().orc_sweep_heat(ndim, _dims(dims), so // 2, _dp(w), float(a), _dp(u_pad), _dp(out))
     return out
+
+
+def wave_step(u: np.ndarray, uprev: np.ndarray, kappa: np.ndarray, so: int, coeffs=None):
+    """One source-free leapfrog step (zero ghosts): returns (u^{n+1}, u^n)."""
+    P, C = wave_run(uprev, u, kappa, so, 1, coeffs=coeffs)
+    return C, P
+
+
+def wave_step_adjoint(lam_next: np.ndarray, lam_cur: np.ndarray, kappa: np.ndarray, so: int, coeffs=None):
+    """Transpose of :func:`wave_step`: cotangents (lam^{n+1}, lam^n) of (u^{n+1}, u^n) to those of
+    (u^n, u^{n-1}): (lam^n + 2 lam^{n+1} + L(kappa lam^{n+1}), -lam^{n+1})."""
+    A = _f64(lam_next)
+    cur = _f64(lam_cur).copy()
+    prev = np.empty_like(cur)
+    K = _f64(kappa)
+    w = weights_array(so, coeffs)
+    rc = lib().orc_wave_adjoint(A.ndim, _dims(tuple(reversed(A.shape))), so // 2, _dp(w), _dp(K), _dp(A),
+                                _dp(cur), _dp(prev))
+    if rc != 0:
+        raise MemoryError("oracle wave_step_adjoint out of memory")
+    return cur, prev
 
 
 def energy(u: np.ndarray, uprev: np.ndarray, kappa: np.ndarray, so: int, bc: int = BC_ZERO,

@@ -309,6 +309,53 @@ int orc_wave_run(int ndim, const int64_t n[3], int r, const double *w, int bc,
 }
 
 /*
+ * Adjoint (transpose) of one source-free leapfrog step, dense inputs, zero ghosts.
+ * The step maps (u^n, u^{n-1}) to (u^{n+1}, u^n) with
+ *     u^{n+1} = 2 u^n - u^{n-1} + K L u^n,   K = diag(kappa),
+ * a linear map whose transpose takes cotangents (lam^{n+1}, lam^n) to
+ *     lam^n'     = lam^n + 2 lam^{n+1} + L (K lam^{n+1})     (L is symmetric)
+ *     lam^{n-1}' = -lam^{n+1}.
+ * lam_cur holds lam^n on entry and lam^n' on exit; lam_prev receives lam^{n-1}'.
+ * Used to train a closure through whole coarse-grid rollouts (backpropagation
+ * through the time steps of Section 6.1's scheme).
+ */
+int orc_wave_adjoint(int ndim, const int64_t n[3], int r, const double *w, const double *kappa,
+                     const double *lam_next, double *lam_cur, double *lam_prev)
+{
+    lay_t L = mk_layout(ndim, n, r);
+    int64_t sz = L.px * L.py * L.pz, dn = L.nx * L.ny * L.nz, d;
+    double *P = calloc((size_t)sz, sizeof(double));
+    if (!P)
+        return -2;
+    /* K lam^{n+1} on a padded array with zero ghosts */
+    {
+        int64_t i, j, k;
+        for (k = 0; k < L.nz; k++)
+            for (j = 0; j < L.ny; j++)
+                for (i = 0; i < L.nx; i++) {
+                    d = (k * L.ny + j) * L.nx + i;
+                    P[at(&L, i, j, k)] = kappa[d] * lam_next[d];
+                }
+    }
+    {
+        int64_t k;
+#pragma omp parallel for schedule(static)
+        for (k = 0; k < L.nz; k++) {
+            int64_t i, j, dd;
+            for (j = 0; j < L.ny; j++)
+                for (i = 0; i < L.nx; i++) {
+                    dd = (k * L.ny + j) * L.nx + i;
+                    lam_cur[dd] += 2.0 * lam_next[dd] + star(&L, ndim, w, P, i, j, k);
+                }
+        }
+    }
+    for (d = 0; d < dn; d++)
+        lam_prev[d] = -lam_next[d];
+    free(P);
+    return 0;
+}
+
+/*
  * Discrete leapfrog energy between levels u^{n-1} (uprev) and u^n (u), dense inputs:
  *   E = sum_p (u_p - uprev_p)^2 / kappa_p + sum_p u_p (A uprev)_p,   A = -L,
  * with the ghosts of uprev given by bc.  For the source-free scheme this is

@@ -68,6 +68,28 @@ def uniform_field(seed: int, shape: Sequence[int], chunk: int = 1 << 24) -> np.n
     return out.reshape(tuple(shape))
 
 
+def uniform_box(seed: int, shape: Sequence[int], lo: Sequence[int], hi: Sequence[int]) -> np.ndarray:
+    """The sub-box [lo, hi) (per axis, in the order of ``shape``) of ``uniform_field(seed, shape)``,
+    without generating the rest of the field."""
+    shape = tuple(int(v) for v in shape)
+    lo = [int(v) for v in lo]
+    hi = [int(v) for v in hi]
+    strides = [int(np.prod(shape[a + 1:])) for a in range(len(shape))]
+    sub = tuple(h - l for l, h in zip(lo, hi))
+    out = np.empty(sub, dtype=np.float32)
+    # linear indices of one leading-axis slice of the box, then shifted per slice
+    inner = np.zeros((1,), dtype=np.int64)
+    for a in range(1, len(shape)):
+        inner = (inner[:, None] + (np.arange(lo[a], hi[a], dtype=np.int64) * strides[a])[None, :]).reshape(-1)
+    gold, key = GOLDEN, stream_key(seed)
+    for k, i0 in enumerate(range(lo[0], hi[0])):
+        idx = (inner + i0 * strides[0] + 1).astype(np.uint64)
+        with np.errstate(over="ignore"):
+            d = mix64(key + idx * gold)
+        out[k] = ((d >> np.uint64(40)).astype(np.float64) * (1.0 / (1 << 24))).astype(np.float32).reshape(sub[1:])
+    return out
+
+
 def uniform_ints(seed: int, lo: int, hi: int, count: int, start: int = 0) -> np.ndarray:
     """``count`` integers uniform in [lo, hi] (inclusive), by floor of U[0,1)."""
     u = uniform01(seed, count, start).astype(np.float64)

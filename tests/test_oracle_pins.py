@@ -276,3 +276,51 @@ def test_decomposed_wave_equals_global(orc, so):
     gp, gc = orc.decomposed_wave_run(um, u0, kap, so, 5, (2, 2, 2))
     np.testing.assert_array_equal(gc, rc)
     np.testing.assert_array_equal(gp, rp)
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of the leapfrog step (used to train a closure through rollouts) and
+# the dependency-cone sampling of long heat runs
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("so,shape", [(2, (5, 4, 6)), (4, (4, 6, 5)), (8, (3, 9, 7))])
+def test_wave_adjoint_is_the_transpose_of_the_step_matrix(orc, so, shape):
+    """The adjoint equals T^T applied to the cotangents, T the dense block step matrix
+    [[2I + K L, -I], [I, 0]] built independently of the loop code."""
+    from oracle.brute import laplacian_matrix
+    rng = np.random.default_rng(so)
+    kap = rng.uniform(0.01, 0.3, shape)
+    a, b = rng.standard_normal(shape), rng.standard_normal(shape)
+    L = laplacian_matrix(shape, orc.central_weights_f64(so))
+    K = np.diag(kap.reshape(-1))
+    n = L.shape[0]
+    T = np.block([[2.0 * np.eye(n) + K @ L, -np.eye(n)], [np.eye(n), np.zeros((n, n))]])
+    want = T.T @ np.concatenate([a.reshape(-1), b.reshape(-1)])
+    cur, prev = orc.wave_step_adjoint(a, b, kap, so)
+    assert np.allclose(cur.reshape(-1), want[:n], rtol=1e-13, atol=1e-13)
+    assert np.allclose(prev.reshape(-1), want[n:], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("so", [2, 4, 8])
+def test_wave_adjoint_dot_product(orc, so):
+    """<step(x), y> = <x, step^T(y)> on a grid too large for the dense matrix."""
+    rng = np.random.default_rng(10 + so)
+    shape = (13, 17, 19)
+    kap = rng.uniform(0.01, 0.3, shape)
+    u, up, a, b = (rng.standard_normal(shape) for _ in range(4))
+    n1, n0 = orc.wave_step(u, up, kap, so)
+    cur, prev = orc.wave_step_adjoint(a, b, kap, so)
+    lhs = np.sum(n1 * a) + np.sum(n0 * b)
+    rhs = np.sum(u * cur) + np.sum(up * prev)
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.sqrt(np.sum(n1 * n1) * np.sum(a * a)))
+
+
+@pytest.mark.parametrize("so", [2, 4, 8])
+def test_cone_boxes_equal_the_whole_grid_run(orc, so):
+    from oracle.cones import heat_on_box
+    dims = (30, 28, 33)
+    a = 0.8 * synthetic.heat_a_max(3, so)
+    full = orc.heat_run(synthetic.uniform_field(2, dims), so, a, 6)
+    for lo, hi in (((10, 11, 12), (14, 16, 15)), ((0, 0, 0), (4, 5, 6)), ((26, 0, 29), (30, 28, 33))):
+        got = heat_on_box(lambda l, h: synthetic.uniform_box(2, dims, l, h), dims, lo, hi, so, a, 6)
+        assert np.array_equal(got, full[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]])
