@@ -44,6 +44,8 @@ N = 1024
 SOS = (2, 4, 8)
 STEPS_PER_RUN = 50
 BYTES_PER_PT = 8  # FP32 heat: read u, write u+
+# closure training in the secondary lines (rollout windows, epochs, Adam rate, trainable weights)
+CLOSURE_WINDOW, CLOSURE_EPOCHS, CLOSURE_LR, CLOSURE_TRAINABLE = 25, 4, 3e-3, "centre"
 def workload() -> str:
     return f"heat3d {N}^3 FP32, space orders {'/'.join(map(str, SOS))}, 50 steps each, zero Dirichlet halo"
 
@@ -68,6 +70,9 @@ def parse():
                         "the order-8 layered wave at --n^3 in FP32 or BF16 storage, the closure "
                         "network's forward pass at --n^3, or the fused three-field order-4 system at "
                         "--n^3; prints one timing line")
+    p.add_argument("--plan", default=None,
+                   help="variant,txt,zchunks,dyn: fix the plan of every timed grid (profiler captures of a "
+                        "smaller grid with the full-size plan); implies no tuning")
     p.add_argument("--tune", default="on", choices=["on", "cache", "off"],
                    help="on: autotune each kernel before timing; cache: use plans cached in "
                         "GBST_TUNE_CACHE (no tuning launches); off: default plans")
@@ -323,34 +328,50 @@ def extras(torch, hbm: float, tune: bool, acc: dict | None = None):
     out = {}
     stream = torch.cuda.Stream()
 
-    # heat 1024^3 order 4 on a 2x2x2 decomposition (halo exchange overlapped with the
-    # sweep, and not) vs the undecomposed grid
-    case = synthetic.heat3d(1024, 4)
-    u0 = synthetic.uniform_field_torch(case.seed, (1024,) * 3, "cuda")
-    res = {}
-    for name, dec, ov in (("undecomposed", (1, 1, 1), -1), ("decomp_2x2x2", (2, 2, 2), 1),
-                          ("decomp_2x2x2_no_overlap", (2, 2, 2), 0)):
-        g = Grid(3, case.dims, 4, "heat", dt=case.a, decomp=dec, stream=stream)
-        g.set_overlap(ov)
-        g.set_field("u", u0)
-        if tune:
-            g.tune(reps=2)
-        g.set_field("u", u0)
-        ms = timed_runs(torch, stream, lambda: g.run(STEPS_PER_RUN))
-        pts = STEPS_PER_RUN * 1024 ** 3
-        o = torch.empty_like(u0)
-        g.get_field("u", out=o)
-        res[name] = o
-        plan = json.loads(g.describe())
-        out[f"heat3d_so4_{name}"] = {"gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6,
-                                     "frac": 8 * pts / ms / 1e6 / hbm, "steps": STEPS_PER_RUN,
-                                     "overlap": plan["overlap"], "interior_units": plan["interior_units"],
-                                     "units": plan["units"]}
-        g.close()
-    for name in ("decomp_2x2x2", "decomp_2x2x2_no_overlap"):
-        out[f"heat3d_so4_{name}"]["bitwise_equal_to_undecomposed"] = bool(
-            torch.equal(res["undecomposed"], res[name]))
-    del res, u0, o
+    # heat 1024^3, orders 2/4/8, on a 2x2x2 decomposition (single-device dmp.swap mode) vs the
+    # undecomposed grid, bitwise; order 4 also with the exchange overlapped with the sweep.  The
+    # sweep launches are timed by the library's own events, the rest of a step is the face copies.
+    for so in (2, 4, 8):
+        case = synthetic.heat3d(1024, so)
+        u0 = synthetic.uniform_field_torch(case.seed, (1024,) * 3, "cuda")
+        res = {}
+        variants = [("undecomposed", (1, 1, 1), -1), ("decomp_2x2x2", (2, 2, 2), 0)]
+        if so == 4:
+            variants.append(("decomp_2x2x2_overlap", (2, 2, 2), 1))
+        for name, dec, ov in variants:
+            g = Grid(3, case.dims, so, "heat", dt=case.a, decomp=dec, stream=stream)
+            g.set_overlap(ov)
+            g.set_field("u", u0)
+            if tune:
+                g.tune(reps=2)
+            g.set_field("u", u0)
+            ms = timed_runs(torch, stream, lambda: g.run(STEPS_PER_RUN))
+            pts = STEPS_PER_RUN * 1024 ** 3
+            o = torch.empty_like(u0)
+            g.get_field("u", out=o)
+            res[name] = o
+            g.set_profile(True)
+            g.run(STEPS_PER_RUN)
+            g.run(STEPS_PER_RUN)
+            sweep_ms, nl = g.last_kernel_time()
+            g.set_profile(False)
+            plan = json.loads(g.describe())
+            tb = int(plan.get("tb", 1))
+            steps_timed = STEPS_PER_RUN  # the events of the last run cover all its sweep launches
+            out[f"heat3d_so{so}_{name}"] = {
+                "gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6, "frac": 8 * pts / ms / 1e6 / hbm,
+                "steps": STEPS_PER_RUN, "ms_per_step": ms / STEPS_PER_RUN,
+                "sweep_ms_per_step": sweep_ms / max(1, steps_timed),
+                "other_ms_per_step": ms / STEPS_PER_RUN - sweep_ms / max(1, steps_timed),
+                "overlap": plan["overlap"], "interior_units": plan["interior_units"], "units": plan["units"],
+                "halo_boxes": plan["halo_boxes"], "tb": tb}
+            g.close()
+        for name in res:
+            if name != "undecomposed":
+                r = out[f"heat3d_so{so}_{name}"]
+                r["bitwise_equal_to_undecomposed"] = bool(torch.equal(res["undecomposed"], res[name]))
+                r["of_undecomposed"] = r["gpts"] / out[f"heat3d_so{so}_undecomposed"]["gpts"]
+        del res, u0, o
 
     # acoustic wave 768^3, order 8, five layers, Ricker 10 Hz: FP32 vs BF16 storage
     wc = synthetic.wave3d()
@@ -503,42 +524,38 @@ def extras(torch, hbm: float, tune: bool, acc: dict | None = None):
         g.close()
     del singles
 
-    # learned closure: 256^3 coarse / 512^3 fine, order 4, trained on four seeded models,
-    # evaluated on a fifth against the restricted fine solution up to step 400
-    from paper_2404_02218_gb300.closure import PairConfig, evaluate, new_closure, train
+    # learned closure: 256^3 coarse / 512^3 fine, order 4.  The network takes FP32 stencil
+    # features, starts as the modified-equation correction, and is trained on coarse-grid
+    # rollouts of four seeded models (backpropagation through the steps); it is evaluated on a
+    # fifth against the restricted fine solution up to step 400.
+    from paper_2404_02218_gb300.closure import (PairConfig, evaluate, new_feature_closure,
+                                                train_rollout)
     cfg = PairConfig(nc=256, steps=400)
     t0 = time.time()
-    cl = new_closure(cfg, cfg.nc ** 3)
-    losses = train(cl, (10, 11, 12, 13), cfg, lr=2e-3, epochs=1)
+    cl = new_feature_closure(cfg, cfg.nc ** 3)
+    init = evaluate(cl, 99, cfg, checkpoints=(200,))
+    losses = train_rollout(cl, (10, 11, 12, 13), cfg, window=CLOSURE_WINDOW, n_from=200, epochs=CLOSURE_EPOCHS,
+                           lr=CLOSURE_LR, trainable=CLOSURE_TRAINABLE)
     t_train = time.time() - t0
     res = evaluate(cl, 99, cfg, checkpoints=(50, 100, 150, 200, 300))
-    # forward throughput of the three convolutions at 256^3 (padded and useful FLOPs)
+    # forward throughput of the network (features + three convolutions) at 256^3
     n3 = cfg.nc ** 3
     up = torch.randn((cfg.nc,) * 3, device="cuda") * 0.1
     cn = torch.full((cfg.nc,) * 3, 0.6, device="cuda")
     torch.cuda.synchronize()
     ms = timed_runs(torch, cl.stream, lambda: cl.forward(up, up, cn), reps=10)
-    cl.set_conv_impl(1)
-    ms_legacy = timed_runs(torch, cl.stream, lambda: cl.forward(up, up, cn), reps=10)
-    cl.set_conv_impl(0)
-    padded = 27 * 2 * (16 * 16 + 16 * 16 + 16 * 16)  # every layer runs N = 16 output channels
-    useful = 27 * 2 * (4 * 16 + 16 * 16 + 16 * 1)
+    padded = 27 * 2 * (16 * 16 + 16 * 16 + 16 * 16)  # every layer runs K = 16 and N = 16
+    useful = 27 * 2 * (8 * 16 + 16 * 16 + 16 * 1)
     bf16 = measured_peaks()[0].get("bf16_tflops", 1900.0)
-    res.update({"train_seconds": t_train, "updates": len(losses), "forward_ms_256": ms,
-                "forward_tflops_padded": padded * n3 / ms / 1e9, "forward_tflops_useful": useful * n3 / ms / 1e9,
-                "forward_frac_of_bf16_peak": padded * n3 / ms / 1e9 / bf16,
-                "kernel": "tcgen05.mma kind::f16 M128 N16 K16, BF16 in, FP32 accumulators in tensor memory",
-                "forward_ms_256_mma_sync": ms_legacy})
+    res.update({"gain_at_initialisation": init["gain"], "rel_l2_at_initialisation": init["rel_l2_closure"],
+                "train_seconds": t_train, "updates": len(losses), "loss_first": losses[0], "loss_last": losses[-1],
+                "training": f"rollouts of {CLOSURE_WINDOW} steps from step 200, {CLOSURE_EPOCHS} epochs over "
+                            f"seeds 10-13, trainable: {CLOSURE_TRAINABLE}",
+                "forward_ms_256": ms, "forward_tflops_padded": padded * n3 / ms / 1e9,
+                "forward_tflops_useful": useful * n3 / ms / 1e9, "forward_frac_of_bf16_peak": padded * n3 / ms / 1e9 / bf16,
+                "kernel": "features: FP32 dense stencils; convolutions: tcgen05.mma kind::f16 M128 N16 K16, BF16 in, "
+                          "FP32 accumulators in tensor memory"})
     out["closure_256_so4"] = res
-    cl.close()
-    # the same network on the small pair the tests train (96^3 coarse, 100 steps, 20 epochs)
-    cfg96 = PairConfig(nc=96, steps=100)
-    t0 = time.time()
-    cl = new_closure(cfg96, cfg96.nc ** 3)
-    losses = train(cl, (10, 11, 12, 13), cfg96, lr=2e-3, epochs=20)
-    res96 = evaluate(cl, 99, cfg96, checkpoints=(25, 50, 75))
-    res96.update({"train_seconds": time.time() - t0, "updates": len(losses)})
-    out["closure_96_so4_100steps"] = res96
     cl.close()
     return out
 
@@ -570,9 +587,12 @@ def run_case(args):
             g.tune(reps=2)
         fn, pts = (lambda: g.run(10)), 3 * 10 * n ** 3
     else:
-        from paper_2404_02218_gb300.closure import Closure, init_params
-        cl = Closure(n ** 3, 1.0)
-        cl.set_params(init_params(seed=5))
+        from paper_2404_02218_gb300.closure import Closure, modified_equation_params
+        # the feature-input network (cin 8) as the benchmark runs it, with seeded weights
+        cl = Closure(n ** 3, 1.0, cin=8)
+        sc = [1.0, 1.0, 1.0, 1.0, 0.002, 0.002, 8.0, 15.0]
+        cl.set_features(4, sc)
+        cl.set_params(modified_equation_params(sc, 2.3, 0.0625))
         up = synthetic.uniform_field_torch(5, (n, n, n), "cuda") - 0.5
         cn = torch.full((n, n, n), 0.6, device="cuda")
         fn, pts = (lambda: cl.forward(up, up, cn)), n ** 3
@@ -613,26 +633,25 @@ def kernel_name(plan: dict) -> str:
 
 
 def ncu_traffic(plan: dict):
-    """DRAM bytes per launch from the committed ncu traffic summary, if it was taken on the
-    current kernel code with the same kernel instance, z-chunking and work assignment.
-
-    The summary's table rows read
-    ``| kernel instance | source sha | dram bytes per launch | zchunks | dyn |``."""
-    path = os.path.join(ROOT, "profiles", "sweep_heat3d_so8_1024_dram_traffic.md")
+    """DRAM bytes per launch of the dominant kernel at the bench's size, from the committed ncu
+    capture rows in profiles/dram_traffic.json, used only when a row was taken on the current
+    kernel code with the same kernel instance, z-chunk length and work assignment.  Rows captured
+    on a smaller cube are scaled to N^3 by the points processed (dram bytes grow with them)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
-        lines = open(path).read().splitlines()
-    except OSError:
+        rows = json.load(open(path))["rows"]
+    except (OSError, ValueError, KeyError):
         return None
     want = kernel_name(plan)
     sha = kernel_source_sha(want.split("<")[0])
-    for ln in lines:
-        cells = [c.strip().strip("`") for c in ln.strip().strip("|").split("|")]
-        if len(cells) >= 5 and cells[0] == want and cells[1] == sha:
-            try:
-                if int(cells[3]) == plan.get("zchunks") and int(cells[4]) == plan.get("dyn", 0):
-                    return float(cells[2])
-            except ValueError:
-                continue
+    zlen = N / max(1, plan.get("zchunks", 1))
+    for r in rows:
+        if r.get("kernel_instance") != want or r.get("source_sha") != sha or r.get("dyn") != plan.get("dyn", 0):
+            continue
+        n = int(r["n"])
+        if abs(n / max(1, int(r["zchunks"])) - zlen) > 0.25 * zlen:
+            continue
+        return float(r["dram_bytes_per_launch"]) * (N / n) ** 3
     return None
 
 
@@ -663,7 +682,11 @@ def run_ours(args):
         case = synthetic.heat3d(N, so)
         g = Grid(3, case.dims, so, "heat", h=1.0, dt=case.a, alpha=1.0, stream=stream)
         g.set_field("u", u0)
-        if args.tune == "on":
+        if args.plan:
+            v, txt, zc, dyn = (int(x) for x in args.plan.split(","))
+            g.set_plan(v, txt, zc)
+            g.set_schedule(dyn)
+        elif args.tune == "on":
             rep = g.tune(reps=3)
             tuning[f"heat3d_so{so}"] = {"candidates": len(rep["candidates"]), "best": rep["best"]}
         grids[so] = g

@@ -249,8 +249,8 @@ gbst_status stencil_debug_barrier_extra(gbst_handle h, unsigned int extra);
  *   x = s (u+, u^n, c_n^2 u+, c_n^2 u^n),  o = net(x),  u+ <- u+ + o / t
  * (s = in_scale; t = the output scale, closure_set_out_scale, default s).
  * BF16 weights and activations, FP32 accumulation on the tensor cores, FP32
- * master weights and Adam (beta 0.9/0.999, eps 1e-8).  cin must be 4 and
- * hidden 16.  Parameters are a flat
+ * master weights and Adam (beta 0.9/0.999, eps 1e-8).  cin is 4 (the inputs
+ * above) or 8 (FP32 stencil features, closure_set_features); hidden is 16.  Parameters are a flat
  * FP32 vector in the order w1[16][cin][3][3][3], b1[16], w2[16][16][3][3][3],
  * b2[16], w3[1][16][3][3][3], b3[1] (zero after creation).  Device arrays are
  * dense FP32, x fastest, nx*ny*nz <= max_points.  All calls are ordered on
@@ -289,10 +289,72 @@ gbst_status closure_freeze_biases(gbst_closure c, int freeze);
  * closure_loss_grad / closure_get_params / closure_get_grads. */
 gbst_status closure_set_conv_impl(gbst_closure c, int impl);
 
+/* Per-parameter mask of closure_adam_step (host array of n = parameter count
+ * bytes, non-zero = the parameter trains; NULL: every parameter trains, the
+ * default).  Combines with closure_freeze_biases.  Synchronises the stream. */
+gbst_status closure_set_trainable(gbst_closure c, const unsigned char *mask, int64_t n);
+/* Feature inputs (closures created with cin = 8; none of this is in the paper).
+ * The network's 8 input channels are x_k = scales[k] f_k with, for u+ the plain
+ * coarse step, u^n the current level and cn2 = c_n^2,
+ *   f0 = u+, f1 = u^n, f2 = cn2 u+, f3 = cn2 u^n,
+ *   f4 = cn2 sum_a delta_a^6 u^n          (delta^6 = (1, -6, 15, -20, 15, -6, 1) per axis),
+ *   f5 = cn2 L(cn2 L u^n),  f6 = sum_a D_a(cn2) D_a(u^n),  f7 = (sum_a |D_a cn2|) L u^n,
+ * L the central star of space_order (2, 4 or 8, default 4), D_a the central
+ * difference, zero outside the grid; computed in FP32, then rounded to BF16.
+ * f4 and f5 are, up to the constants kappa_ref / 90 and kappa_ref^2 / 12, the
+ * leading one-step defects of the order-4 leapfrog scheme (its spatial
+ * truncation and its dt^4 u_tttt / 12 term); f6, f7 couple the field to velocity
+ * jumps.  Every channel vanishes with the field.  n must be 8. */
+gbst_status closure_set_features(gbst_closure c, int space_order, const double *scales, int n);
+/* The unscaled FP32 features f0..f7 of (u_plus, u_n, c_norm) into out, channel-major
+ * (out + k * nx*ny*nz); device arrays; asynchronous on the closure's stream. */
+gbst_status closure_feature_values(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,
+                                   int64_t nx, int64_t ny, int64_t nz, float *out);
+/* Backward pass of one corrected step (closures with cin = 8), for training
+ * through rollouts.  The corrected step is u^{n+1} = u+ + correction(u+, u^n).
+ * Given grad_out = dLoss/du^{n+1} (dense device FP32), adds dLoss/d(parameters)
+ * into the closure's gradient (zeroed first unless accumulate) and writes the
+ * cotangents of the step's inputs: grad_up = dLoss/du+ (grad_out plus the path
+ * through the network and its features) and grad_un = dLoss/du^n.  grad_up must
+ * not alias grad_out.  Asynchronous on the closure's stream (a bounded wait that
+ * expires is reported by the next closure_loss_grad / closure_get_params /
+ * closure_get_grads). */
+gbst_status closure_backward(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,
+                             int64_t nx, int64_t ny, int64_t nz, const float *grad_out, float *grad_up,
+                             float *grad_un, int accumulate);
+/* Transpose of one source-free leapfrog step (Section 6.1's scheme) on dense
+ * FP32 device arrays [nz][ny][nx] (x fastest) with zero ghosts, used to train a
+ * closure through whole coarse-grid rollouts.  The step maps (u^n, u^{n-1}) to
+ * (u^{n+1}, u^n) with u^{n+1} = 2 u^n - u^{n-1} + kappa L u^n (L the central
+ * star of space_order 2, 4 or 8, unit spacing; kappa per point).  Given the
+ * cotangents lam_next of u^{n+1} and lam_cur of u^n it writes
+ *     lam_cur  <- lam_cur + 2 lam_next + L(kappa lam_next)    (L is symmetric)
+ *     lam_prev <- -lam_next                                    (if lam_prev != NULL)
+ * FP32 arithmetic.  Asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ * default); the caller owns every array; lam_cur must not alias lam_next. */
+gbst_status stencil_wave_adjoint_dense(int space_order, int64_t nx, int64_t ny, int64_t nz, const float *kappa,
+                                       const float *lam_next, float *lam_cur, float *lam_prev, void *stream);
+
 /* Attach a closure to a single (undecomposed) 3D wave grid: from then on every
  * step of stencil_run is the plain sweep followed by u^{n+1} += closure
  * correction (c_ref normalises the velocity, c_norm = c / c_ref).  NULL detaches. */
 gbst_status stencil_attach_closure(gbst_handle h, gbst_closure c, double c_ref);
+
+/* Gradient of a rollout loss of the closure attached to h (which must have
+ * feature inputs, cin = 8), by backpropagation through the coarse time steps.
+ * From the levels u^{n0} = u_cur and u^{n0-1} = u_prev (dense device FP32, the
+ * grid's interior) at step index n0 = step0, the grid takes nsteps corrected
+ * steps (sweep with its source, then u^{n+1} = u+ + correction) and
+ *     loss = (1 / nsteps) sum_j |u^{n0+j+1} - refs[j]|^2 / |refs[j]|^2
+ * (refs: a host array of nsteps dense device fields).  The parameters' gradient
+ * of this loss replaces the closure's gradient (closure_get_grads, then
+ * closure_adam_step); the backward pass uses closure_backward and the transpose
+ * of the leapfrog step (stencil_wave_adjoint_dense).  The grid is left at step
+ * n0 + nsteps.  Synchronises the grid's stream; *loss receives the loss.
+ * Work buffers of 3 nsteps + 6 dense fields are allocated on the first call
+ * (through the grid's allocator) and kept. */
+gbst_status stencil_closure_rollout_grad(gbst_handle h, const float *u_cur, const float *u_prev, int64_t step0,
+                                         const float *const *refs, int nsteps, double *loss);
 
 /* Every stride-th interior point (0, stride, 2 stride, .. along each axis) of a
  * field into a dense FP32 device array of ceil(dims/stride) points (injection

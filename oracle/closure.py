@@ -138,3 +138,140 @@ def adam_step(p: dict, g: dict, state: dict, lr: float, t: int, beta1: float = 0
         mh = m / (1.0 - beta1 ** t)
         vh = v / (1.0 - beta2 ** t)
         p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
+
+
+# ---------------------------------------------------------------------------
+# Input features of the closure, computed from the fields in FP64 (the library
+# computes them in FP32 before rounding to the network's BF16 inputs).  The
+# paper has no learned part; these follow the modified-equation view of the
+# leapfrog scheme: for u_tt = c^2 Lap(u) the scheme's one-step defect is, to
+# leading order, kappa/90 sum_a d^6u/dx_a^6 (the order-4 star's truncation) plus
+# kappa L(kappa L u)/12 (the leapfrog's dt^4 u_tttt / 12 term); where the
+# velocity jumps, grad(kappa).grad(u) and |grad kappa| L u carry the local
+# coupling.  All vanish with the field.  cn2 = (c / c_ref)^2 stands in for kappa
+# (kappa = kappa_ref cn2; the constant goes into the channel scale).
+# ---------------------------------------------------------------------------
+
+SIXTH_DIFFERENCE = (-20.0, 15.0, -6.0, 1.0)  # per-axis weights of delta^6, w_0 .. w_3
+
+
+def shifted(u: np.ndarray, ax: int, m: int) -> np.ndarray:
+    """v[p] = u[p + m e_ax], zero outside the array (the zero halo)."""
+    u = _c(u)
+    out = np.zeros_like(u)
+    n = u.shape[ax]
+    if abs(m) >= n:
+        return out
+    src = [slice(None)] * u.ndim
+    dst = [slice(None)] * u.ndim
+    if m >= 0:
+        src[ax], dst[ax] = slice(m, n), slice(0, n - m)
+    else:
+        src[ax], dst[ax] = slice(0, n + m), slice(-m, n)
+    out[tuple(dst)] = u[tuple(src)]
+    return out
+
+
+def star(u: np.ndarray, w) -> np.ndarray:
+    """sum over axes, sum over m = -r..r of w_|m| u[p + m e_axis]  (w = w_0 .. w_r)."""
+    u = _c(u)
+    out = u.ndim * w[0] * u
+    for ax in range(u.ndim):
+        for m in range(1, len(w)):
+            out = out + w[m] * (shifted(u, ax, m) + shifted(u, ax, -m))
+    return out
+
+
+def central_difference(u: np.ndarray, ax: int) -> np.ndarray:
+    """(u[p + e_ax] - u[p - e_ax]) / 2."""
+    return 0.5 * (shifted(u, ax, 1) - shifted(u, ax, -1))
+
+
+def feature_channels(up: np.ndarray, un: np.ndarray, cn2: np.ndarray, weights, scales) -> np.ndarray:
+    """The 8 input channels x[k] = scales[k] f_k of the closure:
+    f0 = u+, f1 = u^n, f2 = cn2 u+, f3 = cn2 u^n, f4 = cn2 sum_a delta_a^6 u^n,
+    f5 = cn2 L(cn2 L u^n), f6 = sum_a D_a(cn2) D_a(u^n), f7 = (sum_a |D_a cn2|) L u^n
+    (L the grid's star with the given weights, D_a the central difference)."""
+    up, un, cn2 = _c(up), _c(un), _c(cn2)
+    Lu = star(un, weights)
+    grads = [central_difference(cn2, a) for a in range(un.ndim)]
+    f = [up, un, cn2 * up, cn2 * un, cn2 * star(un, SIXTH_DIFFERENCE), cn2 * star(cn2 * Lu, weights),
+         sum(g * central_difference(un, a) for a, g in enumerate(grads)), sum(np.abs(g) for g in grads) * Lu]
+    return np.stack([s * v for s, v in zip(scales, f)])
+
+
+def feature_channels_adjoint(dx: np.ndarray, cn2: np.ndarray, weights, scales):
+    """Transpose of feature_channels: the cotangents dx[k] of x[k] to those of (u+, u^n).
+    Uses that star() is symmetric and D_a antisymmetric under the zero halo."""
+    dx, cn2 = _c(dx), _c(cn2)
+    grads = [central_difference(cn2, a) for a in range(cn2.ndim)]
+    gabs = sum(np.abs(g) for g in grads)
+    d = [scales[k] * dx[k] for k in range(8)]
+    g_up = d[0] + cn2 * d[2]
+    g_un = d[1] + cn2 * d[3] + star(cn2 * d[4], SIXTH_DIFFERENCE)
+    g_un = g_un + star(cn2 * star(cn2 * d[5], weights), weights)
+    g_un = g_un - sum(central_difference(g * d[6], a) for a, g in enumerate(grads))
+    g_un = g_un + star(gabs * d[7], weights)
+    return g_up, g_un
+
+
+def backward_with_input(cache: dict, dout: np.ndarray, p: dict):
+    """backward() plus the cotangent of the network input x."""
+    g = {}
+    g["w3"], g["b3"] = conv3d_bwd_weight(cache["y2"], dout)
+    dy2 = conv3d_bwd_data(dout, p["w3"])
+    dz2 = dy2 * gelu_grad(cache["z2"])
+    g["w2"], g["b2"] = conv3d_bwd_weight(cache["y1"], dz2)
+    dy1 = conv3d_bwd_data(dz2, p["w2"])
+    dz1 = dy1 * gelu_grad(cache["z1"])
+    g["w1"], g["b1"] = conv3d_bwd_weight(cache["x"], dz1)
+    return g, conv3d_bwd_data(dz1, p["w1"])
+
+
+def corrected_step(u: np.ndarray, uprev: np.ndarray, kappa: np.ndarray, cn2: np.ndarray, p: dict, weights,
+                   scales, out_scale: float):
+    """One source-free coarse step with the closure: u+ = 2u - uprev + kappa L u (Section 6.1's
+    scheme), u^{n+1} = u+ + net(x(u+, u)) / out_scale.  Returns (u^{n+1}, u+, cache)."""
+    up = 2.0 * _c(u) - _c(uprev) + _c(kappa) * star(u, weights)
+    x = feature_channels(up, u, cn2, weights, scales)
+    out, cache = forward(x, p)
+    return up + out[0] / out_scale, up, cache
+
+
+def rollout_loss_and_grads(p: dict, u_cur, u_prev, kappa, cn2, refs, weights, scales, out_scale: float):
+    """FP64 reference of the rollout training gradient: len(refs) corrected steps from
+    (u^{n0}, u^{n0-1}) = (u_cur, u_prev), loss = mean_j |u^{n0+j+1} - refs[j]|^2 / |refs[j]|^2,
+    gradient w.r.t. every parameter by backpropagation through the steps (chain rule written
+    out: network backward, feature transpose, leapfrog transpose)."""
+    K = len(refs)
+    us, ups, caches = [_c(u_prev), _c(u_cur)], [], []
+    for j in range(K):
+        un, up, cache = corrected_step(us[-1], us[-2], kappa, cn2, p, weights, scales, out_scale)
+        us.append(un)
+        ups.append(up)
+        caches.append(cache)
+    loss = 0.0
+    glev = []  # dLoss/du^{n0+j+1} from its own loss term
+    for j in range(K):
+        d = us[j + 2] - refs[j]
+        nr = float(np.sum(_c(refs[j]) ** 2))
+        loss += float(np.sum(d * d)) / nr / K
+        glev.append(2.0 * d / nr / K)
+    grads = {k: np.zeros_like(p[k]) for k in PARAM_ORDER}
+    lam = {K + 1: glev[K - 1].copy()}  # cotangent of level index (j + 1) -> us[j + 1]
+    if K >= 2:
+        lam[K] = glev[K - 2].copy()
+    w = list(weights)
+    for j in range(K - 1, -1, -1):
+        a = lam[j + 2]                         # cotangent of u^{n0+j+1} = us[j + 2]
+        g, dx = backward_with_input(caches[j], (a / out_scale)[None], p)
+        for k in PARAM_ORDER:
+            grads[k] += g[k]
+        g_up, g_un = feature_channels_adjoint(dx, cn2, w, scales)
+        A = a + g_up                           # cotangent of u+
+        if j == 0:
+            break
+        # u+ = 2 u^n - u^{n-1} + kappa L u^n
+        lam[j + 1] = lam[j + 1] + 2.0 * A + star(_c(kappa) * A, w) + g_un
+        lam[j] = -A + (glev[j - 2] if j >= 2 else 0.0)
+    return loss, grads

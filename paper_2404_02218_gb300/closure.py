@@ -91,6 +91,20 @@ class Closure:
     def freeze_biases(self, on: bool = True):
         N.closure_freeze_biases(self.h, on)
 
+    def set_features(self, space_order: int, scales):
+        """Feature inputs (closures created with cin = 8): channel scales and the star's order."""
+        N.closure_set_features(self.h, space_order, scales)
+        self.feature_scales = list(scales)
+
+    def feature_values(self, up, un, cn):
+        """The eight unscaled FP32 features, shape (8, nz, ny, nx)."""
+        self._sync_in()
+        out = self._torch.empty((8,) + tuple(up.shape), dtype=self._torch.float32, device=up.device)
+        N.closure_feature_values(self.h, up.data_ptr(), un.data_ptr(), cn.data_ptr(), tuple(reversed(up.shape)),
+                                 out.data_ptr())
+        self._torch.cuda.current_stream().wait_stream(self.stream)
+        return out
+
     def set_conv_impl(self, impl: int):
         """0: tcgen05 convolutions (default); 1: mma.sync convolutions."""
         N.closure_set_conv_impl(self.h, impl)
@@ -397,3 +411,173 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, att
     g.close()
     pair.close()
     return out
+
+
+# ------------------------------------------------- feature inputs, rollouts ---
+#
+# Reading of the learned part (none of it is in the paper): the network's
+# inputs are FP32 stencil features of the coarse field (closure_set_features),
+# among them the two leading one-step defects of the order-4 leapfrog scheme,
+# kappa sum_a delta_a^6 u / 90 (spatial truncation) and kappa L(kappa L u) / 12
+# (the dt^4 u_tttt / 12 term), which BF16 inputs of the raw field cannot resolve
+# (they are ~1e-4 of the field and need sixth differences).  The network starts
+# as exactly that modified-equation correction (GELU(x) - GELU(-x) = x gives
+# linear pass-through channels) and is then trained on coarse-grid rollouts
+# against the restricted fine solution, by backpropagation through the time
+# steps (stencil_closure_rollout_grad), on windows after the source has died
+# out, where the error that remains at the last step is made.
+
+FEATURE_SPACE_ORDER = 4
+TAP_CENTRE = 13  # (dz, dy, dx) = (0, 0, 0) in the [3][3][3] tap order
+
+
+def kappa_ref(pair: "FineCoarsePair") -> float:
+    """kappa = kappa_ref * (c / C_REF)^2 on the coarse grid."""
+    return (C_REF * pair.dtc / (2.0 * pair.cfg.hf)) ** 2
+
+
+def feature_scales(seed: int, cfg: PairConfig, every: int = 8) -> list:
+    """1 / max |f_k| of the eight features along the restricted fine trajectory of one seed
+    (features of consecutive restricted levels; sampled every `every` coarse steps)."""
+    import torch
+    from . import native as NN
+    pair = FineCoarsePair(seed, cfg)
+    nc = pair.nc
+    cl = Closure(nc ** 3, 1.0, cin=8)
+    cl.set_features(FEATURE_SPACE_ORDER, [1.0] * 8)
+    shp = (nc,) * 3
+    r_prev = torch.zeros(shp, dtype=torch.float32, device="cuda")
+    r_cur = torch.zeros_like(r_prev)
+    up = torch.empty_like(r_prev)
+    m = np.zeros(8)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for n in range(cfg.steps):
+        if n % every == 0 and n > 0:
+            coarse_step(pair, r_cur, r_prev, n, up)
+            f = cl.feature_values(up, r_cur, pair.cnorm)
+            torch.cuda.synchronize()
+            for k in range(8):
+                NN.gbst_reduce_dense_f64_noalloc(f[k].data_ptr(), NN.GBST_F32, f[k].numel(), NN.GBST_RED_MAXABS,
+                                                 out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+                torch.cuda.synchronize()
+                m[k] = max(m[k], float(out.item()))
+        pair.fine.run(2)
+        nxt = pair.restrict()
+        r_prev, r_cur = r_cur, nxt
+    cl.close()
+    pair.close()
+    return [1.0 / v if v > 0 else 1.0 for v in m]
+
+
+def modified_equation_params(scales, t: float, kref: float, a: float = 1.0, b: float = 1.0, cin: int = 8,
+                             hidden: int = 16, seed: int = 5, spread: float = 0.05) -> np.ndarray:
+    """Parameters of the network that computes exactly o / t = a kref f4 / 90 + b kref^2 f5 / 12
+    through four linear pass-through channels (hidden 0, 1 = +x4, -x4; 2, 3 = +x5, -x5; layer 2
+    repeats the differences y(+) - y(-), which equal the inputs since GELU(x) - GELU(-x) = x).
+    The other hidden channels start with small seeded weights and no path to the output."""
+    import synthetic
+    w1 = np.zeros((hidden, cin, 27))
+    w2 = np.zeros((hidden, hidden, 27))
+    w3 = np.zeros((1, hidden, 27))
+    c = TAP_CENTRE
+    w1[0, 4, c], w1[1, 4, c], w1[2, 5, c], w1[3, 5, c] = 1.0, -1.0, 1.0, -1.0
+    for k, (p_, m_) in enumerate(((0, 1), (2, 3))):
+        w2[2 * k, p_, c], w2[2 * k, m_, c] = 1.0, -1.0
+        w2[2 * k + 1, p_, c], w2[2 * k + 1, m_, c] = -1.0, 1.0
+    alpha = a * t * kref / (90.0 * scales[4])
+    beta = b * t * kref * kref / (12.0 * scales[5])
+    w3[0, 0, c], w3[0, 1, c], w3[0, 2, c], w3[0, 3, c] = alpha, -alpha, beta, -beta
+    # the free channels 4..15: seeded weights within 1/sqrt(fan_in) * spread, no output path yet
+    u1 = synthetic.uniform01(seed, (hidden - 4) * cin * 27).astype(np.float64).reshape(hidden - 4, cin, 27)
+    w1[4:] = (2 * u1 - 1) * spread / np.sqrt(cin * 27)
+    u2 = synthetic.uniform01(seed, (hidden - 4) * hidden * 27, start=10 ** 6).astype(np.float64)
+    w2[4:] = ((2 * u2 - 1) * spread / np.sqrt(hidden * 27)).reshape(hidden - 4, hidden, 27)
+    p = {"w1": w1.reshape(hidden, cin, 3, 3, 3), "b1": np.zeros(hidden), "w2": w2.reshape(hidden, hidden, 3, 3, 3),
+         "b2": np.zeros(hidden), "w3": w3.reshape(1, hidden, 3, 3, 3), "b3": np.zeros(1)}
+    return flatten_params(p)
+
+
+def output_weight_mask(cin: int = 8, hidden: int = 16, channels=(0, 1, 2, 3), taps: str = "centre") -> np.ndarray:
+    """Trainable-parameter mask (closure_set_trainable) selecting the last layer's weights from the
+    given hidden channels: their centre taps ("centre") or all 27 taps ("all")."""
+    n = hidden * cin * 27 + hidden + hidden * hidden * 27 + hidden + hidden * 27 + 1
+    off = hidden * cin * 27 + hidden + hidden * hidden * 27 + hidden
+    m = np.zeros(n, dtype=np.uint8)
+    for k in channels:
+        if taps == "centre":
+            m[off + k * 27 + TAP_CENTRE] = 1
+        else:
+            m[off + k * 27: off + (k + 1) * 27] = 1
+    return m
+
+
+def new_feature_closure(cfg: PairConfig, max_points: int, scale_seed: int = 10, stream=None) -> Closure:
+    """A feature-input closure that starts as the modified-equation correction (biases zero, frozen)."""
+    scales = feature_scales(scale_seed, cfg)
+    probe = FineCoarsePair(scale_seed, cfg)
+    kref = kappa_ref(probe)
+    probe.close()
+    t = 90.0 * scales[4] / kref  # makes the f4 pass-through weight of layer 3 equal to a
+    cl = Closure(max_points, 1.0, cin=8, stream=stream)
+    cl.set_features(FEATURE_SPACE_ORDER, scales)
+    cl.set_out_scale(t)
+    cl.freeze_biases(True)
+    cl.set_params(modified_equation_params(scales, t, kref))
+    cl.kref = kref
+    return cl
+
+
+def restricted_trajectory(pair: "FineCoarsePair", n_from: int, steps: int) -> dict:
+    """Restricted fine levels n_from - 1 .. steps (dense FP32 CUDA tensors), keyed by coarse step."""
+    out = {}
+    for n in range(steps):
+        pair.fine.run(2)
+        if n + 1 >= n_from - 1:
+            out[n + 1] = pair.restrict()
+    return out
+
+
+def train_rollout(closure: Closure, seeds, cfg: PairConfig, window: int = 25, n_from: int = 200, epochs: int = 2,
+                  lr: float = 3e-3, lr_final: float = None, trainable="centre", log=None):
+    """Train on coarse-grid rollouts: for windows [n0, n0 + window) with n0 >= n_from, start the
+    corrected coarse grid from the restricted fine levels (n0, n0 - 1), take `window` corrected
+    steps, and descend the mean relative squared error against the restricted fine levels
+    (gradient by backpropagation through the steps, in the library).  Returns the losses.
+
+    trainable: "centre" or "all" trains only the last layer's weights from the four
+    modified-equation pass-through channels (their centre taps, or all 27 taps); None trains
+    every weight.  (Training every weight makes Adam move the twelve free hidden channels by
+    about lr per step, corrections far larger than the physical one, and the rollouts
+    diverged; measured.)"""
+    if trainable is None:
+        N.closure_set_trainable(closure.h, None)
+    else:
+        N.closure_set_trainable(closure.h, output_weight_mask(taps=trainable))
+    losses = []
+    t0 = time.time()
+    nwin = len(range(n_from, cfg.steps - window + 1, window))
+    total = max(1, epochs * len(seeds) * nwin)
+    lr_final = lr / 10 if lr_final is None else lr_final
+    trajs = {}
+    for sd in seeds:
+        pair = FineCoarsePair(sd, cfg, stream=closure.stream)
+        trajs[sd] = (restricted_trajectory(pair, n_from, cfg.steps), pair)
+    k = 0
+    for ep in range(epochs):
+        for sd in seeds:
+            ref, pair = trajs[sd]
+            g = pair.coarse
+            N.stencil_attach_closure(g.h, closure.h, C_REF)
+            for n0 in range(n_from, cfg.steps - window + 1, window):
+                refs = [ref[n0 + j + 1].data_ptr() for j in range(window)]
+                L = N.stencil_closure_rollout_grad(g.h, ref[n0].data_ptr(), ref[n0 - 1].data_ptr(), n0, refs)
+                closure.adam_step(lr * (lr_final / lr) ** (k / total))
+                losses.append(L)
+                k += 1
+            N.stencil_attach_closure(g.h, None, C_REF)
+            if log:
+                log(f"epoch {ep} seed {sd}: {len(losses)} updates, last loss {losses[-1]:.3e}, "
+                    f"{time.time() - t0:.1f}s")
+    for sd in seeds:
+        trajs[sd][1].close()
+    return losses

@@ -321,6 +321,12 @@ struct gbst_grid_s {
     // learned closure applied after every sweep (single 3D wave grid)
     gbst_closure closure = nullptr;
     float *cl_up = nullptr, *cl_un = nullptr, *cl_cn = nullptr, *cl_corr = nullptr;
+    // training the attached closure through rollouts (stencil_closure_rollout_grad)
+    std::vector<float *> roll_up, roll_un, roll_u;  // per step: u+, u^n, u^{n+1} (then its loss gradient)
+    float *roll_a[3] = {nullptr, nullptr, nullptr};  // cotangents of three consecutive levels
+    float *roll_A = nullptr, *roll_gun = nullptr, *roll_kap = nullptr;
+    double *roll_sums = nullptr;  // 2 per step
+    int roll_cap = 0;
 };
 
 namespace {
@@ -747,6 +753,9 @@ gbst_status build_copies(gbst_handle h)
     h->max_box_elems = 0;
     for (const CopyBox &b : boxes)
         h->max_box_elems = std::max(h->max_box_elems, b.ex * b.ey * b.ez);
+    if (h->max_box_elems >= (int64_t(1) << 31))
+        return fail(GBST_EINVAL, "a halo face of %lld cells is too large (limit 2^31 - 1)",
+                    static_cast<long long>(h->max_box_elems));
     if (!boxes.empty()) {
         h->dboxes = static_cast<CopyBox *>(dalloc(h, boxes.size() * sizeof(CopyBox)));
         if (!h->dboxes)
@@ -1674,6 +1683,128 @@ gbst_status stencil_attach_closure(gbst_handle h, gbst_closure c, double c_ref)
     h->closure = c;
     GBST_CUDA(cudaStreamSynchronize(h->stream));
     return GBST_OK;
+}
+
+// Gradient of a rollout loss of the attached closure, by backpropagation through the
+// coarse time steps (see gbstencil.h).
+gbst_status stencil_closure_rollout_grad(gbst_handle h, const float *u_cur, const float *u_prev, int64_t step0,
+                                         const float *const *refs, int nsteps, double *loss)
+{
+    gbst_status st = check_handle(h);
+    if (st != GBST_OK)
+        return st;
+    if (!u_cur || !u_prev || !refs || !loss || nsteps < 1 || nsteps > 4096)
+        return fail(GBST_EINVAL, "stencil_closure_rollout_grad: null argument or nsteps not in [1, 4096]");
+    for (int j = 0; j < nsteps; ++j)
+        if (!refs[j])
+            return fail(GBST_EINVAL, "stencil_closure_rollout_grad: refs[%d] is null", j);
+    gbst_closure c = h->closure;
+    if (!c || !closure_has_features(c))
+        return fail(GBST_ENOTSUP, "stencil_closure_rollout_grad: needs an attached closure with feature inputs");
+    const Sub &sb = h->subs[0];
+    const int64_t nx = sb.lu.nx, ny = sb.lu.ny, nz = sb.lu.nz, n = nx * ny * nz;
+    const size_t fb = static_cast<size_t>(n) * sizeof(float);
+    cudaStream_t s = h->stream;
+    // work buffers, kept for later calls
+    if (h->roll_cap < nsteps) {
+        while (static_cast<int>(h->roll_up.size()) < nsteps) {
+            float *a = static_cast<float *>(dalloc(h, fb)), *b = static_cast<float *>(dalloc(h, fb)),
+                  *c2 = static_cast<float *>(dalloc(h, fb));
+            if (!a || !b || !c2)
+                return fail(GBST_ENOMEM, "rollout buffers (%d steps of %lld points)", nsteps,
+                            static_cast<long long>(n));
+            h->roll_up.push_back(a);
+            h->roll_un.push_back(b);
+            h->roll_u.push_back(c2);
+        }
+        if (!h->roll_A) {
+            for (auto &pa : h->roll_a)
+                pa = static_cast<float *>(dalloc(h, fb));
+            h->roll_A = static_cast<float *>(dalloc(h, fb));
+            h->roll_gun = static_cast<float *>(dalloc(h, fb));
+            h->roll_kap = static_cast<float *>(dalloc(h, fb));
+            if (!h->roll_a[0] || !h->roll_a[1] || !h->roll_a[2] || !h->roll_A || !h->roll_gun || !h->roll_kap)
+                return fail(GBST_ENOMEM, "rollout buffers");
+        }
+        h->roll_sums = static_cast<double *>(dalloc(h, 2 * sizeof(double) * static_cast<size_t>(nsteps)));
+        if (!h->roll_sums)
+            return fail(GBST_ENOMEM, "rollout buffers");
+        h->roll_cap = nsteps;
+    }
+    // dense kappa of the grid (the leapfrog step's coefficient)
+    XferArgs xk{};
+    xk.padded = h->hgrids[0].kappa;
+    xk.storage = GBST_F32;
+    xk.pitch = sb.lk.pitch;
+    xk.rows = sb.lk.rows;
+    xk.origin = sb.lk.origin;
+    xk.nx = nx;
+    xk.ny = ny;
+    xk.nz = nz;
+    xk.gnx = nx;
+    xk.gny = ny;
+    xk.dense_dtype = GBST_F32;
+    xk.dense = h->roll_kap;
+    GBST_CUDA(launch_gather(xk, s));
+    // forward: nsteps corrected steps from (u_cur, u_prev), keeping u+, u^n and u^{n+1}
+    if ((st = stencil_set_field(h, GBST_U, u_cur, GBST_F32, 1)) != GBST_OK ||
+        (st = stencil_set_field(h, GBST_U_PREV, u_prev, GBST_F32, 1)) != GBST_OK ||
+        (st = stencil_set_step(h, step0)) != GBST_OK)
+        return st;
+    XferArgs xu = xk;
+    xu.storage = h->d.storage;
+    xu.pitch = sb.lu.pitch;
+    xu.rows = sb.lu.rows;
+    xu.origin = sb.lu.origin;
+    for (int j = 0; j < nsteps; ++j) {
+        if ((st = stencil_run(h, 1)) != GBST_OK)
+            return st;
+        GBST_CUDA(cudaMemcpyAsync(h->roll_up[j], h->cl_up, fb, cudaMemcpyDeviceToDevice, s));
+        GBST_CUDA(cudaMemcpyAsync(h->roll_un[j], h->cl_un, fb, cudaMemcpyDeviceToDevice, s));
+        xu.padded = h->hgrids[0].buf[h->parity];
+        xu.dense = h->roll_u[j];
+        GBST_CUDA(launch_gather(xu, s));
+    }
+    // loss = mean over the steps of |u^{n0+j+1} - ref_j|^2 / |ref_j|^2; roll_u[j] <- its gradient
+    GBST_CUDA(cudaMemsetAsync(h->roll_sums, 0, 2 * sizeof(double) * static_cast<size_t>(nsteps), s));
+    for (int j = 0; j < nsteps; ++j) {
+        if ((st = rollout_sums(h->roll_u[j], refs[j], n, h->roll_sums + 2 * j, s)) != GBST_OK ||
+            (st = rollout_grad(h->roll_u[j], refs[j], n, h->roll_sums + 2 * j, 1.0 / nsteps, s)) != GBST_OK)
+            return st;
+    }
+    // backward: a_next = cotangent of u^{n0+j+1}, a_cur of u^{n0+j}, a_prev of u^{n0+j-1}
+    float *a_next = h->roll_a[0], *a_cur = h->roll_a[1], *a_prev = h->roll_a[2];
+    GBST_CUDA(cudaMemcpyAsync(a_next, h->roll_u[nsteps - 1], fb, cudaMemcpyDeviceToDevice, s));
+    if (nsteps >= 2)
+        GBST_CUDA(cudaMemcpyAsync(a_cur, h->roll_u[nsteps - 2], fb, cudaMemcpyDeviceToDevice, s));
+    for (int j = nsteps - 1; j >= 0; --j) {
+        st = closure_backward(c, h->roll_up[j], h->roll_un[j], h->cl_cn, nx, ny, nz, a_next, h->roll_A, h->roll_gun,
+                              j < nsteps - 1 ? 1 : 0);
+        if (st != GBST_OK)
+            return st;
+        if (j == 0)
+            break;  // the initial levels are given, their cotangents are not needed
+        // u+ = 2 u^n - u^{n-1} + kappa L u^n (+ source): a_cur += 2A + L(kappa A) + gun, a_prev = -A (+ loss)
+        st = stencil_wave_adjoint_dense(h->d.space_order, nx, ny, nz, h->roll_kap, h->roll_A, a_cur, a_prev, s);
+        if (st != GBST_OK)
+            return st;
+        if ((st = dense_axpy(a_cur, h->roll_gun, 1.0f, n, s)) != GBST_OK)
+            return st;
+        if (j >= 2 && (st = dense_axpy(a_prev, h->roll_u[j - 2], 1.0f, n, s)) != GBST_OK)
+            return st;
+        float *t = a_next;
+        a_next = a_cur;
+        a_cur = a_prev;
+        a_prev = t;
+    }
+    std::vector<double> sums(2 * static_cast<size_t>(nsteps));
+    GBST_CUDA(cudaMemcpyAsync(sums.data(), h->roll_sums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GBST_CUDA(cudaStreamSynchronize(s));
+    double l = 0.0;
+    for (int j = 0; j < nsteps; ++j)
+        l += sums[2 * j + 1] > 0.0 ? sums[2 * j] / sums[2 * j + 1] : 0.0;
+    *loss = l / nsteps;
+    return poll_device_error(h);
 }
 
 gbst_status stencil_get_field_strided(gbst_handle h, int field, float *dst, int stride)

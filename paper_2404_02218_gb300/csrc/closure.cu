@@ -33,7 +33,7 @@ constexpr int NSLOT = 4;             // plane ring: z-1, z, z+1 and one prefetch
 constexpr int NTHR = 256;            // 8 warps; warp w: row w/2, 16-point segment w%2
 constexpr int ZCHUNK = 16;           // output planes per CTA
 
-enum Epi { EPI_GELU = 0, EPI_LINEAR_F32 = 1, EPI_DGELU = 2 };
+enum Epi { EPI_GELU = 0, EPI_LINEAR_F32 = 1, EPI_DGELU = 2, EPI_LINEAR_BF16 = 3 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -229,6 +229,8 @@ __global__ void __launch_bounds__(NTHR) k_conv(const ConvArgs a)
                         *reinterpret_cast<__nv_bfloat162 *>(a.zout + p * CH + c) = __floats2bfloat162_rn(v0, v1);
                     *reinterpret_cast<__nv_bfloat162 *>(a.out + p * CH + c) =
                         __floats2bfloat162_rn(gelu(v0), gelu(v1));
+                } else if (EPI == EPI_LINEAR_BF16) {  // data gradient of the network's input
+                    *reinterpret_cast<__nv_bfloat162 *>(a.out + p * CH + c) = __floats2bfloat162_rn(v0, v1);
                 } else {  // EPI_DGELU: data gradient times GELU'(pre-activation below)
                     const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162 *>(a.aux + p * CH + c);
                     v0 *= gelu_grad(__bfloat162float(zz.x));
@@ -441,6 +443,14 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                     *reinterpret_cast<uint4 *>(a.out + p * CH + c0) = make_uint4(yy[0], yy[1], yy[2], yy[3]);
                     if (a.zout)
                         *reinterpret_cast<uint4 *>(a.zout + p * CH + c0) = make_uint4(zz[0], zz[1], zz[2], zz[3]);
+                } else if (EPI == EPI_LINEAR_BF16) {  // data gradient of the network's input
+                    uint32_t oo[4];
+#pragma unroll
+                    for (int c = 0; c < 8; c += 2) {
+                        const __nv_bfloat162 ob = __floats2bfloat162_rn(v[c], v[c + 1]);
+                        oo[c >> 1] = *reinterpret_cast<const uint32_t *>(&ob);
+                    }
+                    *reinterpret_cast<uint4 *>(a.out + p * CH + c0) = make_uint4(oo[0], oo[1], oo[2], oo[3]);
                 } else {  // EPI_DGELU: data gradient times GELU'(pre-activation below)
                     const uint4 q0 = *reinterpret_cast<const uint4 *>(a.aux + p * CH + c0);
                     const uint32_t aw[4] = {q0.x, q0.y, q0.z, q0.w};
@@ -625,11 +635,12 @@ struct BiasRanges {
 };
 
 __global__ void k_adam(float *p, const float *g, float *m1, float *m2, int n, float lr, float b1, float b2,
-                       float omb1, float omb2, float eps, float bc1, float bc2, BiasRanges frozen)
+                       float omb1, float omb2, float eps, float bc1, float bc2, BiasRanges frozen,
+                       const unsigned char *trainable)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if ((i >= frozen.lo[0] && i < frozen.hi[0]) || (i >= frozen.lo[1] && i < frozen.hi[1]) ||
-            (i >= frozen.lo[2] && i < frozen.hi[2]))
+            (i >= frozen.lo[2] && i < frozen.hi[2]) || (trainable && !trainable[i]))
             continue;
         const float gi = g[i];
         const float mi = b1 * m1[i] + omb1 * gi;
@@ -637,6 +648,19 @@ __global__ void k_adam(float *p, const float *g, float *m1, float *m2, int n, fl
         m1[i] = mi;
         m2[i] = vi;
         p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+// dout channel 0 = g / t (the correction is o / t), the other channels 0.
+__global__ void k_seed(const float *g, float inv_t, int64_t n, __nv_bfloat16 *dout)
+{
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        __nv_bfloat162 *q = reinterpret_cast<__nv_bfloat162 *>(dout + p * CH);
+        q[0] = __floats2bfloat162_rn(g[p] * inv_t, 0.f);
+#pragma unroll
+        for (int k = 1; k < 8; ++k)
+            q[k] = __floats2bfloat162_rn(0.f, 0.f);
     }
 }
 
@@ -677,9 +701,19 @@ struct gbst_closure_s {
     double loss_weight = 1.0;   // factor on the loss (and its gradient) of the next loss_grad calls
     int conv_impl = 0;          // 0: tcgen05 (tensor memory), 1: mma.sync (cross-check)
     int *derr = nullptr;        // device error word of the tcgen05 convolutions
+    unsigned char *trainable = nullptr;      // per-parameter Adam mask (null: all parameters train)
+    unsigned char *trainable_buf = nullptr;  // its device storage
+    // feature inputs (cin 8): FP32 stencil features, see closure_set_features
+    bool feat = false;
+    int feat_r = 2;
+    double feat_w[5] = {0, 0, 0, 0, 0};
+    double feat_s[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    ClosureFeatBufs fb;
+    __nv_bfloat16 *dx = nullptr;  // cotangent of the network input (backward to the fields)
 };
 
 cudaStream_t gbst::closure_stream(gbst_closure c) { return c ? c->stream : nullptr; }
+bool gbst::closure_has_features(gbst_closure c) { return c && c->feat; }
 
 namespace {
 
@@ -814,8 +848,7 @@ gbst_status refresh_weights(gbst_closure c)
     const int cins[3] = {c->cin, c->hidden, c->hidden}, couts[3] = {c->hidden, c->hidden, 1};
     const int pads[3] = {CH, CH, 8};
     for (int l = 0; l < 3; ++l) {
-        k_convert<<<8, 256, 0, c->stream>>>(c->p + c->off[2 * l], cins[l], couts[l], pads[l], c->wf[l],
-                                             l > 0 ? c->wb[l] : nullptr);
+        k_convert<<<8, 256, 0, c->stream>>>(c->p + c->off[2 * l], cins[l], couts[l], pads[l], c->wf[l], c->wb[l]);
     }
     c->weights_dirty = false;
     const cudaError_t e = cudaGetLastError();
@@ -829,7 +862,14 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     if (st != GBST_OK)
         return st;
     const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
-    k_prep<<<blocks_for(n), 256, 0, c->stream>>>(up, un, cn, static_cast<float>(c->scale), n, c->x);
+    if (c->feat) {
+        st = closure_features_forward(up, un, cn, d.nx, d.ny, d.nz, c->feat_r, c->feat_w, c->feat_s, c->fb, c->x,
+                                      c->stream);
+        if (st != GBST_OK)
+            return st;
+    } else {
+        k_prep<<<blocks_for(n), 256, 0, c->stream>>>(up, un, cn, static_cast<float>(c->scale), n, c->x);
+    }
     ConvArgs a{};
     a.d = d;
     a.in = c->x;
@@ -858,6 +898,68 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
 }
 
+// Backward pass from c->dout (the cotangent of o, channel 0) through the three layers:
+// adds every parameter's gradient into c->g; with input_grad, also the cotangent of the
+// network input into c->dx.  Needs the activations of forward(.., keep = true).
+cudaError_t backprop(gbst_closure c, Dims d, bool input_grad)
+{
+    cudaStream_t s = c->stream;
+    // layer 3: dW3 from y2 and dOut; dZ2 = conv(dOut, W3 flipped^T) * GELU'(z2)
+    WgradArgs w{};
+    w.d = d;
+    w.x = c->y2;
+    w.dz = c->dout;
+    w.grad_w = c->g + c->off[4];
+    w.grad_b = c->g + c->off[5];
+    w.cin = c->hidden;
+    w.cout = 1;
+    cudaError_t e = launch_wgrad(w, s);
+    ConvArgs a{};
+    a.d = d;
+    a.in = c->dout;
+    a.wt = c->wb[2];
+    a.aux = c->z2;
+    a.out = c->dz2;
+    a.cout_valid = CH;
+    if (e == cudaSuccess)
+        e = conv<16, EPI_DGELU>(c, a);
+    // layer 2
+    w.x = c->y1;
+    w.dz = c->dz2;
+    w.grad_w = c->g + c->off[2];
+    w.grad_b = c->g + c->off[3];
+    w.cin = c->hidden;
+    w.cout = c->hidden;
+    if (e == cudaSuccess)
+        e = launch_wgrad(w, s);
+    a.in = c->dz2;
+    a.wt = c->wb[1];
+    a.aux = c->z1;
+    a.out = c->dz1;
+    if (e == cudaSuccess)
+        e = conv<16, EPI_DGELU>(c, a);
+    // layer 1
+    w.x = c->x;
+    w.dz = c->dz1;
+    w.grad_w = c->g + c->off[0];
+    w.grad_b = c->g + c->off[1];
+    w.cin = c->cin;
+    w.cout = c->hidden;
+    if (e == cudaSuccess)
+        e = launch_wgrad(w, s);
+    if (input_grad && e == cudaSuccess) {
+        a.in = c->dz1;
+        a.wt = c->wb[0];
+        a.aux = nullptr;
+        a.bias = nullptr;
+        a.out = c->dx;
+        e = conv<16, EPI_LINEAR_BF16>(c, a);
+    }
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -868,8 +970,10 @@ gbst_status closure_create(int cin, int hidden, int64_t max_points, double in_sc
     if (!out)
         return record_error(GBST_EINVAL, "closure_create: null out");
     *out = nullptr;
-    if (cin != 4 || hidden != 16)
-        return record_error(GBST_ENOTSUP, "closure_create: the network has 4 input and 16 hidden channels");
+    if ((cin != 4 && cin != 8) || hidden != 16)
+        return record_error(GBST_ENOTSUP,
+                            "closure_create: the network has 4 (fields) or 8 (fields and FP32 stencil features) "
+                            "input channels and 16 hidden channels");
     if (max_points < 1 || !(in_scale > 0.0))
         return record_error(GBST_EINVAL, "closure_create: max_points and in_scale must be positive");
     gbst_closure c = new (std::nothrow) gbst_closure_s;
@@ -911,6 +1015,22 @@ gbst_status closure_create(int cin, int hidden, int64_t max_points, double in_sc
     for (auto pp : acts) {
         *pp = static_cast<__nv_bfloat16 *>(cl_alloc(c, ab));
         ok = ok && *pp;
+    }
+    if (cin == 8) {
+        c->feat = true;
+        const size_t fbytes = static_cast<size_t>(max_points) * sizeof(float);
+        float **fbufs[9] = {&c->fb.cn2, &c->fb.g[0], &c->fb.g[1], &c->fb.g[2], &c->fb.lu,
+                            &c->fb.t5,  &c->fb.t6,   &c->fb.e7,   &c->fb.tmp};
+        for (auto pp : fbufs) {
+            *pp = static_cast<float *>(cl_alloc(c, fbytes));
+            ok = ok && *pp;
+        }
+        c->dx = static_cast<__nv_bfloat16 *>(cl_alloc(c, ab));
+        ok = ok && c->dx;
+        double w[9];
+        stencil_fd_weights(4, w);
+        for (int m = 0; m <= 2; ++m)
+            c->feat_w[m] = w[m];
     }
     c->o = static_cast<float *>(cl_alloc(c, static_cast<size_t>(max_points) * sizeof(float)));
     c->dloss = static_cast<double *>(cl_alloc(c, 256));
@@ -1015,52 +1135,8 @@ gbst_status closure_loss_grad(gbst_closure c, const float *u_plus, const float *
         e = cudaMemsetAsync(c->g, 0, c->nparams * sizeof(float), s);
     k_loss<<<blocks_for(n), 256, 0, s>>>(c->o, u_plus, u_ref, static_cast<float>(c->out_scale),
                                          static_cast<float>(c->loss_weight), n, c->dloss, c->dout);
-    // layer 3: dW3 from y2 and dOut; dZ2 = conv(dOut, W3 flipped^T) * GELU'(z2)
-    WgradArgs w{};
-    w.d = d;
-    w.x = c->y2;
-    w.dz = c->dout;
-    w.grad_w = c->g + c->off[4];
-    w.grad_b = c->g + c->off[5];
-    w.cin = c->hidden;
-    w.cout = 1;
     if (e == cudaSuccess)
-        e = launch_wgrad(w, s);
-    ConvArgs a{};
-    a.d = d;
-    a.in = c->dout;
-    a.wt = c->wb[2];
-    a.aux = c->z2;
-    a.out = c->dz2;
-    a.cout_valid = CH;
-    if (e == cudaSuccess)
-        e = conv<16, EPI_DGELU>(c, a);
-    // layer 2
-    w.x = c->y1;
-    w.dz = c->dz2;
-    w.grad_w = c->g + c->off[2];
-    w.grad_b = c->g + c->off[3];
-    w.cin = c->hidden;
-    w.cout = c->hidden;
-    if (e == cudaSuccess)
-        e = launch_wgrad(w, s);
-    a.in = c->dz2;
-    a.wt = c->wb[1];
-    a.aux = c->z1;
-    a.out = c->dz1;
-    if (e == cudaSuccess)
-        e = conv<16, EPI_DGELU>(c, a);
-    // layer 1 (no data gradient for the inputs)
-    w.x = c->x;
-    w.dz = c->dz1;
-    w.grad_w = c->g + c->off[0];
-    w.grad_b = c->g + c->off[1];
-    w.cin = c->cin;
-    w.cout = c->hidden;
-    if (e == cudaSuccess)
-        e = launch_wgrad(w, s);
-    if (e == cudaSuccess)
-        e = cudaGetLastError();
+        e = backprop(c, d, false);
     double l = 0.0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&l, c->dloss, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1073,6 +1149,105 @@ gbst_status closure_loss_grad(gbst_closure c, const float *u_plus, const float *
         return st;
     *loss = c->loss_weight * l / static_cast<double>(n);
     return GBST_OK;
+}
+
+gbst_status closure_set_trainable(gbst_closure c, const unsigned char *mask, int64_t n)
+{
+    if (!c)
+        return record_error(GBST_EINVAL, "closure_set_trainable: null closure");
+    if (!mask) {
+        c->trainable = nullptr;  // (the buffer, if any, stays owned by the closure)
+        return GBST_OK;
+    }
+    if (n != c->nparams)
+        return record_error(GBST_EINVAL, "closure_set_trainable: n must be the parameter count");
+    if (!c->trainable_buf) {
+        c->trainable_buf = static_cast<unsigned char *>(cl_alloc(c, static_cast<size_t>(n)));
+        if (!c->trainable_buf)
+            return record_error(GBST_ENOMEM, "closure_set_trainable: device memory");
+    }
+    if (cudaMemcpyAsync(c->trainable_buf, mask, static_cast<size_t>(n), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return record_error(GBST_ECUDA, "closure_set_trainable: copy failed");
+    c->trainable = c->trainable_buf;
+    return GBST_OK;
+}
+
+gbst_status closure_set_features(gbst_closure c, int space_order, const double *scales, int n)
+{
+    if (!c || !scales || n != 8)
+        return record_error(GBST_EINVAL, "closure_set_features: null closure or scales, or n != 8");
+    if (!c->feat)
+        return record_error(GBST_ENOTSUP, "closure_set_features: the closure was created with 4 input channels");
+    if (space_order != 2 && space_order != 4 && space_order != 8)
+        return record_error(GBST_EINVAL, "closure_set_features: space_order must be 2, 4 or 8");
+    for (int k = 0; k < 8; ++k)
+        if (!std::isfinite(scales[k]))
+            return record_error(GBST_EINVAL, "closure_set_features: scales must be finite");
+    double w[9];
+    gbst_status st = stencil_fd_weights(space_order, w);
+    if (st != GBST_OK)
+        return st;
+    c->feat_r = space_order / 2;
+    for (int m = 0; m < 5; ++m)
+        c->feat_w[m] = m <= c->feat_r ? w[m] : 0.0;
+    for (int k = 0; k < 8; ++k)
+        c->feat_s[k] = scales[k];
+    return GBST_OK;
+}
+
+gbst_status closure_feature_values(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,
+                                   int64_t nx, int64_t ny, int64_t nz, float *out)
+{
+    if (!c || !u_plus || !u_n || !c_norm || !out)
+        return record_error(GBST_EINVAL, "closure_feature_values: null argument");
+    if (!c->feat)
+        return record_error(GBST_ENOTSUP, "closure_feature_values: the closure was created with 4 input channels");
+    Dims d;
+    gbst_status st = check_dims(c, nx, ny, nz, &d);
+    if (st != GBST_OK)
+        return st;
+    st = closure_features_forward(u_plus, u_n, c_norm, nx, ny, nz, c->feat_r, c->feat_w, c->feat_s, c->fb, c->x,
+                                  c->stream);
+    if (st != GBST_OK)
+        return st;
+    return closure_features_values(u_plus, u_n, nx, ny, nz, c->fb, out, c->stream);
+}
+
+gbst_status closure_backward(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,
+                             int64_t nx, int64_t ny, int64_t nz, const float *grad_out, float *grad_up,
+                             float *grad_un, int accumulate)
+{
+    const float *grad_corr = grad_out;
+    if (!c || !u_plus || !u_n || !c_norm || !grad_corr || !grad_up || !grad_un || grad_up == grad_out)
+        return record_error(GBST_EINVAL, "closure_backward: null argument");
+    if (!c->feat)
+        return record_error(GBST_ENOTSUP, "closure_backward: the closure was created with 4 input channels");
+    Dims d;
+    gbst_status st = check_dims(c, nx, ny, nz, &d);
+    if (st != GBST_OK)
+        return st;
+    st = forward(c, u_plus, u_n, c_norm, d, true);
+    if (st != GBST_OK)
+        return st;
+    const int64_t n = nx * ny * nz;
+    cudaError_t e = cudaSuccess;
+    if (!accumulate)
+        e = cudaMemsetAsync(c->g, 0, c->nparams * sizeof(float), c->stream);
+    k_seed<<<blocks_for(n), 256, 0, c->stream>>>(grad_corr, static_cast<float>(1.0 / c->out_scale), n, c->dout);
+    if (e == cudaSuccess)
+        e = backprop(c, d, true);
+    if (e != cudaSuccess)
+        return record_error(GBST_ECUDA, cudaGetErrorString(e));
+    st = closure_features_adjoint(c->dx, nx, ny, nz, c->feat_r, c->feat_w, c->feat_s, c->fb, grad_up, grad_un,
+                                  c->stream);
+    if (st != GBST_OK)
+        return st;
+    // u^{n+1} = u+ + correction: the identity path of u+
+    k_scale_add<<<blocks_for(n), 256, 0, c->stream>>>(grad_up, grad_out, 1.0f, n);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
 }
 
 gbst_status closure_set_out_scale(gbst_closure c, double out_scale)
@@ -1122,7 +1297,8 @@ gbst_status closure_adam_step(gbst_closure c, double lr)
     }
     k_adam<<<blocks_for(c->nparams), 256, 0, c->stream>>>(c->p, c->g, c->m1, c->m2, static_cast<int>(c->nparams),
                                                           static_cast<float>(lr), b1, b2, static_cast<float>(1.0 - 0.9),
-                                                          static_cast<float>(1.0 - 0.999), 1e-8f, bc1, bc2, fr);
+                                                          static_cast<float>(1.0 - 0.999), 1e-8f, bc1, bc2, fr,
+                                                          c->trainable);
     c->weights_dirty = true;
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));

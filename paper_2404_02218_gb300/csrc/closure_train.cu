@@ -1,0 +1,478 @@
+// Dense-array stencil kernels that train and feed the learned closure.
+//
+// The closure works on dense [nz][ny][nx] FP32 arrays (x fastest) of one coarse
+// grid, zero outside the interior.  Training it through whole coarse-grid
+// rollouts needs the transpose of the leapfrog step of Section 6.1's scheme
+// (backpropagation through the time steps), and its input features are
+// stencils of the field computed in FP32 before they are rounded to the
+// network's BF16 inputs.  These kernels are simple one-thread-per-point
+// stencils: each output point reads its star neighbours (L2-resident at the
+// closure's grid sizes), so they cost a few tens of microseconds at 256^3,
+// small next to the network.
+#include <cmath>
+#include <cstdio>
+
+#include "gbst_internal.h"
+
+namespace gbst {
+namespace {
+
+struct DenseDims {
+    int nx, ny, nz;
+};
+
+struct FeatScales {
+    float s[8];
+};
+
+constexpr int kThr = 256;
+
+inline int blocks_for_dense(int64_t n) { return static_cast<int>(std::min<int64_t>(65535 * 8, (n + kThr - 1) / kThr)); }
+
+// out[p] (=|+=) alpha * post[p] * sum_axes sum_{m=-R..R} w_|m| (pre * in)[p + m e_axis]
+// with zero outside the interior; pre / post may be null (factor 1).
+template <int R>
+__global__ void __launch_bounds__(kThr) k_star(DenseDims d, const float *__restrict__ in,
+                                               const float *__restrict__ pre, const float *__restrict__ post,
+                                               float4 w03, float w4, float alpha, int accumulate,
+                                               float *__restrict__ out)
+{
+    const float w[5] = {w03.x, w03.y, w03.z, w03.w, w4};
+    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
+    const int64_t sy = d.nx, sz = static_cast<int64_t>(d.nx) * d.ny;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr) {
+        const int x = static_cast<int>(p % d.nx);
+        const int y = static_cast<int>((p / d.nx) % d.ny);
+        const int z = static_cast<int>(p / sz);
+        auto val = [&](int64_t q) { return pre ? pre[q] * in[q] : in[q]; };
+        float s = 3.0f * w[0] * val(p);
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+            float a = 0.0f;
+            if (x - m >= 0) a += val(p - m);
+            if (x + m < d.nx) a += val(p + m);
+            if (y - m >= 0) a += val(p - m * sy);
+            if (y + m < d.ny) a += val(p + m * sy);
+            if (z - m >= 0) a += val(p - m * sz);
+            if (z + m < d.nz) a += val(p + m * sz);
+            s = fmaf(w[m], a, s);
+        }
+        float v = alpha * s;
+        if (post)
+            v *= post[p];
+        out[p] = accumulate ? out[p] + v : v;
+    }
+}
+
+// Transpose of one source-free leapfrog step:
+//   lam_cur += 2 lam_next + L(kappa lam_next);  lam_prev = -lam_next (when given).
+template <int R>
+__global__ void __launch_bounds__(kThr) k_wave_adjoint(DenseDims d, const float *__restrict__ kappa,
+                                                       const float *__restrict__ lam_next, float4 w03, float w4,
+                                                       float *__restrict__ lam_cur, float *__restrict__ lam_prev)
+{
+    const float w[5] = {w03.x, w03.y, w03.z, w03.w, w4};
+    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
+    const int64_t sy = d.nx, sz = static_cast<int64_t>(d.nx) * d.ny;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr) {
+        const int x = static_cast<int>(p % d.nx);
+        const int y = static_cast<int>((p / d.nx) % d.ny);
+        const int z = static_cast<int>(p / sz);
+        auto val = [&](int64_t q) { return kappa[q] * lam_next[q]; };
+        float s = 3.0f * w[0] * val(p);
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+            float a = 0.0f;
+            if (x - m >= 0) a += val(p - m);
+            if (x + m < d.nx) a += val(p + m);
+            if (y - m >= 0) a += val(p - m * sy);
+            if (y + m < d.ny) a += val(p + m * sy);
+            if (z - m >= 0) a += val(p - m * sz);
+            if (z + m < d.nz) a += val(p + m * sz);
+            s = fmaf(w[m], a, s);
+        }
+        const float ln = lam_next[p];
+        lam_cur[p] = lam_cur[p] + (2.0f * ln + s);
+        if (lam_prev)
+            lam_prev[p] = -ln;
+    }
+}
+
+// Value of a dense array at p + m e_axis, zero outside the interior.
+__device__ __forceinline__ float at_off(const float *__restrict__ u, DenseDims d, int64_t p, int x, int y, int z,
+                                        int axis, int m)
+{
+    if (axis == 0)
+        return (x + m >= 0 && x + m < d.nx) ? u[p + m] : 0.0f;
+    if (axis == 1)
+        return (y + m >= 0 && y + m < d.ny) ? u[p + static_cast<int64_t>(m) * d.nx] : 0.0f;
+    return (z + m >= 0 && z + m < d.nz) ? u[p + static_cast<int64_t>(m) * d.nx * d.ny] : 0.0f;
+}
+
+// cn2 = c_n^2 and its central differences g_a = (cn2[p + e_a] - cn2[p - e_a]) / 2 (zero outside).
+__global__ void __launch_bounds__(kThr) k_cn2_grads(DenseDims d, const float *__restrict__ cn, float *__restrict__ cn2,
+                                                    float *__restrict__ g0, float *__restrict__ g1,
+                                                    float *__restrict__ g2)
+{
+    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr) {
+        const int x = static_cast<int>(p % d.nx), y = static_cast<int>((p / d.nx) % d.ny);
+        const int z = static_cast<int>(p / (static_cast<int64_t>(d.nx) * d.ny));
+        const float c = cn[p];
+        cn2[p] = c * c;
+        float *g[3] = {g0, g1, g2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float cp = at_off(cn, d, p, x, y, z, a, 1), cm = at_off(cn, d, p, x, y, z, a, -1);
+            g[a][p] = 0.5f * (cp * cp - cm * cm);
+        }
+    }
+}
+
+// Network input x (channels-last BF16, 16 channels) from the FP32 features:
+//   f0 = u+, f1 = u^n, f2 = cn2 u+, f3 = cn2 u^n, f4 = t6 (= cn2 sum delta^6 u^n),
+//   f5 = t5 (= cn2 L(cn2 L u^n)), f6 = sum_a g_a D_a u^n, f7 = (sum_a |g_a|) Lu;  x_k = s_k f_k.
+__global__ void __launch_bounds__(kThr) k_pack_features(DenseDims d, const float *__restrict__ up,
+                                                        const float *__restrict__ un, const float *__restrict__ cn2,
+                                                        const float *__restrict__ t6, const float *__restrict__ t5,
+                                                        const float *__restrict__ lu, const float *__restrict__ g0,
+                                                        const float *__restrict__ g1, const float *__restrict__ g2,
+                                                        FeatScales sc, __nv_bfloat16 *__restrict__ xout)
+{
+    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr) {
+        const int x = static_cast<int>(p % d.nx), y = static_cast<int>((p / d.nx) % d.ny);
+        const int z = static_cast<int>(p / (static_cast<int64_t>(d.nx) * d.ny));
+        const float c2 = cn2[p], a = up[p], b = un[p];
+        const float ga[3] = {g0[p], g1[p], g2[p]};
+        float f6 = 0.0f, gabs = 0.0f;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const float du = 0.5f * (at_off(un, d, p, x, y, z, ax, 1) - at_off(un, d, p, x, y, z, ax, -1));
+            f6 = fmaf(ga[ax], du, f6);
+            gabs += fabsf(ga[ax]);
+        }
+        const float f[8] = {a, b, c2 * a, c2 * b, t6[p], t5[p], f6, gabs * lu[p]};
+        __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(xout + p * 16);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            o[k] = __floats2bfloat162_rn(sc.s[2 * k] * f[2 * k], sc.s[2 * k + 1] * f[2 * k + 1]);
+#pragma unroll
+        for (int k = 4; k < 8; ++k)
+            o[k] = __floats2bfloat162_rn(0.0f, 0.0f);
+    }
+}
+
+// The same eight features in FP32, unscaled, channel-major (out + k n).
+__global__ void __launch_bounds__(kThr) k_feature_values(DenseDims d, const float *__restrict__ up,
+                                                         const float *__restrict__ un, const float *__restrict__ cn2,
+                                                         const float *__restrict__ t6, const float *__restrict__ t5,
+                                                         const float *__restrict__ lu, const float *__restrict__ g0,
+                                                         const float *__restrict__ g1, const float *__restrict__ g2,
+                                                         float *__restrict__ out)
+{
+    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr) {
+        const int x = static_cast<int>(p % d.nx), y = static_cast<int>((p / d.nx) % d.ny);
+        const int z = static_cast<int>(p / (static_cast<int64_t>(d.nx) * d.ny));
+        const float c2 = cn2[p], a = up[p], b = un[p];
+        const float ga[3] = {g0[p], g1[p], g2[p]};
+        float f6 = 0.0f, gabs = 0.0f;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const float du = 0.5f * (at_off(un, d, p, x, y, z, ax, 1) - at_off(un, d, p, x, y, z, ax, -1));
+            f6 = fmaf(ga[ax], du, f6);
+            gabs += fabsf(ga[ax]);
+        }
+        const float f[8] = {a, b, c2 * a, c2 * b, t6[p], t5[p], f6, gabs * lu[p]};
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            out[k * n + p] = f[k];
+    }
+}
+
+// First pass of the features' transpose, from the cotangent dx of the network input
+// (channels-last BF16): d_k = s_k dx_k;
+//   g_up = d0 + cn2 d2,  g_un = d1 + cn2 d3  (pointwise parts, written),
+//   e4 = cn2 d4, e5 = cn2 d5, e6 = d6, e7 = (sum_a |g_a|) d7  (for the stencil parts).
+__global__ void __launch_bounds__(kThr) k_unpack_features_adj(DenseDims d, const __nv_bfloat16 *__restrict__ dx,
+                                                              const float *__restrict__ cn2,
+                                                              const float *__restrict__ g0,
+                                                              const float *__restrict__ g1,
+                                                              const float *__restrict__ g2, FeatScales sc,
+                                                              float *__restrict__ g_up, float *__restrict__ g_un,
+                                                              float *__restrict__ e4, float *__restrict__ e5,
+                                                              float *__restrict__ e6, float *__restrict__ e7)
+{
+    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr) {
+        const __nv_bfloat162 *q = reinterpret_cast<const __nv_bfloat162 *>(dx + p * 16);
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 t = __bfloat1622float2(q[k]);
+            v[2 * k] = sc.s[2 * k] * t.x;
+            v[2 * k + 1] = sc.s[2 * k + 1] * t.y;
+        }
+        const float c2 = cn2[p];
+        g_up[p] = fmaf(c2, v[2], v[0]);
+        g_un[p] = fmaf(c2, v[3], v[1]);
+        e4[p] = c2 * v[4];
+        e5[p] = c2 * v[5];
+        e6[p] = v[6];
+        e7[p] = (fabsf(g0[p]) + fabsf(g1[p]) + fabsf(g2[p])) * v[7];
+    }
+}
+
+// out[p] += alpha * sum_a (D_a (g_a * e))[p],  D_a the central difference, zero outside.
+__global__ void __launch_bounds__(kThr) k_div_acc(DenseDims d, const float *__restrict__ e,
+                                                  const float *__restrict__ g0, const float *__restrict__ g1,
+                                                  const float *__restrict__ g2, float alpha, float *__restrict__ out)
+{
+    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
+    const float *g[3] = {g0, g1, g2};
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr) {
+        const int x = static_cast<int>(p % d.nx), y = static_cast<int>((p / d.nx) % d.ny);
+        const int z = static_cast<int>(p / (static_cast<int64_t>(d.nx) * d.ny));
+        float s = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t st = a == 0 ? 1 : a == 1 ? d.nx : static_cast<int64_t>(d.nx) * d.ny;
+            const int c = a == 0 ? x : a == 1 ? y : z, nc = a == 0 ? d.nx : a == 1 ? d.ny : d.nz;
+            const float hi = c + 1 < nc ? g[a][p + st] * e[p + st] : 0.0f;
+            const float lo = c - 1 >= 0 ? g[a][p - st] * e[p - st] : 0.0f;
+            s += 0.5f * (hi - lo);
+        }
+        out[p] = fmaf(alpha, s, out[p]);
+    }
+}
+
+// sums[0] += sum (u - ref)^2, sums[1] += sum ref^2  (FP64, one atomic per warp)
+__global__ void __launch_bounds__(kThr) k_roll_sums(const float *__restrict__ u, const float *__restrict__ ref,
+                                                    int64_t n, double *sums)
+{
+    double a = 0.0, b = 0.0;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr) {
+        const double r = ref[p], d = static_cast<double>(u[p]) - r;
+        a += d * d;
+        b += r * r;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sums[0], a);
+        atomicAdd(&sums[1], b);
+    }
+}
+
+// u <- scale * 2 (u - ref) / sums[1]  (the gradient of scale * |u - ref|^2 / |ref|^2)
+__global__ void __launch_bounds__(kThr) k_roll_grad(float *__restrict__ u, const float *__restrict__ ref, int64_t n,
+                                                    const double *sums, double scale)
+{
+    const double f = sums[1] > 0.0 ? 2.0 * scale / sums[1] : 0.0;
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr)
+        u[p] = static_cast<float>(f * (static_cast<double>(u[p]) - ref[p]));
+}
+
+__global__ void __launch_bounds__(kThr) k_axpy(float *__restrict__ y, const float *__restrict__ x, float a, int64_t n)
+{
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * kThr)
+        y[p] = fmaf(a, x[p], y[p]);
+}
+
+gbst_status dense_dims(int64_t nx, int64_t ny, int64_t nz, DenseDims *d, const char *who)
+{
+    char msg[200];
+    if (nx < 1 || ny < 1 || nz < 1 || nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30) ||
+        nx * ny > (int64_t(1) << 40)) {
+        snprintf(msg, sizeof msg, "%s: dims must be positive and at most 2^30 per axis", who);
+        return record_error(GBST_EINVAL, msg);
+    }
+    d->nx = static_cast<int>(nx);
+    d->ny = static_cast<int>(ny);
+    d->nz = static_cast<int>(nz);
+    return GBST_OK;
+}
+
+gbst_status launched(const char *who)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        return GBST_OK;
+    char msg[200];
+    snprintf(msg, sizeof msg, "%s: %s", who, cudaGetErrorString(e));
+    return record_error(GBST_ECUDA, msg);
+}
+
+}  // namespace
+
+// Star stencil of radius r (weights w[0..r]) on a dense array; see k_star.
+gbst_status dense_star(int r, const double *w, int64_t nx, int64_t ny, int64_t nz, const float *in, const float *pre,
+                       const float *post, double alpha, bool accumulate, float *out, cudaStream_t s)
+{
+    DenseDims d;
+    gbst_status st = dense_dims(nx, ny, nz, &d, "dense stencil");
+    if (st != GBST_OK)
+        return st;
+    if (r < 1 || r > 4)
+        return record_error(GBST_EINVAL, "dense stencil: radius must be 1..4");
+    float wf[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m <= r; ++m)
+        wf[m] = static_cast<float>(w[m]);
+    const float4 w03 = make_float4(wf[0], wf[1], wf[2], wf[3]);
+    const int64_t n = nx * ny * nz;
+    const int blocks = blocks_for_dense(n);
+    const float a = static_cast<float>(alpha);
+    const int acc = accumulate ? 1 : 0;
+    switch (r) {
+    case 1: k_star<1><<<blocks, kThr, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
+    case 2: k_star<2><<<blocks, kThr, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
+    case 3: k_star<3><<<blocks, kThr, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
+    default: k_star<4><<<blocks, kThr, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
+    }
+    return launched("dense stencil");
+}
+
+namespace {
+constexpr double kSixth[4] = {-20.0, 15.0, -6.0, 1.0};  // delta^6 per axis, w_0 .. w_3
+
+FeatScales to_scales(const double *sc)
+{
+    FeatScales f;
+    for (int k = 0; k < 8; ++k)
+        f.s[k] = static_cast<float>(sc[k]);
+    return f;
+}
+}  // namespace
+
+// Closure input features (8 channels) from (u+, u^n, c_n) into x (channels-last BF16, 16
+// channels, the last 8 zero): x_k = scales[k] f_k, see k_pack_features.  r, w: the star L.
+gbst_status closure_features_forward(const float *up, const float *un, const float *cn, int64_t nx, int64_t ny,
+                                     int64_t nz, int r, const double *w, const double *scales,
+                                     const ClosureFeatBufs &b, __nv_bfloat16 *x, cudaStream_t s)
+{
+    DenseDims d;
+    gbst_status st = dense_dims(nx, ny, nz, &d, "closure features");
+    if (st != GBST_OK)
+        return st;
+    const int blocks = blocks_for_dense(nx * ny * nz);
+    k_cn2_grads<<<blocks, kThr, 0, s>>>(d, cn, b.cn2, b.g[0], b.g[1], b.g[2]);
+    if ((st = launched("closure features")) != GBST_OK)
+        return st;
+    if ((st = dense_star(r, w, nx, ny, nz, un, nullptr, nullptr, 1.0, false, b.lu, s)) != GBST_OK)
+        return st;
+    if ((st = dense_star(r, w, nx, ny, nz, b.lu, b.cn2, b.cn2, 1.0, false, b.t5, s)) != GBST_OK)
+        return st;
+    if ((st = dense_star(3, kSixth, nx, ny, nz, un, nullptr, b.cn2, 1.0, false, b.t6, s)) != GBST_OK)
+        return st;
+    k_pack_features<<<blocks, kThr, 0, s>>>(d, up, un, b.cn2, b.t6, b.t5, b.lu, b.g[0], b.g[1], b.g[2],
+                                            to_scales(scales), x);
+    return launched("closure features");
+}
+
+// Transpose of closure_features_forward (which must have run for the same c_n, so that
+// b.cn2 and b.g hold its values): from the cotangent dx of x, g_up and g_un are written.
+gbst_status closure_features_adjoint(const __nv_bfloat16 *dx, int64_t nx, int64_t ny, int64_t nz, int r,
+                                     const double *w, const double *scales, const ClosureFeatBufs &b, float *g_up,
+                                     float *g_un, cudaStream_t s)
+{
+    DenseDims d;
+    gbst_status st = dense_dims(nx, ny, nz, &d, "closure feature adjoint");
+    if (st != GBST_OK)
+        return st;
+    const int blocks = blocks_for_dense(nx * ny * nz);
+    float *e4 = b.t6, *e5 = b.t5, *e6 = b.lu, *e7 = b.e7;
+    k_unpack_features_adj<<<blocks, kThr, 0, s>>>(d, dx, b.cn2, b.g[0], b.g[1], b.g[2], to_scales(scales), g_up,
+                                                  g_un, e4, e5, e6, e7);
+    if ((st = launched("closure feature adjoint")) != GBST_OK)
+        return st;
+    if ((st = dense_star(3, kSixth, nx, ny, nz, e4, nullptr, nullptr, 1.0, true, g_un, s)) != GBST_OK)
+        return st;
+    if ((st = dense_star(r, w, nx, ny, nz, e5, nullptr, nullptr, 1.0, false, b.tmp, s)) != GBST_OK)
+        return st;
+    if ((st = dense_star(r, w, nx, ny, nz, b.tmp, b.cn2, nullptr, 1.0, true, g_un, s)) != GBST_OK)
+        return st;
+    k_div_acc<<<blocks, kThr, 0, s>>>(d, e6, b.g[0], b.g[1], b.g[2], -1.0f, g_un);
+    if ((st = launched("closure feature adjoint")) != GBST_OK)
+        return st;
+    return dense_star(r, w, nx, ny, nz, e7, nullptr, nullptr, 1.0, true, g_un, s);
+}
+
+// The unscaled FP32 features f_0 .. f_7, channel-major (out + k * n), after
+// closure_features_forward has filled b for the same inputs.
+gbst_status closure_features_values(const float *up, const float *un, int64_t nx, int64_t ny, int64_t nz,
+                                    const ClosureFeatBufs &b, float *out, cudaStream_t s)
+{
+    DenseDims d;
+    gbst_status st = dense_dims(nx, ny, nz, &d, "closure feature values");
+    if (st != GBST_OK)
+        return st;
+    k_feature_values<<<blocks_for_dense(nx * ny * nz), kThr, 0, s>>>(d, up, un, b.cn2, b.t6, b.t5, b.lu, b.g[0],
+                                                                    b.g[1], b.g[2], out);
+    return launched("closure feature values");
+}
+
+gbst_status rollout_sums(const float *u, const float *ref, int64_t n, double *sums, cudaStream_t s)
+{
+    k_roll_sums<<<std::min(blocks_for_dense(n), 4096), kThr, 0, s>>>(u, ref, n, sums);
+    return launched("rollout loss");
+}
+
+gbst_status rollout_grad(float *u, const float *ref, int64_t n, const double *sums, double scale, cudaStream_t s)
+{
+    k_roll_grad<<<blocks_for_dense(n), kThr, 0, s>>>(u, ref, n, sums, scale);
+    return launched("rollout loss gradient");
+}
+
+gbst_status dense_axpy(float *y, const float *x, float a, int64_t n, cudaStream_t s)
+{
+    k_axpy<<<blocks_for_dense(n), kThr, 0, s>>>(y, x, a, n);
+    return launched("dense axpy");
+}
+
+}  // namespace gbst
+
+using namespace gbst;
+
+extern "C" gbst_status stencil_wave_adjoint_dense(int space_order, int64_t nx, int64_t ny, int64_t nz,
+                                                  const float *kappa, const float *lam_next, float *lam_cur,
+                                                  float *lam_prev, void *stream)
+{
+    static const char *who = "stencil_wave_adjoint_dense";
+    if (!kappa || !lam_next || !lam_cur)
+        return record_error(GBST_EINVAL, "stencil_wave_adjoint_dense: null kappa, lam_next or lam_cur");
+    if (space_order != 2 && space_order != 4 && space_order != 8)
+        return record_error(GBST_EINVAL, "stencil_wave_adjoint_dense: space_order must be 2, 4 or 8");
+    DenseDims d;
+    gbst_status st = dense_dims(nx, ny, nz, &d, who);
+    if (st != GBST_OK)
+        return st;
+    double w[9];
+    st = stencil_fd_weights(space_order, w);
+    if (st != GBST_OK)
+        return st;
+    float wf[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m <= space_order / 2; ++m)
+        wf[m] = static_cast<float>(w[m]);
+    const float4 w03 = make_float4(wf[0], wf[1], wf[2], wf[3]);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int blocks = blocks_for_dense(nx * ny * nz);
+    switch (space_order) {
+    case 2: k_wave_adjoint<1><<<blocks, kThr, 0, s>>>(d, kappa, lam_next, w03, wf[4], lam_cur, lam_prev); break;
+    case 4: k_wave_adjoint<2><<<blocks, kThr, 0, s>>>(d, kappa, lam_next, w03, wf[4], lam_cur, lam_prev); break;
+    default: k_wave_adjoint<4><<<blocks, kThr, 0, s>>>(d, kappa, lam_next, w03, wf[4], lam_cur, lam_prev); break;
+    }
+    return launched(who);
+}

@@ -193,6 +193,25 @@ cudaStream_t closure_stream(gbst_closure c);
 
 // Record the message returned by stencil_last_error() for the calling thread.
 gbst_status record_error(gbst_status st, const char *msg);
+// Dense-array stencils of the closure (closure_train.cu).
+gbst_status dense_star(int r, const double *w, int64_t nx, int64_t ny, int64_t nz, const float *in, const float *pre,
+                       const float *post, double alpha, bool accumulate, float *out, cudaStream_t s);
+struct ClosureFeatBufs {
+    float *cn2 = nullptr, *g[3] = {nullptr, nullptr, nullptr}, *lu = nullptr, *t5 = nullptr, *t6 = nullptr,
+          *e7 = nullptr, *tmp = nullptr;  // dense, one value per point each
+};
+gbst_status closure_features_forward(const float *up, const float *un, const float *cn, int64_t nx, int64_t ny,
+                                     int64_t nz, int r, const double *w, const double *scales,
+                                     const ClosureFeatBufs &b, __nv_bfloat16 *x, cudaStream_t s);
+gbst_status closure_features_adjoint(const __nv_bfloat16 *dx, int64_t nx, int64_t ny, int64_t nz, int r,
+                                     const double *w, const double *scales, const ClosureFeatBufs &b, float *g_up,
+                                     float *g_un, cudaStream_t s);
+bool closure_has_features(gbst_closure c);
+gbst_status rollout_sums(const float *u, const float *ref, int64_t n, double *sums, cudaStream_t s);
+gbst_status rollout_grad(float *u, const float *ref, int64_t n, const double *sums, double scale, cudaStream_t s);
+gbst_status dense_axpy(float *y, const float *x, float a, int64_t n, cudaStream_t s);
+gbst_status closure_features_values(const float *up, const float *un, int64_t nx, int64_t ny, int64_t nz,
+                                    const ClosureFeatBufs &b, float *out, cudaStream_t s);
 
 // Tensor-map encoding through the driver entry point.
 // Tiled tensor map of a 4D BF16 tensor (dims innermost first; strides in bytes of dims 1..3).

@@ -82,20 +82,50 @@ SimpleFn simple_for_r(int R)
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_halo_copies(const GridDev *grids, const CopyBox *boxes, int parity, int es)
+// dmp.swap face copies, one box per blockIdx.y.  Rows of ex elements: boxes with
+// long rows (faces normal to y or z) give each warp one row at a time, moved in
+// 16-byte pieces when the row's two ends allow it; boxes with short rows (faces
+// normal to x, ex = r) give each thread one (row, element) pair.  Index
+// arithmetic is 32-bit (a box holds fewer than 2^31 elements; checked on the host).
+__global__ void __launch_bounds__(256) k_halo_copies(const GridDev *grids, const CopyBox *boxes, int parity, int es)
 {
     const CopyBox b = boxes[blockIdx.y];
     const GridDev &gs = grids[b.src_grid];
     const GridDev &gd = grids[b.dst_grid];
     const unsigned char *src = static_cast<const unsigned char *>(gs.buf[parity]) + b.src_off;
     unsigned char *dst = static_cast<unsigned char *>(gd.buf[parity]) + b.dst_off;
-    const int64_t n = b.ex * b.ey * b.ez;
+    const uint32_t ex = static_cast<uint32_t>(b.ex), ey = static_cast<uint32_t>(b.ey);
+    const uint32_t nrows = ey * static_cast<uint32_t>(b.ez);
     const int64_t sps = gs.pitch * es, spp = gs.pitch * gs.rows * es;
     const int64_t dps = gd.pitch * es, dpp = gd.pitch * gd.rows * es;
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t i = p % b.ex, j = (p / b.ex) % b.ey, k = p / (b.ex * b.ey);
-        const int64_t so = k * spp + j * sps + i * es, d = k * dpp + j * dps + i * es;
+    const uint32_t row_bytes = ex * static_cast<uint32_t>(es);
+    if (ex >= 32) {
+        const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        // row starts differ by multiples of the pitch (a multiple of 128 bytes)
+        const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) | row_bytes) & 15) == 0;
+        for (uint32_t row = blockIdx.x * nw + warp; row < nrows; row += gridDim.x * nw) {
+            const uint32_t j = row % ey, k = row / ey;
+            const unsigned char *s = src + k * spp + j * sps;
+            unsigned char *d = dst + k * dpp + j * dps;
+            if (vec) {
+                for (uint32_t c = lane; c < row_bytes / 16; c += 32)
+                    reinterpret_cast<uint4 *>(d)[c] = reinterpret_cast<const uint4 *>(s)[c];
+            } else if (es == 4) {
+                for (uint32_t i = lane; i < ex; i += 32)
+                    reinterpret_cast<uint32_t *>(d)[i] = reinterpret_cast<const uint32_t *>(s)[i];
+            } else {
+                for (uint32_t i = lane; i < ex; i += 32)
+                    reinterpret_cast<uint16_t *>(d)[i] = reinterpret_cast<const uint16_t *>(s)[i];
+            }
+        }
+        return;
+    }
+    const uint32_t n = nrows * ex;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const uint32_t row = t / ex, i = t - row * ex;
+        const uint32_t j = row % ey, k = row / ey;
+        const int64_t so = k * spp + j * sps + static_cast<int64_t>(i) * es;
+        const int64_t d = k * dpp + j * dps + static_cast<int64_t>(i) * es;
         if (es == 4)
             *reinterpret_cast<uint32_t *>(dst + d) = *reinterpret_cast<const uint32_t *>(src + so);
         else

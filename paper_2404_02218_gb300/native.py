@@ -105,6 +105,13 @@ def lib() -> ctypes.CDLL:
                 "stencil_variant_count": ([], i32),
                 "stencil_variant_info": ([i32, ctypes.c_char_p, ctypes.c_size_t], i32),
                 "gbst_reduce_dense_f64_noalloc": ([vp, i32, i64, i32, vp, vp], i32),
+                "stencil_wave_adjoint_dense": ([i32, i64, i64, i64, vp, vp, vp, vp, vp], i32),
+                "closure_set_features": ([H, i32, ctypes.POINTER(dbl), i32], i32),
+                "closure_set_trainable": ([H, vp, i64], i32),
+                "closure_feature_values": ([H, vp, vp, vp, i64, i64, i64, vp], i32),
+                "closure_backward": ([H, vp, vp, vp, i64, i64, i64, vp, vp, vp, i32], i32),
+                "stencil_closure_rollout_grad": ([H, vp, vp, i64, ctypes.POINTER(vp), i32, ctypes.POINTER(dbl)],
+                                                 i32),
                 "stencil_batch_create": ([ctypes.POINTER(gbst_desc), i32, ctypes.POINTER(H)], i32),
                 "stencil_batch_size": ([H, ctypes.POINTER(i32)], i32),
                 "stencil_system_create": ([ctypes.POINTER(gbst_desc), i32, ctypes.POINTER(dbl), ctypes.POINTER(H)],
@@ -269,6 +276,55 @@ def gbst_reduce_dense_f64_noalloc(x_ptr: int, dtype: int, n: int, kind: int, out
     _check(lib().gbst_reduce_dense_f64_noalloc(ctypes.c_void_p(x_ptr), dtype, int(n), kind,
                                                ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)),
            "gbst_reduce_dense_f64_noalloc")
+
+
+def stencil_wave_adjoint_dense(space_order: int, dims, kappa_ptr: int, lam_next_ptr: int, lam_cur_ptr: int,
+                               lam_prev_ptr: int = 0, stream: int = 0):
+    """Transpose of one leapfrog step on dense device arrays (dims = (nx, ny, nz))."""
+    nx, ny, nz = (int(v) for v in dims)
+    _check(lib().stencil_wave_adjoint_dense(space_order, nx, ny, nz, ctypes.c_void_p(kappa_ptr),
+                                            ctypes.c_void_p(lam_next_ptr), ctypes.c_void_p(lam_cur_ptr),
+                                            ctypes.c_void_p(lam_prev_ptr or None), ctypes.c_void_p(stream)),
+           "stencil_wave_adjoint_dense")
+
+
+def closure_set_trainable(c, mask=None):
+    """mask: uint8 numpy array of the parameter count (non-zero trains), or None for all."""
+    if mask is None:
+        _check(lib().closure_set_trainable(c, None, 0), "closure_set_trainable")
+        return
+    import numpy as _np
+    m = _np.ascontiguousarray(mask, dtype=_np.uint8)
+    _check(lib().closure_set_trainable(c, ctypes.c_void_p(m.ctypes.data), m.size), "closure_set_trainable")
+
+
+def closure_set_features(c, space_order: int, scales):
+    arr = (ctypes.c_double * 8)(*[float(v) for v in scales])
+    _check(lib().closure_set_features(c, space_order, arr, 8), "closure_set_features")
+
+
+def closure_feature_values(c, up_ptr: int, un_ptr: int, cn_ptr: int, dims, out_ptr: int):
+    nx, ny, nz = (int(v) for v in dims)
+    _check(lib().closure_feature_values(c, ctypes.c_void_p(up_ptr), ctypes.c_void_p(un_ptr), ctypes.c_void_p(cn_ptr),
+                                        nx, ny, nz, ctypes.c_void_p(out_ptr)), "closure_feature_values")
+
+
+def closure_backward(c, up_ptr: int, un_ptr: int, cn_ptr: int, dims, grad_corr_ptr: int, grad_up_ptr: int,
+                     grad_un_ptr: int, accumulate: bool = False):
+    nx, ny, nz = (int(v) for v in dims)
+    _check(lib().closure_backward(c, ctypes.c_void_p(up_ptr), ctypes.c_void_p(un_ptr), ctypes.c_void_p(cn_ptr),
+                                  nx, ny, nz, ctypes.c_void_p(grad_corr_ptr), ctypes.c_void_p(grad_up_ptr),
+                                  ctypes.c_void_p(grad_un_ptr), int(bool(accumulate))), "closure_backward")
+
+
+def stencil_closure_rollout_grad(h, u_cur_ptr: int, u_prev_ptr: int, step0: int, ref_ptrs) -> float:
+    """Rollout loss of the attached closure and its parameter gradient (kept in the closure)."""
+    arr = (ctypes.c_void_p * len(ref_ptrs))(*[ctypes.c_void_p(p) for p in ref_ptrs])
+    out = ctypes.c_double(0.0)
+    _check(lib().stencil_closure_rollout_grad(h, ctypes.c_void_p(u_cur_ptr), ctypes.c_void_p(u_prev_ptr), int(step0),
+                                              arr, len(ref_ptrs), ctypes.byref(out)),
+           "stencil_closure_rollout_grad")
+    return out.value
 
 
 def stencil_batch_create(descs) -> ctypes.c_void_p:

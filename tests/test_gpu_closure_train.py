@@ -1,0 +1,203 @@
+"""Training support of the learned closure on the GPU: the transpose of the
+leapfrog step (backpropagation through coarse-grid rollouts), against the FP64
+oracle's adjoint and by the dot-product identity with the library's own
+forward step."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _fields(shape, seed, n):
+    return [synthetic.uniform_field(seed + k, shape).astype(np.float64) * 2.0 - 1.0 for k in range(n)]
+
+
+@pytest.mark.parametrize("so", [2, 4, 8])
+@pytest.mark.parametrize("dims", [(37, 29, 23), (1, 1, 1), (130, 5, 9)])
+def test_wave_adjoint_matches_oracle(torch_cuda, so, dims):
+    torch = torch_cuda
+    from paper_2404_02218_gb300 import native as N
+    shape = tuple(reversed(dims))
+    kap = synthetic.uniform_field(70, shape).astype(np.float64) * 0.2 + 0.01
+    a, b = _fields(shape, 71, 2)
+    t = {k: torch.from_numpy(v.astype(np.float32)).cuda() for k, v in (("k", kap), ("a", a), ("b", b))}
+    prev = torch.full_like(t["a"], 7.0)
+    N.stencil_wave_adjoint_dense(so, dims, t["k"].data_ptr(), t["a"].data_ptr(), t["b"].data_ptr(),
+                                 prev.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    cur_ref, prev_ref = oracle.wave_step_adjoint(a.astype(np.float32), b.astype(np.float32),
+                                                 kap.astype(np.float32), so)
+    got = t["b"].double().cpu().numpy()
+    scale = np.max(np.abs(cur_ref))
+    assert np.max(np.abs(got - cur_ref)) <= 1e-5 * scale
+    assert np.array_equal(prev.cpu().numpy(), -a.astype(np.float32))
+
+
+@pytest.mark.parametrize("so", [2, 4, 8])
+def test_wave_adjoint_dot_product_with_the_library_step(torch_cuda, so):
+    """<T x, y> = <x, T^T y>: T is one step of the library's own wave sweep."""
+    torch = torch_cuda
+    from paper_2404_02218_gb300 import native as N
+    from paper_2404_02218_gb300.grid import Grid
+    dims = (45, 38, 31)
+    shape = tuple(reversed(dims))
+    h, dt = 10.0, 5e-4
+    c = 1500.0 + 3000.0 * synthetic.uniform_field(80, shape)
+    g = Grid(3, dims, so, "wave", h=h, dt=dt)
+    g.set_field("vel", c)
+    u, up, a, b = (torch.from_numpy(f.astype(np.float32)).cuda() for f in _fields(shape, 81, 4))
+    g.set_field("u", u)
+    g.set_field("u_prev", up)
+    g.run(1)
+    n1, n0 = torch.empty_like(u), torch.empty_like(u)
+    g.get_field("u", out=n1)
+    g.get_field("u_prev", out=n0)
+    g.close()
+    kap = torch.from_numpy(oracle.kappa_from_velocity(c, dt, h).astype(np.float32)).cuda()
+    cur, prev = b.clone(), torch.empty_like(a)
+    N.stencil_wave_adjoint_dense(so, dims, kap.data_ptr(), a.data_ptr(), cur.data_ptr(), prev.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    lhs = float((n1.double() * a.double()).sum() + (n0.double() * b.double()).sum())
+    rhs = float((u.double() * cur.double()).sum() + (up.double() * prev.double()).sum())
+    bound = 1e-5 * float(n1.double().norm() * a.double().norm() + u.double().norm() * cur.double().norm())
+    assert abs(lhs - rhs) <= bound
+
+
+# ---------------------------------------------------------------------------
+# Feature inputs, backward pass to the fields, rollout gradient, rollout training
+# ---------------------------------------------------------------------------
+
+def _closure8(torch, n, seed=7, t=2.0, scales=None):
+    from paper_2404_02218_gb300.closure import Closure, flatten_params
+    from oracle import closure as oc
+    cl = Closure(n, 1.0, cin=8)
+    sc = list(scales) if scales is not None else [1.0, 1.3, 0.8, 1.1, 0.02, 0.5, 2.0, 0.7]
+    cl.set_features(4, sc)
+    cl.set_out_scale(t)
+    p = oc.init_params(8, 16, seed)
+    cl.set_params(flatten_params(p))
+    return cl, p, sc
+
+
+def _bf16(torch, a):
+    """The BF16 rounding the library applies to the weights, in FP64."""
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+def test_feature_values_match_oracle(torch_cuda):
+    torch = torch_cuda
+    from oracle import closure as oc
+    dims = (37, 21, 19)
+    shape = tuple(reversed(dims))
+    up, un = _fields(shape, 90, 2)
+    cn = 0.3 + 0.7 * synthetic.uniform_field(92, shape).astype(np.float64)
+    cl, _, sc = _closure8(torch, int(np.prod(dims)))
+    t = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (up, un, cn)]
+    got = cl.feature_values(*t).double().cpu().numpy()
+    cl.close()
+    f32 = [a.astype(np.float32).astype(np.float64) for a in (up, un, cn)]
+    ref = oc.feature_channels(f32[0], f32[1], f32[2] ** 2, oracle.central_weights_f64(4), np.ones(8))
+    for k in range(8):
+        assert np.max(np.abs(got[k] - ref[k])) <= 1e-5 * np.max(np.abs(ref[k])), k
+
+
+def test_closure_backward_matches_oracle(torch_cuda):
+    """Cotangents of (u+, u^n) and the parameter gradient of one corrected step."""
+    torch = torch_cuda
+    from paper_2404_02218_gb300 import native as N
+    from oracle import closure as oc
+    dims = (40, 18, 16)
+    shape = tuple(reversed(dims))
+    up, un, gout = _fields(shape, 100, 3)
+    cn = 0.3 + 0.7 * synthetic.uniform_field(103, shape).astype(np.float64)
+    t_out = 2.0
+    cl, p, sc = _closure8(torch, int(np.prod(dims)), t=t_out)
+    T = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (up, un, cn, gout)]
+    g_up, g_un = torch.empty_like(T[0]), torch.empty_like(T[0])
+    N.closure_backward(cl.h, T[0].data_ptr(), T[1].data_ptr(), T[2].data_ptr(), dims, T[3].data_ptr(),
+                       g_up.data_ptr(), g_un.data_ptr(), False)
+    torch.cuda.synchronize()
+    grads = cl.get_grads()
+    cl.close()
+    pb = {k: _bf16(torch, v) for k, v in p.items()}
+    w = oracle.central_weights_f64(4)
+    x = oc.feature_channels(up, un, cn ** 2, w, sc)
+    _, cache = oc.forward(x, pb)
+    g, dx = oc.backward_with_input(cache, (gout / t_out)[None], pb)
+    r_up, r_un = oc.feature_channels_adjoint(dx, cn ** 2, w, sc)
+    r_up = r_up + gout
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    assert rel(g_up.double().cpu().numpy(), r_up) <= 3e-2
+    assert rel(g_un.double().cpu().numpy(), r_un) <= 3e-2
+    flat = np.concatenate([g[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    for lo, hi in ((0, 16 * 8 * 27), (16 * 8 * 27 + 16, 16 * 8 * 27 + 16 + 16 * 16 * 27)):
+        assert rel(grads[lo:hi], flat[lo:hi]) <= 3e-2
+
+
+def test_rollout_gradient_matches_oracle(torch_cuda):
+    """stencil_closure_rollout_grad (three corrected steps of an attached closure, no source)
+    against the FP64 chain rule of oracle.closure.rollout_loss_and_grads."""
+    torch = torch_cuda
+    from paper_2404_02218_gb300 import native as N
+    from paper_2404_02218_gb300.grid import Grid
+    from oracle import closure as oc
+    dims = (34, 27, 22)
+    shape = tuple(reversed(dims))
+    h, dt, c_ref = 20.0, 1.5e-3, 4500.0
+    c = 1500.0 + 3000.0 * synthetic.uniform_field(110, shape).astype(np.float64)
+    c32 = c.astype(np.float32)
+    u, up = _fields(shape, 111, 2)
+    refs = _fields(shape, 113, 3)
+    t_out = 3.0
+    cl, p, sc = _closure8(torch, int(np.prod(dims)), t=t_out, scales=[1.0, 1.0, 1.0, 1.0, 0.05, 2.0, 1.5, 0.5])
+    g = Grid(3, dims, 4, "wave", h=h, dt=dt, stream=cl.stream)
+    g.set_field("vel", c32)
+    N.stencil_attach_closure(g.h, cl.h, c_ref)
+    T = [torch.from_numpy(a.astype(np.float32)).cuda() for a in [u, up] + refs]
+    loss = N.stencil_closure_rollout_grad(g.h, T[0].data_ptr(), T[1].data_ptr(), 0, [r.data_ptr() for r in T[2:]])
+    grads = cl.get_grads()
+    g.close()
+    cl.close()
+    pb = {k: _bf16(torch, v) for k, v in p.items()}
+    c64 = c32.astype(np.float64)
+    kap = (c64 * dt / h) ** 2
+    cn2 = (c64 / c_ref) ** 2
+    f32 = [a.astype(np.float32).astype(np.float64) for a in [u, up] + refs]
+    rl, rg = oc.rollout_loss_and_grads(pb, f32[0], f32[1], kap, cn2, f32[2:], oracle.central_weights_f64(4), sc, t_out)
+    assert loss == pytest.approx(rl, rel=1e-2)
+    flat = np.concatenate([rg[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    for lo, hi in ((0, 16 * 8 * 27), (16 * 8 * 27 + 16, 16 * 8 * 27 + 16 + 16 * 16 * 27),
+                   (16 * 8 * 27 + 32 + 16 * 16 * 27, 16 * 8 * 27 + 32 + 16 * 16 * 27 + 16 * 27)):
+        assert float(np.linalg.norm(grads[lo:hi] - flat[lo:hi]) / np.linalg.norm(flat[lo:hi])) <= 5e-2
+
+
+def test_rollout_training_gains_over_the_plain_coarse_solve(torch_cuda):
+    """128^3 coarse / 256^3 fine, order 4, 300 coarse steps: the feature closure, trained on
+    rollouts of four seeded models after their source phase, reduces the relative L2 error of
+    the coarse solve at step 300 on a fifth model (test seed 99)."""
+    from paper_2404_02218_gb300.closure import PairConfig, evaluate, new_feature_closure, train_rollout
+    cfg = PairConfig(nc=128, steps=300)
+    cl = new_feature_closure(cfg, cfg.nc ** 3)
+    before = evaluate(cl, 99, cfg)
+    losses = train_rollout(cl, (10, 11, 12, 13), cfg, window=25, n_from=150, epochs=4, lr=3e-3)
+    after = evaluate(cl, 99, cfg)
+    cl.close()
+    print(f"closure 128^3 / 300 steps: plain {after['rel_l2_plain_coarse']:.4e}, initial {before['rel_l2_closure']:.4e}"
+          f" (gain {before['gain']:.3f}), trained {after['rel_l2_closure']:.4e} (gain {after['gain']:.3f}); "
+          f"{len(losses)} updates, loss {losses[0]:.3e} -> {losses[-1]:.3e}")
+    assert np.all(np.isfinite(losses))
+    assert after["gain"] > 1.0
