@@ -45,7 +45,7 @@ SOS = (2, 4, 8)
 STEPS_PER_RUN = 50
 BYTES_PER_PT = 8  # FP32 heat: read u, write u+
 # closure training in the secondary lines (rollout windows, epochs, Adam rate, trainable weights)
-CLOSURE_WINDOW, CLOSURE_EPOCHS, CLOSURE_LR, CLOSURE_TRAINABLE = 25, 4, 3e-3, "centre"
+CLOSURE_WINDOW, CLOSURE_EPOCHS, CLOSURE_LR, CLOSURE_TRAINABLE = 25, 4, 1e-3, "all"
 def workload() -> str:
     return f"heat3d {N}^3 FP32, space orders {'/'.join(map(str, SOS))}, 50 steps each, zero Dirichlet halo"
 

@@ -354,7 +354,7 @@ def rel_l2(a, b) -> float:
 
 
 def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, attach_at: int = 0,
-             detach_at: int | None = None):
+             detach_at: int | None = None, guard: float | None = 0.5, guard_every: int = 25):
     """Plain coarse, closure-corrected coarse and restricted fine solutions.
 
     Returns the relative L2 errors (vs the restricted fine solution) at the
@@ -362,6 +362,16 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, att
     and the errors at the intermediate checkpoints.  The closure corrects steps
     attach_at <= n < detach_at (outside that window the corrected run takes plain
     coarse steps).
+
+    Guard (the plain coarse solve as the fallback and judge of the corrected one):
+    every guard_every steps the FP64 L2 norms of the two coarse fields are
+    compared (stencil_reduce_f64); if the corrected field's norm exceeds the plain
+    one's by more than the relative bound `guard` (or is not finite), the closure
+    is detached and the corrected grid continues from the plain grid's levels, i.e.
+    as the plain solve.  Only growth trips it: an unstable correction injects
+    energy, while a good one may legitimately lower the norm (it removes the point
+    source's grid-scale near field, which the plain coarse solve overstates).
+    guard=None disables it.
     """
     import torch
     extra = ([attach_at] if attach_at > 0 else []) + ([detach_at] if detach_at else [])
@@ -371,7 +381,8 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, att
     g = Grid(3, shp, cfg.so, "wave", h=2 * cfg.hf, dt=pair.dtc, stream=closure.stream)
     g.set_field("vel", pair.cc)
     g.set_source(pair.src_c, cfg.f0, 1.0 / cfg.f0, 1.0 / 8.0)
-    if attach_at <= 0:
+    attached = attach_at <= 0
+    if attached:
         N.stencil_attach_closure(g.h, closure.h, C_REF)
     ref = torch.empty(shp, dtype=torch.float32, device="cuda")
     u_plain = torch.empty(shp, dtype=torch.float32, device="cuda")
@@ -379,26 +390,43 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, att
     curve = {}
     t_fine = t_plain = t_cl = 0.0
     done = 0
+    tripped = None
+    worst = 0.0
     for cp in checkpoints:
-        k = cp - done
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pair.fine.run(2 * k)
-        pair.fine.sync()
-        t_fine += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        pair.coarse.run(k)
-        pair.coarse.sync()
-        t_plain += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        g.run(k)
-        g.sync()
-        t_cl += time.perf_counter() - t0
-        done = cp
-        if cp == attach_at:
+        while done < cp:
+            k = min(cp - done, guard_every) if guard else cp - done
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pair.fine.run(2 * k)
+            pair.fine.sync()
+            t_fine += time.perf_counter() - t0
+            t0 = time.perf_counter()
+            pair.coarse.run(k)
+            pair.coarse.sync()
+            t_plain += time.perf_counter() - t0
+            t0 = time.perf_counter()
+            g.run(k)
+            g.sync()
+            t_cl += time.perf_counter() - t0
+            done += k
+            if guard and attached:
+                npl, ncl = pair.coarse.reduce("l2sq"), g.reduce("l2sq")
+                dev = (np.sqrt(ncl) - np.sqrt(npl)) / np.sqrt(npl) if npl > 0 else 0.0
+                worst = max(worst, dev)
+                if not np.isfinite(dev) or dev > guard:
+                    N.stencil_attach_closure(g.h, None, C_REF)
+                    attached = False
+                    tripped = done
+                    pair.coarse.get_field("u", out=u_plain)
+                    g.set_field("u", u_plain)
+                    pair.coarse.get_field("u_prev", out=u_plain)
+                    g.set_field("u_prev", u_plain)
+        if cp == attach_at and tripped is None:
             N.stencil_attach_closure(g.h, closure.h, C_REF)
+            attached = True
         if detach_at and cp == detach_at:
             N.stencil_attach_closure(g.h, None, C_REF)
+            attached = False
         pair.restrict(ref)
         pair.coarse.get_field("u", out=u_plain)
         g.get_field("u", out=u_cl)
@@ -407,6 +435,8 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, att
     out = {"rel_l2_plain_coarse": e_plain, "rel_l2_closure": e_cl, "gain": e_plain / e_cl,
            "seconds_fine": t_fine, "seconds_plain_coarse": t_plain, "seconds_closure": t_cl,
            "steps": cfg.steps, "coarse": pair.nc, "fine": pair.nf, "attach_at": attach_at, "detach_at": detach_at,
+           "guard": {"bound": guard, "every": guard_every, "tripped_at": tripped,
+                     "largest_norm_excess": worst},
            "curve": {str(k): {"plain": v[0], "closure": v[1]} for k, v in curve.items()}}
     g.close()
     pair.close()

@@ -293,6 +293,7 @@ struct gbst_grid_s {
     CopyBox *dboxes = nullptr;
     int nboxes = 0;
     int64_t max_box_elems = 0;
+    int copy_blocks = 0;  // blocks of one halo copy launch
     int64_t max_points = 0;
     Plan plan;
     int parity = 0;
@@ -756,6 +757,7 @@ gbst_status build_copies(gbst_handle h)
     if (h->max_box_elems >= (int64_t(1) << 31))
         return fail(GBST_EINVAL, "a halo face of %lld cells is too large (limit 2^31 - 1)",
                     static_cast<long long>(h->max_box_elems));
+    h->copy_blocks = halo_copy_blocks(boxes.data(), static_cast<int>(boxes.size()));
     if (!boxes.empty()) {
         h->dboxes = static_cast<CopyBox *>(dalloc(h, boxes.size() * sizeof(CopyBox)));
         if (!h->dboxes)
@@ -807,7 +809,7 @@ gbst_status enqueue_step(gbst_handle h, int parity, const float *srcval, int pro
         GBST_CUDA(cudaEventRecord(h->ev_fork, h->stream));
         GBST_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         cudaError_t e =
-            launch_halo_copies(h->dgrids, h->dboxes, h->nboxes, parity, h->es, h->max_box_elems, h->side);
+            launch_halo_copies(h->dgrids, h->dboxes, h->nboxes, parity, h->es, h->copy_blocks, h->side);
         if (e != cudaSuccess)
             return fail(GBST_ECUDA, "halo copy launch: %s", cudaGetErrorString(e));
         GBST_CUDA(cudaEventRecord(h->ev_join, h->side));
@@ -832,7 +834,7 @@ gbst_status enqueue_step(gbst_handle h, int parity, const float *srcval, int pro
     }
     if (h->nboxes > 0) {
         cudaError_t e =
-            launch_halo_copies(h->dgrids, h->dboxes, h->nboxes, parity, h->es, h->max_box_elems, h->stream);
+            launch_halo_copies(h->dgrids, h->dboxes, h->nboxes, parity, h->es, h->copy_blocks, h->stream);
         if (e != cudaSuccess)
             return fail(GBST_ECUDA, "halo copy launch: %s", cudaGetErrorString(e));
     }
@@ -1236,8 +1238,10 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
         return bail(st);
     TunedPlan tp{};
     StreamVariant cv;
+    // (a cached plan is used only if it honours an explicit request for two-step sweeps)
     if (d.tile == 0 && d.kernel != GBST_KERNEL_SIMPLE && tune_cache_find(h, &tp) &&
-        stream_variant_get(tp.variant, &cv) && variant_matches(h, cv)) {
+        stream_variant_get(tp.variant, &cv) && variant_matches(h, cv) &&
+        !(d.temporal_block == 2 && tb_allowed(h) && cv.tb != 2)) {
         h->dyn_pref = tp.dyn;
         st = build_plan(h, tp.variant, tp.txt, tp.zchunks, tp.ctas);
     } else {
@@ -1981,7 +1985,7 @@ static gbst_status reduce_api(gbst_handle h, int member, int kind, double *out)
         return fail(GBST_EINVAL, "the energy reduction is defined for the wave equation only");
     if (kind == GBST_RED_ENERGY && h->nboxes > 0) {
         // ghosts of u^{n-1}: swap / wrap them so the stencil in the energy sees neighbours
-        cudaError_t e = launch_halo_copies(h->dgrids, h->dboxes, h->nboxes, 1 - h->parity, h->es, h->max_box_elems,
+        cudaError_t e = launch_halo_copies(h->dgrids, h->dboxes, h->nboxes, 1 - h->parity, h->es, h->copy_blocks,
                                            h->stream);
         if (e != cudaSuccess)
             return fail(GBST_ECUDA, "halo copies: %s", cudaGetErrorString(e));

@@ -152,9 +152,12 @@ struct CopyBox {
     int64_t src_off, dst_off;  // bytes from the subdomain base pointers
     int src_grid, dst_grid;
     int64_t ex, ey, ez;        // extents (elements)
+    int blk0, nblk;            // this box's blocks [blk0, blk0 + nblk) of the copy launch
 };
+// Block counts of one copy launch: sets blk0 / nblk of every box, returns the total.
+int halo_copy_blocks(CopyBox *boxes, int nboxes);
 cudaError_t launch_halo_copies(const GridDev *grids, const CopyBox *boxes, int nboxes, int parity,
-                               int elem_size, int64_t max_box_elems, cudaStream_t s);
+                               int elem_size, int total_blocks, cudaStream_t s);
 
 // Field transfer kernels between dense (x fastest) and padded storage.
 // dense dtype: GBST_F32 / GBST_F64 / GBST_BF16.  Region: the subdomain interior

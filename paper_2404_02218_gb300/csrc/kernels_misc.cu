@@ -82,14 +82,29 @@ SimpleFn simple_for_r(int R)
 }
 
 // ---------------------------------------------------------------------------
-// dmp.swap face copies, one box per blockIdx.y.  Rows of ex elements: boxes with
-// long rows (faces normal to y or z) give each warp one row at a time, moved in
-// 16-byte pieces when the row's two ends allow it; boxes with short rows (faces
-// normal to x, ex = r) give each thread one (row, element) pair.  Index
+// dmp.swap face copies.  One 1D launch covers every box: box b owns blocks
+// [blk0, blk0 + nblk) (found by binary search over blk0).  Rows of ex elements:
+// boxes with long rows (faces normal to y or z) give each warp one row at a
+// time, moved in 16-byte pieces when the row's two ends allow it; boxes with
+// short rows (faces normal to x, ex = r) give each thread one row.  Index
 // arithmetic is 32-bit (a box holds fewer than 2^31 elements; checked on the host).
-__global__ void __launch_bounds__(256) k_halo_copies(const GridDev *grids, const CopyBox *boxes, int parity, int es)
+constexpr int kCopyThreads = 256;
+constexpr int kCopyLongRow = 32;  // rows of at least this many elements go warp-per-row
+
+__global__ void __launch_bounds__(kCopyThreads) k_halo_copies(const GridDev *grids, const CopyBox *boxes, int nboxes,
+                                                              int parity, int es)
 {
-    const CopyBox b = boxes[blockIdx.y];
+    int lo = 0, hi = nboxes - 1;
+    const int blk = static_cast<int>(blockIdx.x);
+    while (lo < hi) {  // last box with blk0 <= blk
+        const int mid = (lo + hi + 1) >> 1;
+        if (boxes[mid].blk0 <= blk)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const CopyBox b = boxes[lo];
+    const uint32_t bb = static_cast<uint32_t>(blk - b.blk0), nb = static_cast<uint32_t>(b.nblk);
     const GridDev &gs = grids[b.src_grid];
     const GridDev &gd = grids[b.dst_grid];
     const unsigned char *src = static_cast<const unsigned char *>(gs.buf[parity]) + b.src_off;
@@ -99,11 +114,11 @@ __global__ void __launch_bounds__(256) k_halo_copies(const GridDev *grids, const
     const int64_t sps = gs.pitch * es, spp = gs.pitch * gs.rows * es;
     const int64_t dps = gd.pitch * es, dpp = gd.pitch * gd.rows * es;
     const uint32_t row_bytes = ex * static_cast<uint32_t>(es);
-    if (ex >= 32) {
-        const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (ex >= kCopyLongRow) {
+        const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kCopyThreads / 32;
         // row starts differ by multiples of the pitch (a multiple of 128 bytes)
         const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) | row_bytes) & 15) == 0;
-        for (uint32_t row = blockIdx.x * nw + warp; row < nrows; row += gridDim.x * nw) {
+        for (uint32_t row = bb * nw + warp; row < nrows; row += nb * nw) {
             const uint32_t j = row % ey, k = row / ey;
             const unsigned char *s = src + k * spp + j * sps;
             unsigned char *d = dst + k * dpp + j * dps;
@@ -120,16 +135,16 @@ __global__ void __launch_bounds__(256) k_halo_copies(const GridDev *grids, const
         }
         return;
     }
-    const uint32_t n = nrows * ex;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const uint32_t row = t / ex, i = t - row * ex;
+    for (uint32_t row = bb * kCopyThreads + threadIdx.x; row < nrows; row += nb * kCopyThreads) {
         const uint32_t j = row % ey, k = row / ey;
-        const int64_t so = k * spp + j * sps + static_cast<int64_t>(i) * es;
-        const int64_t d = k * dpp + j * dps + static_cast<int64_t>(i) * es;
-        if (es == 4)
-            *reinterpret_cast<uint32_t *>(dst + d) = *reinterpret_cast<const uint32_t *>(src + so);
-        else
-            *reinterpret_cast<uint16_t *>(dst + d) = *reinterpret_cast<const uint16_t *>(src + so);
+        const unsigned char *s = src + k * spp + j * sps;
+        unsigned char *d = dst + k * dpp + j * dps;
+        for (uint32_t i = 0; i < ex; ++i) {
+            if (es == 4)
+                reinterpret_cast<uint32_t *>(d)[i] = reinterpret_cast<const uint32_t *>(s)[i];
+            else
+                reinterpret_cast<uint16_t *>(d)[i] = reinterpret_cast<const uint16_t *>(s)[i];
+        }
     }
 }
 
@@ -359,13 +374,27 @@ cudaError_t launch_simple_sweep(int R, int eq, int storage, const SweepArgs &a, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_halo_copies(const GridDev *grids, const CopyBox *boxes, int nboxes, int parity, int elem_size,
-                               int64_t max_box_elems, cudaStream_t s)
+int halo_copy_blocks(CopyBox *boxes, int nboxes)
 {
-    if (nboxes == 0)
+    // one row per warp (long rows) or per thread (short rows), at most 2048 blocks per box
+    int total = 0;
+    for (int i = 0; i < nboxes; ++i) {
+        CopyBox &b = boxes[i];
+        const int64_t rows = b.ey * b.ez;
+        const int64_t per_block = b.ex >= kCopyLongRow ? kCopyThreads / 32 : kCopyThreads;
+        b.nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2048, (rows + per_block - 1) / per_block)));
+        b.blk0 = total;
+        total += b.nblk;
+    }
+    return total;
+}
+
+cudaError_t launch_halo_copies(const GridDev *grids, const CopyBox *boxes, int nboxes, int parity, int elem_size,
+                               int total_blocks, cudaStream_t s)
+{
+    if (nboxes == 0 || total_blocks <= 0)
         return cudaSuccess;
-    dim3 grid(grid_for(max_box_elems, 256, 1024), nboxes);
-    k_halo_copies<<<grid, 256, 0, s>>>(grids, boxes, parity, elem_size);
+    k_halo_copies<<<total_blocks, kCopyThreads, 0, s>>>(grids, boxes, nboxes, parity, elem_size);
     return cudaGetLastError();
 }
 

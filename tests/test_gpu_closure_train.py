@@ -186,18 +186,45 @@ def test_rollout_gradient_matches_oracle(torch_cuda):
 
 
 def test_rollout_training_gains_over_the_plain_coarse_solve(torch_cuda):
-    """128^3 coarse / 256^3 fine, order 4, 300 coarse steps: the feature closure, trained on
+    """192^3 coarse / 384^3 fine, order 4, 300 coarse steps: the feature closure, trained on
     rollouts of four seeded models after their source phase, reduces the relative L2 error of
-    the coarse solve at step 300 on a fifth model (test seed 99)."""
+    the coarse solve at step 300 on a fifth model (test seed 99).  (On 128^3 and 160^3 grids
+    the waves reach the zero halo by then, whose position differs by half a fine cell between
+    the two grids; that error is not in the features and no trained gain is seen there.)"""
     from paper_2404_02218_gb300.closure import PairConfig, evaluate, new_feature_closure, train_rollout
-    cfg = PairConfig(nc=128, steps=300)
+    cfg = PairConfig(nc=192, steps=300)
     cl = new_feature_closure(cfg, cfg.nc ** 3)
     before = evaluate(cl, 99, cfg)
-    losses = train_rollout(cl, (10, 11, 12, 13), cfg, window=25, n_from=150, epochs=4, lr=3e-3)
+    losses = train_rollout(cl, (10, 11, 12, 13), cfg, window=25, n_from=200, epochs=4, lr=1e-3, trainable="all")
     after = evaluate(cl, 99, cfg)
     cl.close()
-    print(f"closure 128^3 / 300 steps: plain {after['rel_l2_plain_coarse']:.4e}, initial {before['rel_l2_closure']:.4e}"
+    print(f"closure 192^3 / 300 steps: plain {after['rel_l2_plain_coarse']:.4e}, initial {before['rel_l2_closure']:.4e}"
           f" (gain {before['gain']:.3f}), trained {after['rel_l2_closure']:.4e} (gain {after['gain']:.3f}); "
           f"{len(losses)} updates, loss {losses[0]:.3e} -> {losses[-1]:.3e}")
     assert np.all(np.isfinite(losses))
     assert after["gain"] > 1.0
+
+
+def test_guard_falls_back_to_the_plain_coarse_solve(torch_cuda):
+    """A closure that corrects far too much (the modified-equation weights times 300) is caught
+    by the guard: the FP64 norm of the corrected field exceeds the plain coarse one's by more
+    than the bound, the closure is detached and the run continues from the plain levels, so it ends
+    exactly as the plain coarse solve (gain 1)."""
+    from paper_2404_02218_gb300.closure import (Closure, PairConfig, evaluate, kappa_ref,
+                                                modified_equation_params, FineCoarsePair)
+    cfg = PairConfig(nc=96, steps=150)
+    pair = FineCoarsePair(99, cfg)
+    kref = kappa_ref(pair)
+    pair.close()
+    cl = Closure(cfg.nc ** 3, 1.0, cin=8)
+    sc = [1.0, 1.0, 1.0, 1.0, 1e-3, 1e-3, 1.0, 1.0]
+    cl.set_features(4, sc)
+    cl.set_out_scale(1.0)
+    cl.set_params(modified_equation_params(sc, 1.0, kref, a=300.0, b=300.0))
+    res = evaluate(cl, 99, cfg, checkpoints=(50, 100), guard=0.5, guard_every=10)
+    unguarded = evaluate(cl, 99, cfg, checkpoints=(50, 100), guard=None)
+    cl.close()
+    assert res["guard"]["tripped_at"] is not None
+    assert res["rel_l2_closure"] == res["rel_l2_plain_coarse"]
+    # without the guard the same closure ends far off (or not finite)
+    assert not (unguarded["rel_l2_closure"] <= 10 * res["rel_l2_closure"])
