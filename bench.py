@@ -65,7 +65,7 @@ def parse():
                    help="skip the secondary measurements (decomposition, wave FP32/BF16, batch, closure)")
     p.add_argument("--n", type=int, default=1024, help="grid edge (profiling runs use a smaller cube)")
     p.add_argument("--sos", default="2,4,8", help="space orders to run (profiling runs use one)")
-    p.add_argument("--case", default=None, choices=["wave3d_f32", "wave3d_bf16", "closure", "system3"],
+    p.add_argument("--case", default=None, choices=["wave3d_f32", "wave3d_bf16", "closure", "system3", "decomp"],
                    help="run one small named case instead of the bench (for profiler captures): "
                         "the order-8 layered wave at --n^3 in FP32 or BF16 storage, the closure "
                         "network's forward pass at --n^3, or the fused three-field order-4 system at "
@@ -574,6 +574,16 @@ def run_case(args):
         g = Grid(3, wc.dims, 8, "wave", h=wc.h, dt=wc.dt, storage=st, stream=stream)
         g.set_field("vel", c)
         g.set_source(wc.src, wc.f0, wc.t0, wc.amp)
+        if args.tune == "on":
+            g.tune(reps=2)
+        fn, pts = (lambda: g.run(10)), 10 * n ** 3
+    elif args.case == "decomp":
+        # heat, order of the first --sos entry, on a 2x2x2 decomposition (face exchange each step)
+        so = SOS[0]
+        case = synthetic.heat3d(n, so)
+        g = Grid(3, case.dims, so, "heat", dt=case.a, decomp=(2, 2, 2), stream=stream)
+        g.set_overlap(0)
+        g.set_field("u", synthetic.uniform_field_torch(case.seed, (n, n, n), "cuda"))
         if args.tune == "on":
             g.tune(reps=2)
         fn, pts = (lambda: g.run(10)), 10 * n ** 3

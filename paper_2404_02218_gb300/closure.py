@@ -354,7 +354,7 @@ def rel_l2(a, b) -> float:
 
 
 def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, attach_at: int = 0,
-             detach_at: int | None = None, guard: float | None = 0.5, guard_every: int = 25):
+             detach_at: int | None = None, guard: float | None = 2.0, guard_every: int = 25):
     """Plain coarse, closure-corrected coarse and restricted fine solutions.
 
     Returns the relative L2 errors (vs the restricted fine solution) at the
@@ -368,9 +368,11 @@ def evaluate(closure: Closure, seed: int, cfg: PairConfig, checkpoints=None, att
     compared (stencil_reduce_f64); if the corrected field's norm exceeds the plain
     one's by more than the relative bound `guard` (or is not finite), the closure
     is detached and the corrected grid continues from the plain grid's levels, i.e.
-    as the plain solve.  Only growth trips it: an unstable correction injects
-    energy, while a good one may legitimately lower the norm (it removes the point
-    source's grid-scale near field, which the plain coarse solve overstates).
+    as the plain solve.  It is a divergence detector: an unstable correction grows
+    without bound and trips any bound within a few checks, while a good correction
+    may legitimately move the norm far from the plain coarse one in the source phase
+    (the 4-channel network at 96^3 raises it by 57 % at step 25 while cutting the
+    error from 52 % to 16 %); hence the default of 2 (three times the plain norm).
     guard=None disables it.
     """
     import torch

@@ -86,7 +86,7 @@ SimpleFn simple_for_r(int R)
 // [blk0, blk0 + nblk) (found by binary search over blk0).  Rows of ex elements:
 // boxes with long rows (faces normal to y or z) give each warp one row at a
 // time, moved in 16-byte pieces when the row's two ends allow it; boxes with
-// short rows (faces normal to x, ex = r) give each thread one row.  Index
+// short rows (faces normal to x, ex = r) give each thread one element.  Index
 // arithmetic is 32-bit (a box holds fewer than 2^31 elements; checked on the host).
 constexpr int kCopyThreads = 256;
 constexpr int kCopyLongRow = 32;  // rows of at least this many elements go warp-per-row
@@ -135,16 +135,18 @@ __global__ void __launch_bounds__(kCopyThreads) k_halo_copies(const GridDev *gri
         }
         return;
     }
-    for (uint32_t row = bb * kCopyThreads + threadIdx.x; row < nrows; row += nb * kCopyThreads) {
+    // short rows: consecutive threads take consecutive elements of consecutive rows, so a
+    // warp's loads and stores cover whole rows' bytes (32 / ex rows per instruction)
+    const uint32_t n = nrows * ex;
+    for (uint32_t t = bb * kCopyThreads + threadIdx.x; t < n; t += nb * kCopyThreads) {
+        const uint32_t row = t / ex, i = t - row * ex;
         const uint32_t j = row % ey, k = row / ey;
-        const unsigned char *s = src + k * spp + j * sps;
-        unsigned char *d = dst + k * dpp + j * dps;
-        for (uint32_t i = 0; i < ex; ++i) {
-            if (es == 4)
-                reinterpret_cast<uint32_t *>(d)[i] = reinterpret_cast<const uint32_t *>(s)[i];
-            else
-                reinterpret_cast<uint16_t *>(d)[i] = reinterpret_cast<const uint16_t *>(s)[i];
-        }
+        const int64_t so = k * spp + j * sps + static_cast<int64_t>(i) * es;
+        const int64_t d = k * dpp + j * dps + static_cast<int64_t>(i) * es;
+        if (es == 4)
+            *reinterpret_cast<uint32_t *>(dst + d) = *reinterpret_cast<const uint32_t *>(src + so);
+        else
+            *reinterpret_cast<uint16_t *>(dst + d) = *reinterpret_cast<const uint16_t *>(src + so);
     }
 }
 
@@ -380,9 +382,10 @@ int halo_copy_blocks(CopyBox *boxes, int nboxes)
     int total = 0;
     for (int i = 0; i < nboxes; ++i) {
         CopyBox &b = boxes[i];
-        const int64_t rows = b.ey * b.ez;
+        // long rows: one per warp; short rows: one element per thread
+        const int64_t work = b.ex >= kCopyLongRow ? b.ey * b.ez : b.ex * b.ey * b.ez;
         const int64_t per_block = b.ex >= kCopyLongRow ? kCopyThreads / 32 : kCopyThreads;
-        b.nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2048, (rows + per_block - 1) / per_block)));
+        b.nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2048, (work + per_block - 1) / per_block)));
         b.blk0 = total;
         total += b.nblk;
     }

@@ -221,7 +221,7 @@ def test_guard_falls_back_to_the_plain_coarse_solve(torch_cuda):
     cl.set_features(4, sc)
     cl.set_out_scale(1.0)
     cl.set_params(modified_equation_params(sc, 1.0, kref, a=300.0, b=300.0))
-    res = evaluate(cl, 99, cfg, checkpoints=(50, 100), guard=0.5, guard_every=10)
+    res = evaluate(cl, 99, cfg, checkpoints=(50, 100), guard=2.0, guard_every=10)
     unguarded = evaluate(cl, 99, cfg, checkpoints=(50, 100), guard=None)
     cl.close()
     assert res["guard"]["tripped_at"] is not None
