@@ -479,6 +479,111 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     }
 }
 
+// Last layer (16 channels -> 1) on the CUDA cores.  A tensor-core tile would pad
+// the single output channel to 16 (the MMA's smallest N); here a CTA owns a
+// 64 x 8 (x, y) tile and marches along z, each thread four columns x = x0 + tx +
+// 16 j (j = 0..3) of one row.  Every input plane is read once from shared memory
+// (the 3 x 3 neighbourhood of each column, 16 channels as 8 pairs) and feeds the
+// three output planes it touches -- z+1, z and z-1 -- through three accumulators
+// per column, in packed FP32x2 FMAs over channel pairs; each weight pair is read
+// once per plane for the four columns.  Output plane z-1 is then complete.  BF16
+// weights (the forward layout [tap][8][16], row 0), FP32 accumulation, zero padding.
+constexpr int T1X = 64, T1Y = 8, T1NT = 16 * T1Y, H1X = T1X + 2, H1Y = T1Y + 2;
+constexpr int P1PTS = H1X * H1Y, P1BYTES = P1PTS * 32, N1SLOT = 3, Z1CH = 16;
+
+__device__ __forceinline__ void load_plane1(unsigned char *slot, const __nv_bfloat16 *in, Dims d, int x0, int y0,
+                                            int z)
+{
+    const bool zin = z >= 0 && z < d.nz;
+    for (int idx = threadIdx.x; idx < P1PTS * 2; idx += T1NT) {
+        const int pt = idx >> 1, half = idx & 1;
+        const int gx = x0 - 1 + pt % H1X, gy = y0 - 1 + pt / H1X;
+        const bool valid = zin && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+        const __nv_bfloat16 *src =
+            valid ? in + ((static_cast<int64_t>(z) * d.ny + gy) * d.nx + gx) * CH + half * 8 : in;
+        cp_async16(smem_addr(slot + pt * 32 + half * 16), src, valid);
+    }
+}
+
+__global__ void __launch_bounds__(T1NT) k_conv_out1(const __nv_bfloat16 *in, const __nv_bfloat16 *wt,
+                                                     const float *bias, Dims d, float *out)
+{
+    __shared__ float2 w2[27][CH / 2];  // [tap][channel pair]
+    extern __shared__ __align__(128) unsigned char ring[];
+    const int tiles_x = (d.nx + T1X - 1) / T1X;
+    const int x0 = (blockIdx.x % tiles_x) * T1X, y0 = (blockIdx.x / tiles_x) * T1Y;
+    const int z0 = blockIdx.y * Z1CH, z1 = min(d.nz, z0 + Z1CH);
+    for (int i = threadIdx.x; i < 27 * CH / 2; i += T1NT) {
+        const int t = i / (CH / 2), k = i % (CH / 2);
+        w2[t][k] = make_float2(__bfloat162float(wt[t * 8 * CH + 2 * k]), __bfloat162float(wt[t * 8 * CH + 2 * k + 1]));
+    }
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int y = y0 + ty;
+    const float b = bias ? bias[0] : 0.f;
+    const int nin = z1 - z0 + 2;  // input planes z0 - 1 .. z1
+    load_plane1(ring, in, d, x0, y0, z0 - 1);
+    cp_commit();
+    load_plane1(ring + P1BYTES, in, d, x0, y0, z0);
+    cp_commit();
+    // accumulators of output planes zi - 1 (lo), zi (mid), zi + 1 (hi), per column j (pair sums)
+    float2 lo[4], mid[4], hi[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        lo[j] = mid[j] = hi[j] = make_float2(0.f, 0.f);
+    for (int q = 0; q < nin; ++q) {
+        const int zi = z0 - 1 + q;
+        if (q + 2 < nin)
+            load_plane1(ring + ((q + 2) % N1SLOT) * P1BYTES, in, d, x0, y0, zi + 2);
+        cp_commit();
+        cp_wait<2>();  // plane q has landed (the two newer groups may be in flight)
+        __syncthreads();
+        const unsigned char *pl = ring + (q % N1SLOT) * P1BYTES;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int t = dy * 3 + dx;
+                uint32_t v[4][8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned char *pp = pl + ((ty + dy) * H1X + tx + 16 * j + dx) * 32;
+                    const uint4 a = *reinterpret_cast<const uint4 *>(pp);
+                    const uint4 c = *reinterpret_cast<const uint4 *>(pp + 16);
+                    v[j][0] = a.x, v[j][1] = a.y, v[j][2] = a.z, v[j][3] = a.w;
+                    v[j][4] = c.x, v[j][5] = c.y, v[j][6] = c.z, v[j][7] = c.w;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    // input plane zi reaches output zi + 1 through tap dz = 0, zi through dz = 1,
+                    // zi - 1 through dz = 2
+                    const float2 wh = w2[t][k], wm = w2[9 + t][k], wl = w2[18 + t][k];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float2 x2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v[j][k]));
+                        hi[j] = __ffma2_rn(wh, x2, hi[j]);
+                        mid[j] = __ffma2_rn(wm, x2, mid[j]);
+                        lo[j] = __ffma2_rn(wl, x2, lo[j]);
+                    }
+                }
+            }
+        __syncthreads();  // the slot of plane q is refilled two iterations later
+        if (zi - 1 >= z0 && y < d.ny) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int x = x0 + tx + 16 * j;
+                if (x < d.nx)
+                    out[(static_cast<int64_t>(zi - 1) * d.ny + y) * d.nx + x] = (lo[j].x + lo[j].y) + b;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            lo[j] = mid[j];
+            mid[j] = hi[j];
+            hi[j] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
 struct WgradArgs {
     const __nv_bfloat16 *x;   // layer input [z][y][x][16]
     const __nv_bfloat16 *dz;  // output gradient [z][y][x][16]
@@ -830,6 +935,21 @@ cudaError_t launch_wgrad(const WgradArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_conv_out1(const ConvArgs &a, cudaStream_t s)
+{
+    static bool attr = false;
+    const int smem = N1SLOT * P1BYTES;
+    if (!attr) {
+        cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_conv_out1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+        attr = true;
+    }
+    const int tiles = ((a.d.nx + T1X - 1) / T1X) * ((a.d.ny + T1Y - 1) / T1Y);
+    dim3 grid(tiles, (a.d.nz + Z1CH - 1) / Z1CH);
+    k_conv_out1<<<grid, T1NT, smem, s>>>(a.in, a.wt, a.bias, a.d, a.out_f32);
+    return cudaGetLastError();
+}
+
 gbst_status check_dims(gbst_closure c, int64_t nx, int64_t ny, int64_t nz, Dims *d)
 {
     if (nx < 1 || ny < 1 || nz < 1 || nx * ny * nz > c->max_pts || nx > (1 << 30) || ny > (1 << 30) ||
@@ -893,8 +1013,8 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     b.bias = c->p + c->off[5];
     b.out_f32 = c->o;
     b.cout_valid = 1;
-    if (e == cudaSuccess)
-        e = conv<8, EPI_LINEAR_F32>(c, b);
+    if (e == cudaSuccess)  // the tcgen05 path runs the one-channel last layer on the CUDA cores
+        e = c->conv_impl == 0 ? launch_conv_out1(b, c->stream) : conv<8, EPI_LINEAR_F32>(c, b);
     return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
 }
 

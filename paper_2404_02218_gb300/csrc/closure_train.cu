@@ -29,6 +29,21 @@ constexpr int kThr = 256;
 
 inline int blocks_for_dense(int64_t n) { return static_cast<int>(std::min<int64_t>(65535 * 8, (n + kThr - 1) / kThr)); }
 
+// Stencil kernels: threads along x, blocks over (x segments, y, z), so that no
+// point pays an integer division for its coordinates.
+constexpr int kDX = 128;
+inline dim3 dense_grid(const DenseDims &d)
+{
+    return dim3(static_cast<unsigned>((d.nx + kDX - 1) / kDX), static_cast<unsigned>(std::min(d.ny, 65535)),
+                static_cast<unsigned>(std::min(d.nz, 65535)));
+}
+// Every interior point (x, y, z) of d once, with its linear index p, over dense_grid(d).
+#define GBST_DENSE_POINTS(d)                                                                                   \
+    for (int z = blockIdx.z; z < (d).nz; z += gridDim.z)                                                       \
+        for (int y = blockIdx.y; y < (d).ny; y += gridDim.y)                                                   \
+            for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < (d).nx; x += gridDim.x * blockDim.x)       \
+                if (const int64_t p = (static_cast<int64_t>(z) * (d).ny + y) * (d).nx + x; true)
+
 // out[p] (=|+=) alpha * post[p] * sum_axes sum_{m=-R..R} w_|m| (pre * in)[p + m e_axis]
 // with zero outside the interior; pre / post may be null (factor 1).
 template <int R>
@@ -38,13 +53,8 @@ __global__ void __launch_bounds__(kThr) k_star(DenseDims d, const float *__restr
                                                float *__restrict__ out)
 {
     const float w[5] = {w03.x, w03.y, w03.z, w03.w, w4};
-    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
     const int64_t sy = d.nx, sz = static_cast<int64_t>(d.nx) * d.ny;
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * kThr) {
-        const int x = static_cast<int>(p % d.nx);
-        const int y = static_cast<int>((p / d.nx) % d.ny);
-        const int z = static_cast<int>(p / sz);
+    GBST_DENSE_POINTS(d) {
         auto val = [&](int64_t q) { return pre ? pre[q] * in[q] : in[q]; };
         float s = 3.0f * w[0] * val(p);
 #pragma unroll
@@ -73,13 +83,8 @@ __global__ void __launch_bounds__(kThr) k_wave_adjoint(DenseDims d, const float 
                                                        float *__restrict__ lam_cur, float *__restrict__ lam_prev)
 {
     const float w[5] = {w03.x, w03.y, w03.z, w03.w, w4};
-    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
     const int64_t sy = d.nx, sz = static_cast<int64_t>(d.nx) * d.ny;
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * kThr) {
-        const int x = static_cast<int>(p % d.nx);
-        const int y = static_cast<int>((p / d.nx) % d.ny);
-        const int z = static_cast<int>(p / sz);
+    GBST_DENSE_POINTS(d) {
         auto val = [&](int64_t q) { return kappa[q] * lam_next[q]; };
         float s = 3.0f * w[0] * val(p);
 #pragma unroll
@@ -116,11 +121,7 @@ __global__ void __launch_bounds__(kThr) k_cn2_grads(DenseDims d, const float *__
                                                     float *__restrict__ g0, float *__restrict__ g1,
                                                     float *__restrict__ g2)
 {
-    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * kThr) {
-        const int x = static_cast<int>(p % d.nx), y = static_cast<int>((p / d.nx) % d.ny);
-        const int z = static_cast<int>(p / (static_cast<int64_t>(d.nx) * d.ny));
+    GBST_DENSE_POINTS(d) {
         const float c = cn[p];
         cn2[p] = c * c;
         float *g[3] = {g0, g1, g2};
@@ -142,11 +143,7 @@ __global__ void __launch_bounds__(kThr) k_pack_features(DenseDims d, const float
                                                         const float *__restrict__ g1, const float *__restrict__ g2,
                                                         FeatScales sc, __nv_bfloat16 *__restrict__ xout)
 {
-    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * kThr) {
-        const int x = static_cast<int>(p % d.nx), y = static_cast<int>((p / d.nx) % d.ny);
-        const int z = static_cast<int>(p / (static_cast<int64_t>(d.nx) * d.ny));
+    GBST_DENSE_POINTS(d) {
         const float c2 = cn2[p], a = up[p], b = un[p];
         const float ga[3] = {g0[p], g1[p], g2[p]};
         float f6 = 0.0f, gabs = 0.0f;
@@ -157,13 +154,16 @@ __global__ void __launch_bounds__(kThr) k_pack_features(DenseDims d, const float
             gabs += fabsf(ga[ax]);
         }
         const float f[8] = {a, b, c2 * a, c2 * b, t6[p], t5[p], f6, gabs * lu[p]};
-        __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(xout + p * 16);
+        uint32_t w4[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            o[k] = __floats2bfloat162_rn(sc.s[2 * k] * f[2 * k], sc.s[2 * k + 1] * f[2 * k + 1]);
-#pragma unroll
-        for (int k = 4; k < 8; ++k)
-            o[k] = __floats2bfloat162_rn(0.0f, 0.0f);
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(sc.s[2 * k] * f[2 * k], sc.s[2 * k + 1] * f[2 * k + 1]);
+            w4[k] = *reinterpret_cast<const uint32_t *>(&b2);
+        }
+        // channels 0-7, then 8-15 (zero): two 16-byte stores
+        uint4 *o = reinterpret_cast<uint4 *>(xout + p * 16);
+        o[0] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        o[1] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -175,11 +175,7 @@ __global__ void __launch_bounds__(kThr) k_feature_values(DenseDims d, const floa
                                                          const float *__restrict__ g1, const float *__restrict__ g2,
                                                          float *__restrict__ out)
 {
-    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * kThr) {
-        const int x = static_cast<int>(p % d.nx), y = static_cast<int>((p / d.nx) % d.ny);
-        const int z = static_cast<int>(p / (static_cast<int64_t>(d.nx) * d.ny));
+    GBST_DENSE_POINTS(d) {
         const float c2 = cn2[p], a = up[p], b = un[p];
         const float ga[3] = {g0[p], g1[p], g2[p]};
         float f6 = 0.0f, gabs = 0.0f;
@@ -192,7 +188,7 @@ __global__ void __launch_bounds__(kThr) k_feature_values(DenseDims d, const floa
         const float f[8] = {a, b, c2 * a, c2 * b, t6[p], t5[p], f6, gabs * lu[p]};
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-            out[k * n + p] = f[k];
+            out[k * (static_cast<int64_t>(d.nx) * d.ny * d.nz) + p] = f[k];
     }
 }
 
@@ -235,12 +231,8 @@ __global__ void __launch_bounds__(kThr) k_div_acc(DenseDims d, const float *__re
                                                   const float *__restrict__ g0, const float *__restrict__ g1,
                                                   const float *__restrict__ g2, float alpha, float *__restrict__ out)
 {
-    const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
     const float *g[3] = {g0, g1, g2};
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(kThr) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * kThr) {
-        const int x = static_cast<int>(p % d.nx), y = static_cast<int>((p / d.nx) % d.ny);
-        const int z = static_cast<int>(p / (static_cast<int64_t>(d.nx) * d.ny));
+    GBST_DENSE_POINTS(d) {
         float s = 0.0f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -337,10 +329,10 @@ gbst_status dense_star(int r, const double *w, int64_t nx, int64_t ny, int64_t n
     const float a = static_cast<float>(alpha);
     const int acc = accumulate ? 1 : 0;
     switch (r) {
-    case 1: k_star<1><<<blocks, kThr, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
-    case 2: k_star<2><<<blocks, kThr, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
-    case 3: k_star<3><<<blocks, kThr, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
-    default: k_star<4><<<blocks, kThr, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
+    case 1: k_star<1><<<dense_grid(d), kDX, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
+    case 2: k_star<2><<<dense_grid(d), kDX, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
+    case 3: k_star<3><<<dense_grid(d), kDX, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
+    default: k_star<4><<<dense_grid(d), kDX, 0, s>>>(d, in, pre, post, w03, wf[4], a, acc, out); break;
     }
     return launched("dense stencil");
 }
@@ -368,7 +360,7 @@ gbst_status closure_features_forward(const float *up, const float *un, const flo
     if (st != GBST_OK)
         return st;
     const int blocks = blocks_for_dense(nx * ny * nz);
-    k_cn2_grads<<<blocks, kThr, 0, s>>>(d, cn, b.cn2, b.g[0], b.g[1], b.g[2]);
+    k_cn2_grads<<<dense_grid(d), kDX, 0, s>>>(d, cn, b.cn2, b.g[0], b.g[1], b.g[2]);
     if ((st = launched("closure features")) != GBST_OK)
         return st;
     if ((st = dense_star(r, w, nx, ny, nz, un, nullptr, nullptr, 1.0, false, b.lu, s)) != GBST_OK)
@@ -377,7 +369,7 @@ gbst_status closure_features_forward(const float *up, const float *un, const flo
         return st;
     if ((st = dense_star(3, kSixth, nx, ny, nz, un, nullptr, b.cn2, 1.0, false, b.t6, s)) != GBST_OK)
         return st;
-    k_pack_features<<<blocks, kThr, 0, s>>>(d, up, un, b.cn2, b.t6, b.t5, b.lu, b.g[0], b.g[1], b.g[2],
+    k_pack_features<<<dense_grid(d), kDX, 0, s>>>(d, up, un, b.cn2, b.t6, b.t5, b.lu, b.g[0], b.g[1], b.g[2],
                                             to_scales(scales), x);
     return launched("closure features");
 }
@@ -404,7 +396,7 @@ gbst_status closure_features_adjoint(const __nv_bfloat16 *dx, int64_t nx, int64_
         return st;
     if ((st = dense_star(r, w, nx, ny, nz, b.tmp, b.cn2, nullptr, 1.0, true, g_un, s)) != GBST_OK)
         return st;
-    k_div_acc<<<blocks, kThr, 0, s>>>(d, e6, b.g[0], b.g[1], b.g[2], -1.0f, g_un);
+    k_div_acc<<<dense_grid(d), kDX, 0, s>>>(d, e6, b.g[0], b.g[1], b.g[2], -1.0f, g_un);
     if ((st = launched("closure feature adjoint")) != GBST_OK)
         return st;
     return dense_star(r, w, nx, ny, nz, e7, nullptr, nullptr, 1.0, true, g_un, s);
@@ -419,7 +411,7 @@ gbst_status closure_features_values(const float *up, const float *un, int64_t nx
     gbst_status st = dense_dims(nx, ny, nz, &d, "closure feature values");
     if (st != GBST_OK)
         return st;
-    k_feature_values<<<blocks_for_dense(nx * ny * nz), kThr, 0, s>>>(d, up, un, b.cn2, b.t6, b.t5, b.lu, b.g[0],
+    k_feature_values<<<dense_grid(d), kDX, 0, s>>>(d, up, un, b.cn2, b.t6, b.t5, b.lu, b.g[0],
                                                                     b.g[1], b.g[2], out);
     return launched("closure feature values");
 }
@@ -470,9 +462,9 @@ extern "C" gbst_status stencil_wave_adjoint_dense(int space_order, int64_t nx, i
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int blocks = blocks_for_dense(nx * ny * nz);
     switch (space_order) {
-    case 2: k_wave_adjoint<1><<<blocks, kThr, 0, s>>>(d, kappa, lam_next, w03, wf[4], lam_cur, lam_prev); break;
-    case 4: k_wave_adjoint<2><<<blocks, kThr, 0, s>>>(d, kappa, lam_next, w03, wf[4], lam_cur, lam_prev); break;
-    default: k_wave_adjoint<4><<<blocks, kThr, 0, s>>>(d, kappa, lam_next, w03, wf[4], lam_cur, lam_prev); break;
+    case 2: k_wave_adjoint<1><<<dense_grid(d), kDX, 0, s>>>(d, kappa, lam_next, w03, wf[4], lam_cur, lam_prev); break;
+    case 4: k_wave_adjoint<2><<<dense_grid(d), kDX, 0, s>>>(d, kappa, lam_next, w03, wf[4], lam_cur, lam_prev); break;
+    default: k_wave_adjoint<4><<<dense_grid(d), kDX, 0, s>>>(d, kappa, lam_next, w03, wf[4], lam_cur, lam_prev); break;
     }
     return launched(who);
 }
