@@ -873,10 +873,16 @@ cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
     if (occ < 0) {
         const void *fn = reinterpret_cast<const void *>(&k_conv_tc<COUT, EPI>);
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        // the largest shared-memory carveout, so that two CTAs fit on an SM
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NTHREADS, SMEM) != cudaSuccess || occ < 1) {
             cudaGetLastError();
             occ = 2;
         }
+        // (the query answered 1 on GB300 although the launch's limits from registers and shared
+        // memory are both 2; a grid of two CTAs per SM runs as one wave when both fit and as two
+        // otherwise, as the units are strided over the grid)
+        occ = std::max(occ, 2);
     }
     // activation [z][y][x][16] BF16: dims (channel, x, y, z), boxes of 8 channels x 130 points x 3 rows
     CUtensorMap m;

@@ -38,7 +38,7 @@ constexpr int BOXY = RY + 2;             // input rows per plane (y halo 1 each 
 constexpr int ROWB = BOXX * 16;          // bytes of one row of 8 channels
 constexpr int HALF = (BOXY * ROWB + 127) / 128 * 128;  // one 8-channel box
 constexpr int SLOT = 2 * HALF;           // one input plane (both channel halves)
-constexpr int NS = 4;                    // plane slots: z-1, z, z+1 and one in flight
+constexpr int NS = 3;                    // plane slots: z-1, z, z+1 (89 KB per CTA: two CTAs per SM)
 constexpr int TCOLS = 2 * RY * 16;       // tensor-memory columns: two accumulator sets of RY x 16
 constexpr int WBYTES = 27 * 2 * 16 * 16; // weights: [tap][half][co 16][8 ci] BF16
 constexpr int HDR = 256;                 // barriers and flags
