@@ -232,7 +232,7 @@ def wave_accuracy_gpu(torch, g, wc, radius):
     return {"lo": lo, "hi": hi, "box": box, "outside_maxabs": out_max, "outside_l2sq": out_l2sq}
 
 
-def accuracy_vs_oracle(heat_gpu, wave_gpu, wc):
+def accuracy_vs_oracle(heat_gpu, wave_gpu, wc, heat2d_gpu=None, batch_gpu=None):
     """The FP64 oracle on the captured samples: heat boxes from their dependency cones, the wave
     box whole.  Returns the errors and the oracle's point-updates and seconds."""
     import oracle
@@ -275,6 +275,30 @@ def accuracy_vs_oracle(heat_gpu, wave_gpu, wc):
                 "sample": f"oracle on the {'x'.join(str(h - l) for l, h in zip(lo, hi))} box around the source "
                           f"(all {wc.nsteps} steps); outside it the GPU field is compared with 0",
                 "energy_drift_source_free": w.get("energy_drift")}
+    if heat2d_gpu is not None:
+        c1 = synthetic.heat2d_256()
+        t0 = time.perf_counter()
+        ref = oracle.heat_run(c1.initial(), c1.so, c1.a, c1.nsteps)
+        secs += time.perf_counter() - t0
+        res[f"heat2d_256_so2_{c1.nsteps}steps"] = {"max_rel": oracle.max_rel_error(heat2d_gpu, ref),
+                                                   "rel_l2": oracle.rel_l2_error(heat2d_gpu, ref),
+                                                   "sample": "whole grid"}
+    if batch_gpu:
+        cases = synthetic.batch_wave_cases()
+        worst = worst_l2 = 0.0
+        for i, got in batch_gpu.items():
+            c = cases[i]
+            kap = oracle.kappa_from_velocity(c.velocity(), c.dt, c.h)
+            z = np.zeros(kap.shape)
+            t0 = time.perf_counter()
+            _, ref = oracle.wave_run(z, z, kap, c.so, c.nsteps, src=c.src, f0=c.f0, t0=c.t0, amp=c.amp, dt=c.dt,
+                                     h=c.h)
+            secs += time.perf_counter() - t0
+            worst = max(worst, oracle.max_rel_error(got, ref))
+            worst_l2 = max(worst_l2, oracle.rel_l2_error(got, ref))
+        res[f"batch64_wave_so4_{cases[0].nsteps}steps"] = {
+            "max_rel": worst, "rel_l2": worst_l2,
+            "sample": f"members {sorted(batch_gpu)} (the three smallest) whole, one persistent launch"}
     return res, secs
 
 
@@ -420,6 +444,12 @@ def extras(torch, hbm: float, tune: bool, acc: dict | None = None):
         g.set_field("u", c1.initial())
         lat[use_graph] = timed_runs(torch, stream, lambda: g.run(c1.nsteps), reps=5)
         g.close()
+    if acc is not None:
+        g = Grid(2, c1.dims, c1.so, "heat", dt=c1.a, stream=stream)
+        g.set_field("u", c1.initial())
+        g.run(c1.nsteps)
+        acc["heat2d"] = g.get_field("u")
+        g.close()
     out["heat2d_256_so2_100steps"] = {"us_per_step_graph": 1e3 * lat[True] / c1.nsteps,
                                       "us_per_step_no_graph": 1e3 * lat[False] / c1.nsteps,
                                       "gpts_graph": c1.nsteps * 256 * 256 / lat[True] / 1e6,
@@ -505,6 +535,15 @@ def extras(torch, hbm: float, tune: bool, acc: dict | None = None):
                                           "launches_per_run": 1, "points": pts_step,
                                           "plan": json.loads(b.describe())}
     b.close()
+    if acc is not None:
+        # the configured run from rest (300 steps, one persistent launch): the three smallest members
+        b = Batch(3, members, 4, "wave", stream=stream)
+        setup(b)
+        b.set_persistent(True)
+        b.run(nsteps)
+        order = np.argsort([int(np.prod(cs.dims)) for cs in cases])[:3]
+        acc["batch"] = {int(i): b.get_field(int(i), "u") for i in order}
+        b.close()
     singles = []
     for cs in cases:
         g = Grid(3, cs.dims, 4, "wave", h=cs.h, dt=cs.dt, stream=stream)
@@ -852,7 +891,8 @@ def run_ours(args):
                "kind": "oracle", "sample": desc}
         if acc is not None:
             import synthetic
-            accuracy, acc_secs = accuracy_vs_oracle(acc.get("heat"), acc.get("wave"), synthetic.wave3d())
+            accuracy, acc_secs = accuracy_vs_oracle(acc.get("heat"), acc.get("wave"), synthetic.wave3d(),
+                                                    acc.get("heat2d"), acc.get("batch"))
             accuracy["oracle_seconds"] = acc_secs
             accuracy["tolerance"] = {"f32": 1e-5, "bf16": 2e-2, "measure": "max |gpu - oracle| / max |oracle|"}
 

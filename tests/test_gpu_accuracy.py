@@ -101,3 +101,27 @@ def test_heat3d_1024_50_steps_cone_boxes(torch_cuda, so):
     # max |u| <= 1 under a stable heat step from U[0,1): the absolute bound is a relative one
     print(f"heat 1024^3 order {so}, {case.nsteps} steps: max abs error on the boxes {worst:.3e}")
     assert worst <= 1e-5
+
+
+def test_batch64_300_steps_smallest_members_whole(torch_cuda):
+    """The 64-grid batch over its configured 300 steps in one persistent launch: the three
+    smallest members (96-110 points per axis) whole against the oracle."""
+    from paper_2404_02218_gb300.grid import Batch
+    cases = synthetic.batch_wave_cases()
+    b = Batch(3, [dict(dims=c.dims, h=c.h, dt=c.dt) for c in cases], 4, "wave")
+    for i, c in enumerate(cases):
+        b.set_field(i, "vel", c.velocity())
+        b.set_source(i, c.src, c.f0, c.t0, c.amp)
+    b.set_persistent(True)
+    b.run(cases[0].nsteps)
+    order = np.argsort([int(np.prod(c.dims)) for c in cases])
+    for i in order[:3]:
+        c = cases[int(i)]
+        kap = oracle.kappa_from_velocity(c.velocity(), c.dt, c.h)
+        z = np.zeros(kap.shape)
+        _, ref = oracle.wave_run(z, z, kap, 4, c.nsteps, src=c.src, f0=c.f0, t0=c.t0, amp=c.amp, dt=c.dt, h=c.h)
+        got = b.get_field(int(i), "u")
+        err = oracle.max_rel_error(got, ref)
+        print(f"batch member {int(i)} {c.dims}, {c.nsteps} steps: max rel {err:.3e}")
+        assert err <= 1e-5
+    b.close()
