@@ -256,9 +256,11 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *full = reinterpret_cast<uint64_t *>(sm);  // [NS] input plane landed
     uint64_t *empty = full + NS;                          // [NS] input plane no longer read
-    uint64_t *tfull = empty + NS;                         // [2] accumulator ready
-    uint64_t *tempty = tfull + 2;                         // [2] accumulator read out
-    uint64_t *fin = tempty + 2;                           // all issued MMAs complete
+    uint64_t *tfull = empty + NS;                         // [NACC] accumulator set ready
+    uint64_t *tempty = tfull + NACC;                      // [NACC] accumulator set read out
+    uint64_t *fin = tempty + NACC;                        // all issued MMAs complete
+    static_assert((2 * NS + 2 * NACC + 1) * 8 + 8 <= HDR, "barrier header");
+    static_assert(RY == 4, "the epilogue reads four rows per accumulator set");
     volatile int *abort_flag = reinterpret_cast<volatile int *>(fin + 1);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1) + 1;
     unsigned char *wsm = sm + HDR;
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
             bar_init(&full[s], 1);
             bar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             bar_init(&tfull[b], 1);
             bar_init(&tempty[b], NEPI);
         }
@@ -334,50 +336,51 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     } else if (warp == WMMA) {
         // ------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            int it = 0, waited = 0, ot = 0;
+            int it = 0, ot = 0;  // input planes consumed, outputs started (over all units)
             bool ok = true;
-            const uint32_t wbase = sa(wsm);
+            const uint32_t wlo = sdesc_lo(sa(wsm), 256), slot_lo0 = sdesc_lo(sa(slots), HALF);
+            constexpr uint32_t whi = sdesc_hi(128), ahi = sdesc_hi(128);
             for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
                 int y0, x0, z0, z1;
                 um.decode(u, y0, x0, z0, z1);
-                const int base = it, nout = z1 - z0;
-                for (int k = 0; k < nout && ok; ++k) {
-                    // input planes base+k .. base+k+2 (z-1, z, z+1) resident
-                    while (ok && waited <= base + k + 2) {
-                        ok = bar_wait(&full[waited % NS], (waited / NS) & 1, abort_flag);
-                        ++waited;
-                    }
-                    const int b = ot & 1;
-                    if (ok && ot >= 2)
-                        ok = bar_wait(&tempty[b], ((ot >> 1) - 1) & 1, abort_flag);
-                    if (!ok)
+                const int nout = z1 - z0;
+                // input plane j (z0 - 1 + j) feeds outputs j (dz = 0), j - 1 (dz = 1), j - 2 (dz = 2)
+                for (int j = 0; j < nout + 2; ++j, ++it) {
+                    const int s = it % NS;
+                    if (!(ok = bar_wait(&full[s], (it / NS) & 1, abort_flag)))
                         break;
                     fence_after();
-                    const uint32_t d = tbase + b * (RY * 16);
+                    const uint32_t alo = slot_lo0 + static_cast<uint32_t>(s * SLOT / 16);
 #pragma unroll
-                    for (int dz = 0; dz < 3; ++dz) {
-                        const uint32_t pa = sa(slots + ((base + k + dz) % NS) * SLOT);
+                    for (int dz = 2; dz >= 0; --dz) {
+                        const int k = j - dz;  // output index within the unit
+                        if (k < 0 || k >= nout)
+                            continue;
+                        const int o = ot + k, b = o % NACC;
+                        if (dz == 0 && o >= NACC) {  // first taps of output o: its set has been read out
+                            if (!(ok = bar_wait(&tempty[b], ((o / NACC) - 1) & 1, abort_flag)))
+                                break;
+                            fence_after();
+                        }
+                        const uint32_t d = tbase + b * (RY * 16);
 #pragma unroll
                         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                             for (int dx = 0; dx < 3; ++dx) {
                                 const int tap = (dz * 3 + dy) * 3 + dx;
-                                const uint64_t bd = sdesc(wbase + tap * 512, 256, 128);
 #pragma unroll
                                 for (int r = 0; r < RY; ++r)
-                                    mma_bf16(d + r * 16, sdesc(pa + (r + dy) * ROWB + dx * 16, HALF, 128), bd,
-                                             tap > 0 ? 1u : 0u);
+                                    mma_bf16_h(d + r * 16, alo + ((r + dy) * ROWB + dx * 16) / 16, ahi,
+                                               wlo + tap * 32, whi, (dz == 0 && dy == 0 && dx == 0) ? 0u : 1u);
                             }
+                        if (dz == 2)
+                            mma_commit(&tfull[b]);  // output o complete
                     }
-                    mma_commit(&tfull[b]);               // accumulator b holds output plane z0 + k
-                    mma_commit(&empty[(base + k) % NS]);  // input plane z0 + k - 1 is done
-                    ++ot;
+                    if (!ok)
+                        break;
+                    mma_commit(&empty[s]);  // plane read by all its MMAs
                 }
-                if (!ok)
-                    break;
-                mma_commit(&empty[(base + nout) % NS]);  // the unit's last two input planes
-                mma_commit(&empty[(base + nout + 1) % NS]);
-                it = base + nout + 2;
+                ot += nout;
             }
             // every issued MMA completes before the tensor memory is released
             mma_commit(fin);
@@ -401,15 +404,13 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
             um.decode(u, y0, x0, z0, z1);
             const int x = x0 + quad * 32 + lane;
             for (int z = z0; z < z1; ++z) {
-                const int b = ot & 1;
-                ok = __all_sync(0xffffffffu, bar_wait(&tfull[b], (ot >> 1) & 1, abort_flag));
+                const int b = ot % NACC;
+                ok = __all_sync(0xffffffffu, bar_wait(&tfull[b], (ot / NACC) & 1, abort_flag));
                 if (!ok)
                     break;
                 fence_after();
                 float vr[RY][8];
-#pragma unroll
-                for (int r = 0; r < RY; ++r)
-                    tmem_ld8(tbase + (static_cast<uint32_t>(quad * 32) << 16) + b * (RY * 16) + r * 16 + c0, vr[r]);
+                tmem_ld8x4(tbase + (static_cast<uint32_t>(quad * 32) << 16) + b * (RY * 16) + c0, 16, vr);
                 fence_before();
                 __syncwarp();
                 if (lane == 0)

@@ -10,18 +10,25 @@
 // a K-major, unswizzled tcgen05 operand: 8 points x 16 bytes form a contiguous
 // core matrix.  A_tap of row r is then just a shifted view of the plane slot
 // (start address + (r + dy) * row + dx * 16 bytes), no data movement per tap.
-// The weights of all taps sit in shared memory in the same layout.  The MMAs
-// of a plane are issued tap-major across the RY rows, so consecutive MMAs
-// accumulate into different tensor-memory columns (RY independent chains:
-// an M = 128, N = 16 MMA is short, and a single chain would wait on itself).
+// The weights of all taps sit in shared memory in the same layout.
+//
+// Input-stationary order: when input plane p has landed, its 27 taps are
+// issued at once into the three outputs that read it (p + 1 through dz = 0,
+// p through dz = 1, p - 1 through dz = 2; dz = 2 first, which completes output
+// p - 1), and the plane is released right after.  So a plane is read by the
+// tensor cores exactly once, the ring of NS slots keeps NS - 1 planes of
+// prefetch in flight, and four accumulator sets rotate: three being summed,
+// one being read out by the epilogue.  Within a tap the RY rows go to
+// different tensor-memory columns (RY independent chains: an M = 128, N = 16
+// MMA is short, and a single chain would wait on itself).
 //
 // Warp roles: warps 0-7 epilogue (warp w reads tensor-memory lanes
 // 32 (w & 3) .. +31 = points, channels 8 (w >> 2) .. +7 of each row), warp 8
-// TMA producer, warp 9 allocates 2 RY 16 tensor-memory columns (two
-// accumulator sets) and one lane issues the MMAs.
+// TMA producer, warp 9 allocates NACC RY 16 tensor-memory columns and one lane
+// issues the MMAs.
 // Pipelines: input plane ring (full / empty mbarriers; a tcgen05.commit frees
-// a plane once the MMAs reading it are done) and the accumulator pair
-// (tfull: commit after the 27 MMAs of a plane; tempty: the epilogue warps).
+// a plane once the MMAs reading it are done) and the accumulator sets
+// (tfull: commit after an output's last nine taps; tempty: the epilogue warps).
 // Every wait is bounded; on expiry the CTA sets the error word, lets issued
 // work finish (bounded) and releases its tensor memory.
 #pragma once
@@ -39,7 +46,8 @@ constexpr int ROWB = BOXX * 16;          // bytes of one row of 8 channels
 constexpr int HALF = (BOXY * ROWB + 127) / 128 * 128;  // one 8-channel box
 constexpr int SLOT = 2 * HALF;           // one input plane (both channel halves)
 constexpr int NS = 3;                    // plane slots: z-1, z, z+1 (89 KB per CTA: two CTAs per SM)
-constexpr int TCOLS = 2 * RY * 16;       // tensor-memory columns: two accumulator sets of RY x 16
+constexpr int NACC = 4;                  // accumulator sets: three outputs being summed, one read out
+constexpr int TCOLS = NACC * RY * 16;    // tensor-memory columns (256: two CTAs per SM fill the 512)
 constexpr int WBYTES = 27 * 2 * 16 * 16; // weights: [tap][half][co 16][8 ci] BF16
 constexpr int HDR = 256;                 // barriers and flags
 constexpr int SMEM = HDR + WBYTES + NS * SLOT;
@@ -120,6 +128,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// The same descriptor as two 32-bit halves, so that a per-tap offset is one
+// 32-bit add on the low half (start address field; offsets stay inside the slot).
+__device__ __forceinline__ uint32_t sdesc_lo(uint32_t addr, uint32_t lbo)
+{
+    return ((addr >> 4) & 0x3FFFu) | (((lbo >> 4) & 0x3FFFu) << 16);
+}
+constexpr uint32_t sdesc_hi(uint32_t sbo) { return ((sbo >> 4) & 0x3FFFu) | (1u << 14); }
+
 // Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = 16.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
@@ -130,6 +146,19 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+// The same MMA with the descriptors given as 32-bit halves.
+__device__ __forceinline__ void mma_bf16_h(uint32_t d_tmem, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                           uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "mov.b64 da, {%1, %2};\n\t"
+        "mov.b64 db, {%3, %4};\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d_tmem),
+        "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(kIdesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
@@ -149,6 +178,30 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 #pragma unroll
     for (int i = 0; i < 8; ++i)
         v[i] = __uint_as_float(r[i]);
+}
+
+// Four loads of 8 columns (one per output row) and a single wait: the values
+// pass through the wait (as read-write operands of an empty statement after
+// it), so no use can be scheduled before the loads have completed.
+__device__ __forceinline__ void tmem_ld8x4(uint32_t taddr, uint32_t stride, float (&v)[4][8])
+{
+    uint32_t r[4][8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]), "=r"(r[q][4]), "=r"(r[q][5]),
+                       "=r"(r[q][6]), "=r"(r[q][7])
+                     : "r"(taddr + q * stride));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        asm volatile(""
+                     : "+r"(r[q][0]), "+r"(r[q][1]), "+r"(r[q][2]), "+r"(r[q][3]), "+r"(r[q][4]), "+r"(r[q][5]),
+                       "+r"(r[q][6]), "+r"(r[q][7]));
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            v[q][i] = __uint_as_float(r[q][i]);
+    }
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
