@@ -284,7 +284,8 @@ gbst_status closure_set_loss_weight(gbst_closure c, double w);
 gbst_status closure_freeze_biases(gbst_closure c, int freeze);
 /* Convolution kernels: impl 0 (default) = tcgen05 MMAs with accumulators in
  * tensor memory, operands staged by TMA; impl 1 = the mma.sync kernels (kept
- * as an independent cross-check of the same arithmetic).  A bounded wait that
+ * as an independent cross-check of the same arithmetic); impl 2 = tcgen05 for
+ * the two hidden layers, the one-channel last layer on the CUDA cores.  A bounded wait that
  * expires in a tcgen05 kernel is reported as GBST_ETIMEOUT by the next
  * closure_loss_grad / closure_get_params / closure_get_grads. */
 gbst_status closure_set_conv_impl(gbst_closure c, int impl);

@@ -106,7 +106,8 @@ class Closure:
         return out
 
     def set_conv_impl(self, impl: int):
-        """0: tcgen05 convolutions (default); 1: mma.sync convolutions."""
+        """0: tcgen05 convolutions (default); 1: mma.sync convolutions; 2: tcgen05 for the
+        hidden layers, the one-channel last layer on the CUDA cores."""
         N.closure_set_conv_impl(self.h, impl)
 
     def close(self):

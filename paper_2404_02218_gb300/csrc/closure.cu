@@ -267,13 +267,16 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     unsigned char *slots = sm + HDR + WBYTES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // weights [tap][co][16 ci] -> [tap][half][co 0..15][8 ci]; rows co >= COUT stay zero
-    for (int i = threadIdx.x; i < 27 * 2 * 16; i += blockDim.x) {
-        const int tap = i >> 5, half = (i >> 4) & 1, co = i & 15;
+    // weights [tap][co][16 ci] -> [dy dx][half][block 0..4: dz = 2, 1, 0, 2, 1][co 0..15][8 ci];
+    // rows co >= COUT stay zero
+    for (int i = threadIdx.x; i < 9 * 2 * WBLK * 16; i += blockDim.x) {
+        const int co = i & 15, blk = (i >> 4) % WBLK, half = (i / (16 * WBLK)) & 1, t9 = i / (32 * WBLK);
+        const int dz = (5 - blk) % 3;
+        const int tap = dz * 9 + t9;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (co < COUT)
             v = *reinterpret_cast<const uint4 *>(a.wt + (tap * COUT + co) * CH + half * 8);
-        *reinterpret_cast<uint4 *>(wsm + ((tap * 2 + half) * 16 + co) * 16) = v;
+        *reinterpret_cast<uint4 *>(wsm + t9 * WTAP + half * WHALF + (blk * 16 + co) * 16) = v;
     }
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -301,6 +304,15 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     __syncthreads();
     fence_after();
     const uint32_t tbase = *tmem_slot;
+    if (warp < NEPI) {  // the MMAs only accumulate: every slot starts at zero
+        const uint32_t lanes = static_cast<uint32_t>((warp & 3) * 32) << 16;
+        for (int c = (warp >> 2) * 8; c < RY * ROWCOLS; c += 16)
+            tmem_zero8(tbase + lanes + c);
+        tmem_wait_st();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
 
     if (warp == WPROD) {
         // ---------------------------------------------------------- producer
@@ -335,61 +347,82 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
         }
     } else if (warp == WMMA) {
         // ------------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            int it = 0, ot = 0;  // input planes consumed, outputs started (over all units)
-            bool ok = true;
-            const uint32_t wlo = sdesc_lo(sa(wsm), 256), slot_lo0 = sdesc_lo(sa(slots), HALF);
-            constexpr uint32_t whi = sdesc_hi(128), ahi = sdesc_hi(128);
-            for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-                int y0, x0, z0, z1;
-                um.decode(u, y0, x0, z0, z1);
-                const int nout = z1 - z0;
-                // input plane j (z0 - 1 + j) feeds outputs j (dz = 0), j - 1 (dz = 1), j - 2 (dz = 2)
-                for (int j = 0; j < nout + 2; ++j, ++it) {
-                    const int s = it % NS;
-                    if (!(ok = bar_wait(&full[s], (it / NS) & 1, abort_flag)))
-                        break;
-                    fence_after();
-                    const uint32_t alo = slot_lo0 + static_cast<uint32_t>(s * SLOT / 16);
+        // (the whole warp runs the loop; elect.sync picks the issuing lane)
+        int it = 0, ot = 0;  // input planes consumed, outputs started (over all units)
+        bool ok = true;
+        const uint32_t wlo = sdesc_lo(sa(wsm), WHALF), slot_lo0 = sdesc_lo(sa(slots), HALF);
+        constexpr uint32_t whi = sdesc_hi(128), ahi = sdesc_hi(128);
+        for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            int y0, x0, z0, z1;
+            um.decode(u, y0, x0, z0, z1);
+            const int nout = z1 - z0;
+            // input plane j (z0 - 1 + j) feeds outputs j (dz = 0), j - 1 (dz = 1), j - 2 (dz = 2)
+            for (int j = 0; j < nout + 2; ++j, ++it) {
+                const int s = it % NS;
+                if (!(ok = __all_sync(0xffffffffu, bar_wait(&full[s], (it / NS) & 1, abort_flag))))
+                    break;
+                fence_after();
+                const uint32_t alo = slot_lo0 + static_cast<uint32_t>(s * SLOT / 16);
+                if (j >= 2 && j < nout) {
+                    // all three outputs inside the unit: one N = 48 MMA per tap and row
+                    const int o0 = ot + j;  // first taps of output o0: its slot has been read out
+                    if (o0 >= NACC) {
+                        if (!(ok = __all_sync(0xffffffffu,
+                                              bar_wait(&tempty[o0 % NACC], ((o0 / NACC) - 1) & 1, abort_flag))))
+                            break;
+                        fence_after();
+                    }
+                    const uint32_t wwin = static_cast<uint32_t>((2 - o0 % NACC) * 256 / 16);
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                            for (int r = 0; r < RY; ++r)
+                                mma_bf16_warp(tbase + r * ROWCOLS, alo + ((r + dy) * ROWB + dx * 16) / 16, ahi,
+                                              wlo + wwin + (dy * 3 + dx) * (WTAP / 16), whi, idesc_bf16(48));
+                    mma_commit_warp(&tfull[(o0 - 2) % NACC]);  // output o0 - 2 complete
+                } else {
+                    // a unit's first or last two planes: one N = 16 MMA per valid output
 #pragma unroll
                     for (int dz = 2; dz >= 0; --dz) {
                         const int k = j - dz;  // output index within the unit
                         if (k < 0 || k >= nout)
                             continue;
                         const int o = ot + k, b = o % NACC;
-                        if (dz == 0 && o >= NACC) {  // first taps of output o: its set has been read out
-                            if (!(ok = bar_wait(&tempty[b], ((o / NACC) - 1) & 1, abort_flag)))
+                        if (dz == 0 && o >= NACC) {
+                            if (!(ok = __all_sync(0xffffffffu,
+                                                  bar_wait(&tempty[b], ((o / NACC) - 1) & 1, abort_flag))))
                                 break;
                             fence_after();
                         }
-                        const uint32_t d = tbase + b * (RY * 16);
+                        const uint32_t wblk = static_cast<uint32_t>((2 - dz) * 256 / 16);
 #pragma unroll
                         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-                            for (int dx = 0; dx < 3; ++dx) {
-                                const int tap = (dz * 3 + dy) * 3 + dx;
+                            for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                                 for (int r = 0; r < RY; ++r)
-                                    mma_bf16_h(d + r * 16, alo + ((r + dy) * ROWB + dx * 16) / 16, ahi,
-                                               wlo + tap * 32, whi, (dz == 0 && dy == 0 && dx == 0) ? 0u : 1u);
-                            }
+                                    mma_bf16_warp(tbase + r * ROWCOLS + b * 16,
+                                                  alo + ((r + dy) * ROWB + dx * 16) / 16, ahi,
+                                                  wlo + wblk + (dy * 3 + dx) * (WTAP / 16), whi, idesc_bf16(16));
                         if (dz == 2)
-                            mma_commit(&tfull[b]);  // output o complete
+                            mma_commit_warp(&tfull[b]);  // output o complete
                     }
                     if (!ok)
                         break;
-                    mma_commit(&empty[s]);  // plane read by all its MMAs
                 }
-                ot += nout;
+                mma_commit_warp(&empty[s]);  // plane read by all its MMAs
             }
-            // every issued MMA completes before the tensor memory is released
-            mma_commit(fin);
-            const unsigned long long t0 = now_ns();
-            while (!bar_try(fin, 0) && now_ns() - t0 < 100000000ull) {
-            }
-            if (!ok)
-                atomicCAS(err, 0, static_cast<int>(kDevTimeoutTma));
+            ot += nout;
         }
+        // every issued MMA completes before the tensor memory is released
+        mma_commit_warp(fin);
+        const unsigned long long t0 = now_ns();
+        while (!bar_try(fin, 0) && now_ns() - t0 < 100000000ull) {
+        }
+        if (!ok && lane == 0)
+            atomicCAS(err, 0, static_cast<int>(kDevTimeoutTma));
     } else {
         // ---------------------------------------------------------- epilogue
         const int quad = warp & 3, c0 = (warp >> 2) * 8;  // points 32 quad .., channels c0 .. c0 + 7
@@ -410,7 +443,12 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                     break;
                 fence_after();
                 float vr[RY][8];
-                tmem_ld8x4(tbase + (static_cast<uint32_t>(quad * 32) << 16) + b * (RY * 16) + c0, 16, vr);
+                const uint32_t ta = tbase + (static_cast<uint32_t>(quad * 32) << 16) + b * 16 + c0;
+                tmem_ld8x4(ta, ROWCOLS, vr);
+#pragma unroll
+                for (int r = 0; r < RY; ++r)  // the slot starts the next output at zero
+                    tmem_zero8(ta + r * ROWCOLS);
+                tmem_wait_st();
                 fence_before();
                 __syncwarp();
                 if (lane == 0)
@@ -770,6 +808,13 @@ __global__ void k_seed(const float *g, float inv_t, int64_t n, __nv_bfloat16 *do
     }
 }
 
+__global__ void k_scale(float *dst, const float *src, float scale, int64_t n)
+{
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        dst[p] = scale * src[p];
+}
+
 __global__ void k_scale_add(float *dst, const float *src, float scale, int64_t n)
 {
     for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
@@ -805,7 +850,7 @@ struct gbst_closure_s {
     double out_scale = 1.0;     // target in network units: out_scale * (u_ref - u+)
     bool freeze_biases = false; // Adam leaves the biases unchanged
     double loss_weight = 1.0;   // factor on the loss (and its gradient) of the next loss_grad calls
-    int conv_impl = 0;          // 0: tcgen05 (tensor memory), 1: mma.sync (cross-check)
+    int conv_impl = 0;          // 0: tcgen05, 1: mma.sync, 2: tcgen05 with the last layer on the CUDA cores
     int *derr = nullptr;        // device error word of the tcgen05 convolutions
     unsigned char *trainable = nullptr;      // per-parameter Adam mask (null: all parameters train)
     unsigned char *trainable_buf = nullptr;  // its device storage
@@ -908,7 +953,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
 template <int COUT, int EPI>
 cudaError_t conv(gbst_closure c, const ConvArgs &a)
 {
-    return c->conv_impl == 0 ? launch_conv_tc<COUT, EPI>(a, c->derr, c->stream) : launch_conv<COUT, EPI>(a, c->stream);
+    return c->conv_impl != 1 ? launch_conv_tc<COUT, EPI>(a, c->derr, c->stream) : launch_conv<COUT, EPI>(a, c->stream);
 }
 
 // Device error word of the tcgen05 kernels (a bounded wait expired): reported once, then cleared.
@@ -991,7 +1036,7 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
     if (c->feat) {
         st = closure_features_forward(up, un, cn, d.nx, d.ny, d.nz, c->feat_r, c->feat_w, c->feat_s, c->fb, c->x,
-                                      c->stream);
+                                      keep, c->stream);
         if (st != GBST_OK)
             return st;
     } else {
@@ -1020,8 +1065,8 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     b.bias = c->p + c->off[5];
     b.out_f32 = c->o;
     b.cout_valid = 1;
-    if (e == cudaSuccess)  // the tcgen05 path runs the one-channel last layer on the CUDA cores
-        e = c->conv_impl == 0 ? launch_conv_out1(b, c->stream) : conv<8, EPI_LINEAR_F32>(c, b);
+    if (e == cudaSuccess)  // impl 2 runs the one-channel last layer on the CUDA cores
+        e = c->conv_impl == 2 ? launch_conv_out1(b, c->stream) : conv<8, EPI_LINEAR_F32>(c, b);
     return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
 }
 
@@ -1236,9 +1281,7 @@ gbst_status closure_forward(gbst_closure c, const float *u_plus, const float *u_
     if (st != GBST_OK)
         return st;
     const int64_t n = nx * ny * nz;
-    if (cudaMemsetAsync(correction, 0, n * sizeof(float), c->stream) != cudaSuccess)
-        return record_error(GBST_ECUDA, "closure_forward: memset");
-    k_scale_add<<<blocks_for(n), 256, 0, c->stream>>>(correction, c->o, static_cast<float>(1.0 / c->out_scale), n);
+    k_scale<<<blocks_for(n), 256, 0, c->stream>>>(correction, c->o, static_cast<float>(1.0 / c->out_scale), n);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
 }
@@ -1336,7 +1379,7 @@ gbst_status closure_feature_values(gbst_closure c, const float *u_plus, const fl
     if (st != GBST_OK)
         return st;
     st = closure_features_forward(u_plus, u_n, c_norm, nx, ny, nz, c->feat_r, c->feat_w, c->feat_s, c->fb, c->x,
-                                  c->stream);
+                                  true, c->stream);
     if (st != GBST_OK)
         return st;
     return closure_features_values(u_plus, u_n, nx, ny, nz, c->fb, out, c->stream);
@@ -1395,8 +1438,8 @@ gbst_status closure_set_loss_weight(gbst_closure c, double w)
 
 gbst_status closure_set_conv_impl(gbst_closure c, int impl)
 {
-    if (!c || (impl != 0 && impl != 1))
-        return record_error(GBST_EINVAL, "closure_set_conv_impl: null closure or impl not 0 / 1");
+    if (!c || impl < 0 || impl > 2)
+        return record_error(GBST_EINVAL, "closure_set_conv_impl: null closure or impl not 0, 1 or 2");
     c->conv_impl = impl;
     return GBST_OK;
 }

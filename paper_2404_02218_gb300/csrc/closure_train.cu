@@ -167,6 +167,165 @@ __global__ void __launch_bounds__(kThr) k_pack_features(DenseDims d, const float
     }
 }
 
+// z-marching forms of the forward features (inference): a block owns a 32 x 8
+// (x, y) tile and a chunk of kFZC planes, each thread one column; the z
+// neighbours of the star stencils come from register queues (one new load per
+// plane and field), the x and y neighbours from L1.  Same arithmetic, in the
+// same order, as k_star / k_cn2_grads / k_pack_features.
+constexpr int kFX = 32, kFY = 8, kFZC = 32;
+inline dim3 zmarch_grid(const DenseDims &d)
+{
+    return dim3(static_cast<unsigned>((d.nx + kFX - 1) / kFX), static_cast<unsigned>((d.ny + kFY - 1) / kFY),
+                static_cast<unsigned>((d.nz + kFZC - 1) / kFZC));
+}
+
+// lu = L u^n (star of radius R, weights w), as k_star with no pre / post factor.
+template <int R>
+__global__ void __launch_bounds__(kFX *kFY) k_lap_z(DenseDims d, const float *__restrict__ un, float4 w03, float w4,
+                                                    float *__restrict__ lu)
+{
+    const float w[5] = {w03.x, w03.y, w03.z, w03.w, w4};
+    const int x = blockIdx.x * kFX + threadIdx.x, y = blockIdx.y * kFY + threadIdx.y;
+    if (x >= d.nx || y >= d.ny)
+        return;
+    const int z0 = blockIdx.z * kFZC, z1 = min(d.nz, z0 + kFZC);
+    const int64_t sy = d.nx, sz = static_cast<int64_t>(d.nx) * d.ny, pxy = static_cast<int64_t>(y) * d.nx + x;
+    float q[2 * R + 1];  // u^n at z - R .. z + R (zero outside)
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) {
+        const int zz = z0 - R + k;
+        q[k] = (zz >= 0 && zz < d.nz) ? un[zz * sz + pxy] : 0.0f;
+    }
+    for (int z = z0; z < z1; ++z) {
+        const int64_t p = z * sz + pxy;
+        float s = 3.0f * w[0] * q[R];
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+            float a = 0.0f;
+            if (x - m >= 0) a += un[p - m];
+            if (x + m < d.nx) a += un[p + m];
+            if (y - m >= 0) a += un[p - m * sy];
+            if (y + m < d.ny) a += un[p + m * sy];
+            if (z - m >= 0) a += q[R - m];
+            if (z + m < d.nz) a += q[R + m];
+            s = fmaf(w[m], a, s);
+        }
+        lu[p] = s;
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k)
+            q[k] = q[k + 1];
+        q[2 * R] = (z + R + 1 < d.nz) ? un[p + (R + 1) * sz] : 0.0f;
+    }
+}
+
+// The packed network input from u+, u^n, c_n and lu = L u^n: cn2 and g_a as
+// k_cn2_grads, t6 and t5 as the k_star calls of closure_features_forward, the
+// channels as k_pack_features.  R: the radius of L; w6: the sixth-difference star.
+template <int R>
+__global__ void __launch_bounds__(kFX *kFY) k_features_z(DenseDims d, const float *__restrict__ up,
+                                                         const float *__restrict__ un, const float *__restrict__ cn,
+                                                         const float *__restrict__ lu, float4 w03, float w4,
+                                                         float4 w6, FeatScales sc, __nv_bfloat16 *__restrict__ xout)
+{
+    constexpr int QC = R;  // queue radius of c_n and lu (R >= 1 also covers the gradients)
+    const float w[5] = {w03.x, w03.y, w03.z, w03.w, w4};
+    const float v6[4] = {w6.x, w6.y, w6.z, w6.w};
+    const int x = blockIdx.x * kFX + threadIdx.x, y = blockIdx.y * kFY + threadIdx.y;
+    if (x >= d.nx || y >= d.ny)
+        return;
+    const int z0 = blockIdx.z * kFZC, z1 = min(d.nz, z0 + kFZC);
+    const int64_t sy = d.nx, sz = static_cast<int64_t>(d.nx) * d.ny, pxy = static_cast<int64_t>(y) * d.nx + x;
+    float qu[7], qc[2 * QC + 1], ql[2 * QC + 1];  // u^n at z - 3 .. z + 3; c_n, lu at z - QC .. z + QC
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const int zz = z0 - 3 + k;
+        qu[k] = (zz >= 0 && zz < d.nz) ? un[zz * sz + pxy] : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * QC + 1; ++k) {
+        const int zz = z0 - QC + k;
+        const bool in = zz >= 0 && zz < d.nz;
+        qc[k] = in ? cn[zz * sz + pxy] : 0.0f;
+        ql[k] = in ? lu[zz * sz + pxy] : 0.0f;
+    }
+    for (int z = z0; z < z1; ++z) {
+        const int64_t p = z * sz + pxy;
+        const float c = qc[QC], c2 = c * c, a = up[p], b = qu[3];
+        // g_a = (cn2[p + e_a] - cn2[p - e_a]) / 2 and D_a u^n, zero outside
+        float ga[3], du[3];
+        {
+            const float cxp = x + 1 < d.nx ? cn[p + 1] : 0.0f, cxm = x - 1 >= 0 ? cn[p - 1] : 0.0f;
+            const float cyp = y + 1 < d.ny ? cn[p + sy] : 0.0f, cym = y - 1 >= 0 ? cn[p - sy] : 0.0f;
+            ga[0] = 0.5f * (cxp * cxp - cxm * cxm);
+            ga[1] = 0.5f * (cyp * cyp - cym * cym);
+            ga[2] = 0.5f * (qc[QC + 1] * qc[QC + 1] - qc[QC - 1] * qc[QC - 1]);
+            const float uxp = x + 1 < d.nx ? un[p + 1] : 0.0f, uxm = x - 1 >= 0 ? un[p - 1] : 0.0f;
+            const float uyp = y + 1 < d.ny ? un[p + sy] : 0.0f, uym = y - 1 >= 0 ? un[p - sy] : 0.0f;
+            du[0] = 0.5f * (uxp - uxm);
+            du[1] = 0.5f * (uyp - uym);
+            du[2] = 0.5f * (qu[4] - qu[2]);
+        }
+        float f6 = 0.0f, gabs = 0.0f;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            f6 = fmaf(ga[ax], du[ax], f6);
+            gabs += fabsf(ga[ax]);
+        }
+        // t6 = cn2 * sum_axes delta^6 u^n
+        float s6 = 3.0f * v6[0] * b;
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) {
+            float t = 0.0f;
+            if (x - m >= 0) t += un[p - m];
+            if (x + m < d.nx) t += un[p + m];
+            if (y - m >= 0) t += un[p - m * sy];
+            if (y + m < d.ny) t += un[p + m * sy];
+            if (z - m >= 0) t += qu[3 - m];
+            if (z + m < d.nz) t += qu[3 + m];
+            s6 = fmaf(v6[m], t, s6);
+        }
+        // t5 = cn2 * L(cn2 lu)
+        auto cl = [&](int64_t q) {
+            const float cq = cn[q];
+            return (cq * cq) * lu[q];
+        };
+        float s5 = 3.0f * w[0] * (c2 * ql[QC]);
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+            float t = 0.0f;
+            if (x - m >= 0) t += cl(p - m);
+            if (x + m < d.nx) t += cl(p + m);
+            if (y - m >= 0) t += cl(p - m * sy);
+            if (y + m < d.ny) t += cl(p + m * sy);
+            if (z - m >= 0) t += (qc[QC - m] * qc[QC - m]) * ql[QC - m];
+            if (z + m < d.nz) t += (qc[QC + m] * qc[QC + m]) * ql[QC + m];
+            s5 = fmaf(w[m], t, s5);
+        }
+        const float f[8] = {a, b, c2 * a, c2 * b, s6 * c2, s5 * c2, f6, gabs * ql[QC]};
+        uint32_t w4p[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(sc.s[2 * k] * f[2 * k], sc.s[2 * k + 1] * f[2 * k + 1]);
+            w4p[k] = *reinterpret_cast<const uint32_t *>(&b2);
+        }
+        uint4 *o = reinterpret_cast<uint4 *>(xout + p * 16);
+        o[0] = make_uint4(w4p[0], w4p[1], w4p[2], w4p[3]);
+        o[1] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            qu[k] = qu[k + 1];
+        qu[6] = (z + 4 < d.nz) ? un[p + 4 * sz] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 2 * QC; ++k) {
+            qc[k] = qc[k + 1];
+            ql[k] = ql[k + 1];
+        }
+        const bool in = z + QC + 1 < d.nz;
+        qc[2 * QC] = in ? cn[p + (QC + 1) * sz] : 0.0f;
+        ql[2 * QC] = in ? lu[p + (QC + 1) * sz] : 0.0f;
+    }
+}
+
 // The same eight features in FP32, unscaled, channel-major (out + k n).
 __global__ void __launch_bounds__(kThr) k_feature_values(DenseDims d, const float *__restrict__ up,
                                                          const float *__restrict__ un, const float *__restrict__ cn2,
@@ -351,15 +510,44 @@ FeatScales to_scales(const double *sc)
 
 // Closure input features (8 channels) from (u+, u^n, c_n) into x (channels-last BF16, 16
 // channels, the last 8 zero): x_k = scales[k] f_k, see k_pack_features.  r, w: the star L.
+// aux: also leave cn2, g_a, t5 and t6 in b (the transpose and closure_features_values read
+// them); without it the two z-marching kernels compute the same x.
 gbst_status closure_features_forward(const float *up, const float *un, const float *cn, int64_t nx, int64_t ny,
                                      int64_t nz, int r, const double *w, const double *scales,
-                                     const ClosureFeatBufs &b, __nv_bfloat16 *x, cudaStream_t s)
+                                     const ClosureFeatBufs &b, __nv_bfloat16 *x, bool aux, cudaStream_t s)
 {
     DenseDims d;
     gbst_status st = dense_dims(nx, ny, nz, &d, "closure features");
     if (st != GBST_OK)
         return st;
-    const int blocks = blocks_for_dense(nx * ny * nz);
+    if (!aux) {
+        // two z-marching launches: lu, then every channel (only b.lu is written besides x)
+        if (r < 1 || r > 4)
+            return record_error(GBST_EINVAL, "closure features: radius must be 1..4");
+        float wf[5] = {0, 0, 0, 0, 0};
+        for (int m = 0; m <= r; ++m)
+            wf[m] = static_cast<float>(w[m]);
+        const float4 w03 = make_float4(wf[0], wf[1], wf[2], wf[3]);
+        const float4 w6 = make_float4(static_cast<float>(kSixth[0]), static_cast<float>(kSixth[1]),
+                                      static_cast<float>(kSixth[2]), static_cast<float>(kSixth[3]));
+        const FeatScales sc = to_scales(scales);
+        const dim3 g = zmarch_grid(d), t(kFX, kFY);
+        switch (r) {
+        case 1: k_lap_z<1><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+        case 2: k_lap_z<2><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+        case 3: k_lap_z<3><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+        default: k_lap_z<4><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+        }
+        if ((st = launched("closure features")) != GBST_OK)
+            return st;
+        switch (r) {
+        case 1: k_features_z<1><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+        case 2: k_features_z<2><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+        case 3: k_features_z<3><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+        default: k_features_z<4><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+        }
+        return launched("closure features");
+    }
     k_cn2_grads<<<dense_grid(d), kDX, 0, s>>>(d, cn, b.cn2, b.g[0], b.g[1], b.g[2]);
     if ((st = launched("closure features")) != GBST_OK)
         return st;

@@ -12,23 +12,31 @@
 // (start address + (r + dy) * row + dx * 16 bytes), no data movement per tap.
 // The weights of all taps sit in shared memory in the same layout.
 //
-// Input-stationary order: when input plane p has landed, its 27 taps are
-// issued at once into the three outputs that read it (p + 1 through dz = 0,
-// p through dz = 1, p - 1 through dz = 2; dz = 2 first, which completes output
-// p - 1), and the plane is released right after.  So a plane is read by the
-// tensor cores exactly once, the ring of NS slots keeps NS - 1 planes of
-// prefetch in flight, and four accumulator sets rotate: three being summed,
-// one being read out by the epilogue.  Within a tap the RY rows go to
-// different tensor-memory columns (RY independent chains: an M = 128, N = 16
-// MMA is short, and a single chain would wait on itself).
+// Input-stationary order: when input plane p has landed, its taps are issued
+// at once into the three outputs that read it (p + 1 through dz = 0, p through
+// dz = 1, p - 1 through dz = 2), which completes output p - 1, and the plane
+// is released right after; the ring of NS slots keeps NS - 1 planes of
+// prefetch in flight.  The three outputs share the A operand of a tap
+// (dy, dx), so one MMA with N = 48 computes all three: output o accumulates in
+// tensor-memory slot o mod 3 (16 columns per row), and the weights of a tap are
+// stored as five 16-row blocks in dz order 2, 1, 0, 2, 1, so that the three
+// consecutive blocks starting at block 2 - ((p + 1) mod 3) line up with slots
+// 0, 1, 2.  An M = 128 MMA reads its 4 KB A tile from shared memory whatever
+// its N (about 32 cycles at 128 bytes per cycle, plus N / 4 for B), so the
+// N = 48 form does the work of three N = 16 MMAs in 44 instead of 117 cycles.
+// All MMAs accumulate; the epilogue zeroes a slot right after reading it.
+// At a unit's first two and last two planes some of the three outputs lie
+// outside the unit; those planes issue one N = 16 MMA per valid output.
 //
 // Warp roles: warps 0-7 epilogue (warp w reads tensor-memory lanes
 // 32 (w & 3) .. +31 = points, channels 8 (w >> 2) .. +7 of each row), warp 8
-// TMA producer, warp 9 allocates NACC RY 16 tensor-memory columns and one lane
-// issues the MMAs.
+// TMA producer (one lane), warp 9 allocates the tensor memory and issues the
+// MMAs (the whole warp runs the loop, elect.sync picks the issuing lane: a
+// loop run by one lane alone issued an MMA only every 144 cycles).
 // Pipelines: input plane ring (full / empty mbarriers; a tcgen05.commit frees
-// a plane once the MMAs reading it are done) and the accumulator sets
-// (tfull: commit after an output's last nine taps; tempty: the epilogue warps).
+// a plane once the MMAs reading it are done) and the three accumulator slots
+// (tfull: commit after an output's last taps; tempty: the epilogue warps,
+// after reading and zeroing the slot).
 // Every wait is bounded; on expiry the CTA sets the error word, lets issued
 // work finish (bounded) and releases its tensor memory.
 #pragma once
@@ -45,10 +53,14 @@ constexpr int BOXY = RY + 2;             // input rows per plane (y halo 1 each 
 constexpr int ROWB = BOXX * 16;          // bytes of one row of 8 channels
 constexpr int HALF = (BOXY * ROWB + 127) / 128 * 128;  // one 8-channel box
 constexpr int SLOT = 2 * HALF;           // one input plane (both channel halves)
-constexpr int NS = 3;                    // plane slots: z-1, z, z+1 (89 KB per CTA: two CTAs per SM)
-constexpr int NACC = 4;                  // accumulator sets: three outputs being summed, one read out
-constexpr int TCOLS = NACC * RY * 16;    // tensor-memory columns (256: two CTAs per SM fill the 512)
-constexpr int WBYTES = 27 * 2 * 16 * 16; // weights: [tap][half][co 16][8 ci] BF16
+constexpr int NS = 3;                    // plane slots: two planes of prefetch (98.5 KB per CTA: two CTAs per SM)
+constexpr int NACC = 3;                  // accumulator slots: output o in slot o mod 3
+constexpr int ROWCOLS = NACC * 16;       // tensor-memory columns of one output row (the N = 48 MMA)
+constexpr int TCOLS = 256;               // allocated columns (RY x 48 = 192 used; two CTAs per SM fill the 512)
+constexpr int WBLK = 5;                  // weight blocks per tap: dz = 2, 1, 0, 2, 1
+constexpr int WHALF = WBLK * 16 * 16;    // bytes of one 8-channel K half of a tap: [80 rows][8 ci] BF16
+constexpr int WTAP = 2 * WHALF;          // bytes of one tap (dy, dx)
+constexpr int WBYTES = 9 * WTAP;         // weights: [dy dx][half][block][co 16][8 ci] BF16
 constexpr int HDR = 256;                 // barriers and flags
 constexpr int SMEM = HDR + WBYTES + NS * SLOT;
 constexpr int NEPI = 8;                  // epilogue warps: lane quadrant w & 3, channels 8 (w >> 2) ..
@@ -120,65 +132,55 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, no swizzle.  lbo: bytes between
-// core matrices along K, sbo: bytes between 8-row groups along M / N.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
-           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// The same descriptor as two 32-bit halves, so that a per-tap offset is one
-// 32-bit add on the low half (start address field; offsets stay inside the slot).
+// Shared-memory matrix descriptor (K-major, no swizzle) as two 32-bit halves,
+// so that a per-tap offset is one 32-bit add on the low half (start address
+// field; offsets stay inside the operand).  lbo: bytes between core matrices
+// along K, sbo: bytes between 8-row groups along M / N.
 __device__ __forceinline__ uint32_t sdesc_lo(uint32_t addr, uint32_t lbo)
 {
     return ((addr >> 4) & 0x3FFFu) | (((lbo >> 4) & 0x3FFFu) << 16);
 }
 constexpr uint32_t sdesc_hi(uint32_t sbo) { return ((sbo >> 4) & 0x3FFFu) | (1u << 14); }
 
-// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = 16.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = n.
+constexpr uint32_t idesc_bf16(uint32_t n)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-// The same MMA with the descriptors given as 32-bit halves.
-__device__ __forceinline__ void mma_bf16_h(uint32_t d_tmem, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
-                                           uint32_t accumulate)
+// D[tmem] += A B, issued by one lane that elect.sync picks: the whole (converged)
+// warp executes the statement.  Descriptors as 32-bit halves.
+__device__ __forceinline__ void mma_bf16_warp(uint32_t d_tmem, uint32_t alo, uint32_t ahi, uint32_t blo,
+                                              uint32_t bhi, uint32_t idesc)
 {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "{\n\t.reg .pred e;\n\t.reg .b32 l;\n\t.reg .b64 da, db;\n\t"
+        "elect.sync l|e, 0xffffffff;\n\t"
         "mov.b64 da, {%1, %2};\n\t"
         "mov.b64 db, {%3, %4};\n\t"
-        "setp.ne.b32 p, %6, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d_tmem),
-        "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(kIdesc), "r"(accumulate));
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, 1;\n\t}" ::"r"(d_tmem),
+        "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc));
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
+// tcgen05.commit of the MMAs issued so far, from one elected lane of the converged warp.
+__device__ __forceinline__ void mma_commit_warp(uint64_t *bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t.reg .b32 l;\n\t"
+        "elect.sync l|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(sa(bar))
+        : "memory");
+}
+
+// Zero 8 consecutive FP32 columns of the warp's 32 lanes (no wait).
+__device__ __forceinline__ void tmem_zero8(uint32_t taddr)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+                 "r"(0u)
                  : "memory");
 }
 
-// 8 consecutive FP32 columns of the warp's 32 lanes (one lane per thread).
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
-{
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        v[i] = __uint_as_float(r[i]);
-}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Four loads of 8 columns (one per output row) and a single wait: the values
 // pass through the wait (as read-write operands of an empty statement after

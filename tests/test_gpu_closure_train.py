@@ -113,6 +113,28 @@ def test_feature_values_match_oracle(torch_cuda):
         assert np.max(np.abs(got[k] - ref[k])) <= 1e-5 * np.max(np.abs(ref[k])), k
 
 
+@pytest.mark.parametrize("dims", [(37, 21, 19), (45, 13, 70), (1, 1, 1)])
+def test_feature_forward_matches_oracle(torch_cuda, dims):
+    """The inference forward (z-marching feature kernels: ragged 32 x 8 tiles, several
+    32-plane chunks) against the oracle network on the oracle's features."""
+    torch = torch_cuda
+    from oracle import closure as oc
+    shape = tuple(reversed(dims))
+    up, un = _fields(shape, 94, 2)
+    cn = 0.3 + 0.7 * synthetic.uniform_field(96, shape).astype(np.float64)
+    t_out = 2.0
+    cl, p, sc = _closure8(torch, int(np.prod(dims)), t=t_out)
+    t = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (up, un, cn)]
+    got = cl.forward(*t).double().cpu().numpy()
+    cl.close()
+    pb = {k: _bf16(torch, v) for k, v in p.items()}
+    f32 = [a.astype(np.float32).astype(np.float64) for a in (up, un, cn)]
+    x = oc.feature_channels(f32[0], f32[1], f32[2] ** 2, oracle.central_weights_f64(4), sc)
+    o, _ = oc.forward(x, pb)
+    ref = o[0] / t_out  # the correction is the network output over the output scale
+    assert np.linalg.norm(got - ref) <= 3e-2 * np.linalg.norm(ref)
+
+
 def test_closure_backward_matches_oracle(torch_cuda):
     """Cotangents of (u+, u^n) and the parameter gradient of one corrected step."""
     torch = torch_cuda
