@@ -311,6 +311,12 @@ gbst_status closure_set_features(gbst_closure c, int space_order, const double *
  * (out + k * nx*ny*nz); device arrays; asynchronous on the closure's stream. */
 gbst_status closure_feature_values(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,
                                    int64_t nx, int64_t ny, int64_t nz, float *out);
+/* The activation of the closure's hidden layers, y[i] = GELU(x[i]) = x[i] Phi(x[i])
+ * for i < n, as the forward convolutions evaluate it (device arrays, FP32, y may
+ * equal x; asynchronous on `stream`, a cudaStream_t or null).  Phi comes from the
+ * erfc approximation of Abramowitz & Stegun 7.1.26; the result is within
+ * 1.8e-7 max(1, |x|) of the exact GELU.  GBST_EINVAL for null arrays or n < 0. */
+gbst_status closure_gelu(const float *x, float *y, int64_t n, void *stream);
 /* Backward pass of one corrected step (closures with cin = 8), for training
  * through rollouts.  The corrected step is u^{n+1} = u+ + correction(u+, u^n).
  * Given grad_out = dLoss/du^{n+1} (dense device FP32), adds dLoss/d(parameters)

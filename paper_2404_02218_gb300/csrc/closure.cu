@@ -86,7 +86,47 @@ __device__ __forceinline__ void cp_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU(x) = x Phi(x) of the forward convolutions.  Phi from the complementary
+// error function approximation of Abramowitz & Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26 (|error| <= 1.5e-7 in erf):
+// erfc(z) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z),
+// with z = |x| / sqrt(2), so that 1 - Phi(|x|) = erfc(z) / 2.  Below, p is divided
+// by sqrt(2) and the a_k by 2; the exponential is 2^(-x^2 log2(e) / 2).  In FP32
+// the result is within 1.8e-7 max(1, |x|) of the exact GELU.  Two special-function
+// instructions (reciprocal, exp2) and packed FP32x2 arithmetic for two values.
+constexpr float kGp = 0.231641900f;                   // p / sqrt(2), p = 0.3275911
+constexpr float kGa1 = 0.127414796f, kGa2 = -0.142248368f, kGa3 = 0.710706871f, kGa4 = -0.726576014f,
+                kGa5 = 0.530702715f;                  // a_k / 2
+constexpr float kGe = -0.721347520f;                  // -log2(e) / 2
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 gelu2(float2 v)
+{
+    const float2 ax = make_float2(fabsf(v.x), fabsf(v.y));
+    const float2 d = __ffma2_rn(make_float2(kGp, kGp), ax, make_float2(1.0f, 1.0f));
+    const float2 t = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+    float2 q = __ffma2_rn(t, make_float2(kGa5, kGa5), make_float2(kGa4, kGa4));
+    q = __ffma2_rn(t, q, make_float2(kGa3, kGa3));
+    q = __ffma2_rn(t, q, make_float2(kGa2, kGa2));
+    q = __ffma2_rn(t, q, make_float2(kGa1, kGa1));
+    q = __fmul2_rn(q, t);
+    const float2 sx = __fmul2_rn(__fmul2_rn(v, make_float2(kGe, kGe)), v);
+    const float2 h = __fmul2_rn(q, make_float2(ex2_approx(sx.x), ex2_approx(sx.y)));  // 1 - Phi(|x|)
+    const float2 phi = make_float2(v.x >= 0.0f ? 1.0f - h.x : h.x, v.y >= 0.0f ? 1.0f - h.y : h.y);
+    return __fmul2_rn(v, phi);
+}
+__device__ __forceinline__ float gelu(float x) { return gelu2(make_float2(x, 0.0f)).x; }
+// GELU'(x) of the backward pass (exact erf form).
 __device__ __forceinline__ float gelu_grad(float x)
 {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
@@ -227,8 +267,8 @@ __global__ void __launch_bounds__(NTHR) k_conv(const ConvArgs a)
                         v1 = 0.f;
                     if (a.zout)
                         *reinterpret_cast<__nv_bfloat162 *>(a.zout + p * CH + c) = __floats2bfloat162_rn(v0, v1);
-                    *reinterpret_cast<__nv_bfloat162 *>(a.out + p * CH + c) =
-                        __floats2bfloat162_rn(gelu(v0), gelu(v1));
+                    const float2 g = gelu2(make_float2(v0, v1));
+                    *reinterpret_cast<__nv_bfloat162 *>(a.out + p * CH + c) = __floats2bfloat162_rn(g.x, g.y);
                 } else if (EPI == EPI_LINEAR_BF16) {  // data gradient of the network's input
                     *reinterpret_cast<__nv_bfloat162 *>(a.out + p * CH + c) = __floats2bfloat162_rn(v0, v1);
                 } else {  // EPI_DGELU: data gradient times GELU'(pre-activation below)
@@ -466,22 +506,37 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                 if (EPI == EPI_LINEAR_F32) {
                     a.out_f32[p] = v[0] + bias[0];
                 } else if (EPI == EPI_GELU) {
-                    uint32_t zz[4], yy[4];
+                    // channels >= cout_valid (padding) are zero
+                    float2 zv[4];
 #pragma unroll
-                    for (int c = 0; c < 8; c += 2) {
-                        float v0 = v[c] + bias[c], v1 = v[c + 1] + bias[c + 1];
-                        if (c0 + c >= a.cout_valid)
-                            v0 = 0.f;
-                        if (c0 + c + 1 >= a.cout_valid)
-                            v1 = 0.f;
-                        const __nv_bfloat162 zb = __floats2bfloat162_rn(v0, v1);
-                        const __nv_bfloat162 yb = __floats2bfloat162_rn(gelu(v0), gelu(v1));
-                        zz[c >> 1] = *reinterpret_cast<const uint32_t *>(&zb);
-                        yy[c >> 1] = *reinterpret_cast<const uint32_t *>(&yb);
+                    for (int c = 0; c < 8; c += 2)
+                        zv[c >> 1] = __fadd2_rn(make_float2(v[c], v[c + 1]), make_float2(bias[c], bias[c + 1]));
+                    if (c0 + 8 > a.cout_valid) {
+#pragma unroll
+                        for (int c = 0; c < 8; c += 2) {
+                            if (c0 + c >= a.cout_valid)
+                                zv[c >> 1].x = 0.f;
+                            if (c0 + c + 1 >= a.cout_valid)
+                                zv[c >> 1].y = 0.f;
+                        }
+                    }
+                    uint32_t yy[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float2 g = gelu2(zv[k]);
+                        const __nv_bfloat162 yb = __floats2bfloat162_rn(g.x, g.y);
+                        yy[k] = *reinterpret_cast<const uint32_t *>(&yb);
                     }
                     *reinterpret_cast<uint4 *>(a.out + p * CH + c0) = make_uint4(yy[0], yy[1], yy[2], yy[3]);
-                    if (a.zout)
+                    if (a.zout) {
+                        uint32_t zz[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const __nv_bfloat162 zb = __floats2bfloat162_rn(zv[k].x, zv[k].y);
+                            zz[k] = *reinterpret_cast<const uint32_t *>(&zb);
+                        }
                         *reinterpret_cast<uint4 *>(a.zout + p * CH + c0) = make_uint4(zz[0], zz[1], zz[2], zz[3]);
+                    }
                 } else if (EPI == EPI_LINEAR_BF16) {  // data gradient of the network's input
                     uint32_t oo[4];
 #pragma unroll
@@ -806,6 +861,13 @@ __global__ void k_seed(const float *g, float inv_t, int64_t n, __nv_bfloat16 *do
         for (int k = 1; k < 8; ++k)
             q[k] = __floats2bfloat162_rn(0.f, 0.f);
     }
+}
+
+__global__ void k_gelu(const float *x, float *y, int64_t n)
+{
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        y[p] = gelu(x[p]);
 }
 
 __global__ void k_scale(float *dst, const float *src, float scale, int64_t n)
@@ -1365,6 +1427,17 @@ gbst_status closure_set_features(gbst_closure c, int space_order, const double *
     for (int k = 0; k < 8; ++k)
         c->feat_s[k] = scales[k];
     return GBST_OK;
+}
+
+gbst_status closure_gelu(const float *x, float *y, int64_t n, void *stream)
+{
+    if (!x || !y || n < 0)
+        return record_error(GBST_EINVAL, "closure_gelu: null array or n < 0");
+    if (n == 0)
+        return GBST_OK;
+    k_gelu<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
 }
 
 gbst_status closure_feature_values(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,

@@ -129,6 +129,7 @@ def lib() -> ctypes.CDLL:
                 "closure_get_params": ([H, vp, i64], i32),
                 "closure_get_grads": ([H, vp, i64], i32),
                 "closure_forward": ([H, vp, vp, vp, i64, i64, i64, vp], i32),
+                "closure_gelu": ([vp, vp, i64, vp], i32),
                 "closure_loss_grad": ([H, vp, vp, vp, vp, i64, i64, i64, ctypes.POINTER(dbl)], i32),
                 "closure_adam_step": ([H, dbl], i32),
                 "closure_set_out_scale": ([H, dbl], i32),
@@ -406,6 +407,11 @@ def closure_get_params(c, host_ptr: int, n: int):
 
 def closure_get_grads(c, host_ptr: int, n: int):
     _check(lib().closure_get_grads(c, ctypes.c_void_p(host_ptr), int(n)), "closure_get_grads")
+
+
+def closure_gelu(x_ptr: int, y_ptr: int, n: int, stream: int = 0):
+    _check(lib().closure_gelu(ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), int(n), ctypes.c_void_p(stream)),
+           "closure_gelu")
 
 
 def closure_forward(c, up: int, un: int, cn: int, dims, corr: int):

@@ -225,3 +225,25 @@ def test_training_reduces_coarse_error(torch_cuda):
     print("closure result:", res)
     assert np.isfinite(res["rel_l2_closure"])
     assert res["gain"] > 1.0
+
+
+def test_gelu_within_its_stated_bound(torch_cuda):
+    """The hidden layers' activation (Abramowitz & Stegun 7.1.26 form of Phi) against the
+    exact GELU in FP64 on a dense grid, the signed zeros and large magnitudes."""
+    from math import erf
+    from paper_2404_02218_gb300 import native as N
+    torch = torch_cuda
+    xs = np.concatenate([np.linspace(-14.0, 14.0, 1_000_001), [0.0, -0.0, 40.0, -40.0, 1e-30, -1e-30]])
+    x = torch.from_numpy(xs.astype(np.float32)).cuda()
+    y = torch.empty_like(x)
+    N.closure_gelu(x.data_ptr(), y.data_ptr(), x.numel())
+    torch.cuda.synchronize()
+    xf = xs.astype(np.float32).astype(np.float64)
+    exact = xf * 0.5 * (1.0 + np.vectorize(erf)(xf / np.sqrt(2.0)))
+    err = np.abs(y.double().cpu().numpy() - exact)
+    assert np.all(err <= 1.8e-7 * np.maximum(1.0, np.abs(xf)))
+    # n = 0 is a no-op; in place works
+    N.closure_gelu(x.data_ptr(), x.data_ptr(), 0)
+    N.closure_gelu(x.data_ptr(), x.data_ptr(), x.numel())
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
