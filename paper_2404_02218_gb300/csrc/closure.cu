@@ -287,12 +287,13 @@ __global__ void __launch_bounds__(NTHR) k_conv(const ConvArgs a)
 // 3x3x3 convolution on tcgen05 (see conv_tc.cuh): same arguments and
 // epilogues as k_conv; the input is read through the tensor map `tmap`
 // (channels-last [z][y][x][16] BF16, boxes of 8 channels x 130 points x 3 rows).
-template <int COUT, int EPI>
+template <int COUT, int EPI, int CIN>
 __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     k_conv_tc(const __grid_constant__ CUtensorMap tmap, const ConvArgs a, const convtc::UnitMap um, const int nunits,
               int *err)
 {
     using namespace convtc;
+    using G = Geo<CIN>;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *full = reinterpret_cast<uint64_t *>(sm);  // [NS] input plane landed
     uint64_t *empty = full + NS;                          // [NS] input plane no longer read
@@ -304,19 +305,27 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(fin + 1);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1) + 1;
     unsigned char *wsm = sm + HDR;
-    unsigned char *slots = sm + HDR + WBYTES;
+    unsigned char *slots = sm + HDR + G::NTAP * WTAP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // weights [tap][co][16 ci] -> [dy dx][half][block 0..4: dz = 2, 1, 0, 2, 1][co 0..15][8 ci];
-    // rows co >= COUT stay zero
-    for (int i = threadIdx.x; i < 9 * 2 * WBLK * 16; i += blockDim.x) {
-        const int co = i & 15, blk = (i >> 4) % WBLK, half = (i / (16 * WBLK)) & 1, t9 = i / (32 * WBLK);
+    // weights [tap][co][16 ci] -> [tap t][half][block 0..4: dz = 2, 1, 0, 2, 1][co 0..15][8 ci];
+    // rows co >= COUT stay zero.  CIN 16: t = (dy, dx), half = channels 0-7 | 8-15.  CIN 8:
+    // t = (dy, pair | single); the pair's halves are dx = -1 | 0, the single's dx = +1 | zero.
+    for (int i = threadIdx.x; i < G::NTAP * 2 * WBLK * 16; i += blockDim.x) {
+        const int co = i & 15, blk = (i >> 4) % WBLK, half = (i / (16 * WBLK)) & 1, t = i / (32 * WBLK);
         const int dz = (5 - blk) % 3;
-        const int tap = dz * 9 + t9;
+        int tap, ci0;
+        if (CIN == 16) {
+            tap = dz * 9 + t;
+            ci0 = half * 8;
+        } else {
+            tap = (t % 2 == 0) ? dz * 9 + (t / 2) * 3 + half : (half == 0 ? dz * 9 + (t / 2) * 3 + 2 : -1);
+            ci0 = 0;
+        }
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (co < COUT)
-            v = *reinterpret_cast<const uint4 *>(a.wt + (tap * COUT + co) * CH + half * 8);
-        *reinterpret_cast<uint4 *>(wsm + t9 * WTAP + half * WHALF + (blk * 16 + co) * 16) = v;
+        if (co < COUT && tap >= 0)
+            v = *reinterpret_cast<const uint4 *>(a.wt + (tap * COUT + co) * CH + ci0);
+        *reinterpret_cast<uint4 *>(wsm + t * WTAP + half * WHALF + (blk * 16 + co) * 16) = v;
     }
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -368,10 +377,11 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                         ok = false;
                         break;
                     }
-                    bar_expect(&full[s], 2 * BOX_BYTES);
-                    unsigned char *dst = slots + s * SLOT;
+                    bar_expect(&full[s], G::NBOX * BOXY * G::BOXX * 16);
+                    unsigned char *dst = slots + s * G::SLOT;
                     tma_load_4d(dst, &tmap, &full[s], 0, x0 - 1, y0 - 1, p);
-                    tma_load_4d(dst + HALF, &tmap, &full[s], 8, x0 - 1, y0 - 1, p);
+                    if (G::NBOX == 2)
+                        tma_load_4d(dst + G::HALF, &tmap, &full[s], 8, x0 - 1, y0 - 1, p);
                     ++it;
                 }
             }
@@ -390,7 +400,7 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
         // (the whole warp runs the loop; elect.sync picks the issuing lane)
         int it = 0, ot = 0;  // input planes consumed, outputs started (over all units)
         bool ok = true;
-        const uint32_t wlo = sdesc_lo(sa(wsm), WHALF), slot_lo0 = sdesc_lo(sa(slots), HALF);
+        const uint32_t wlo = sdesc_lo(sa(wsm), WHALF), slot_lo0 = sdesc_lo(sa(slots), G::LBO_A);
         constexpr uint32_t whi = sdesc_hi(128), ahi = sdesc_hi(128);
         for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
             int y0, x0, z0, z1;
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                 if (!(ok = __all_sync(0xffffffffu, bar_wait(&full[s], (it / NS) & 1, abort_flag))))
                     break;
                 fence_after();
-                const uint32_t alo = slot_lo0 + static_cast<uint32_t>(s * SLOT / 16);
+                const uint32_t alo = slot_lo0 + static_cast<uint32_t>(s * G::SLOT / 16);
                 if (j >= 2 && j < nout) {
                     // all three outputs inside the unit: one N = 48 MMA per tap and row
                     const int o0 = ot + j;  // first taps of output o0: its slot has been read out
@@ -414,13 +424,11 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                     }
                     const uint32_t wwin = static_cast<uint32_t>((2 - o0 % NACC) * 256 / 16);
 #pragma unroll
-                    for (int dy = 0; dy < 3; ++dy)
+                    for (int t = 0; t < G::NTAP; ++t)
 #pragma unroll
-                        for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                            for (int r = 0; r < RY; ++r)
-                                mma_bf16_warp(tbase + r * ROWCOLS, alo + ((r + dy) * ROWB + dx * 16) / 16, ahi,
-                                              wlo + wwin + (dy * 3 + dx) * (WTAP / 16), whi, idesc_bf16(48));
+                        for (int r = 0; r < RY; ++r)
+                            mma_bf16_warp(tbase + r * ROWCOLS, alo + G::a_off(t, r) / 16, ahi,
+                                          wlo + wwin + t * (WTAP / 16), whi, idesc_bf16(48));
                     mma_commit_warp(&tfull[(o0 - 2) % NACC]);  // output o0 - 2 complete
                 } else {
                     // a unit's first or last two planes: one N = 16 MMA per valid output
@@ -438,14 +446,11 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                         }
                         const uint32_t wblk = static_cast<uint32_t>((2 - dz) * 256 / 16);
 #pragma unroll
-                        for (int dy = 0; dy < 3; ++dy)
+                        for (int t = 0; t < G::NTAP; ++t)
 #pragma unroll
-                            for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                                for (int r = 0; r < RY; ++r)
-                                    mma_bf16_warp(tbase + r * ROWCOLS + b * 16,
-                                                  alo + ((r + dy) * ROWB + dx * 16) / 16, ahi,
-                                                  wlo + wblk + (dy * 3 + dx) * (WTAP / 16), whi, idesc_bf16(16));
+                            for (int r = 0; r < RY; ++r)
+                                mma_bf16_warp(tbase + r * ROWCOLS + b * 16, alo + G::a_off(t, r) / 16, ahi,
+                                              wlo + wblk + t * (WTAP / 16), whi, idesc_bf16(16));
                         if (dz == 2)
                             mma_commit_warp(&tfull[b]);  // output o complete
                     }
@@ -973,32 +978,36 @@ int num_sms_dev()
     return n > 0 ? n : 1;
 }
 
-template <int COUT, int EPI>
+// CIN: channels per point of the input (16, or 8 for the packed feature input of layer 1).
+template <int COUT, int EPI, int CIN = 16>
 cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
 {
     using namespace convtc;
+    using G = Geo<CIN>;
+    constexpr int smem = tc_smem<CIN>();
     static int occ = -1;
     if (occ < 0) {
-        const void *fn = reinterpret_cast<const void *>(&k_conv_tc<COUT, EPI>);
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        const void *fn = reinterpret_cast<const void *>(&k_conv_tc<COUT, EPI, CIN>);
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         // the largest shared-memory carveout, so that two CTAs fit on an SM
         cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NTHREADS, SMEM) != cudaSuccess || occ < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NTHREADS, smem) != cudaSuccess || occ < 1) {
             cudaGetLastError();
             occ = 2;
         }
         // (the query answered 1 on GB300 although the launch's limits from registers and shared
         // memory are both 2; a grid of two CTAs per SM runs as one wave when both fit and as two
-        // otherwise, as the units are strided over the grid)
-        occ = std::max(occ, 2);
+        // otherwise, as the units are strided over the grid).  Tensor memory (256 columns per
+        // CTA) allows no more than two.
+        occ = 2;
     }
-    // activation [z][y][x][16] BF16: dims (channel, x, y, z), boxes of 8 channels x 130 points x 3 rows
+    // activation [z][y][x][CIN] BF16: dims (channel, x, y, z), boxes of 8 channels x BOXX points x 6 rows
     CUtensorMap m;
-    const uint64_t dims[4] = {static_cast<uint64_t>(CH), static_cast<uint64_t>(a.d.nx),
+    const uint64_t dims[4] = {static_cast<uint64_t>(CIN), static_cast<uint64_t>(a.d.nx),
                               static_cast<uint64_t>(a.d.ny), static_cast<uint64_t>(a.d.nz)};
-    const uint64_t strides[3] = {CH * 2ull, static_cast<uint64_t>(a.d.nx) * CH * 2,
-                                 static_cast<uint64_t>(a.d.nx) * a.d.ny * CH * 2};
-    const uint32_t box[4] = {8, BOXX, BOXY, 1};
+    const uint64_t strides[3] = {CIN * 2ull, static_cast<uint64_t>(a.d.nx) * CIN * 2,
+                                 static_cast<uint64_t>(a.d.nx) * a.d.ny * CIN * 2};
+    const uint32_t box[4] = {8, static_cast<uint32_t>(G::BOXX), BOXY, 1};
     std::string msg;
     if (!encode_tmap_bf16_4d(&m, a.in, dims, strides, box, &msg))
         return cudaErrorInvalidValue;
@@ -1007,7 +1016,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
     if (nunits > (1ll << 31) - 1)
         return cudaErrorInvalidValue;
     const int ctas = static_cast<int>(std::min<int64_t>(nunits, static_cast<int64_t>(num_sms_dev()) * occ));
-    k_conv_tc<COUT, EPI><<<ctas, NTHREADS, SMEM, s>>>(m, a, um, static_cast<int>(nunits), err);
+    k_conv_tc<COUT, EPI, CIN><<<ctas, NTHREADS, smem, s>>>(m, a, um, static_cast<int>(nunits), err);
     return cudaGetLastError();
 }
 
@@ -1096,9 +1105,12 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     if (st != GBST_OK)
         return st;
     const int64_t n = static_cast<int64_t>(d.nx) * d.ny * d.nz;
+    // inference on the tensor cores: the 8 feature channels packed at 16 bytes per point, layer 1
+    // with K = 16 spanning a point and its x neighbour
+    const bool x8 = c->feat && !keep && c->conv_impl != 1;
     if (c->feat) {
         st = closure_features_forward(up, un, cn, d.nx, d.ny, d.nz, c->feat_r, c->feat_w, c->feat_s, c->fb, c->x,
-                                      keep, c->stream);
+                                      keep, x8 ? 8 : 16, c->stream);
         if (st != GBST_OK)
             return st;
     } else {
@@ -1112,7 +1124,7 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     a.out = c->y1;
     a.zout = keep ? c->z1 : nullptr;
     a.cout_valid = c->hidden;
-    cudaError_t e = conv<16, EPI_GELU>(c, a);
+    cudaError_t e = x8 ? launch_conv_tc<16, EPI_GELU, 8>(a, c->derr, c->stream) : conv<16, EPI_GELU>(c, a);
     a.in = c->y1;
     a.wt = c->wf[1];
     a.bias = c->p + c->off[3];
@@ -1452,7 +1464,7 @@ gbst_status closure_feature_values(gbst_closure c, const float *u_plus, const fl
     if (st != GBST_OK)
         return st;
     st = closure_features_forward(u_plus, u_n, c_norm, nx, ny, nz, c->feat_r, c->feat_w, c->feat_s, c->fb, c->x,
-                                  true, c->stream);
+                                  true, 16, c->stream);
     if (st != GBST_OK)
         return st;
     return closure_features_values(u_plus, u_n, nx, ny, nz, c->fb, out, c->stream);

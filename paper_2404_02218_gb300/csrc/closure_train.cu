@@ -220,8 +220,9 @@ __global__ void __launch_bounds__(kFX *kFY) k_lap_z(DenseDims d, const float *__
 
 // The packed network input from u+, u^n, c_n and lu = L u^n: cn2 and g_a as
 // k_cn2_grads, t6 and t5 as the k_star calls of closure_features_forward, the
-// channels as k_pack_features.  R: the radius of L; w6: the sixth-difference star.
-template <int R>
+// channels as k_pack_features.  R: the radius of L; w6: the sixth-difference star;
+// XCH: channels per point of x (16: the last 8 zero; 8: packed, 16 bytes per point).
+template <int R, int XCH>
 __global__ void __launch_bounds__(kFX *kFY) k_features_z(DenseDims d, const float *__restrict__ up,
                                                          const float *__restrict__ un, const float *__restrict__ cn,
                                                          const float *__restrict__ lu, float4 w03, float w4,
@@ -308,9 +309,10 @@ __global__ void __launch_bounds__(kFX *kFY) k_features_z(DenseDims d, const floa
             const __nv_bfloat162 b2 = __floats2bfloat162_rn(sc.s[2 * k] * f[2 * k], sc.s[2 * k + 1] * f[2 * k + 1]);
             w4p[k] = *reinterpret_cast<const uint32_t *>(&b2);
         }
-        uint4 *o = reinterpret_cast<uint4 *>(xout + p * 16);
+        uint4 *o = reinterpret_cast<uint4 *>(xout + p * XCH);
         o[0] = make_uint4(w4p[0], w4p[1], w4p[2], w4p[3]);
-        o[1] = make_uint4(0u, 0u, 0u, 0u);
+        if (XCH == 16)
+            o[1] = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int k = 0; k < 6; ++k)
             qu[k] = qu[k + 1];
@@ -511,15 +513,18 @@ FeatScales to_scales(const double *sc)
 // Closure input features (8 channels) from (u+, u^n, c_n) into x (channels-last BF16, 16
 // channels, the last 8 zero): x_k = scales[k] f_k, see k_pack_features.  r, w: the star L.
 // aux: also leave cn2, g_a, t5 and t6 in b (the transpose and closure_features_values read
-// them); without it the two z-marching kernels compute the same x.
+// them); without it the two z-marching kernels compute the same x.  xch: channels per point
+// of x, 16 (the last 8 zero) or, without aux, 8 (packed).
 gbst_status closure_features_forward(const float *up, const float *un, const float *cn, int64_t nx, int64_t ny,
                                      int64_t nz, int r, const double *w, const double *scales,
-                                     const ClosureFeatBufs &b, __nv_bfloat16 *x, bool aux, cudaStream_t s)
+                                     const ClosureFeatBufs &b, __nv_bfloat16 *x, bool aux, int xch, cudaStream_t s)
 {
     DenseDims d;
     gbst_status st = dense_dims(nx, ny, nz, &d, "closure features");
     if (st != GBST_OK)
         return st;
+    if (xch != 16 && (xch != 8 || aux))
+        return record_error(GBST_EINVAL, "closure features: x has 16 channels per point, or 8 without aux");
     if (!aux) {
         // two z-marching launches: lu, then every channel (only b.lu is written besides x)
         if (r < 1 || r > 4)
@@ -540,11 +545,20 @@ gbst_status closure_features_forward(const float *up, const float *un, const flo
         }
         if ((st = launched("closure features")) != GBST_OK)
             return st;
-        switch (r) {
-        case 1: k_features_z<1><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
-        case 2: k_features_z<2><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
-        case 3: k_features_z<3><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
-        default: k_features_z<4><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+        if (xch == 8) {
+            switch (r) {
+            case 1: k_features_z<1, 8><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+            case 2: k_features_z<2, 8><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+            case 3: k_features_z<3, 8><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+            default: k_features_z<4, 8><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+            }
+        } else {
+            switch (r) {
+            case 1: k_features_z<1, 16><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+            case 2: k_features_z<2, 16><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+            case 3: k_features_z<3, 16><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+            default: k_features_z<4, 16><<<g, t, 0, s>>>(d, up, un, cn, b.lu, w03, wf[4], w6, sc, x); break;
+            }
         }
         return launched("closure features");
     }

@@ -48,25 +48,52 @@ namespace convtc {
 
 constexpr int TXP = 128;                 // output points per CTA row segment (MMA M)
 constexpr int RY = 4;                    // output rows per CTA (independent accumulation chains)
-constexpr int BOXX = TXP + 2;            // input points per row (x halo 1 each side)
 constexpr int BOXY = RY + 2;             // input rows per plane (y halo 1 each side)
-constexpr int ROWB = BOXX * 16;          // bytes of one row of 8 channels
-constexpr int HALF = (BOXY * ROWB + 127) / 128 * 128;  // one 8-channel box
-constexpr int SLOT = 2 * HALF;           // one input plane (both channel halves)
-constexpr int NS = 3;                    // plane slots: two planes of prefetch (98.5 KB per CTA: two CTAs per SM)
+constexpr int NS = 3;                    // plane slots: two planes of prefetch
 constexpr int NACC = 3;                  // accumulator slots: output o in slot o mod 3
 constexpr int ROWCOLS = NACC * 16;       // tensor-memory columns of one output row (the N = 48 MMA)
 constexpr int TCOLS = 256;               // allocated columns (RY x 48 = 192 used; two CTAs per SM fill the 512)
 constexpr int WBLK = 5;                  // weight blocks per tap: dz = 2, 1, 0, 2, 1
 constexpr int WHALF = WBLK * 16 * 16;    // bytes of one 8-channel K half of a tap: [80 rows][8 ci] BF16
-constexpr int WTAP = 2 * WHALF;          // bytes of one tap (dy, dx)
-constexpr int WBYTES = 9 * WTAP;         // weights: [dy dx][half][block][co 16][8 ci] BF16
+constexpr int WTAP = 2 * WHALF;          // bytes of one tap
 constexpr int HDR = 256;                 // barriers and flags
-constexpr int SMEM = HDR + WBYTES + NS * SLOT;
 constexpr int NEPI = 8;                  // epilogue warps: lane quadrant w & 3, channels 8 (w >> 2) ..
 constexpr int NTHREADS = (NEPI + 2) * 32;
 constexpr int ZCH = 32;                  // output planes per work unit
-constexpr uint32_t BOX_BYTES = BOXY * BOXX * 16;  // bytes one box delivers
+
+// Plane geometry by input width.  CIN = 16: two 8-channel boxes per plane, the
+// K = 16 operand of a tap is (channels 0-7 | channels 8-15) of one point, nine
+// (dy, dx) taps.  CIN = 8 (16 bytes per point): one box, and the K = 16 operand
+// pairs a point with its x neighbour (the second core matrix along K starts 16
+// bytes later), so taps dx = -1 and 0 form one MMA and dx = +1 another (its
+// second K half has zero weights): six taps (dy, pair | single).  Its rows carry
+// two extra points so that the single tap's second half stays inside the row.
+template <int CIN>
+struct Geo;
+template <>
+struct Geo<16> {
+    static constexpr int BOXX = TXP + 2;                           // input points per row (x halo 1 each side)
+    static constexpr int ROWB = BOXX * 16;                         // bytes of one row of 8 channels
+    static constexpr int HALF = (BOXY * ROWB + 127) / 128 * 128;   // one 8-channel box
+    static constexpr int SLOT = 2 * HALF;                          // one input plane
+    static constexpr int NBOX = 2;
+    static constexpr int LBO_A = HALF;                             // K half 2: channels 8-15, same point
+    static constexpr int NTAP = 9;
+    __host__ __device__ static constexpr int a_off(int t, int r) { return (r + t / 3) * ROWB + (t % 3) * 16; }
+};
+template <>
+struct Geo<8> {
+    static constexpr int BOXX = TXP + 4;
+    static constexpr int ROWB = BOXX * 16;
+    static constexpr int HALF = (BOXY * ROWB + 127) / 128 * 128;
+    static constexpr int SLOT = HALF;
+    static constexpr int NBOX = 1;
+    static constexpr int LBO_A = 16;                               // K half 2: the next point
+    static constexpr int NTAP = 6;
+    __host__ __device__ static constexpr int a_off(int t, int r) { return (r + t / 2) * ROWB + (t % 2) * 32; }
+};
+template <int CIN>
+constexpr int tc_smem() { return HDR + Geo<CIN>::NTAP * WTAP + NS * Geo<CIN>::SLOT; }
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 

@@ -205,7 +205,7 @@ struct ClosureFeatBufs {
 };
 gbst_status closure_features_forward(const float *up, const float *un, const float *cn, int64_t nx, int64_t ny,
                                      int64_t nz, int r, const double *w, const double *scales,
-                                     const ClosureFeatBufs &b, __nv_bfloat16 *x, bool aux, cudaStream_t s);
+                                     const ClosureFeatBufs &b, __nv_bfloat16 *x, bool aux, int xch, cudaStream_t s);
 gbst_status closure_features_adjoint(const __nv_bfloat16 *dx, int64_t nx, int64_t ny, int64_t nz, int r,
                                      const double *w, const double *scales, const ClosureFeatBufs &b, float *g_up,
                                      float *g_un, cudaStream_t s);

@@ -116,7 +116,8 @@ def test_feature_values_match_oracle(torch_cuda):
 @pytest.mark.parametrize("dims", [(37, 21, 19), (45, 13, 70), (1, 1, 1)])
 def test_feature_forward_matches_oracle(torch_cuda, dims):
     """The inference forward (z-marching feature kernels: ragged 32 x 8 tiles, several
-    32-plane chunks) against the oracle network on the oracle's features."""
+    32-plane chunks; layer 1 on the 8-channel packed input) against the mma.sync path
+    and the oracle network on the oracle's features."""
     torch = torch_cuda
     from oracle import closure as oc
     shape = tuple(reversed(dims))
@@ -126,7 +127,10 @@ def test_feature_forward_matches_oracle(torch_cuda, dims):
     cl, p, sc = _closure8(torch, int(np.prod(dims)), t=t_out)
     t = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (up, un, cn)]
     got = cl.forward(*t).double().cpu().numpy()
+    cl.set_conv_impl(1)  # mma.sync: 16-channel input layout, every layer padded to K = 16
+    other = cl.forward(*t).double().cpu().numpy()
     cl.close()
+    assert np.linalg.norm(got - other) <= 2e-3 * np.linalg.norm(other)
     pb = {k: _bf16(torch, v) for k, v in p.items()}
     f32 = [a.astype(np.float32).astype(np.float64) for a in (up, un, cn)]
     x = oc.feature_channels(f32[0], f32[1], f32[2] ** 2, oracle.central_weights_f64(4), sc)
