@@ -172,6 +172,7 @@ struct ConvArgs {
     __nv_bfloat16 *zout;       // EPI_GELU: pre-activations (optional)
     const __nv_bfloat16 *aux;  // EPI_DGELU: pre-activations of the layer below
     float *out_f32;            // EPI_LINEAR_F32: channel 0, dense [z][y][x]
+    float oscale;              // EPI_LINEAR_F32: factor on the output (1 for the network units)
     Dims d;
     int cout_valid;            // output channels that are real (the rest are written as 0)
 };
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(NTHR) k_conv(const ConvArgs a)
                 float v0 = acc[t][2 * half8], v1 = acc[t][2 * half8 + 1];
                 if (EPI == EPI_LINEAR_F32) {
                     if (c == 0)
-                        a.out_f32[p] = v0 + a.bias[0];
+                        a.out_f32[p] = (v0 + a.bias[0]) * a.oscale;
                 } else if (EPI == EPI_GELU) {
                     v0 += a.bias[c];
                     v1 += a.bias[c + 1];
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                 const float (&v)[8] = vr[r];
                 const int64_t p = (static_cast<int64_t>(z) * a.d.ny + y) * a.d.nx + x;
                 if (EPI == EPI_LINEAR_F32) {
-                    a.out_f32[p] = v[0] + bias[0];
+                    a.out_f32[p] = (v[0] + bias[0]) * a.oscale;
                 } else if (EPI == EPI_GELU) {
                     // channels >= cout_valid (padding) are zero
                     float2 zv[4];
@@ -605,7 +606,7 @@ __device__ __forceinline__ void load_plane1(unsigned char *slot, const __nv_bflo
 }
 
 __global__ void __launch_bounds__(T1NT) k_conv_out1(const __nv_bfloat16 *in, const __nv_bfloat16 *wt,
-                                                     const float *bias, Dims d, float *out)
+                                                     const float *bias, Dims d, float oscale, float *out)
 {
     __shared__ float2 w2[27][CH / 2];  // [tap][channel pair]
     extern __shared__ __align__(128) unsigned char ring[];
@@ -671,7 +672,7 @@ __global__ void __launch_bounds__(T1NT) k_conv_out1(const __nv_bfloat16 *in, con
             for (int j = 0; j < 4; ++j) {
                 const int x = x0 + tx + 16 * j;
                 if (x < d.nx)
-                    out[(static_cast<int64_t>(zi - 1) * d.ny + y) * d.nx + x] = (lo[j].x + lo[j].y) + b;
+                    out[(static_cast<int64_t>(zi - 1) * d.ny + y) * d.nx + x] = ((lo[j].x + lo[j].y) + b) * oscale;
             }
         }
 #pragma unroll
@@ -875,13 +876,6 @@ __global__ void k_gelu(const float *x, float *y, int64_t n)
         y[p] = gelu(x[p]);
 }
 
-__global__ void k_scale(float *dst, const float *src, float scale, int64_t n)
-{
-    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
-         p += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        dst[p] = scale * src[p];
-}
-
 __global__ void k_scale_add(float *dst, const float *src, float scale, int64_t n)
 {
     for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
@@ -1069,7 +1063,7 @@ cudaError_t launch_conv_out1(const ConvArgs &a, cudaStream_t s)
     }
     const int tiles = ((a.d.nx + T1X - 1) / T1X) * ((a.d.ny + T1Y - 1) / T1Y);
     dim3 grid(tiles, (a.d.nz + Z1CH - 1) / Z1CH);
-    k_conv_out1<<<grid, T1NT, smem, s>>>(a.in, a.wt, a.bias, a.d, a.out_f32);
+    k_conv_out1<<<grid, T1NT, smem, s>>>(a.in, a.wt, a.bias, a.d, a.oscale, a.out_f32);
     return cudaGetLastError();
 }
 
@@ -1098,8 +1092,10 @@ gbst_status refresh_weights(gbst_closure c)
     return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
 }
 
-// Forward pass into c->o (network units).  keep: also store the pre-activations.
-gbst_status forward(gbst_closure c, const float *up, const float *un, const float *cn, Dims d, bool keep)
+// Forward pass into out (default c->o, network units) times oscale.  keep: also store the
+// pre-activations.
+gbst_status forward(gbst_closure c, const float *up, const float *un, const float *cn, Dims d, bool keep,
+                    float *out = nullptr, float oscale = 1.0f)
 {
     gbst_status st = refresh_weights(c);
     if (st != GBST_OK)
@@ -1137,7 +1133,8 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     b.in = c->y2;
     b.wt = c->wf[2];
     b.bias = c->p + c->off[5];
-    b.out_f32 = c->o;
+    b.out_f32 = out ? out : c->o;
+    b.oscale = oscale;
     b.cout_valid = 1;
     if (e == cudaSuccess)  // impl 2 runs the one-channel last layer on the CUDA cores
         e = c->conv_impl == 2 ? launch_conv_out1(b, c->stream) : conv<8, EPI_LINEAR_F32>(c, b);
@@ -1351,13 +1348,8 @@ gbst_status closure_forward(gbst_closure c, const float *u_plus, const float *u_
     gbst_status st = check_dims(c, nx, ny, nz, &d);
     if (st != GBST_OK)
         return st;
-    st = forward(c, u_plus, u_n, c_norm, d, false);
-    if (st != GBST_OK)
-        return st;
-    const int64_t n = nx * ny * nz;
-    k_scale<<<blocks_for(n), 256, 0, c->stream>>>(correction, c->o, static_cast<float>(1.0 / c->out_scale), n);
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
+    // the last layer writes o / t into correction
+    return forward(c, u_plus, u_n, c_norm, d, false, correction, static_cast<float>(1.0 / c->out_scale));
 }
 
 gbst_status closure_loss_grad(gbst_closure c, const float *u_plus, const float *u_n, const float *c_norm,
