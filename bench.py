@@ -583,8 +583,10 @@ def extras(torch, hbm: float, tune: bool, acc: dict | None = None):
     cn = torch.full((cfg.nc,) * 3, 0.6, device="cuda")
     torch.cuda.synchronize()
     ms = timed_runs(torch, cl.stream, lambda: cl.forward(up, up, cn), reps=10)
-    tensor = 27 * 2 * (16 * 16 + 16 * 16)  # the two tcgen05 layers (K = 16: 8 inputs padded, N = 16)
-    useful = 27 * 2 * (8 * 16 + 16 * 16 + 16 * 1)  # the last layer (16 -> 1) runs on the CUDA cores
+    # MMA work issued per point: layer 1 as 18 K = 16 taps (a point and its x neighbour), layers 2-3
+    # as 27 taps, 16 output columns each (layer 3 has one real channel)
+    tensor = 2 * 16 * 16 * (18 + 27 + 27)
+    useful = 27 * 2 * (8 * 16 + 16 * 16 + 16 * 1)
     bf16 = measured_peaks()[0].get("bf16_tflops", 1900.0)
     res.update({"gain_at_initialisation": init["gain"], "rel_l2_at_initialisation": init["rel_l2_closure"],
                 "train_seconds": t_train, "updates": len(losses), "loss_first": losses[0], "loss_last": losses[-1],
@@ -593,9 +595,9 @@ def extras(torch, hbm: float, tune: bool, acc: dict | None = None):
                 "forward_ms_256": ms, "forward_tflops_useful": useful * n3 / ms / 1e9,
                 "forward_tensor_tflops_over_whole_forward": tensor * n3 / ms / 1e9,
                 "forward_frac_of_bf16_peak": tensor * n3 / ms / 1e9 / bf16,
-                "kernel": "features: FP32 dense stencils; layers 1-2: tcgen05.mma kind::f16 M128 N16 K16, BF16 in, "
-                          "FP32 accumulators in tensor memory; layer 3 (16 -> 1): packed FP32x2 FMAs on the CUDA "
-                          "cores"})
+                "kernel": "features: two z-marching FP32 stencil kernels; layers 1-3: tcgen05.mma kind::f16 "
+                          "M128 N48 K16 (three output planes per MMA), BF16 in, FP32 accumulators in tensor "
+                          "memory, GELU epilogue in packed FP32x2"})
     out["closure_256_so4"] = res
     cl.close()
     return out
