@@ -2097,9 +2097,9 @@ gbst_status stencil_variant_info(int i, char *buf, size_t len)
         return fail(GBST_EINVAL, "bad variant index or buffer");
     snprintf(buf, len,
              "{\"R\": %d, \"eq\": %d, \"storage\": %d, \"has_z\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, "
-             "\"minb\": %d, \"txt\": %d, \"tb\": %d, \"ys\": %d, \"nf\": %d}",
+             "\"minb\": %d, \"txt\": %d, \"tb\": %d, \"ys\": %d, \"nf\": %d, \"opt\": %d}",
              v.R, v.eq, v.storage, v.has_z ? 1 : 0, v.nthreads, v.py, v.depth, v.minb, v.txt, v.tb, v.ys ? 1 : 0,
-             v.nf);
+             v.nf, v.opt);
     return GBST_OK;
 }
 

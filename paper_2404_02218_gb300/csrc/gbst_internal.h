@@ -112,7 +112,16 @@ struct StreamVariant {
     int tb = 1;     // time steps per launch: 1, or 2 (temporally blocked heat kernel)
     bool ys = false; // 2D grid streamed along y (one-row tiles)
     int nf = 1;      // fields of a fused multi-field system sweep (1: a single field)
+    int opt = 0;     // streaming-kernel options (kOpt* bits)
 };
+
+// Streaming-kernel options.  kOptScalarOddX: the x-neighbour sums of odd
+// offsets m (operands that straddle the thread's packed FP32x2 point pairs) as
+// two scalar additions each instead of one packed addition of re-paired
+// registers (the same results bit for bit).
+constexpr int kOptScalarOddX = 2;
+// Threads of one CTA of a streaming variant (consumers and the producer warp).
+inline int block_threads(const StreamVariant &v) { return v.nthreads + 32; }
 
 // Tile of a variant: width in points, height in rows (a temporally blocked
 // variant's nthreads counts its main and edge warps; the tile is the grown

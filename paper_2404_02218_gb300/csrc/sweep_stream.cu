@@ -13,13 +13,14 @@ const Entry *table_r2_2d(int *n);
 const Entry *table_r4_2d(int *n);
 const Entry *table_sys(int *n);
 const Entry *table_r2_rows4(int *n);
+const Entry *table_sx(int *n);
 }  // namespace sweep
 
 namespace {
 using sweep::Entry;
 
 struct Registry {
-    static constexpr int kTables = 9;
+    static constexpr int kTables = 10;
     const Entry *tab[kTables];
     int n[kTables];
     Registry()
@@ -33,6 +34,7 @@ struct Registry {
         tab[6] = sweep::table_r4_2d(&n[6]);
         tab[7] = sweep::table_sys(&n[7]);
         tab[8] = sweep::table_r2_rows4(&n[8]);
+        tab[9] = sweep::table_sx(&n[9]);
     }
     int total() const
     {
@@ -65,7 +67,7 @@ const Entry *find(const StreamVariant &v)
         const Entry *e = r.at(i);
         if (e->v.R == v.R && e->v.eq == v.eq && e->v.storage == v.storage && e->v.has_z == v.has_z &&
             e->v.nthreads == v.nthreads && e->v.py == v.py && e->v.depth == v.depth && e->v.minb == v.minb &&
-            e->v.txt == v.txt && e->v.tb == v.tb && e->v.ys == v.ys && e->v.nf == v.nf)
+            e->v.txt == v.txt && e->v.tb == v.tb && e->v.ys == v.ys && e->v.nf == v.nf && e->v.opt == v.opt)
             return e;
     }
     return nullptr;
@@ -139,7 +141,7 @@ int stream_occupancy(const StreamVariant &v, size_t smem)
     if (!e || !allow_max_smem(e))
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, e->fn, v.nthreads + 32, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, e->fn, block_threads(v), smem) != cudaSuccess)
         return 0;
     return n;
 }
@@ -152,13 +154,13 @@ cudaError_t launch_stream_sweep(const StreamVariant &v, const SweepArgs &a, int 
         return cudaErrorInvalidDeviceFunction;
     const int slot_bytes = stream_slot_bytes(v, smem);
     if (!cooperative) {
-        e->fn<<<ctas, v.nthreads + 32, smem, s>>>(a, slot_bytes);
+        e->fn<<<ctas, block_threads(v), smem, s>>>(a, slot_bytes);
         return cudaGetLastError();
     }
     // persistent launch: every CTA must be resident for the grid barrier
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(ctas);
-    cfg.blockDim = dim3(v.nthreads + 32);
+    cfg.blockDim = dim3(block_threads(v));
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

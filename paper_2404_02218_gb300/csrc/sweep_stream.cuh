@@ -277,10 +277,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *counter, unsigned int
 // TX points (plus the x halo), the register queue holds the 2r+1 rows around
 // the output row, and there is no middle axis; the update is the 2D one,
 // ((x- + x+) + (y- + y+)) per offset, bit-identical to the 2D tile mode.
-template <int R, int EQ, int ST, bool HAS_Z, int NC, int PY, int D, int MINB, int TXT, bool YS = false>
+//
+// OPT & kOptScalarOddX: the x-neighbour sums of odd offsets, whose operands
+// straddle the thread's packed point pairs, as two scalar additions instead of
+// one packed addition of re-paired registers (the same results bit for bit).
+template <int R, int EQ, int ST, bool HAS_Z, int NC, int PY, int D, int MINB, int TXT, bool YS = false, int OPT = 0>
 __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs a, const int slot_bytes)
 {
     using St = Storage<ST>;
+    constexpr bool SX = (OPT & kOptScalarOddX) != 0;
     constexpr int NT = NC * 32;         // consumer threads
     constexpr int PX = St::PX;
     constexpr int ES = St::ES;
@@ -552,7 +557,13 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                                     const int e = 2 * pp;
                                     const float2 xm = make_float2(xel(r_, e - m), xel(r_, e + 1 - m));
                                     const float2 xp = make_float2(xel(r_, e + m), xel(r_, e + 1 + m));
-                                    float2 t = __fadd2_rn(xm, xp);
+                                    float2 t;
+                                    if (SX && (m & 1)) {
+                                        t.x = __fadd_rn(xm.x, xp.x);
+                                        t.y = __fadd_rn(xm.y, xp.y);
+                                    } else {
+                                        t = __fadd2_rn(xm, xp);
+                                    }
                                     if (MID)
                                         t = __fadd2_rn(t, __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
                                     if (ZQ)
@@ -660,11 +671,11 @@ struct Entry {
     KernelFn fn;
 };
 
-template <int R, int EQ, int ST, bool HZ, int NC, int PY, int D, int MINB, int TXT, bool YS = false>
+template <int R, int EQ, int ST, bool HZ, int NC, int PY, int D, int MINB, int TXT, bool YS = false, int OPT = 0>
 constexpr Entry entry()
 {
-    return Entry{StreamVariant{R, EQ, ST, HZ, NC * 32, PY, D, MINB, TXT, 1, YS},
-                 &k_stream<R, EQ, ST, HZ, NC, PY, D, MINB, TXT, YS>};
+    return Entry{StreamVariant{R, EQ, ST, HZ, NC * 32, PY, D, MINB, TXT, 1, YS, 1, OPT},
+                 &k_stream<R, EQ, ST, HZ, NC, PY, D, MINB, TXT, YS, OPT>};
 }
 
 // both equations for one radius, storage, dimensionality and shape

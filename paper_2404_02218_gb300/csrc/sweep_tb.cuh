@@ -73,7 +73,7 @@ struct TbShape {
 // QC -+ m.  (Taking the x neighbours from adjacent lanes by shuffles, with the
 // tile-edge lanes reading shared memory -- by a branch or by predicated loads --
 // measured 4-23 % slower for order 2.)
-template <int R, int PY, int QC>
+template <int R, int PY, int QC, bool SX>
 __device__ __forceinline__ void tb_update(const float2 (&q)[2 * R + 1][PY][2], const unsigned char *cb,
                                           const int row, const float2 wc2, const float2 (&w2)[R + 1],
                                           const float2 a2, float (&o)[PY][4])
@@ -120,7 +120,14 @@ __device__ __forceinline__ void tb_update(const float2 (&q)[2 * R + 1][PY][2], c
                 const int e = 2 * pp;
                 const float2 xm = make_float2(xel(r_, e - m), xel(r_, e + 1 - m));
                 const float2 xp = make_float2(xel(r_, e + m), xel(r_, e + 1 + m));
-                float2 t = __fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
+                float2 xs;
+                if (SX && (m & 1)) {  // operands straddle the packed pairs: two scalar additions
+                    xs.x = __fadd_rn(xm.x, xp.x);
+                    xs.y = __fadd_rn(xm.y, xp.y);
+                } else {
+                    xs = __fadd2_rn(xm, xp);
+                }
+                float2 t = __fadd2_rn(xs, __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
                 t = __fadd2_rn(t, __fadd2_rn(q[(QC - m + 2 * QN) % QN][r_][pp], q[(QC + m) % QN][r_][pp]));
                 sv[r_][pp] = __ffma2_rn(w2[m], t, sv[r_][pp]);
             }
@@ -136,7 +143,7 @@ __device__ __forceinline__ void tb_update(const float2 (&q)[2 * R + 1][PY][2], c
         }
 }
 
-template <int R, int NW, int PY, int D, int MINB>
+template <int R, int NW, int PY, int D, int MINB, int OPT = 0>
 __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, const int slot_bytes)
 {
     using Sh = TbShape<R, NW, PY, D>;
@@ -358,7 +365,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                     static_assert(NU == R + 2, "u' ring length");
                     constexpr int qc2 = (k - 3 * R - 1 + 4 * QN) % QN;
                     float o[PY][PX];
-                    tb_update<R, PY, qc2>(q2, ubuf + (uw + 1 == NU ? 0 : uw + 1) * Sh::U_BYTES + u_off, U_ROW,
+                    tb_update<R, PY, qc2, (OPT & kOptScalarOddX) != 0>(q2, ubuf + (uw + 1 == NU ? 0 : uw + 1) * Sh::U_BYTES + u_off, U_ROW,
                                           wc2, w2, a2, o);
 #pragma unroll
                     for (int r_ = 0; r_ < PY; ++r_) {
@@ -380,7 +387,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                 constexpr int qc1 = (k - R + QN) % QN;
                 const int slot_c = slot_n >= R ? slot_n - R : slot_n - R + S;
                 float o[PY][PX];
-                tb_update<R, PY, qc1>(q1, slots + slot_c * slot_bytes + in_off, IN_ROW, wc2, w2, a2, o);
+                tb_update<R, PY, qc1, (OPT & kOptScalarOddX) != 0>(q1, slots + slot_c * slot_bytes + in_off, IN_ROW, wc2, w2, a2, o);
                 // u' plane index (interior z) of this result; u' is zero outside the interior
                 const int zq = u.z0 - 3 * R + j;
                 if (static_cast<unsigned>(zq) >= static_cast<unsigned>(nz)) {
@@ -462,11 +469,11 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
 
 }  // namespace
 
-template <int R, int NW, int PY, int D, int MINB>
+template <int R, int NW, int PY, int D, int MINB, int OPT = 0>
 constexpr Entry tb_entry()
 {
-    return Entry{StreamVariant{R, GBST_HEAT, GBST_F32, true, (NW + 1) * 32, PY, D, MINB, 32, 2},
-                 &k_tb<R, NW, PY, D, MINB>};
+    return Entry{StreamVariant{R, GBST_HEAT, GBST_F32, true, (NW + 1) * 32, PY, D, MINB, 32, 2, false, 1, OPT},
+                 &k_tb<R, NW, PY, D, MINB, OPT>};
 }
 
 }  // namespace sweep
