@@ -678,11 +678,12 @@ def kernel_name(plan: dict) -> str:
     """Template instance of a heat FP32 3D plan, as the profiler names it."""
     px = 4
     txt = plan["tile"][0] // px
+    opt = plan.get("opt", 0)
     if plan.get("tb", 1) == 2:
         nw = plan["threads"] // 32 - 1
-        return f"k_tb<{plan['R']}, {nw}, {plan['py']}, {plan['depth']}, {plan['minb']}>"
+        return f"k_tb<{plan['R']}, {nw}, {plan['py']}, {plan['depth']}, {plan['minb']}, {opt}>"
     nc = plan["threads"] // 32
-    return f"k_stream<{plan['R']}, 0, 0, 1, {nc}, {plan['py']}, {plan['depth']}, {plan['minb']}, {txt}, 0>"
+    return f"k_stream<{plan['R']}, 0, 0, 1, {nc}, {plan['py']}, {plan['depth']}, {plan['minb']}, {txt}, 0, {opt}>"
 
 
 def ncu_traffic(plan: dict):

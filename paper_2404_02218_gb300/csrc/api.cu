@@ -2017,12 +2017,12 @@ gbst_status stencil_describe(gbst_handle h, char *buf, size_t len)
              "{\"kernel\": \"%s\", \"R\": %d, \"threads\": %d, \"py\": %d, \"depth\": %d, \"tile\": [%d, %d], "
              "\"zchunks\": %d, \"units\": %d, \"ctas\": %d, \"occupancy\": %d, \"smem\": %zu, \"subdomains\": %zu, "
              "\"halo_boxes\": %d, \"variant\": %d, \"minb\": %d, \"tb\": %d, \"ys\": %d, \"nf\": %d, \"dyn\": %d, "
-             "\"overlap\": %d, \"interior_units\": %d}",
+             "\"overlap\": %d, \"interior_units\": %d, \"opt\": %d}",
              p.stream ? "stream" : "simple", h->R, p.var.nthreads, p.var.py, p.var.depth, tile_w(p.var, px),
              p.stream ? tile_h(p.var) : (p.var.nthreads / std::max(1, p.txt)) * p.var.py, p.zchunks, p.nunits,
              p.ctas, p.occupancy, p.smem, h->subs.size(), h->nboxes, p.variant, p.var.minb,
              p.stream ? p.var.tb : 1, p.stream && p.var.ys ? 1 : 0, h->nf, p.dyn ? 1 : 0, p.overlap ? 1 : 0,
-             p.nint);
+             p.nint, p.stream ? p.var.opt : 0);
     return GBST_OK;
 }
 
