@@ -696,6 +696,23 @@ int64_t byte_off(const Layout &L, int64_t i, int64_t j, int64_t k)
     return ((k + L.rz) * L.rows + (j + L.r)) * L.pitch * L.es + (i + L.G) * L.es;
 }
 
+// An x face (rows of r elements, each its own DRAM sector at both ends) widened to
+// whole 32-byte sectors: receive [-W, 0) from the sender's last W interior columns,
+// or [n, n + W) from its first W.  The extra ghost cells lie beyond the radius and
+// are never read; writing whole sectors spares the DRAM fills of partly written ones.
+// Only where both x ghost regions hold W elements and the sender has W columns.
+void widen_x_face(CopyBox &b, const Layout &dst, const Layout &src, int dir, int R)
+{
+    const int W = 32 / dst.es;
+    if (R >= W || dst.G < W || src.G < W || src.nx < W)
+        return;
+    if (dir < 0) {
+        b.dst_off -= static_cast<int64_t>(W - R) * dst.es;
+        b.src_off -= static_cast<int64_t>(W - R) * src.es;
+    }
+    b.ex = W;
+}
+
 gbst_status build_copies(gbst_handle h)
 {
     std::vector<CopyBox> boxes;
@@ -724,6 +741,8 @@ gbst_status build_copies(gbst_handle h)
                     b.ex = e.size[0];
                     b.ey = e.size[1];
                     b.ez = e.size[2];
+                    if (e.to[0] != 0)
+                        widen_x_face(b, s.lu, ns.lu, e.to[0], R);
                     boxes.push_back(b);
                     found = true;
                 }
@@ -747,6 +766,8 @@ gbst_status build_copies(gbst_handle h)
                 b.ex = ext[0];
                 b.ey = ext[1];
                 b.ez = ext[2];
+                if (a == 0)
+                    widen_x_face(b, s.lu, s.lu, side == 0 ? -1 : 1, R);
                 boxes.push_back(b);
             }
     }

@@ -86,7 +86,8 @@ SimpleFn simple_for_r(int R)
 // [blk0, blk0 + nblk) (found by binary search over blk0).  Rows of ex elements:
 // boxes with long rows (faces normal to y or z) give each warp one row at a
 // time, moved in 16-byte pieces when the row's two ends allow it; boxes with
-// short rows (faces normal to x, ex = r) give each thread one element.  Index
+// short rows (faces normal to x) give each thread one 16-byte piece when rows
+// and starts allow it, else one element.  Index
 // arithmetic is 32-bit (a box holds fewer than 2^31 elements; checked on the host).
 constexpr int kCopyThreads = 256;
 constexpr int kCopyLongRow = 32;  // rows of at least this many elements go warp-per-row
@@ -132,6 +133,20 @@ __global__ void __launch_bounds__(kCopyThreads) k_halo_copies(const GridDev *gri
                 for (uint32_t i = lane; i < ex; i += 32)
                     reinterpret_cast<uint16_t *>(d)[i] = reinterpret_cast<const uint16_t *>(s)[i];
             }
+        }
+        return;
+    }
+    // short rows of whole 16-byte pieces at 16-byte aligned starts (x faces widened to a
+    // 32-byte sector): consecutive threads take consecutive pieces of consecutive rows
+    if ((row_bytes & 15) == 0 &&
+        ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) | static_cast<uintptr_t>(sps) |
+          static_cast<uintptr_t>(spp) | static_cast<uintptr_t>(dps) | static_cast<uintptr_t>(dpp)) & 15) == 0) {
+        const uint32_t cpr = row_bytes >> 4, n = nrows * cpr;
+        for (uint32_t t = bb * kCopyThreads + threadIdx.x; t < n; t += nb * kCopyThreads) {
+            const uint32_t row = t / cpr, c = t - row * cpr;
+            const uint32_t j = row % ey, k = row / ey;
+            *reinterpret_cast<uint4 *>(dst + k * dpp + j * dps + c * 16u) =
+                *reinterpret_cast<const uint4 *>(src + k * spp + j * sps + c * 16u);
         }
         return;
     }
