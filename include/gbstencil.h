@@ -283,9 +283,13 @@ gbst_status closure_set_loss_weight(gbst_closure c, double w);
  * zero field then gets a zero correction). */
 gbst_status closure_freeze_biases(gbst_closure c, int freeze);
 /* Convolution kernels: impl 0 (default) = tcgen05 MMAs with accumulators in
- * tensor memory, operands staged by TMA; impl 1 = the mma.sync kernels (kept
+ * tensor memory, operands staged by TMA, the one-channel last layer in
+ * tap-split form (the tensor cores contract channels and x taps per input row,
+ * the CUDA cores add the nine y/z taps); impl 1 = the mma.sync kernels (kept
  * as an independent cross-check of the same arithmetic); impl 2 = tcgen05 for
- * the two hidden layers, the one-channel last layer on the CUDA cores.  A bounded wait that
+ * the two hidden layers, the one-channel last layer on the CUDA cores; impl 3 =
+ * tcgen05 with the last layer computed like the hidden ones (its single output
+ * channel padded to the MMA's N).  A bounded wait that
  * expires in a tcgen05 kernel is reported as GBST_ETIMEOUT by the next
  * closure_loss_grad / closure_get_params / closure_get_grads. */
 gbst_status closure_set_conv_impl(gbst_closure c, int impl);

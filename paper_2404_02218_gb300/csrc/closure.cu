@@ -684,6 +684,253 @@ __global__ void __launch_bounds__(T1NT) k_conv_out1(const __nv_bfloat16 *in, con
     }
 }
 
+// Last layer (16 channels -> 1) on tcgen05 in tap-split form.  With the output
+// o(x, y, z) = sum over (dz, dy, dx, ci) of W[dz][dy][dx][ci] h(x+dx-1, y+dy-1, z+dz-1)[ci],
+// the tensor cores first contract the channels and the x taps of every input row:
+//   Y_n(x, y', p) = sum over (dx, ci) of W[dz][dy][dx][ci] h(x+dx-1, y', p)[ci],  n = 3 dz + dy,
+// three N = 16 MMAs (dx = 0, 1, 2: the plane slot shifted by dx points; columns
+// n = 0..8 used) per input row and plane, into tensor memory; the CUDA cores then
+// add the nine (dy, dz) terms: o(x, y, z) = sum over (dz, dy) of Y_{3dz+dy}(x, y+dy-1, z+dz-1).
+// Per plane a CTA (128 x-points, RY = 4 output rows) issues 6 x 3 MMAs for its 6
+// input rows, against 9 N = 48 MMAs per output row in the general kernel: a third
+// of the A-tile reads from shared memory.  Input staging (TMA boxes of 8 channels x
+// 130 points x 6 rows, the producer warp and the plane ring) is the general kernel's.
+// Epilogue warp w reads lanes 32 (w & 3) .. +31 (points) and output rows 2 (w >> 2)
+// and 2 (w >> 2) + 1, i.e. input rows 2 (w >> 2) .. +3 of each plane; each plane
+// feeds output planes p + 1 (dz = 0), p (dz = 1) and p - 1 (dz = 2), kept in three
+// rotating registers per row; output p - 1 is then complete.  The terms of an
+// output add in a fixed order: planes in z order, within a plane dy = 0, 1, 2.
+namespace out1tc {
+constexpr int NSET = 2;                  // accumulator sets (one input plane each)
+constexpr int SETCOLS = 6 * 16;          // 6 input rows x 16 columns
+constexpr int TCOLS = 256;               // allocated tensor-memory columns
+constexpr int WDX = 2 * 16 * 16;         // bytes of one dx weight matrix: [half][16 rows][8 ci] BF16
+constexpr int NSLOT = 4;                 // plane slots
+constexpr int SMEM = convtc::HDR + 3 * WDX + NSLOT * convtc::Geo<16>::SLOT;
+}  // namespace out1tc
+
+// D[tmem] (+)= A B as mma_bf16_warp, with the accumulate flag a runtime value.
+__device__ __forceinline__ void mma_bf16_warp_acc(uint32_t d_tmem, uint32_t alo, uint32_t ahi, uint32_t blo,
+                                                  uint32_t bhi, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred e, a;\n\t.reg .b32 l;\n\t.reg .b64 da, db;\n\t"
+        "setp.ne.b32 a, %6, 0;\n\t"
+        "elect.sync l|e, 0xffffffff;\n\t"
+        "mov.b64 da, {%1, %2};\n\t"
+        "mov.b64 db, {%3, %4};\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, a;\n\t}" ::"r"(d_tmem),
+        "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
+}
+
+// Columns 0..8 of one tensor-memory row set for the warp's 32 lanes (no wait).
+__device__ __forceinline__ void tmem_ld9(uint32_t taddr, uint32_t (&r)[9])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[8]) : "r"(taddr + 8));
+}
+
+__global__ void __launch_bounds__(convtc::NTHREADS, 2)
+    k_conv_out1_tc(const __grid_constant__ CUtensorMap tmap, const ConvArgs a, const convtc::UnitMap um,
+                   const int nunits, int *err)
+{
+    using namespace convtc;
+    using G = Geo<16>;
+    using out1tc::NSET;
+    using out1tc::NSLOT;
+    using out1tc::SETCOLS;
+    using out1tc::WDX;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm);  // [NSLOT] input plane landed
+    uint64_t *empty = full + NSLOT;                       // [NSLOT] input plane no longer read
+    uint64_t *tfull = empty + NSLOT;                      // [NSET] accumulator set ready
+    uint64_t *tempty = tfull + NSET;                      // [NSET] accumulator set read out
+    uint64_t *fin = tempty + NSET;                        // all issued MMAs complete
+    static_assert((2 * NSLOT + 2 * NSET + 1) * 8 + 8 <= HDR, "barrier header");
+    static_assert(RY == 4 && BOXY == 6, "six input rows per plane for four output rows");
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(fin + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1) + 1;
+    unsigned char *wsm = sm + HDR;
+    unsigned char *slots = sm + HDR + 3 * WDX;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // weights [tap][8][16] (row 0 real) -> [dx][half][n = 3 dz + dy][8 ci]; rows n >= 9 zero
+    for (int i = threadIdx.x; i < 3 * 2 * 16; i += blockDim.x) {
+        const int n = i & 15, half = (i >> 4) & 1, dx = i >> 5;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (n < 9) {
+            const int dz = n / 3, dy = n % 3;
+            v = *reinterpret_cast<const uint4 *>(a.wt + (((dz * 3 + dy) * 3 + dx) * 8) * CH + half * 8);
+        }
+        *reinterpret_cast<uint4 *>(wsm + dx * WDX + half * 256 + n * 16) = v;
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSLOT; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < NSET; ++b) {
+            bar_init(&tfull[b], 1);
+            bar_init(&tempty[b], NEPI);
+        }
+        bar_init(fin, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    constexpr int WPROD = NEPI, WMMA = NEPI + 1;
+    if (warp == WMMA) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tmem_slot)),
+                     "n"(out1tc::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = *tmem_slot;
+
+    if (warp == WPROD) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                int y0, x0, z0, z1;
+                um.decode(u, y0, x0, z0, z1);
+                for (int p = z0 - 1; p <= z1; ++p) {
+                    const int s = it % NSLOT;
+                    if (it >= NSLOT && !bar_wait(&empty[s], ((it / NSLOT) - 1) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    bar_expect(&full[s], 2 * BOXY * G::BOXX * 16);
+                    unsigned char *dst = slots + s * G::SLOT;
+                    tma_load_4d(dst, &tmap, &full[s], 0, x0 - 1, y0 - 1, p);
+                    tma_load_4d(dst + G::HALF, &tmap, &full[s], 8, x0 - 1, y0 - 1, p);
+                    ++it;
+                }
+            }
+            if (!ok) {
+                for (int k = it - NSLOT < 0 ? 0 : it - NSLOT; k < it; ++k) {
+                    const unsigned long long t0 = now_ns();
+                    while (!bar_try(&full[k % NSLOT], (k / NSLOT) & 1) && now_ns() - t0 < 50000000ull) {
+                    }
+                }
+                atomicCAS(err, 0, static_cast<int>(kDevTimeoutTma));
+            }
+        }
+    } else if (warp == WMMA) {
+        // ------------------------------------------------------- MMA issuer
+        int it = 0;  // input planes over all units (plane it uses slot it % NSLOT and set it % NSET)
+        bool ok = true;
+        const uint32_t wlo = sdesc_lo(sa(wsm), 256), slot_lo0 = sdesc_lo(sa(slots), G::LBO_A);
+        constexpr uint32_t whi = sdesc_hi(128), ahi = sdesc_hi(128);
+        for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            int y0, x0, z0, z1;
+            um.decode(u, y0, x0, z0, z1);
+            for (int p = z0 - 1; p <= z1; ++p, ++it) {
+                const int s = it % NSLOT, b = it % NSET;
+                if (!(ok = __all_sync(0xffffffffu, bar_wait(&full[s], (it / NSLOT) & 1, abort_flag))))
+                    break;
+                if (it >= NSET &&
+                    !(ok = __all_sync(0xffffffffu, bar_wait(&tempty[b], ((it / NSET) - 1) & 1, abort_flag))))
+                    break;
+                fence_after();
+                const uint32_t alo = slot_lo0 + static_cast<uint32_t>(s * G::SLOT / 16);
+#pragma unroll
+                for (int r = 0; r < BOXY; ++r)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+                        mma_bf16_warp_acc(tbase + b * SETCOLS + r * 16,
+                                          alo + static_cast<uint32_t>((r * G::ROWB + dx * 16) / 16), ahi,
+                                          wlo + static_cast<uint32_t>(dx * WDX / 16), whi, idesc_bf16(16),
+                                          dx > 0 ? 1u : 0u);
+                mma_commit_warp(&tfull[b]);   // the set of plane it is complete
+                mma_commit_warp(&empty[s]);   // plane read by all its MMAs
+            }
+        }
+        mma_commit_warp(fin);
+        const unsigned long long t0 = now_ns();
+        while (!bar_try(fin, 0) && now_ns() - t0 < 100000000ull) {
+        }
+        if (!ok && lane == 0)
+            atomicCAS(err, 0, static_cast<int>(kDevTimeoutTma));
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int quad = warp & 3, h = warp >> 2;  // points 32 quad .., output rows 2h, 2h + 1
+        const float bias = a.bias ? a.bias[0] : 0.f;
+        int it = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            int y0, x0, z0, z1;
+            um.decode(u, y0, x0, z0, z1);
+            const int x = x0 + quad * 32 + lane;
+            // output planes p - 1 (lo), p (mid), p + 1 (hi) of rows 2h + j
+            float lo[2] = {0.f, 0.f}, mid[2] = {0.f, 0.f}, hi[2] = {0.f, 0.f};
+            for (int p = z0 - 1; p <= z1; ++p, ++it) {
+                const int b = it % NSET;
+                ok = __all_sync(0xffffffffu, bar_wait(&tfull[b], (it / NSET) & 1, abort_flag));
+                if (!ok)
+                    break;
+                fence_after();
+                uint32_t rv[4][9];
+                const uint32_t ta = tbase + (static_cast<uint32_t>(quad * 32) << 16) + b * SETCOLS + 2 * h * 16;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    tmem_ld9(ta + i * 16, rv[i]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    asm volatile(""
+                                 : "+r"(rv[i][0]), "+r"(rv[i][1]), "+r"(rv[i][2]), "+r"(rv[i][3]), "+r"(rv[i][4]),
+                                   "+r"(rv[i][5]), "+r"(rv[i][6]), "+r"(rv[i][7]), "+r"(rv[i][8]));
+                fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    bar_arrive(&tempty[b]);
+                // plane p reaches output p + 1 - dz through dz; row 2h + j reads input rows 2h + j + dy
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    float c[3];
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz)
+                        c[dz] = (__uint_as_float(rv[j][3 * dz]) + __uint_as_float(rv[j + 1][3 * dz + 1])) +
+                                __uint_as_float(rv[j + 2][3 * dz + 2]);
+                    hi[j] += c[0];
+                    mid[j] += c[1];
+                    lo[j] += c[2];
+                }
+                const int zo = p - 1;  // complete: it has had planes zo - 1, zo and zo + 1
+                if (zo >= z0 && x < a.d.nx) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int y = y0 + 2 * h + j;
+                        if (y < a.d.ny)
+                            a.out_f32[(static_cast<int64_t>(zo) * a.d.ny + y) * a.d.nx + x] = (lo[j] + bias) * a.oscale;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    lo[j] = mid[j];
+                    mid[j] = hi[j];
+                    hi[j] = 0.f;
+                }
+            }
+        }
+        if (!ok && lane == 0)
+            atomicCAS(err, 0, static_cast<int>(kDevTimeoutTma));
+    }
+    __syncthreads();
+    if (warp == WMMA) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(out1tc::TCOLS)
+                     : "memory");
+    }
+}
+
 struct WgradArgs {
     const __nv_bfloat16 *x;   // layer input [z][y][x][16]
     const __nv_bfloat16 *dz;  // output gradient [z][y][x][16]
@@ -911,7 +1158,8 @@ struct gbst_closure_s {
     double out_scale = 1.0;     // target in network units: out_scale * (u_ref - u+)
     bool freeze_biases = false; // Adam leaves the biases unchanged
     double loss_weight = 1.0;   // factor on the loss (and its gradient) of the next loss_grad calls
-    int conv_impl = 0;          // 0: tcgen05, 1: mma.sync, 2: tcgen05 with the last layer on the CUDA cores
+    int conv_impl = 0;          // 0: tcgen05 (last layer tap-split), 1: mma.sync, 2: tcgen05 with the last
+                                // layer on the CUDA cores, 3: tcgen05 with the last layer as the hidden ones
     int *derr = nullptr;        // device error word of the tcgen05 convolutions
     unsigned char *trainable = nullptr;      // per-parameter Adam mask (null: all parameters train)
     unsigned char *trainable_buf = nullptr;  // its device storage
@@ -1011,6 +1259,38 @@ cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
         return cudaErrorInvalidValue;
     const int ctas = static_cast<int>(std::min<int64_t>(nunits, static_cast<int64_t>(num_sms_dev()) * occ));
     k_conv_tc<COUT, EPI, CIN><<<ctas, NTHREADS, smem, s>>>(m, a, um, static_cast<int>(nunits), err);
+    return cudaGetLastError();
+}
+
+// The one-channel last layer in tap-split form on tcgen05 (k_conv_out1_tc): the
+// general kernel's input staging and work units, two CTAs per SM.
+cudaError_t launch_conv_out1_tc(const ConvArgs &a, int *err, cudaStream_t s)
+{
+    using namespace convtc;
+    using G = Geo<16>;
+    constexpr int smem = out1tc::SMEM;
+    static bool attr = false;
+    if (!attr) {
+        const void *fn = reinterpret_cast<const void *>(&k_conv_out1_tc);
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        attr = true;
+    }
+    CUtensorMap m;
+    const uint64_t dims[4] = {16ull, static_cast<uint64_t>(a.d.nx), static_cast<uint64_t>(a.d.ny),
+                              static_cast<uint64_t>(a.d.nz)};
+    const uint64_t strides[3] = {32ull, static_cast<uint64_t>(a.d.nx) * 32, static_cast<uint64_t>(a.d.nx) * a.d.ny * 32};
+    const uint32_t box[4] = {8, static_cast<uint32_t>(G::BOXX), BOXY, 1};
+    std::string msg;
+    if (!encode_tmap_bf16_4d(&m, a.in, dims, strides, box, &msg))
+        return cudaErrorInvalidValue;
+    UnitMap um{(a.d.nx + TXP - 1) / TXP, (a.d.nz + ZCH - 1) / ZCH, (a.d.ny + RY - 1) / RY, a.d.nz};
+    const int64_t nunits = static_cast<int64_t>(um.nxc) * um.nyc * um.nzc;
+    if (nunits > (1ll << 31) - 1)
+        return cudaErrorInvalidValue;
+    // two CTAs per SM (tensor memory: 256 columns each)
+    const int ctas = static_cast<int>(std::min<int64_t>(nunits, static_cast<int64_t>(num_sms_dev()) * 2));
+    k_conv_out1_tc<<<ctas, NTHREADS, smem, s>>>(m, a, um, static_cast<int>(nunits), err);
     return cudaGetLastError();
 }
 
@@ -1136,8 +1416,12 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     b.out_f32 = out ? out : c->o;
     b.oscale = oscale;
     b.cout_valid = 1;
-    if (e == cudaSuccess)  // impl 2 runs the one-channel last layer on the CUDA cores
-        e = c->conv_impl == 2 ? launch_conv_out1(b, c->stream) : conv<8, EPI_LINEAR_F32>(c, b);
+    if (e == cudaSuccess) {  // the one-channel last layer: tap-split tcgen05 (impl 0), CUDA cores (impl 2)
+        if (c->conv_impl == 0)
+            e = launch_conv_out1_tc(b, c->derr, c->stream);
+        else
+            e = c->conv_impl == 2 ? launch_conv_out1(b, c->stream) : conv<8, EPI_LINEAR_F32>(c, b);
+    }
     return e == cudaSuccess ? GBST_OK : record_error(GBST_ECUDA, cudaGetErrorString(e));
 }
 
@@ -1515,8 +1799,8 @@ gbst_status closure_set_loss_weight(gbst_closure c, double w)
 
 gbst_status closure_set_conv_impl(gbst_closure c, int impl)
 {
-    if (!c || impl < 0 || impl > 2)
-        return record_error(GBST_EINVAL, "closure_set_conv_impl: null closure or impl not 0, 1 or 2");
+    if (!c || impl < 0 || impl > 3)
+        return record_error(GBST_EINVAL, "closure_set_conv_impl: null closure or impl not 0, 1, 2 or 3");
     c->conv_impl = impl;
     return GBST_OK;
 }

@@ -73,7 +73,8 @@ def test_forward_matches_oracle(torch_cuda, dims):
 
 def test_tcgen05_and_mma_sync_convolutions_agree(torch_cuda):
     """The tcgen05 (tensor memory) and mma.sync convolutions compute the same network, with the
-    last layer on the tensor cores (impl 0) or on the CUDA cores (impl 2)."""
+    last layer on the tensor cores in tap-split form (impl 0), on the CUDA cores (impl 2) or
+    on the tensor cores like the hidden layers (impl 3)."""
     from paper_2404_02218_gb300.closure import Closure, flatten_params
     dims = (300, 21, 40)  # several 128-point rows, a ragged row end, two z chunks
     s = 2.0
@@ -86,17 +87,20 @@ def test_tcgen05_and_mma_sync_convolutions_agree(torch_cuda):
     b = cl.forward(tu, tn, tc).cpu().numpy()
     cl.set_conv_impl(2)
     c = cl.forward(tu, tn, tc).cpu().numpy()
+    cl.set_conv_impl(3)
+    d = cl.forward(tu, tn, tc).cpu().numpy()
     assert np.abs(b).max() > 0
     # FP32 sums of the same BF16 products in another order; a few BF16 roundings of
     # intermediate activations may differ by one unit
     assert rel(a, b) <= 2e-3
     assert rel(c, b) <= 2e-3
+    assert rel(d, b) <= 2e-3
     o, _ = ocl.forward(closure_inputs(s, up, un, cn), p)
     assert rel(a * s, o[0]) <= TOL_NET
     cl.close()
 
 
-@pytest.mark.parametrize("impl", [0, 1, 2])
+@pytest.mark.parametrize("impl", [0, 1, 2, 3])
 def test_loss_and_gradients_match_oracle_all_impls(torch_cuda, impl):
     from paper_2404_02218_gb300.closure import Closure, flatten_params, unflatten_params
     dims = (140, 12, 9)
