@@ -90,7 +90,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
 }
 
 bool encode_tmap_bf16_4d(CUtensorMap *m, const void *base, const uint64_t dims[4], const uint64_t strides[3],
-                         const uint32_t box[4], std::string *err)
+                         const uint32_t box[4], std::string *err, bool swizzle32)
 {
     auto fn = tmap_encoder();
     if (!fn) {
@@ -106,8 +106,8 @@ bool encode_tmap_bf16_4d(CUtensorMap *m, const void *base, const uint64_t dims[4
     for (int i = 0; i < 3; ++i)
         st[i] = strides[i];
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), d, st, b, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         *err = "cuTensorMapEncodeTiled failed (" + std::to_string(static_cast<int>(r)) + ") for a 4D BF16 tensor";
         return false;

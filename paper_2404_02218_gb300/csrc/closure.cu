@@ -307,6 +307,8 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1) + 1;
     unsigned char *wsm = sm + HDR;
     unsigned char *slots = sm + HDR + G::NTAP * WTAP;
+    if (G::SW32)  // swizzled slots start on a 1024-byte boundary
+        slots += (1024u - (sa(slots) & 1023u)) & 1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // weights [tap][co][16 ci] -> [tap t][half][block 0..4: dz = 2, 1, 0, 2, 1][co 0..15][8 ci];
@@ -378,11 +380,8 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                         ok = false;
                         break;
                     }
-                    bar_expect(&full[s], G::NBOX * BOXY * G::BOXX * 16);
-                    unsigned char *dst = slots + s * G::SLOT;
-                    tma_load_4d(dst, &tmap, &full[s], 0, x0 - 1, y0 - 1, p);
-                    if (G::NBOX == 2)
-                        tma_load_4d(dst + G::HALF, &tmap, &full[s], 8, x0 - 1, y0 - 1, p);
+                    bar_expect(&full[s], BOXY * G::ROWB);
+                    tma_load_4d(slots + s * G::SLOT, &tmap, &full[s], 0, x0 - 1, y0 - 1, p);
                     ++it;
                 }
             }
@@ -402,7 +401,7 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
         int it = 0, ot = 0;  // input planes consumed, outputs started (over all units)
         bool ok = true;
         const uint32_t wlo = sdesc_lo(sa(wsm), WHALF), slot_lo0 = sdesc_lo(sa(slots), G::LBO_A);
-        constexpr uint32_t whi = sdesc_hi(128), ahi = sdesc_hi(128);
+        constexpr uint32_t whi = sdesc_hi(128), ahi = G::SW32 ? sdesc_hi_sw32(256) : sdesc_hi(128);
         for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
             int y0, x0, z0, z1;
             um.decode(u, y0, x0, z0, z1);
@@ -693,8 +692,8 @@ __global__ void __launch_bounds__(T1NT) k_conv_out1(const __nv_bfloat16 *in, con
 // add the nine (dy, dz) terms: o(x, y, z) = sum over (dz, dy) of Y_{3dz+dy}(x, y+dy-1, z+dz-1).
 // Per plane a CTA (128 x-points, RY = 4 output rows) issues 6 x 3 MMAs for its 6
 // input rows, against 9 N = 48 MMAs per output row in the general kernel: a third
-// of the A-tile reads from shared memory.  Input staging (TMA boxes of 8 channels x
-// 130 points x 6 rows, the producer warp and the plane ring) is the general kernel's.
+// of the A-tile reads from shared memory.  The producer warp and the plane ring are
+// the general kernel's; each plane is one 32-byte swizzled box (out1tc::BOXX).
 // Epilogue warp w reads lanes 32 (w & 3) .. +31 (points) and output rows 2 (w >> 2)
 // and 2 (w >> 2) + 1, i.e. input rows 2 (w >> 2) .. +3 of each plane; each plane
 // feeds output planes p + 1 (dz = 0), p (dz = 1) and p - 1 (dz = 2), kept in three
@@ -706,7 +705,14 @@ constexpr int SETCOLS = 6 * 16;          // 6 input rows x 16 columns
 constexpr int TCOLS = 256;               // allocated tensor-memory columns
 constexpr int WDX = 2 * 16 * 16;         // bytes of one dx weight matrix: [half][16 rows][8 ci] BF16
 constexpr int NSLOT = 4;                 // plane slots
-constexpr int SMEM = convtc::HDR + 3 * WDX + NSLOT * convtc::Geo<16>::SLOT;
+// Input planes: one TMA box of all 16 channels per plane (32-byte rows, the 32-byte
+// swizzled K-major layout), rows of 136 points so that every row starts on a 256-byte
+// pattern boundary; two boxes of 8 channels (16-byte rows, each half of an L2 sector)
+// made twice the L2 requests, which bounded the kernel.
+constexpr int BOXX = 136;
+constexpr int ROWB = BOXX * 32;
+constexpr int SLOT = (convtc::BOXY * ROWB + 1023) / 1024 * 1024;
+constexpr int SMEM = convtc::HDR + 3 * WDX + 1024 + NSLOT * SLOT;
 }  // namespace out1tc
 
 // D[tmem] (+)= A B as mma_bf16_warp, with the accumulate flag a runtime value.
@@ -737,7 +743,6 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                    const int nunits, int *err)
 {
     using namespace convtc;
-    using G = Geo<16>;
     using out1tc::NSET;
     using out1tc::NSLOT;
     using out1tc::SETCOLS;
@@ -754,6 +759,8 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1) + 1;
     unsigned char *wsm = sm + HDR;
     unsigned char *slots = sm + HDR + 3 * WDX;
+    slots += (1024u - (sa(slots) & 1023u)) & 1023u;  // swizzled slots start on a 1024-byte boundary
+    constexpr int SLOTB = out1tc::SLOT;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // weights [tap][8][16] (row 0 real) -> [dx][half][n = 3 dz + dy][8 ci]; rows n >= 9 zero
@@ -806,10 +813,8 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                         ok = false;
                         break;
                     }
-                    bar_expect(&full[s], 2 * BOXY * G::BOXX * 16);
-                    unsigned char *dst = slots + s * G::SLOT;
-                    tma_load_4d(dst, &tmap, &full[s], 0, x0 - 1, y0 - 1, p);
-                    tma_load_4d(dst + G::HALF, &tmap, &full[s], 8, x0 - 1, y0 - 1, p);
+                    bar_expect(&full[s], BOXY * out1tc::ROWB);
+                    tma_load_4d(slots + s * SLOTB, &tmap, &full[s], 0, x0 - 1, y0 - 1, p);
                     ++it;
                 }
             }
@@ -826,8 +831,8 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
         // ------------------------------------------------------- MMA issuer
         int it = 0;  // input planes over all units (plane it uses slot it % NSLOT and set it % NSET)
         bool ok = true;
-        const uint32_t wlo = sdesc_lo(sa(wsm), 256), slot_lo0 = sdesc_lo(sa(slots), G::LBO_A);
-        constexpr uint32_t whi = sdesc_hi(128), ahi = sdesc_hi(128);
+        const uint32_t wlo = sdesc_lo(sa(wsm), 256);
+        constexpr uint32_t whi = sdesc_hi(128);
         for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
             int y0, x0, z0, z1;
             um.decode(u, y0, x0, z0, z1);
@@ -839,15 +844,18 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                     !(ok = __all_sync(0xffffffffu, bar_wait(&tempty[b], ((it / NSET) - 1) & 1, abort_flag))))
                     break;
                 fence_after();
-                const uint32_t alo = slot_lo0 + static_cast<uint32_t>(s * G::SLOT / 16);
+                // K-major, 32-byte swizzle: rows of 32 bytes (16 channels), 8-row groups
+                // 256 bytes apart; the x tap dx starts the operand dx rows later (the
+                // swizzle is a function of the shared-memory address, as the TMA wrote it)
+                const uint32_t sbase = sa(slots + s * SLOTB);
 #pragma unroll
                 for (int r = 0; r < BOXY; ++r)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
                         mma_bf16_warp_acc(tbase + b * SETCOLS + r * 16,
-                                          alo + static_cast<uint32_t>((r * G::ROWB + dx * 16) / 16), ahi,
-                                          wlo + static_cast<uint32_t>(dx * WDX / 16), whi, idesc_bf16(16),
-                                          dx > 0 ? 1u : 0u);
+                                          sdesc_lo(sbase + static_cast<uint32_t>(r * out1tc::ROWB + dx * 32), 16),
+                                          sdesc_hi_sw32(256), wlo + static_cast<uint32_t>(dx * WDX / 16), whi,
+                                          idesc_bf16(16), dx > 0 ? 1u : 0u);
                 mma_commit_warp(&tfull[b]);   // the set of plane it is complete
                 mma_commit_warp(&empty[s]);   // plane read by all its MMAs
             }
@@ -1243,15 +1251,15 @@ cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
         // CTA) allows no more than two.
         occ = 2;
     }
-    // activation [z][y][x][CIN] BF16: dims (channel, x, y, z), boxes of 8 channels x BOXX points x 6 rows
+    // activation [z][y][x][CIN] BF16: dims (channel, x, y, z), boxes of BOXC channels x BOXX points x 6 rows
     CUtensorMap m;
     const uint64_t dims[4] = {static_cast<uint64_t>(CIN), static_cast<uint64_t>(a.d.nx),
                               static_cast<uint64_t>(a.d.ny), static_cast<uint64_t>(a.d.nz)};
     const uint64_t strides[3] = {CIN * 2ull, static_cast<uint64_t>(a.d.nx) * CIN * 2,
                                  static_cast<uint64_t>(a.d.nx) * a.d.ny * CIN * 2};
-    const uint32_t box[4] = {8, static_cast<uint32_t>(G::BOXX), BOXY, 1};
+    const uint32_t box[4] = {static_cast<uint32_t>(G::BOXC), static_cast<uint32_t>(G::BOXX), BOXY, 1};
     std::string msg;
-    if (!encode_tmap_bf16_4d(&m, a.in, dims, strides, box, &msg))
+    if (!encode_tmap_bf16_4d(&m, a.in, dims, strides, box, &msg, G::SW32))
         return cudaErrorInvalidValue;
     UnitMap um{(a.d.nx + TXP - 1) / TXP, (a.d.nz + ZCH - 1) / ZCH, (a.d.ny + RY - 1) / RY, a.d.nz};
     const int64_t nunits = static_cast<int64_t>(um.nxc) * um.nyc * um.nzc;
@@ -1267,7 +1275,6 @@ cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
 cudaError_t launch_conv_out1_tc(const ConvArgs &a, int *err, cudaStream_t s)
 {
     using namespace convtc;
-    using G = Geo<16>;
     constexpr int smem = out1tc::SMEM;
     static bool attr = false;
     if (!attr) {
@@ -1280,9 +1287,9 @@ cudaError_t launch_conv_out1_tc(const ConvArgs &a, int *err, cudaStream_t s)
     const uint64_t dims[4] = {16ull, static_cast<uint64_t>(a.d.nx), static_cast<uint64_t>(a.d.ny),
                               static_cast<uint64_t>(a.d.nz)};
     const uint64_t strides[3] = {32ull, static_cast<uint64_t>(a.d.nx) * 32, static_cast<uint64_t>(a.d.nx) * a.d.ny * 32};
-    const uint32_t box[4] = {8, static_cast<uint32_t>(G::BOXX), BOXY, 1};
+    const uint32_t box[4] = {16u, static_cast<uint32_t>(out1tc::BOXX), BOXY, 1};
     std::string msg;
-    if (!encode_tmap_bf16_4d(&m, a.in, dims, strides, box, &msg))
+    if (!encode_tmap_bf16_4d(&m, a.in, dims, strides, box, &msg, true))
         return cudaErrorInvalidValue;
     UnitMap um{(a.d.nx + TXP - 1) / TXP, (a.d.nz + ZCH - 1) / ZCH, (a.d.ny + RY - 1) / RY, a.d.nz};
     const int64_t nunits = static_cast<int64_t>(um.nxc) * um.nyc * um.nzc;

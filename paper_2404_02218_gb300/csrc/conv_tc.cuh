@@ -6,11 +6,11 @@
 // taps of A_tap[128 points x 16 ci] B_tap[16 ci x 16 co].  A CTA owns 128
 // consecutive x points of RY = 4 rows and marches along z.  For every input
 // plane a TMA load brings rows y0-1..y0+RY, x0-1..x0+128 (out of range ->
-// zeros, which is the zero padding) as two boxes of 8 channels, so each box is
-// a K-major, unswizzled tcgen05 operand: 8 points x 16 bytes form a contiguous
-// core matrix.  A_tap of row r is then just a shifted view of the plane slot
-// (start address + (r + dy) * row + dx * 16 bytes), no data movement per tap.
-// The weights of all taps sit in shared memory in the same layout.
+// zeros, which is the zero padding) as one box of 16 channels in the 32-byte
+// swizzled layout, a K-major tcgen05 operand whose rows are the points' 32
+// bytes (see Geo).  A_tap of row r is then just a shifted view of the plane
+// slot (start address + (r + dy) * row + dx * 32 bytes), no data movement per
+// tap.  The weights of all taps sit in shared memory, K-major and unswizzled.
 //
 // Input-stationary order: when input plane p has landed, its taps are issued
 // at once into the three outputs that read it (p + 1 through dz = 0, p through
@@ -61,39 +61,42 @@ constexpr int NEPI = 8;                  // epilogue warps: lane quadrant w & 3,
 constexpr int NTHREADS = (NEPI + 2) * 32;
 constexpr int ZCH = 32;                  // output planes per work unit
 
-// Plane geometry by input width.  CIN = 16: two 8-channel boxes per plane, the
-// K = 16 operand of a tap is (channels 0-7 | channels 8-15) of one point, nine
-// (dy, dx) taps.  CIN = 8 (16 bytes per point): one box, and the K = 16 operand
-// pairs a point with its x neighbour (the second core matrix along K starts 16
-// bytes later), so taps dx = -1 and 0 form one MMA and dx = +1 another (its
-// second K half has zero weights): six taps (dy, pair | single).  Its rows carry
-// two extra points so that the single tap's second half stays inside the row.
+// Plane geometry by input width.  CIN = 16: one box of all 16 channels per plane
+// (32-byte rows) in the 32-byte swizzled K-major layout, so the K = 16 operand of
+// a tap is one 32-byte row per point; rows of 136 points start on 256-byte pattern
+// boundaries (two boxes of 8 channels, 16-byte rows each half an L2 sector, made
+// twice the L2 requests and bounded the layer).  Nine (dy, dx) taps.  CIN = 8 (16
+// bytes per point, unswizzled): one box, and the K = 16 operand pairs a point with
+// its x neighbour (the second core matrix along K starts 16 bytes later), so taps
+// dx = -1 and 0 form one MMA and dx = +1 another (its second K half has zero
+// weights): six taps (dy, pair | single).  Its rows carry two extra points so that
+// the single tap's second half stays inside the row.
 template <int CIN>
 struct Geo;
 template <>
 struct Geo<16> {
-    static constexpr int BOXX = TXP + 2;                           // input points per row (x halo 1 each side)
-    static constexpr int ROWB = BOXX * 16;                         // bytes of one row of 8 channels
-    static constexpr int HALF = (BOXY * ROWB + 127) / 128 * 128;   // one 8-channel box
-    static constexpr int SLOT = 2 * HALF;                          // one input plane
-    static constexpr int NBOX = 2;
-    static constexpr int LBO_A = HALF;                             // K half 2: channels 8-15, same point
+    static constexpr int BOXX = 136;                               // input points per row (x halo 1 | 7)
+    static constexpr int ROWB = BOXX * 32;                         // bytes of one row, 16 channels
+    static constexpr int SLOT = (BOXY * ROWB + 1023) / 1024 * 1024;
+    static constexpr int BOXC = 16;                                // channels per box
+    static constexpr bool SW32 = true;                             // 32-byte swizzle
+    static constexpr int LBO_A = 16;                               // (unused by a swizzled K-major operand)
     static constexpr int NTAP = 9;
-    __host__ __device__ static constexpr int a_off(int t, int r) { return (r + t / 3) * ROWB + (t % 3) * 16; }
+    __host__ __device__ static constexpr int a_off(int t, int r) { return (r + t / 3) * ROWB + (t % 3) * 32; }
 };
 template <>
 struct Geo<8> {
     static constexpr int BOXX = TXP + 4;
     static constexpr int ROWB = BOXX * 16;
-    static constexpr int HALF = (BOXY * ROWB + 127) / 128 * 128;
-    static constexpr int SLOT = HALF;
-    static constexpr int NBOX = 1;
+    static constexpr int SLOT = (BOXY * ROWB + 127) / 128 * 128;
+    static constexpr int BOXC = 8;
+    static constexpr bool SW32 = false;
     static constexpr int LBO_A = 16;                               // K half 2: the next point
     static constexpr int NTAP = 6;
     __host__ __device__ static constexpr int a_off(int t, int r) { return (r + t / 2) * ROWB + (t % 2) * 32; }
 };
 template <int CIN>
-constexpr int tc_smem() { return HDR + Geo<CIN>::NTAP * WTAP + NS * Geo<CIN>::SLOT; }
+constexpr int tc_smem() { return HDR + Geo<CIN>::NTAP * WTAP + (Geo<CIN>::SW32 ? 1024 : 0) + NS * Geo<CIN>::SLOT; }
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -168,6 +171,10 @@ __device__ __forceinline__ uint32_t sdesc_lo(uint32_t addr, uint32_t lbo)
     return ((addr >> 4) & 0x3FFFu) | (((lbo >> 4) & 0x3FFFu) << 16);
 }
 constexpr uint32_t sdesc_hi(uint32_t sbo) { return ((sbo >> 4) & 0x3FFFu) | (1u << 14); }
+// The same for a K-major operand in the 32-byte swizzled layout (rows of 32 bytes, the
+// two 16-byte halves of a row exchanged in rows 4-7 of every 256 bytes, as a TMA load
+// with 32-byte swizzle writes it); the start address may sit anywhere in the pattern.
+constexpr uint32_t sdesc_hi_sw32(uint32_t sbo) { return sdesc_hi(sbo) | (6u << 29); }
 
 // Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = n.
 constexpr uint32_t idesc_bf16(uint32_t n)

@@ -226,9 +226,10 @@ gbst_status closure_features_values(const float *up, const float *un, int64_t nx
                                     const ClosureFeatBufs &b, float *out, cudaStream_t s);
 
 // Tensor-map encoding through the driver entry point.
-// Tiled tensor map of a 4D BF16 tensor (dims innermost first; strides in bytes of dims 1..3).
+// Tiled tensor map of a 4D BF16 tensor (dims innermost first; strides in bytes of dims 1..3);
+// swizzle32: boxes land in the 32-byte swizzled shared-memory layout (inner box extent 32 bytes).
 bool encode_tmap_bf16_4d(CUtensorMap *m, const void *base, const uint64_t dims[4], const uint64_t strides[3],
-                         const uint32_t box[4], std::string *err);
+                         const uint32_t box[4], std::string *err, bool swizzle32 = false);
 bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h,
                  std::string *err);
 
