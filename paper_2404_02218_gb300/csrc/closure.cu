@@ -288,13 +288,13 @@ __global__ void __launch_bounds__(NTHR) k_conv(const ConvArgs a)
 // 3x3x3 convolution on tcgen05 (see conv_tc.cuh): same arguments and
 // epilogues as k_conv; the input is read through the tensor map `tmap`
 // (channels-last [z][y][x][16] BF16, boxes of 8 channels x 130 points x 3 rows).
-template <int COUT, int EPI, int CIN>
+template <int COUT, int EPI, int CIN, bool BLK = false>
 __global__ void __launch_bounds__(convtc::NTHREADS, 2)
     k_conv_tc(const __grid_constant__ CUtensorMap tmap, const ConvArgs a, const convtc::UnitMap um, const int nunits,
               int *err)
 {
     using namespace convtc;
-    using G = Geo<CIN>;
+    using G = GeoOf<CIN, BLK>;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *full = reinterpret_cast<uint64_t *>(sm);  // [NS] input plane landed
     uint64_t *empty = full + NS;                          // [NS] input plane no longer read
@@ -381,7 +381,8 @@ __global__ void __launch_bounds__(convtc::NTHREADS, 2)
                         break;
                     }
                     bar_expect(&full[s], BOXY * G::ROWB);
-                    tma_load_4d(slots + s * G::SLOT, &tmap, &full[s], 0, x0 - 1, y0 - 1, p);
+                    // blocked view: the box starts at the block of 32 points before x0
+                    tma_load_4d(slots + s * G::SLOT, &tmap, &full[s], 0, BLK ? x0 / 32 - 1 : x0 - 1, y0 - 1, p);
                     ++it;
                 }
             }
@@ -1229,15 +1230,15 @@ int num_sms_dev()
 }
 
 // CIN: channels per point of the input (16, or 8 for the packed feature input of layer 1).
-template <int COUT, int EPI, int CIN = 16>
+template <int COUT, int EPI, int CIN = 16, bool BLK = false>
 cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
 {
     using namespace convtc;
-    using G = Geo<CIN>;
-    constexpr int smem = tc_smem<CIN>();
+    using G = GeoOf<CIN, BLK>;
+    constexpr int smem = tc_smem<CIN, BLK>();
     static int occ = -1;
     if (occ < 0) {
-        const void *fn = reinterpret_cast<const void *>(&k_conv_tc<COUT, EPI, CIN>);
+        const void *fn = reinterpret_cast<const void *>(&k_conv_tc<COUT, EPI, CIN, BLK>);
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         // the largest shared-memory carveout, so that two CTAs fit on an SM
         cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -1251,13 +1252,19 @@ cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
         // CTA) allows no more than two.
         occ = 2;
     }
-    // activation [z][y][x][CIN] BF16: dims (channel, x, y, z), boxes of BOXC channels x BOXX points x 6 rows
+    // activation [z][y][x][CIN] BF16: dims (channel, x, y, z), boxes of CIN channels x BOXX points x 6
+    // rows; blocked view (BLK, nx a multiple of 32): dims (32 points x 8 channels, x / 32, y, z),
+    // boxes of 6 blocks x 6 rows
     CUtensorMap m;
-    const uint64_t dims[4] = {static_cast<uint64_t>(CIN), static_cast<uint64_t>(a.d.nx),
-                              static_cast<uint64_t>(a.d.ny), static_cast<uint64_t>(a.d.nz)};
-    const uint64_t strides[3] = {CIN * 2ull, static_cast<uint64_t>(a.d.nx) * CIN * 2,
-                                 static_cast<uint64_t>(a.d.nx) * a.d.ny * CIN * 2};
-    const uint32_t box[4] = {static_cast<uint32_t>(G::BOXC), static_cast<uint32_t>(G::BOXX), BOXY, 1};
+    const uint64_t row_bytes = static_cast<uint64_t>(a.d.nx) * CIN * 2;
+    if (BLK && a.d.nx % 32 != 0)
+        return cudaErrorInvalidValue;
+    const uint64_t dims[4] = {BLK ? 256ull : static_cast<uint64_t>(CIN),
+                              static_cast<uint64_t>(BLK ? a.d.nx / 32 : a.d.nx), static_cast<uint64_t>(a.d.ny),
+                              static_cast<uint64_t>(a.d.nz)};
+    const uint64_t strides[3] = {BLK ? 512ull : CIN * 2ull, row_bytes, row_bytes * a.d.ny};
+    const uint32_t box[4] = {BLK ? 256u : static_cast<uint32_t>(CIN),
+                             static_cast<uint32_t>(BLK ? GeoB8::BLOCKS : G::BOXX), BOXY, 1};
     std::string msg;
     if (!encode_tmap_bf16_4d(&m, a.in, dims, strides, box, &msg, G::SW32))
         return cudaErrorInvalidValue;
@@ -1266,7 +1273,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s)
     if (nunits > (1ll << 31) - 1)
         return cudaErrorInvalidValue;
     const int ctas = static_cast<int>(std::min<int64_t>(nunits, static_cast<int64_t>(num_sms_dev()) * occ));
-    k_conv_tc<COUT, EPI, CIN><<<ctas, NTHREADS, smem, s>>>(m, a, um, static_cast<int>(nunits), err);
+    k_conv_tc<COUT, EPI, CIN, BLK><<<ctas, NTHREADS, smem, s>>>(m, a, um, static_cast<int>(nunits), err);
     return cudaGetLastError();
 }
 
@@ -1407,7 +1414,9 @@ gbst_status forward(gbst_closure c, const float *up, const float *un, const floa
     a.out = c->y1;
     a.zout = keep ? c->z1 : nullptr;
     a.cout_valid = c->hidden;
-    cudaError_t e = x8 ? launch_conv_tc<16, EPI_GELU, 8>(a, c->derr, c->stream) : conv<16, EPI_GELU>(c, a);
+    cudaError_t e = !x8              ? conv<16, EPI_GELU>(c, a)
+                    : d.nx % 32 == 0 ? launch_conv_tc<16, EPI_GELU, 8, true>(a, c->derr, c->stream)
+                                     : launch_conv_tc<16, EPI_GELU, 8>(a, c->derr, c->stream);
     a.in = c->y1;
     a.wt = c->wf[1];
     a.bias = c->p + c->off[3];

@@ -41,6 +41,8 @@
 // work finish (bounded) and releases its tensor memory.
 #pragma once
 
+#include <type_traits>
+
 #include "gbst_internal.h"
 
 namespace gbst {
@@ -78,7 +80,6 @@ struct Geo<16> {
     static constexpr int BOXX = 136;                               // input points per row (x halo 1 | 7)
     static constexpr int ROWB = BOXX * 32;                         // bytes of one row, 16 channels
     static constexpr int SLOT = (BOXY * ROWB + 1023) / 1024 * 1024;
-    static constexpr int BOXC = 16;                                // channels per box
     static constexpr bool SW32 = true;                             // 32-byte swizzle
     static constexpr int LBO_A = 16;                               // (unused by a swizzled K-major operand)
     static constexpr int NTAP = 9;
@@ -89,14 +90,39 @@ struct Geo<8> {
     static constexpr int BOXX = TXP + 4;
     static constexpr int ROWB = BOXX * 16;
     static constexpr int SLOT = (BOXY * ROWB + 127) / 128 * 128;
-    static constexpr int BOXC = 8;
     static constexpr bool SW32 = false;
     static constexpr int LBO_A = 16;                               // K half 2: the next point
     static constexpr int NTAP = 6;
     __host__ __device__ static constexpr int a_off(int t, int r) { return (r + t / 2) * ROWB + (t % 2) * 32; }
 };
-template <int CIN>
-constexpr int tc_smem() { return HDR + Geo<CIN>::NTAP * WTAP + (Geo<CIN>::SW32 ? 1024 : 0) + NS * Geo<CIN>::SLOT; }
+// CIN = 8 through a blocked view of the input, for rows of a multiple of 32 points:
+// the tensor map sees each row as blocks of 32 points x 8 channels (512 contiguous
+// bytes), and a box of 6 blocks from the block before x0 lands as rows of 192
+// points, the same unswizzled layout as Geo<8> (x0 - 1 at point 31 of a row).  Each
+// TMA box row is then 512 bytes instead of one point's 16, a fraction of the L2
+// requests (one per point row had bounded the layer).
+struct GeoB8 {
+    static constexpr int BOXX = 192;
+    static constexpr int ROWB = BOXX * 16;
+    static constexpr int SLOT = BOXY * ROWB;
+    static constexpr int BLOCKS = BOXX / 32;                       // blocks of 32 points per box row
+    static constexpr bool SW32 = false;
+    static constexpr int LBO_A = 16;
+    static constexpr int NTAP = 6;
+    __host__ __device__ static constexpr int a_off(int t, int r)
+    {
+        return (r + t / 2) * ROWB + 31 * 16 + (t % 2) * 32;
+    }
+};
+template <int CIN, bool BLK>
+using GeoOf = typename std::conditional<BLK, GeoB8, Geo<CIN>>::type;
+
+template <int CIN, bool BLK = false>
+constexpr int tc_smem()
+{
+    using G = GeoOf<CIN, BLK>;
+    return HDR + G::NTAP * WTAP + (G::SW32 ? 1024 : 0) + NS * G::SLOT;
+}
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 

@@ -113,11 +113,13 @@ def test_feature_values_match_oracle(torch_cuda):
         assert np.max(np.abs(got[k] - ref[k])) <= 1e-5 * np.max(np.abs(ref[k])), k
 
 
-@pytest.mark.parametrize("dims", [(37, 21, 19), (45, 13, 70), (1, 1, 1)])
+@pytest.mark.parametrize("dims", [(37, 21, 19), (45, 13, 70), (1, 1, 1), (160, 9, 35)])
 def test_feature_forward_matches_oracle(torch_cuda, dims):
     """The inference forward (z-marching feature kernels: ragged 32 x 8 tiles, several
-    32-plane chunks; layer 1 on the 8-channel packed input) against the mma.sync path
-    and the oracle network on the oracle's features."""
+    32-plane chunks; layer 1 on the 8-channel packed input, read through the blocked
+    view when the rows hold a multiple of 32 points, as 160 does: two 128-point tiles,
+    the second reaching past the row) against the mma.sync path and the oracle network
+    on the oracle's features."""
     torch = torch_cuda
     from oracle import closure as oc
     shape = tuple(reversed(dims))
