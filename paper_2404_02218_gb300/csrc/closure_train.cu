@@ -170,14 +170,36 @@ __global__ void __launch_bounds__(kThr) k_pack_features(DenseDims d, const float
 // z-marching forms of the forward features (inference): a block owns a 32 x 8
 // (x, y) tile and a chunk of kFZC planes, each thread one column; the z
 // neighbours of the star stencils come from register queues (one new load per
-// plane and field), the x and y neighbours from L1.  Same arithmetic, in the
-// same order, as k_star / k_cn2_grads / k_pack_features.
+// plane and field), the x and y neighbours from L1 (lu) or from shared-memory
+// plane tiles (the features).  Same arithmetic, in the same order, as k_star /
+// k_cn2_grads / k_pack_features.
 constexpr int kFX = 32, kFY = 8, kFZC = 32;
 inline dim3 zmarch_grid(const DenseDims &d)
 {
     return dim3(static_cast<unsigned>((d.nx + kFX - 1) / kFX), static_cast<unsigned>((d.ny + kFY - 1) / kFY),
                 static_cast<unsigned>((d.nz + kFZC - 1) / kFZC));
 }
+
+// Plane tiles in shared memory for the z-marching feature kernel: element e of a W x H
+// tile (halo h around the block's kFX x kFY points) is staged by thread e mod
+// (kFX kFY), at an offset within a plane fixed for the whole z-march (-1: outside
+// the grid, staged as 0; -2: no element).  The next plane's values are loaded into
+// registers before the current plane is computed and stored to the other buffer
+// after it, one barrier per plane.
+template <int W, int H>
+struct PlaneTile {
+    static constexpr int NT = kFX * kFY, NE = W * H, K = (NE + NT - 1) / NT;
+    int off[K];
+    __device__ void init(const DenseDims &d, int bx, int by, int h, int tid)
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int e = tid + k * NT;
+            const int gx = bx - h + e % W, gy = by - h + e / W;
+            off[k] = e >= NE ? -2 : (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny) ? gy * d.nx + gx : -1;
+        }
+    }
+};
 
 // lu = L u^n (star of radius R, weights w), as k_star with no pre / post factor.
 template <int R>
@@ -222,6 +244,9 @@ __global__ void __launch_bounds__(kFX *kFY) k_lap_z(DenseDims d, const float *__
 // k_cn2_grads, t6 and t5 as the k_star calls of closure_features_forward, the
 // channels as k_pack_features.  R: the radius of L; w6: the sixth-difference star;
 // XCH: channels per point of x (16: the last 8 zero; 8: packed, 16 bytes per point).
+// The x and y neighbours come from plane tiles of u^n (halo 3: sixth differences,
+// D_a) and of c_n and c_n^2 lu (halo R: t5, g_a), zero outside the grid (an absent
+// neighbour adds 0 where the dense kernels skip it: the same sums).
 template <int R, int XCH>
 __global__ void __launch_bounds__(kFX *kFY) k_features_z(DenseDims d, const float *__restrict__ up,
                                                          const float *__restrict__ un, const float *__restrict__ cn,
@@ -229,102 +254,144 @@ __global__ void __launch_bounds__(kFX *kFY) k_features_z(DenseDims d, const floa
                                                          float4 w6, FeatScales sc, __nv_bfloat16 *__restrict__ xout)
 {
     constexpr int QC = R;  // queue radius of c_n and lu (R >= 1 also covers the gradients)
+    constexpr int HU = 3, UW = kFX + 2 * HU, UH = kFY + 2 * HU;  // u^n tile
+    constexpr int HC = R, CW = kFX + 2 * HC, CH = kFY + 2 * HC;  // c_n and c_n^2 lu tiles
+    using TU = PlaneTile<UW, UH>;
+    using TC = PlaneTile<CW, CH>;
+    __shared__ float su[2][TU::NE], scn[2][TC::NE], scl[2][TC::NE];
     const float w[5] = {w03.x, w03.y, w03.z, w03.w, w4};
     const float v6[4] = {w6.x, w6.y, w6.z, w6.w};
-    const int x = blockIdx.x * kFX + threadIdx.x, y = blockIdx.y * kFY + threadIdx.y;
-    if (x >= d.nx || y >= d.ny)
-        return;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kFX + tx;
+    const int bx = blockIdx.x * kFX, by = blockIdx.y * kFY;
+    const int x = bx + tx, y = by + ty;
+    const bool own = x < d.nx && y < d.ny;  // every thread stages; these compute
     const int z0 = blockIdx.z * kFZC, z1 = min(d.nz, z0 + kFZC);
-    const int64_t sy = d.nx, sz = static_cast<int64_t>(d.nx) * d.ny, pxy = static_cast<int64_t>(y) * d.nx + x;
+    const int64_t sz = static_cast<int64_t>(d.nx) * d.ny, pxy = static_cast<int64_t>(y) * d.nx + x;
+    TU tu;
+    TC tc;
+    tu.init(d, bx, by, HU, tid);
+    tc.init(d, bx, by, HC, tid);
+    float ru[TU::K], rc[TC::K], rl[TC::K];
+    auto fetch = [&](int z) {
+        const int64_t pz = z * sz;
+#pragma unroll
+        for (int k = 0; k < TU::K; ++k)
+            ru[k] = tu.off[k] >= 0 ? un[pz + tu.off[k]] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < TC::K; ++k) {
+            const bool in = tc.off[k] >= 0;
+            rc[k] = in ? cn[pz + tc.off[k]] : 0.0f;
+            rl[k] = in ? lu[pz + tc.off[k]] : 0.0f;
+        }
+    };
+    auto store = [&](int b) {
+#pragma unroll
+        for (int k = 0; k < TU::K; ++k)
+            if (tu.off[k] != -2)
+                su[b][tid + k * TU::NT] = ru[k];
+#pragma unroll
+        for (int k = 0; k < TC::K; ++k)
+            if (tc.off[k] != -2) {
+                scn[b][tid + k * TC::NT] = rc[k];
+                scl[b][tid + k * TC::NT] = (rc[k] * rc[k]) * rl[k];
+            }
+    };
     float qu[7], qc[2 * QC + 1], ql[2 * QC + 1];  // u^n at z - 3 .. z + 3; c_n, lu at z - QC .. z + QC
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         const int zz = z0 - 3 + k;
-        qu[k] = (zz >= 0 && zz < d.nz) ? un[zz * sz + pxy] : 0.0f;
+        qu[k] = (own && zz >= 0 && zz < d.nz) ? un[zz * sz + pxy] : 0.0f;
     }
 #pragma unroll
     for (int k = 0; k < 2 * QC + 1; ++k) {
         const int zz = z0 - QC + k;
-        const bool in = zz >= 0 && zz < d.nz;
+        const bool in = own && zz >= 0 && zz < d.nz;
         qc[k] = in ? cn[zz * sz + pxy] : 0.0f;
         ql[k] = in ? lu[zz * sz + pxy] : 0.0f;
     }
+    fetch(z0);
+    store(0);
+    __syncthreads();
+    const int u0 = (ty + HU) * UW + tx + HU, c0 = (ty + HC) * CW + tx + HC;
     for (int z = z0; z < z1; ++z) {
+        const int b = (z - z0) & 1;
+        if (z + 1 < z1)
+            fetch(z + 1);
         const int64_t p = z * sz + pxy;
-        const float c = qc[QC], c2 = c * c, a = up[p], b = qu[3];
-        // g_a = (cn2[p + e_a] - cn2[p - e_a]) / 2 and D_a u^n, zero outside
-        float ga[3], du[3];
-        {
-            const float cxp = x + 1 < d.nx ? cn[p + 1] : 0.0f, cxm = x - 1 >= 0 ? cn[p - 1] : 0.0f;
-            const float cyp = y + 1 < d.ny ? cn[p + sy] : 0.0f, cym = y - 1 >= 0 ? cn[p - sy] : 0.0f;
-            ga[0] = 0.5f * (cxp * cxp - cxm * cxm);
-            ga[1] = 0.5f * (cyp * cyp - cym * cym);
-            ga[2] = 0.5f * (qc[QC + 1] * qc[QC + 1] - qc[QC - 1] * qc[QC - 1]);
-            const float uxp = x + 1 < d.nx ? un[p + 1] : 0.0f, uxm = x - 1 >= 0 ? un[p - 1] : 0.0f;
-            const float uyp = y + 1 < d.ny ? un[p + sy] : 0.0f, uym = y - 1 >= 0 ? un[p - sy] : 0.0f;
-            du[0] = 0.5f * (uxp - uxm);
-            du[1] = 0.5f * (uyp - uym);
-            du[2] = 0.5f * (qu[4] - qu[2]);
-        }
-        float f6 = 0.0f, gabs = 0.0f;
+        if (own) {
+            const float *tu_ = su[b] + u0, *tcn = scn[b] + c0, *tcl = scl[b] + c0;
+            const float c = qc[QC], c2 = c * c, a = up[p], bq = qu[3];
+            // g_a = (cn2[p + e_a] - cn2[p - e_a]) / 2 and D_a u^n, zero outside
+            float ga[3], du[3];
+            {
+                const float cxp = tcn[1], cxm = tcn[-1], cyp = tcn[CW], cym = tcn[-CW];
+                ga[0] = 0.5f * (cxp * cxp - cxm * cxm);
+                ga[1] = 0.5f * (cyp * cyp - cym * cym);
+                ga[2] = 0.5f * (qc[QC + 1] * qc[QC + 1] - qc[QC - 1] * qc[QC - 1]);
+                du[0] = 0.5f * (tu_[1] - tu_[-1]);
+                du[1] = 0.5f * (tu_[UW] - tu_[-UW]);
+                du[2] = 0.5f * (qu[4] - qu[2]);
+            }
+            float f6 = 0.0f, gabs = 0.0f;
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            f6 = fmaf(ga[ax], du[ax], f6);
-            gabs += fabsf(ga[ax]);
-        }
-        // t6 = cn2 * sum_axes delta^6 u^n
-        float s6 = 3.0f * v6[0] * b;
+            for (int ax = 0; ax < 3; ++ax) {
+                f6 = fmaf(ga[ax], du[ax], f6);
+                gabs += fabsf(ga[ax]);
+            }
+            // t6 = cn2 * sum_axes delta^6 u^n
+            float s6 = 3.0f * v6[0] * bq;
 #pragma unroll
-        for (int m = 1; m <= 3; ++m) {
-            float t = 0.0f;
-            if (x - m >= 0) t += un[p - m];
-            if (x + m < d.nx) t += un[p + m];
-            if (y - m >= 0) t += un[p - m * sy];
-            if (y + m < d.ny) t += un[p + m * sy];
-            if (z - m >= 0) t += qu[3 - m];
-            if (z + m < d.nz) t += qu[3 + m];
-            s6 = fmaf(v6[m], t, s6);
-        }
-        // t5 = cn2 * L(cn2 lu)
-        auto cl = [&](int64_t q) {
-            const float cq = cn[q];
-            return (cq * cq) * lu[q];
-        };
-        float s5 = 3.0f * w[0] * (c2 * ql[QC]);
+            for (int m = 1; m <= 3; ++m) {
+                float t = 0.0f;
+                t += tu_[-m];
+                t += tu_[m];
+                t += tu_[-m * UW];
+                t += tu_[m * UW];
+                if (z - m >= 0) t += qu[3 - m];
+                if (z + m < d.nz) t += qu[3 + m];
+                s6 = fmaf(v6[m], t, s6);
+            }
+            // t5 = cn2 * L(cn2 lu)
+            float s5 = 3.0f * w[0] * (c2 * ql[QC]);
 #pragma unroll
-        for (int m = 1; m <= R; ++m) {
-            float t = 0.0f;
-            if (x - m >= 0) t += cl(p - m);
-            if (x + m < d.nx) t += cl(p + m);
-            if (y - m >= 0) t += cl(p - m * sy);
-            if (y + m < d.ny) t += cl(p + m * sy);
-            if (z - m >= 0) t += (qc[QC - m] * qc[QC - m]) * ql[QC - m];
-            if (z + m < d.nz) t += (qc[QC + m] * qc[QC + m]) * ql[QC + m];
-            s5 = fmaf(w[m], t, s5);
-        }
-        const float f[8] = {a, b, c2 * a, c2 * b, s6 * c2, s5 * c2, f6, gabs * ql[QC]};
-        uint32_t w4p[4];
+            for (int m = 1; m <= R; ++m) {
+                float t = 0.0f;
+                t += tcl[-m];
+                t += tcl[m];
+                t += tcl[-m * CW];
+                t += tcl[m * CW];
+                if (z - m >= 0) t += (qc[QC - m] * qc[QC - m]) * ql[QC - m];
+                if (z + m < d.nz) t += (qc[QC + m] * qc[QC + m]) * ql[QC + m];
+                s5 = fmaf(w[m], t, s5);
+            }
+            const float f[8] = {a, bq, c2 * a, c2 * bq, s6 * c2, s5 * c2, f6, gabs * ql[QC]};
+            uint32_t w4p[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(sc.s[2 * k] * f[2 * k], sc.s[2 * k + 1] * f[2 * k + 1]);
-            w4p[k] = *reinterpret_cast<const uint32_t *>(&b2);
+            for (int k = 0; k < 4; ++k) {
+                const __nv_bfloat162 b2 =
+                    __floats2bfloat162_rn(sc.s[2 * k] * f[2 * k], sc.s[2 * k + 1] * f[2 * k + 1]);
+                w4p[k] = *reinterpret_cast<const uint32_t *>(&b2);
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(xout + p * XCH);
+            o[0] = make_uint4(w4p[0], w4p[1], w4p[2], w4p[3]);
+            if (XCH == 16)
+                o[1] = make_uint4(0u, 0u, 0u, 0u);
         }
-        uint4 *o = reinterpret_cast<uint4 *>(xout + p * XCH);
-        o[0] = make_uint4(w4p[0], w4p[1], w4p[2], w4p[3]);
-        if (XCH == 16)
-            o[1] = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int k = 0; k < 6; ++k)
             qu[k] = qu[k + 1];
-        qu[6] = (z + 4 < d.nz) ? un[p + 4 * sz] : 0.0f;
+        qu[6] = (own && z + 4 < d.nz) ? un[p + 4 * sz] : 0.0f;
 #pragma unroll
         for (int k = 0; k < 2 * QC; ++k) {
             qc[k] = qc[k + 1];
             ql[k] = ql[k + 1];
         }
-        const bool in = z + QC + 1 < d.nz;
+        const bool in = own && z + QC + 1 < d.nz;
         qc[2 * QC] = in ? cn[p + (QC + 1) * sz] : 0.0f;
         ql[2 * QC] = in ? lu[p + (QC + 1) * sz] : 0.0f;
+        if (z + 1 < z1)
+            store(b ^ 1);
+        __syncthreads();
     }
 }
 
