@@ -138,12 +138,14 @@ bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int b
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt =
         storage == GBST_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    // 64-byte L2 promotion: with 128 or 256 bytes the order-8 sweep at 512^3 read 1.18 x
-    // the field from DRAM, with 64 bytes 1.11 x; every sweep's time is the same or
-    // slightly shorter
+    // L2 promotion: 64 bytes for rows of at least 2 KB (with 128 or 256 bytes the order-8
+    // sweep at 512^3 read 1.18 x the field from DRAM, with 64 bytes 1.11 x, in the same
+    // time; the wide-row sweeps are equal or slightly faster), 256 bytes for shorter rows
+    // (the 64-grid batch of 96-256-point rows ran 2 % slower with 64)
+    const CUtensorMapL2promotion promo =
+        L.nx * L.es >= 2048 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
     CUresult r = fn(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_SWIZZLE_NONE, promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         char b[160];
         snprintf(b, sizeof b, "cuTensorMapEncodeTiled failed (%d) for box %dx%d, dims %lld x %lld x %lld",
