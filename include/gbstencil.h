@@ -87,11 +87,15 @@ typedef struct gbst_desc {
     int use_graph;         /* 0: direct launches; 1: capture the step loop as a CUDA graph */
     void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
     const gbst_allocator *allocator; /* NULL = cudaMalloc / cudaFree */
-    int temporal_block;    /* heat, FP32, 3D, zero ghosts, no decomposition only:
+    int temporal_block;    /* heat, FP32, 3D, zero ghosts, space order 2 or 4 only:
                               0 = automatic (single steps by default; stencil_tune may pick
                               two-step blocking), 1 = off, 2 = two time steps per pass over
                               memory (overlapped temporal blocking; results are bit-identical to
-                              single steps; afterwards GBST_U_PREV does not hold u^{n-1}) */
+                              single steps; afterwards GBST_U_PREV does not hold u^{n-1}).  With a
+                              decomposition the ghost regions are 2r deep and every two-step
+                              sweep is preceded by a three-phase exchange (x, y, then z faces
+                              2r deep, the later phases spanning the earlier phases' ghosts, so
+                              that the edge regions two steps reach are filled too) */
 } gbst_desc;
 
 typedef struct gbst_grid_s *gbst_handle;
@@ -157,7 +161,8 @@ gbst_status stencil_set_source(gbst_handle h, const int64_t idx[3], double f0_hz
                                double amp);
 
 /* Advance nsteps time steps, asynchronously on the handle's stream.  Each step
- * is: [decomposition/periodic: halo swap kernel] + one sweep kernel.  Device
+ * is: [decomposition/periodic: halo swap kernel] + one sweep kernel (a two-step
+ * plan: [the three-phase deep exchange] + one sweep per two steps).  Device
  * errors are reported by the next synchronising call. */
 gbst_status stencil_run(gbst_handle h, int64_t nsteps);
 

@@ -121,17 +121,19 @@ bool encode_tmap_bf16_4d(CUtensorMap *m, const void *base, const uint64_t dims[4
 // interior and `lead` ghosts on each side: boxes that reach further read
 // zeros without touching the row padding.
 bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h, int lead,
-                 std::string *err)
+                 std::string *err, int reach)
 {
     auto fn = tmap_encoder();
     if (!fn) {
         *err = "cuTensorMapEncodeTiled is not available from the driver";
         return false;
     }
-    const int64_t shift = L.G - lead;
+    // ghost rows / planes the map covers (coordinate 0 = the first of them)
+    const int ry = reach < 0 ? L.r : std::min(reach, L.r), rz = reach < 0 ? L.rz : std::min(reach, L.rz);
+    const int64_t shift = L.G - lead + ((L.rz - rz) * L.rows + (L.r - ry)) * L.pitch;
     base = static_cast<unsigned char *>(base) + shift * L.es;
-    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(L.nx + 2 * lead), static_cast<cuuint64_t>(L.rows),
-                                static_cast<cuuint64_t>(L.planes)};
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(L.nx + 2 * lead), static_cast<cuuint64_t>(L.ny + 2 * ry),
+                                static_cast<cuuint64_t>(L.nz + 2 * rz)};
     const cuuint64_t strides[2] = {static_cast<cuuint64_t>(L.pitch) * L.es,
                                    static_cast<cuuint64_t>(L.pitch) * L.rows * L.es};
     const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
@@ -299,6 +301,13 @@ struct gbst_grid_s {
     int nboxes = 0;
     int64_t max_box_elems = 0;
     int copy_blocks = 0;  // blocks of one halo copy launch
+    // Two time steps across exchanges (decomposed heat grids): ghost regions 2r deep and
+    // a second copy list, run before every two-step launch in three phases (x, y, then z
+    // faces, each spanning the ghost cells the earlier phases filled).
+    bool deep = false;
+    CopyBox *ddeep = nullptr;
+    int deep_n[3] = {0, 0, 0};       // boxes of each phase (consecutive in ddeep)
+    int deep_blocks[3] = {0, 0, 0};  // blocks of each phase's launch
     int64_t max_points = 0;
     Plan plan;
     int parity = 0;
@@ -410,7 +419,7 @@ void destroy_graphs(gbst_handle h)
 bool tb_allowed(gbst_handle h)
 {
     return h->nf == 1 && h->d.temporal_block != 1 && h->d.eq == GBST_HEAT && h->d.storage == GBST_F32 && h->ndim == 3 &&
-           h->d.bc == GBST_BC_ZERO && h->nboxes == 0 && h->d.kernel != GBST_KERNEL_SIMPLE;
+           h->d.bc == GBST_BC_ZERO && (h->nboxes == 0 || h->deep) && h->d.kernel != GBST_KERNEL_SIMPLE;
 }
 
 bool variant_matches(gbst_handle h, const StreamVariant &v)
@@ -482,13 +491,14 @@ gbst_status build_plan(gbst_handle h, int variant, int txt, int zchunks_req, int
         if (p.stream) {
             std::string err;
             for (int b = 0; b < 2; ++b)
-                if (!encode_tmap(&g.tmap[b], g.buf[b], s.lu, st, box_w, box_h, px, &err))
+                if (!encode_tmap(&g.tmap[b], g.buf[b], s.lu, st, box_w, box_h, px, &err, h->R) ||
+                    (p.var.tb == 2 && !encode_tmap(&g.tmap_tb[b], g.buf[b], s.lu, st, box_w, box_h, px, &err, -1)))
                     return fail(GBST_ECUDA, "%s", err.c_str());
             if (h->d.eq == GBST_WAVE) {
                 for (int b = 0; b < 2; ++b)
-                    if (!encode_tmap(&g.tmap_c[b], g.buf[b], s.lu, st, TX, TY, px, &err))
+                    if (!encode_tmap(&g.tmap_c[b], g.buf[b], s.lu, st, TX, TY, px, &err, h->R))
                         return fail(GBST_ECUDA, "%s", err.c_str());
-                if (!encode_tmap(&g.tmap_k, g.kappa, s.lk, GBST_F32, TX, TY, px, &err))
+                if (!encode_tmap(&g.tmap_k, g.kappa, s.lk, GBST_F32, TX, TY, px, &err, h->R))
                     return fail(GBST_ECUDA, "%s", err.c_str());
             }
         }
@@ -718,6 +728,78 @@ void widen_x_face(CopyBox &b, const Layout &dst, const Layout &src, int dir, int
     b.ex = W;
 }
 
+// Exchange before a two-step launch (deep ghosts, decomposition only): faces 2r deep
+// and the edge regions two steps of a star stencil reach (r x r across two axes).
+// Three phases, each a launch: x faces; y faces over x from one 16-byte chunk before
+// to one after the interior (the neighbour's x ghosts, filled in phase 0, are our
+// x-y edges); z faces over those x columns and y from -2r to ny + 2r (the x-z and
+// y-z edges).  Every received cell is the value the neighbour holds at the same
+// global point, so the two-step kernel sees what it would see undecomposed.
+gbst_status build_deep_copies(gbst_handle h)
+{
+    const int D = 2 * h->R;
+    std::vector<CopyBox> ph[3];
+    auto index_of = [&](const int c[3]) { return (c[2] * h->decomp[1] + c[1]) * h->decomp[0] + c[0]; };
+    for (size_t i = 0; i < h->subs.size(); ++i) {
+        const Sub &s = h->subs[i];
+        const int64_t n[3] = {s.lu.nx, s.lu.ny, s.lu.nz};
+        const int X = 16 / h->es;  // x ghost columns carried by the y and z faces
+        for (int a = 0; a < 3; ++a)
+            for (int dir = -1; dir <= 1; dir += 2) {
+                int nc[3] = {s.c[0], s.c[1], s.c[2]};
+                nc[a] += dir;
+                if (nc[a] < 0 || nc[a] >= h->decomp[a])
+                    continue;
+                const int ni = index_of(nc);
+                const Sub &ns = h->subs[ni];
+                const int64_t nn = a == 0 ? ns.lu.nx : a == 1 ? ns.lu.ny : ns.lu.nz;
+                int64_t dst[3], src[3], ext[3];
+                for (int b = 0; b < 3; ++b) {
+                    if (b == a) {
+                        dst[b] = dir < 0 ? -D : n[b];
+                        src[b] = dir < 0 ? nn - D : 0;
+                        ext[b] = D;
+                    } else if (b < a) {  // axes exchanged in an earlier phase: include their ghosts
+                        const int64_t gh = b == 0 ? X : D;
+                        dst[b] = src[b] = -gh;
+                        ext[b] = n[b] + 2 * gh;
+                    } else {
+                        dst[b] = src[b] = 0;
+                        ext[b] = n[b];
+                    }
+                }
+                CopyBox bx{};
+                bx.dst_grid = static_cast<int>(i);
+                bx.src_grid = ni;
+                bx.dst_off = byte_off(s.lu, dst[0], dst[1], dst[2]);
+                bx.src_off = byte_off(ns.lu, src[0], src[1], src[2]);
+                bx.ex = ext[0];
+                bx.ey = ext[1];
+                bx.ez = ext[2];
+                if (a == 0)
+                    widen_x_face(bx, s.lu, ns.lu, dir, D);
+                if (bx.ex * bx.ey * bx.ez >= (int64_t(1) << 31))
+                    return fail(GBST_EINVAL, "a halo face of %lld cells is too large (limit 2^31 - 1)",
+                                static_cast<long long>(bx.ex * bx.ey * bx.ez));
+                ph[a].push_back(bx);
+            }
+    }
+    std::vector<CopyBox> all;
+    for (int a = 0; a < 3; ++a) {
+        h->deep_n[a] = static_cast<int>(ph[a].size());
+        h->deep_blocks[a] = halo_copy_blocks(ph[a].data(), h->deep_n[a]);
+        all.insert(all.end(), ph[a].begin(), ph[a].end());
+    }
+    if (!all.empty()) {
+        h->ddeep = static_cast<CopyBox *>(dalloc(h, all.size() * sizeof(CopyBox)));
+        if (!h->ddeep)
+            return fail(GBST_ENOMEM, "halo copy list");
+        GBST_CUDA(cudaMemcpyAsync(h->ddeep, all.data(), all.size() * sizeof(CopyBox), cudaMemcpyHostToDevice,
+                                  h->stream));
+    }
+    return GBST_OK;
+}
+
 gbst_status build_copies(gbst_handle h)
 {
     std::vector<CopyBox> boxes;
@@ -791,7 +873,7 @@ gbst_status build_copies(gbst_handle h)
         GBST_CUDA(cudaMemcpyAsync(h->dboxes, boxes.data(), boxes.size() * sizeof(CopyBox), cudaMemcpyHostToDevice,
                                   h->stream));
     }
-    return GBST_OK;
+    return h->deep ? build_deep_copies(h) : GBST_OK;
 }
 
 SweepArgs sweep_args(gbst_handle h, int parity, const float *srcval)
@@ -858,7 +940,17 @@ gbst_status enqueue_step(gbst_handle h, int parity, const float *srcval, int pro
                                                cudaEventRecordExternal));
         return GBST_OK;
     }
-    if (h->nboxes > 0) {
+    if (h->deep && h->plan.stream && h->plan.var.tb == 2) {
+        // two steps follow: faces 2r deep and the edges, in three ordered phases
+        const CopyBox *b = h->ddeep;
+        for (int a = 0; a < 3; ++a) {
+            const cudaError_t e =
+                launch_halo_copies(h->dgrids, b, h->deep_n[a], parity, h->es, h->deep_blocks[a], h->stream);
+            if (e != cudaSuccess)
+                return fail(GBST_ECUDA, "halo copy launch: %s", cudaGetErrorString(e));
+            b += h->deep_n[a];
+        }
+    } else if (h->nboxes > 0) {
         cudaError_t e =
             launch_halo_copies(h->dgrids, h->dboxes, h->nboxes, parity, h->es, h->copy_blocks, h->stream);
         if (e != cudaSuccess)
@@ -1158,6 +1250,13 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
         }
     }
 
+    // decomposed heat grids that two-step blocking can sweep (radius 1 or 2: the
+    // blocked variants) keep ghost regions 2r deep; see build_copies
+    h->deep = !batch && h->nf == 1 && h->decomp[0] * h->decomp[1] * h->decomp[2] > 1 && d.eq == GBST_HEAT &&
+              d.storage == GBST_F32 && d.ndim == 3 && d.bc == GBST_BC_ZERO && d.temporal_block != 1 &&
+              d.kernel != GBST_KERNEL_SIMPLE && R <= 2;
+    const int ghost = h->deep ? 2 * R : R;
+
     auto bail = [&](gbst_status code) {
         destroy_handle(h);
         return code;
@@ -1199,11 +1298,18 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
                     // more than it saved (64 grids of 96-256 points per axis: 353
                     // against 388 GPoints/s)
                     const bool wide = nn[0] * h->es >= kWideRowBytes;
-                    s.lu = make_layout(d.ndim, nn[0], nn[1], nn[2], R, h->es, (wide ? kGhostBytesX : 16) / h->es);
+                    s.lu = make_layout(d.ndim, nn[0], nn[1], nn[2], ghost, h->es, (wide ? kGhostBytesX : 16) / h->es);
                     s.lk = make_layout(d.ndim, nn[0], nn[1], nn[2], R, 4, wide ? kGhostBytesX / 4 : px);
                     h->subs.push_back(s);
                     h->max_points = std::max(h->max_points, nn[0] * nn[1] * nn[2]);
                 }
+    }
+    // a two-step exchange reaches 2r cells into each neighbour: every subdomain needs that many
+    for (const Sub &sb : h->subs) {
+        const int64_t ext[3] = {sb.lu.nx, sb.lu.ny, sb.lu.nz};
+        for (int a = 0; a < 3; ++a)
+            if (h->decomp[a] > 1 && ext[a] < 2 * R)
+                h->deep = false;  // (the layouts keep their deep ghosts; only single steps run)
     }
     const size_t ns = h->subs.size();
     h->hgrids.assign(ns, GridDev{});
@@ -1242,6 +1348,14 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
         g.krows = s.lk.rows;
         g.korigin = s.lk.origin;
         g.heat_a = static_cast<float>(s.alpha * s.dt / (s.h * s.h));
+        g.ghost = s.lu.r;
+        g.face_int = 0;
+        for (int a = 0; a < d.ndim; ++a) {
+            if (s.c[a] > 0)
+                g.face_int |= 1 << (2 * a);
+            if (s.c[a] + 1 < h->decomp[a])
+                g.face_int |= 2 << (2 * a);
+        }
     }
     h->dgrids = static_cast<GridDev *>(dalloc(h, ns * sizeof(GridDev)));
     h->derr = static_cast<int *>(dalloc(h, 256));

@@ -67,7 +67,9 @@ struct alignas(128) GridDev {
     int box_bytes;         // bytes of one TMA box (tile + halo)
     int src_x, src_y, src_z, has_src;  // source position (interior coordinates)
     float heat_a;          // heat: alpha dt / h^2 of this grid
-    int pad_;
+    int ghost;             // ghost rows / planes of the u layout (r, or 2r for two steps across exchanges)
+    int face_int;          // faces shared with another subdomain: bit 2a low, bit 2a + 1 high side of axis a
+    CUtensorMap tmap_tb[2];  // two-step kernel: u buffers with all ghost rows and planes (box = tile + 2r halo)
 };
 
 // A unit of sweep work: one tile of one grid over planes [z0, z1).
@@ -230,7 +232,9 @@ gbst_status closure_features_values(const float *up, const float *un, int64_t nx
 // swizzle32: boxes land in the 32-byte swizzled shared-memory layout (inner box extent 32 bytes).
 bool encode_tmap_bf16_4d(CUtensorMap *m, const void *base, const uint64_t dims[4], const uint64_t strides[3],
                          const uint32_t box[4], std::string *err, bool swizzle32 = false);
-bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h,
-                 std::string *err);
+// Tiled tensor map of a padded field: x from `lead` elements before the interior,
+// `reach` ghost rows / planes on each side (-1: all of the layout's).
+bool encode_tmap(CUtensorMap *m, void *base, const Layout &L, int storage, int box_w, int box_h, int lead,
+                 std::string *err, int reach);
 
 }  // namespace gbst

@@ -193,20 +193,21 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
             const Unit u = a.units[ui];
             const GridDev &g = a.grids[u.grid];
             const int bx = (u.tile % g.tiles_x) * TX, by = (u.tile / g.tiles_x) * TY;
-            const CUtensorMap *map = &g.tmap[parity];
+            const CUtensorMap *map = &g.tmap_tb[parity];  // every ghost row and plane of the layout
             const uint32_t bytes = static_cast<uint32_t>(g.box_bytes);
             const int L = (u.z1 - u.z0) + 4 * R + (single ? 0 : 1);
+            const int gs = g.ghost - 2 * R;  // map coordinate of interior row / plane 0, less 2r
             for (int l = 0; l < L; ++l, ++it) {
                 if (it >= NB && !wait_or_abort(&empty[it % NB], ((it / NB) - 1) & 1, abort_flag))
                     goto drain;
                 if (l == 0)
                     uidx[it % NB] = ui;  // published by the arrive below
                 mbar_arrive_expect_tx(&full[it % NB], bytes);
-                // padded coordinates: x from bx - 2 chunks (ghost G = one chunk), y from
-                // by - 2r (ghost r rows), plane z0 - 2r + l (ghost r planes); outside the
-                // tensor the load fills zeros
-                tma_load_plane(slots + (it % S) * slot_bytes, map, &full[it % NB], bx - PX, by - R,
-                               u.z0 - R + l);
+                // map coordinates: x from bx - 2 chunks (the map starts one chunk before the
+                // interior), y from by - 2r, plane z0 - 2r + l (the map starts `ghost` rows
+                // and planes before the interior); outside the tensor the load fills zeros
+                tma_load_plane(slots + (it % S) * slot_bytes, map, &full[it % NB], bx - PX, by + gs,
+                               u.z0 + gs + l);
             }
         }
         // sentinel iteration: no more units
@@ -288,18 +289,27 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
         unsigned char *__restrict__ outbase = static_cast<unsigned char *>(gp->buf[1 - parity]);
         const float2 a2 = make_float2(gp->heat_a, gp->heat_a);
         const int bx = (u.tile % tiles_x) * TX, by = (u.tile / tiles_x) * TY;
-        // interior masks of this thread's u' points
-        bool yin[PY];
+        // Masks of this thread's u' points: u' is zero outside the global domain (the
+        // ghost cells of a stored u' would be); across a face shared with another
+        // subdomain the ghost region holds that subdomain's u (two-step exchange) and
+        // u' there is the value the neighbour computes itself.  Stores: interior only.
+        const int fi = gp->face_int;
+        const int64_t xlo = (fi & 1) ? -(1ll << 40) : 0, xhi = (fi & 2) ? (1ll << 40) : nx;
+        const int64_t ylo = (fi & 4) ? -(1ll << 40) : 0, yhi = (fi & 8) ? (1ll << 40) : ny;
+        const int zlo = (fi & 16) ? -(1 << 30) : 0, zhi = (fi & 32) ? (1 << 30) : static_cast<int>(nz);
+        bool yin[PY], ysto[PY];
 #pragma unroll
         for (int k = 0; k < PY; ++k) {
             const int64_t y = static_cast<int64_t>(by) - R + rho0 + k;
-            yin[k] = y >= 0 && y < ny;
+            yin[k] = y >= ylo && y < yhi;
+            ysto[k] = y >= 0 && y < ny;
         }
-        bool xin[PX];
+        bool xin[PX], xsto[PX];
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             const int64_t x = static_cast<int64_t>(bx) + cx + i;
-            xin[i] = x >= 0 && x < nx;
+            xin[i] = x >= xlo && x < xhi;
+            xsto[i] = x >= 0 && x < nx;
         }
         // every u' point of this thread lies inside the grid in x and y (the usual
         // case): only planes outside [0, nz) need zeroing
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
         bool st_row[PY];  // rows this thread stores (step-2 rows, or step-1 rows in single mode)
 #pragma unroll
         for (int k = 0; k < PY; ++k)
-            st_row[k] = s2row[k] && yin[k] && bx + cx < nx;
+            st_row[k] = s2row[k] && ysto[k] && bx + cx < nx;
         const int64_t plane_elems = rows * pitch;
         const int64_t row_stride = pitch * 4;
         const int64_t plane_bytes = plane_elems * 4;
@@ -375,7 +385,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                             } else {
 #pragma unroll
                                 for (int i = 0; i < PX; ++i)
-                                    if (xin[i])
+                                    if (xsto[i])
                                         St::store1(op + r_ * row_stride + i * 4, o[r_][i]);
                             }
                         }
@@ -390,7 +400,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                 tb_update<R, PY, qc1, (OPT & kOptScalarOddX) != 0>(q1, slots + slot_c * slot_bytes + in_off, IN_ROW, wc2, w2, a2, o);
                 // u' plane index (interior z) of this result; u' is zero outside the interior
                 const int zq = u.z0 - 3 * R + j;
-                if (static_cast<unsigned>(zq) >= static_cast<unsigned>(nz)) {
+                if (zq < zlo || zq >= zhi) {
 #pragma unroll
                     for (int r_ = 0; r_ < PY; ++r_)
 #pragma unroll
@@ -416,7 +426,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB) k_tb(const SweepArgs a, c
                                 } else {
 #pragma unroll
                                     for (int i = 0; i < PX; ++i)
-                                        if (xin[i])
+                                        if (xsto[i])
                                             St::store1(op + r_ * row_stride + i * 4, o[r_][i]);
                                 }
                             }

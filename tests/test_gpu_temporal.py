@@ -2,10 +2,12 @@
 
 A blocked run must give the same bits as the same number of single steps: the
 step-1 field is recomputed on overlapped tiles with the single-step kernel's
-per-point arithmetic, and its points outside the interior are zero like the
-ghost cells of a stored field.  Checked for every compiled blocked variant,
-several z-chunkings, odd step counts (the last step runs alone), ragged and
-tiny grids, and against the FP64 oracle.
+per-point arithmetic, and its points outside the domain are zero like the ghost
+cells of a stored field.  Checked for every compiled blocked variant, several
+z-chunkings, odd step counts (the last step runs alone), ragged and tiny grids,
+against the FP64 oracle, and on single-device decompositions, where the ghost
+regions are 2r deep and a three-phase exchange (faces and the edges two steps
+reach) precedes every two-step launch.
 """
 import json
 
@@ -113,8 +115,8 @@ def test_blocking_off_and_unsupported_cases_use_single_steps(torch_cuda):
     assert json.loads(g.describe())["tb"] == 1
     rep = g.tune(reps=1)
     assert all(c["tb"] == 1 for c in rep["candidates"])
-    # a decomposition exchanges halos every step: blocking does not apply
-    d, _ = heat(dims, 2, 2, decomp=(2, 1, 1))
+    # order 8 has no blocked variants (two 9-plane queues do not fit the register file)
+    d, _ = heat(dims, 8, 2, decomp=(2, 1, 1))
     assert json.loads(d.describe())["tb"] == 1
     # BF16 storage: not blocked
     b, _ = heat(dims, 2, 2, storage="bf16")
@@ -132,3 +134,57 @@ def test_autotuner_considers_blocking(torch_cuda):
     want = single_steps(dims, 4, u0, 6)
     g.run(6)
     np.testing.assert_array_equal(g.get_field("u"), want)
+
+
+@pytest.mark.parametrize("so", [2, 4])
+@pytest.mark.parametrize("decomp,dims", [((2, 2, 2), (68, 50, 44)), ((3, 2, 1), (130, 37, 29)),
+                                         ((1, 1, 4), (40, 33, 50)), ((2, 1, 1), (1040, 20, 12))])
+def test_blocked_decomposed_equals_single_steps_bitwise(torch_cuda, so, decomp, dims):
+    """Two steps per launch across subdomain exchanges give the undecomposed single steps'
+    bits (ragged splits; (2, 1, 1) of 1040 points: wide rows, 128-byte x ghosts)."""
+    u0 = synthetic.uniform_field(25, tuple(reversed(dims)))
+    want = {n: single_steps(dims, so, u0, n) for n in (1, 2, 5)}
+    g, _ = heat(dims, so, 2, decomp=decomp)
+    assert json.loads(g.describe())["tb"] == 2
+    for n in (1, 2, 5):
+        g.set_field("u", u0)
+        g.run(n)
+        np.testing.assert_array_equal(g.get_field("u"), want[n], err_msg=f"n {n}")
+    g.close()
+
+
+@pytest.mark.parametrize("so", [2, 4])
+def test_blocked_decomposed_every_variant_bitwise(torch_cuda, so):
+    dims = (70, 45, 36)
+    u0 = synthetic.uniform_field(26, tuple(reversed(dims)))
+    want = single_steps(dims, so, u0, 5)
+    g, _ = heat(dims, so, 2, decomp=(2, 2, 2))
+    for v in tb_variants(so):
+        for zc, sched in ((0, 1), (3, 0)):
+            g.set_schedule(sched)
+            g.set_field("u", u0)
+            g.set_plan(v, 0, zc, 0)
+            assert json.loads(g.describe())["tb"] == 2
+            g.run(5)
+            np.testing.assert_array_equal(g.get_field("u"), want, err_msg=f"variant {v} zchunks {zc} schedule {sched}")
+    g.close()
+
+
+def test_decomposed_single_step_plans_on_deep_ghosts(torch_cuda):
+    """A decomposed grid keeps 2r-deep ghosts for blocking; its single-step plans (r-deep
+    face exchange) give the same bits too, and the tuner considers both."""
+    dims = (96, 40, 30)
+    so = 2
+    u0 = synthetic.uniform_field(27, tuple(reversed(dims)))
+    want = single_steps(dims, so, u0, 4)
+    g, _ = heat(dims, so, 0, decomp=(2, 2, 1))
+    g.set_field("u", u0)
+    rep = g.tune(reps=1)
+    assert {c["tb"] for c in rep["candidates"]} == {1, 2}
+    for tb in (1, 2):
+        v = next(c["variant"] for c in rep["candidates"] if c["tb"] == tb)
+        g.set_field("u", u0)
+        g.set_plan(v, 0, 0, 0)
+        g.run(4)
+        np.testing.assert_array_equal(g.get_field("u"), want, err_msg=f"tb {tb}")
+    g.close()
