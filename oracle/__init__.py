@@ -235,5 +235,5 @@ def rel_l2_error(got: np.ndarray, ref: np.ndarray) -> float:
 
 
 from .decomp import (Exchange, decompose_extents, exchanges_for,  # noqa: E402,F401
-                     decomposed_heat_run, decomposed_wave_run)
+                     decomposed_heat_run, decomposed_heat_run_two_step, decomposed_wave_run)
 from . import closure  # noqa: E402,F401

@@ -13,6 +13,9 @@ Follows the paper's Section 4.2 (the ``dmp`` dialect):
   figure and its 108x108, halo-4 listing).
 
 Only faces are exchanged: the star stencils read no edge or corner ghosts.
+Two steps per exchange (temporal blocking; an extension, the paper swaps before
+every step) need halos 2r deep and the edge regions two steps reach: see
+:func:`decomposed_heat_run_two_step`.
 Coordinates are in memref order (slowest dimension first), matching numpy's
 C order for arrays shaped (nz, ny, nx).
 """
@@ -163,3 +166,94 @@ def decomposed_wave_run(uprev: np.ndarray, u: np.ndarray, kappa: np.ndarray, so:
             N[c] = out
         P, C = C, N
     return D.gather(P), D.gather(C)
+
+
+def deep_swap(D: _Decomposition, bufs: dict) -> None:
+    """Halo exchange for two steps (halo 2r): one phase per dimension, fastest first;
+    a phase exchanges faces 2r deep over the full padded extent of the dimensions of
+    earlier phases (their halos are already filled) and the interior of the others,
+    so the edge and corner regions arrive from the diagonal neighbours by way of the
+    face neighbours."""
+    h = D.r
+    nd = D.nd
+    done = set()
+    for d in reversed(range(nd)):  # memref order: the last dimension is x
+        sends = {}
+        for c in D.coords:
+            ls = D.local_shape(c)
+            for direction in (-1, 1):
+                nb = c[d] + direction
+                if nb < 0 or nb >= D.grid[d]:
+                    continue
+                src = []
+                for e in range(nd):
+                    if e == d:
+                        lo = h if direction < 0 else ls[e]  # first / last h interior layers
+                        src.append(slice(lo, lo + h))
+                    elif e in done:
+                        src.append(slice(0, ls[e] + 2 * h))
+                    else:
+                        src.append(slice(h, h + ls[e]))
+                sends[(c, direction)] = bufs[c][tuple(src)].copy()
+        for c in D.coords:
+            ls = D.local_shape(c)
+            for direction in (-1, 1):
+                nb = c[d] + direction
+                if nb < 0 or nb >= D.grid[d]:
+                    continue
+                dst = []
+                for e in range(nd):
+                    if e == d:
+                        lo = 0 if direction < 0 else h + ls[e]
+                        dst.append(slice(lo, lo + h))
+                    elif e in done:
+                        dst.append(slice(0, ls[e] + 2 * h))
+                    else:
+                        dst.append(slice(h, h + ls[e]))
+                ncoord = tuple(ci + (direction if e == d else 0) for e, ci in enumerate(c))
+                bufs[c][tuple(dst)] = sends[(ncoord, -direction)]
+        done.add(d)
+
+
+def decomposed_heat_run_two_step(u0: np.ndarray, so: int, a: float, nsteps: int,
+                                 decomp_xyz: Sequence[int], coeffs=None) -> np.ndarray:
+    """Heat run on a decomposition with two steps per exchange: halos 2r deep, a
+    :func:`deep_swap` before every pair of steps, the first step evaluated on the
+    interior grown by r (zero outside the global domain), the second on the interior.
+    An odd last step runs after a plain swap.  Every step-1 value in a halo is the one
+    the neighbour computes for the same point, so the result equals the global run."""
+    from . import sweep_heat_padded
+    r = so // 2
+    u0 = np.asarray(u0, dtype=np.float64)
+    nd = u0.ndim
+    D = _Decomposition(u0.shape, _grid_memref_order(decomp_xyz, nd), 2 * r)
+    bufs = D.scatter(u0)
+    left = nsteps
+    while left > 0:
+        deep_swap(D, bufs)  # (a lone last step reads only the inner r layers of it)
+        for c in D.coords:
+            ls = D.local_shape(c)
+            grown = tuple(n + 2 * r for n in ls)
+            # step 1 on interior + r: the padded buffer seen as a grown interior with halo r
+            u1 = sweep_heat_padded(bufs[c], nd, tuple(reversed(grown)), so, a, coeffs)
+            # zero outside the global domain (sides without a neighbour)
+            for d in range(nd):
+                if c[d] == 0:
+                    sl = [slice(None)] * nd
+                    sl[d] = slice(0, 2 * r)
+                    u1[tuple(sl)] = 0.0
+                if c[d] == D.grid[d] - 1:
+                    sl = [slice(None)] * nd
+                    sl[d] = slice(2 * r + ls[d], None)
+                    u1[tuple(sl)] = 0.0
+            if left == 1:
+                bufs[c] = u1
+                continue
+            # step 2 on the interior, from the step-1 field with an r-wide halo
+            inner = tuple(slice(r, r + n + 2 * r) for n in ls)
+            u2 = sweep_heat_padded(np.ascontiguousarray(u1[inner]), nd, tuple(reversed(ls)), so, a, coeffs)
+            out = np.zeros_like(bufs[c])
+            out[inner] = u2
+            bufs[c] = out
+        left -= 2 if left >= 2 else 1
+    return D.gather(bufs)

@@ -266,6 +266,70 @@ def test_decomposed_heat_equals_global(orc, so, shape, decomp):
     np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("so", SOS)
+@pytest.mark.parametrize("shape,decomp", [((12, 14, 16), (2, 2, 2)), ((11, 9, 13), (3, 2, 2)),
+                                          ((20, 22), (2, 3, 1))])
+@pytest.mark.parametrize("nsteps", (5, 6))
+def test_decomposed_two_step_heat_equals_global(orc, so, shape, decomp, nsteps):
+    """Two steps per exchange: halos 2r deep and the phased exchange that carries the edge
+    regions; the step-1 values in the halos equal the neighbours' own, so the result is the
+    global run's, in FP64 bit for bit (odd counts end with one step).  Subdomains are at
+    least 2r wide where the shapes allow it."""
+    r = so // 2
+    if any(n // p < 2 * r for n, p in zip(reversed(shape), decomp)):
+        pytest.skip("a subdomain thinner than 2r")
+    u0 = synthetic.uniform_field(42, shape).astype(np.float64)
+    a = 0.8 * synthetic.heat_a_max(len(shape), so)
+    ref = orc.heat_run(u0, so, a, nsteps)
+    got = orc.decomposed_heat_run_two_step(u0, so, a, nsteps, decomp)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_two_step_exchange_without_edges_differs(orc):
+    """The edge regions matter: with faces only (each phase over the interior of the other
+    axes) two steps differ from the global run near the subdomain corners."""
+    from oracle import decomp as dm
+    shape, so, decomp = (12, 14, 16), 2, (2, 2, 2)
+    u0 = synthetic.uniform_field(43, shape).astype(np.float64)
+    a = 0.8 * synthetic.heat_a_max(3, so)
+    ref = orc.heat_run(u0, so, a, 2)
+    saved = dm.deep_swap
+
+    def faces_only(D, bufs):
+        # a deep exchange whose phases never span the earlier phases' halos
+        h = D.r
+        for d in reversed(range(D.nd)):
+            sends = {}
+            for c in D.coords:
+                ls = D.local_shape(c)
+                for direction in (-1, 1):
+                    nb = c[d] + direction
+                    if nb < 0 or nb >= D.grid[d]:
+                        continue
+                    src = [slice(h, h + ls[e]) if e != d else
+                           slice(h if direction < 0 else ls[e], (h if direction < 0 else ls[e]) + h)
+                           for e in range(D.nd)]
+                    sends[(c, direction)] = bufs[c][tuple(src)].copy()
+            for c in D.coords:
+                ls = D.local_shape(c)
+                for direction in (-1, 1):
+                    nb = c[d] + direction
+                    if nb < 0 or nb >= D.grid[d]:
+                        continue
+                    dst = [slice(h, h + ls[e]) if e != d else
+                           slice(0 if direction < 0 else h + ls[e], (0 if direction < 0 else h + ls[e]) + h)
+                           for e in range(D.nd)]
+                    ncoord = tuple(ci + (direction if e == d else 0) for e, ci in enumerate(c))
+                    bufs[c][tuple(dst)] = sends[(ncoord, -direction)]
+
+    dm.deep_swap = faces_only
+    try:
+        got = orc.decomposed_heat_run_two_step(u0, so, a, 2, decomp)
+    finally:
+        dm.deep_swap = saved
+    assert np.max(np.abs(got - ref)) > 1e-6 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("so", (2, 8))
 def test_decomposed_wave_equals_global(orc, so):
     shape = (10, 12, 14)
