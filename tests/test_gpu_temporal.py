@@ -118,6 +118,15 @@ def test_blocking_off_and_unsupported_cases_use_single_steps(torch_cuda):
     # order 8 has no blocked variants (two 9-plane queues do not fit the register file)
     d, _ = heat(dims, 8, 2, decomp=(2, 1, 1))
     assert json.loads(d.describe())["tb"] == 1
+    # subdomains thinner than 2r along a split axis: single steps (on the deep-ghost layout),
+    # still the undecomposed bits
+    thin = (10, 12, 9)
+    t, _ = heat(thin, 4, 2, decomp=(4, 1, 1))
+    assert json.loads(t.describe())["tb"] == 1
+    u0 = synthetic.uniform_field(28, tuple(reversed(thin)))
+    t.set_field("u", u0)
+    t.run(3)
+    np.testing.assert_array_equal(t.get_field("u"), single_steps(thin, 4, u0, 3))
     # BF16 storage: not blocked
     b, _ = heat(dims, 2, 2, storage="bf16")
     assert json.loads(b.describe())["tb"] == 1
