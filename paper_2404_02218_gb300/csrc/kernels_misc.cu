@@ -175,12 +175,55 @@ __device__ __forceinline__ double load_dense(const void *p, int dtype, int64_t i
     return static_cast<double>(__bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]));
 }
 
+// FP32 on both sides, rows of a multiple of 4 elements at 16-byte aligned starts:
+// a warp per row, 16-byte pieces (a thread per element and a row per block moved
+// 1.9 TB/s at 256^3).
+__device__ __forceinline__ bool xfer_vec4(const XferArgs &x)
+{
+    return x.storage == GBST_F32 && x.dense_dtype == GBST_F32 && ((x.nx | x.gx | x.gnx) & 3) == 0 &&
+           ((reinterpret_cast<uintptr_t>(x.padded) | reinterpret_cast<uintptr_t>(x.dense)) & 15) == 0 &&
+           ((x.origin | x.pitch) & 3) == 0;
+}
+
+template <int MODE>  // 0: dense -> padded, 1: padded -> dense, 2: padded += dense
+__device__ __forceinline__ void xfer_rows_vec4(const XferArgs &x)
+{
+    const int64_t nrows = x.ny * x.nz, nx4 = x.nx >> 2;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t row = static_cast<int64_t>(blockIdx.x) * nw + (threadIdx.x >> 5); row < nrows;
+         row += static_cast<int64_t>(gridDim.x) * nw) {
+        const int64_t j = row % x.ny, k = row / x.ny;
+        float4 *pd = reinterpret_cast<float4 *>(static_cast<float *>(x.padded) + x.origin + (k * x.rows + j) * x.pitch);
+        float4 *dd = reinterpret_cast<float4 *>(static_cast<float *>(x.dense) +
+                                                ((x.gz + k) * x.gny + (x.gy + j)) * x.gnx + x.gx);
+        for (int64_t i = lane; i < nx4; i += 32) {
+            if (MODE == 0) {
+                pd[i] = dd[i];
+            } else if (MODE == 1) {
+                dd[i] = pd[i];
+            } else {
+                float4 a = pd[i];
+                const float4 b = dd[i];
+                a.x += b.x;
+                a.y += b.y;
+                a.z += b.z;
+                a.w += b.w;
+                pd[i] = a;
+            }
+        }
+    }
+}
+
 // Dense <-> padded transfers, one block per x row (grid-stride over the ny*nz
 // rows; one division per row), threads along x: both sides are read and
 // written in contiguous runs, which also suits host memory accessed over the
 // host link.
 __global__ void k_scatter(const XferArgs x)
 {
+    if (xfer_vec4(x) && !(x.scale_sq > 0.0)) {
+        xfer_rows_vec4<0>(x);
+        return;
+    }
     const int64_t nrows = x.ny * x.nz;
     for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
         const int64_t j = row % x.ny, k = row / x.ny;
@@ -207,6 +250,10 @@ __global__ void k_scatter(const XferArgs x)
 
 __global__ void k_gather(const XferArgs x)
 {
+    if (xfer_vec4(x)) {
+        xfer_rows_vec4<1>(x);
+        return;
+    }
     const int64_t nrows = x.ny * x.nz;
     for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
         const int64_t j = row % x.ny, k = row / x.ny;
@@ -230,6 +277,10 @@ __global__ void k_gather(const XferArgs x)
 
 __global__ void k_scatter_add(const XferArgs x)
 {
+    if (xfer_vec4(x)) {
+        xfer_rows_vec4<2>(x);
+        return;
+    }
     const int64_t n = x.nx * x.ny * x.nz;
     for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
          p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
