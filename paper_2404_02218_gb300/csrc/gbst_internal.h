@@ -122,6 +122,15 @@ struct StreamVariant {
 // two scalar additions each instead of one packed addition of re-paired
 // registers (the same results bit for bit).
 constexpr int kOptScalarOddX = 2;
+// kOptMixedY (BF16 storage): the sum of the two y-neighbour pairs of offset m
+// widens the halves of one 32-bit word and adds the other word's halves by
+// mixed-precision additions (BF16 + FP32 -> FP32), one widening fewer per pair
+// and the same rounded sums bit for bit.
+constexpr int kOptMixedY = 4;
+// kOptMixedU (BF16 wave): 2u - u^{n-1} as the negated mixed-precision difference
+// u^{n-1} - 2u, folded into the final fused multiply-add (the same bits: rounding
+// to nearest is symmetric).
+constexpr int kOptMixedU = 8;
 // Threads of one CTA of a streaming variant (consumers and the producer warp).
 inline int block_threads(const StreamVariant &v) { return v.nthreads + 32; }
 

@@ -141,6 +141,42 @@ struct Storage<GBST_BF16> {
     }
 };
 
+// 32-bit word pp of a 16-byte chunk (BF16 storage: the point pair pp)
+__device__ __forceinline__ uint32_t word_of(const uint4 &v, int pp)
+{
+    return pp == 0 ? v.x : pp == 1 ? v.y : pp == 2 ? v.z : v.w;
+}
+
+// (lo(a) + lo(b), hi(a) + hi(b)) for two words of BF16 pairs, in FP32 rounded to
+// nearest: a's halves are widened, b's halves enter mixed-precision additions.
+// Each sum of two BF16 values is the same FP32 value as the packed FP32x2 sum of
+// both widened pairs (the operands are exact, the addition commutes).
+__device__ __forceinline__ float2 bf16_pair_sum(uint32_t a, uint32_t b)
+{
+    const float ax = __uint_as_float(a << 16), ay = __uint_as_float(a & 0xffff0000u);
+    float2 r;
+    asm("{\n\t.reg .b16 l, h;\n\t"
+        "mov.b32 {l, h}, %2;\n\t"
+        "add.rn.f32.bf16 %0, l, %3;\n\t"
+        "add.rn.f32.bf16 %1, h, %4;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "r"(b), "f"(ax), "f"(ay));
+    return r;
+}
+
+// (lo(w) - c.x, hi(w) - c.y) for a word of a BF16 pair, in FP32 rounded to nearest.
+__device__ __forceinline__ float2 bf16_pair_sub(uint32_t w, float2 c)
+{
+    float2 r;
+    asm("{\n\t.reg .b16 l, h;\n\t"
+        "mov.b32 {l, h}, %2;\n\t"
+        "sub.rn.f32.bf16 %0, l, %3;\n\t"
+        "sub.rn.f32.bf16 %1, h, %4;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "r"(w), "f"(c.x), "f"(c.y));
+    return r;
+}
+
 // x-halo loads narrowed to the r elements next to the thread's column: the
 // returned 16-byte chunk holds them at their natural positions (zero elsewhere).
 template <int ST, int R>
@@ -281,11 +317,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *counter, unsigned int
 // OPT & kOptScalarOddX: the x-neighbour sums of odd offsets, whose operands
 // straddle the thread's packed point pairs, as two scalar additions instead of
 // one packed addition of re-paired registers (the same results bit for bit).
+// OPT & kOptMixedY (BF16 storage): y-neighbour sums of two halo rows from the
+// packed words by bf16_pair_sum (the same results bit for bit).
+// OPT & kOptMixedU (BF16 wave): u^{n-1} - 2u by bf16_pair_sub, negated into the
+// last fused multiply-add (the same results bit for bit).
 template <int R, int EQ, int ST, bool HAS_Z, int NC, int PY, int D, int MINB, int TXT, bool YS = false, int OPT = 0>
 __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs a, const int slot_bytes)
 {
     using St = Storage<ST>;
     constexpr bool SX = (OPT & kOptScalarOddX) != 0;
+    constexpr bool MY = ST == GBST_BF16 && (OPT & kOptMixedY) != 0;
+    constexpr bool MU = ST == GBST_BF16 && EQ == GBST_WAVE && (OPT & kOptMixedU) != 0;
     constexpr int NT = NC * 32;         // consumer threads
     constexpr int PX = St::PX;
     constexpr int ES = St::ES;
@@ -474,6 +516,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                         const int zc = u.z0 + c;
 
                         float kap[PY][PX], um[PY][PX];
+                        uint32_t umw[PY][PX / 2];  // MU: u^{n-1} as BF16 pairs
                         if (!wait_or_abort(&full[bar_i], par, abort_flag))
                             return false;
                         if (EQ == GBST_WAVE) {
@@ -491,9 +534,15 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                                     kap[r_][4 * v + 3] = __uint_as_float(kv.w);
                                 }
                                 const uint4 uv = lds128(cs + CK + e * ES);
+                                if constexpr (MU) {
     #pragma unroll
-                                for (int i = 0; i < PX; ++i)
-                                    um[r_][i] = St::get(uv, i);
+                                    for (int pp = 0; pp < PX / 2; ++pp)
+                                        umw[r_][pp] = word_of(uv, pp);
+                                } else {
+    #pragma unroll
+                                    for (int i = 0; i < PX; ++i)
+                                        um[r_][i] = St::get(uv, i);
+                                }
                             }
                         }
                         {
@@ -564,8 +613,14 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                                     } else {
                                         t = __fadd2_rn(xm, xp);
                                     }
-                                    if (MID)
-                                        t = __fadd2_rn(t, __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp)));
+                                    if (MID) {
+                                        float2 ys;
+                                        if (MY && r_ - m < 0 && r_ + m >= PY)
+                                            ys = bf16_pair_sum(word_of(ylo[m - r_ - 1], pp), word_of(yhi[r_ + m - PY], pp));
+                                        else
+                                            ys = __fadd2_rn(yrow(r_ - m, pp), yrow(r_ + m, pp));
+                                        t = __fadd2_rn(t, ys);
+                                    }
                                     if (ZQ)
                                         t = __fadd2_rn(t, __fadd2_rn(q[(qc - m + 2 * QN) % QN][r_][pp], q[(qc + m) % QN][r_][pp]));
                                     sv[r_][pp] = __ffma2_rn(w2[m], t, sv[r_][pp]);
@@ -581,6 +636,10 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                                 float2 ov;
                                 if (EQ == GBST_HEAT) {
                                     ov = __ffma2_rn(a2, sv[r_][pp], cv);
+                                } else if constexpr (MU) {
+                                    const float2 k2 = make_float2(kap[r_][2 * pp], kap[r_][2 * pp + 1]);
+                                    const float2 n2 = bf16_pair_sub(umw[r_][pp], __fadd2_rn(cv, cv));
+                                    ov = __ffma2_rn(k2, sv[r_][pp], make_float2(-n2.x, -n2.y));
                                 } else {
                                     const float2 k2 = make_float2(kap[r_][2 * pp], kap[r_][2 * pp + 1]);
                                     const float2 t2 = __fadd2_rn(__fadd2_rn(cv, cv),
