@@ -344,8 +344,8 @@ def timed_runs(torch, stream, fn, reps=1):
 
 
 def extras(torch, hbm: float, tune: bool, acc: dict | None = None):
-    """Decomposition, 768^3 wave FP32 vs BF16, 2D at 16384^2, the 64-grid batch and the closure
-    (not in the timed region).  With acc given, the 768^3 wave runs are also captured for the
+    """Decomposition, 768^3 wave FP32 vs BF16, heat at 512^3 and 8192^2, 2D at 16384^2, the 64-grid
+    batch and the closure (not in the timed region).  With acc given, the 768^3 wave runs are also captured for the
     accuracy comparison (acc["wave"]) after their timing."""
     import synthetic
     from paper_2404_02218_gb300.grid import Grid, Batch
@@ -455,23 +455,40 @@ def extras(torch, hbm: float, tune: bool, acc: dict | None = None):
                                       "gpts_graph": c1.nsteps * 256 * 256 / lat[True] / 1e6,
                                       "bound": "launch / latency (fits L2)"}
 
-    # 2D at the paper's large size: heat 16384^2, orders 2/4/8, and the order-8 acoustic wave
-    n2 = 16384
-    u2 = synthetic.uniform_field_torch(7, (n2, n2), "cuda")
+    # heat at the sizes of the paper's own GPU runs (512^3 and 8192^2; 0.5 and 0.27 GB per field,
+    # larger than L2), orders 2/4/8, and 2D at the large size: heat 16384^2 and the order-8 wave
+    u3 = synthetic.uniform_field_torch(8, (512, 512, 512), "cuda")
     for so in (2, 4, 8):
-        a2 = float(np.float32(0.8 * synthetic.heat_a_max(2, so)))
-        g = Grid(2, (n2, n2), so, "heat", dt=a2, stream=stream)
-        g.set_field("u", u2)
+        case = synthetic.heat3d(512, so)
+        g = Grid(3, case.dims, so, "heat", dt=case.a, stream=stream)
+        g.set_field("u", u3)
         if tune:
             g.tune(reps=2)
-        g.set_field("u", u2)
+        g.set_field("u", u3)
         ms = timed_runs(torch, stream, lambda: g.run(STEPS_PER_RUN))
-        pts = STEPS_PER_RUN * n2 * n2
-        out[f"heat2d_{n2}_so{so}"] = {"gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6,
+        pts = STEPS_PER_RUN * 512 ** 3
+        out[f"heat3d_512_so{so}"] = {"gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6,
                                      "frac": 8 * pts / ms / 1e6 / hbm, "steps": STEPS_PER_RUN,
                                      "plan": json.loads(g.describe())}
         g.close()
-    del u2
+    del u3
+    for n2 in (8192, 16384):
+        u2 = synthetic.uniform_field_torch(7, (n2, n2), "cuda")
+        for so in (2, 4, 8):
+            a2 = float(np.float32(0.8 * synthetic.heat_a_max(2, so)))
+            g = Grid(2, (n2, n2), so, "heat", dt=a2, stream=stream)
+            g.set_field("u", u2)
+            if tune:
+                g.tune(reps=2)
+            g.set_field("u", u2)
+            ms = timed_runs(torch, stream, lambda: g.run(STEPS_PER_RUN))
+            pts = STEPS_PER_RUN * n2 * n2
+            out[f"heat2d_{n2}_so{so}"] = {"gpts": pts / ms / 1e6, "gbs": 8 * pts / ms / 1e6,
+                                         "frac": 8 * pts / ms / 1e6 / hbm, "steps": STEPS_PER_RUN,
+                                         "plan": json.loads(g.describe())}
+            g.close()
+        del u2
+    n2 = 16384
     speeds = synthetic.five_layer_speeds()
     c2 = torch.from_numpy(synthetic.layered_velocity((n2, n2), speeds)).cuda()
     h2 = 10.0
