@@ -301,7 +301,11 @@ gbst_status closure_set_conv_impl(gbst_closure c, int impl);
 
 /* Per-parameter mask of closure_adam_step (host array of n = parameter count
  * bytes, non-zero = the parameter trains; NULL: every parameter trains, the
- * default).  Combines with closure_freeze_biases.  Synchronises the stream. */
+ * default).  Combines with closure_freeze_biases.  A layer whose weights and
+ * biases are all masked out gets no weight gradient from closure_loss_grad and
+ * closure_backward (its entries of the gradient are left as they were, zero
+ * unless accumulating); the data gradient still passes through it.  Synchronises
+ * the stream. */
 gbst_status closure_set_trainable(gbst_closure c, const unsigned char *mask, int64_t n);
 /* Feature inputs (closures created with cin = 8; none of this is in the paper).
  * The network's 8 input channels are x_k = scales[k] f_k with, for u+ the plain

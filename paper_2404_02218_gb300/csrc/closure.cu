@@ -1172,6 +1172,7 @@ struct gbst_closure_s {
     int *derr = nullptr;        // device error word of the tcgen05 convolutions
     unsigned char *trainable = nullptr;      // per-parameter Adam mask (null: all parameters train)
     unsigned char *trainable_buf = nullptr;  // its device storage
+    bool layer_grad[3] = {true, true, true}; // layer l has a trainable weight or bias: its dW, db are computed
     // feature inputs (cin 8): FP32 stencil features, see closure_set_features
     bool feat = false;
     int feat_r = 2;
@@ -1456,7 +1457,7 @@ cudaError_t backprop(gbst_closure c, Dims d, bool input_grad)
     w.grad_b = c->g + c->off[5];
     w.cin = c->hidden;
     w.cout = 1;
-    cudaError_t e = launch_wgrad(w, s);
+    cudaError_t e = c->layer_grad[2] ? launch_wgrad(w, s) : cudaSuccess;
     ConvArgs a{};
     a.d = d;
     a.in = c->dout;
@@ -1473,7 +1474,7 @@ cudaError_t backprop(gbst_closure c, Dims d, bool input_grad)
     w.grad_b = c->g + c->off[3];
     w.cin = c->hidden;
     w.cout = c->hidden;
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && c->layer_grad[1])
         e = launch_wgrad(w, s);
     a.in = c->dz2;
     a.wt = c->wb[1];
@@ -1488,7 +1489,7 @@ cudaError_t backprop(gbst_closure c, Dims d, bool input_grad)
     w.grad_b = c->g + c->off[1];
     w.cin = c->cin;
     w.cout = c->hidden;
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && c->layer_grad[0])
         e = launch_wgrad(w, s);
     if (input_grad && e == cudaSuccess) {
         a.in = c->dz1;
@@ -1693,10 +1694,20 @@ gbst_status closure_set_trainable(gbst_closure c, const unsigned char *mask, int
         return record_error(GBST_EINVAL, "closure_set_trainable: null closure");
     if (!mask) {
         c->trainable = nullptr;  // (the buffer, if any, stays owned by the closure)
+        for (bool &b : c->layer_grad)
+            b = true;
         return GBST_OK;
     }
     if (n != c->nparams)
         return record_error(GBST_EINVAL, "closure_set_trainable: n must be the parameter count");
+    // a layer whose weights and biases are all frozen needs no weight gradient (its data
+    // gradient still flows to the layers below and to the input)
+    for (int l = 0; l < 3; ++l) {
+        bool any = false;
+        for (int64_t i = c->off[2 * l]; i < c->off[2 * l + 1] + c->cnt[2 * l + 1] && !any; ++i)
+            any = mask[i] != 0;
+        c->layer_grad[l] = any;
+    }
     if (!c->trainable_buf) {
         c->trainable_buf = static_cast<unsigned char *>(cl_alloc(c, static_cast<size_t>(n)));
         if (!c->trainable_buf)

@@ -176,6 +176,36 @@ def test_closure_backward_matches_oracle(torch_cuda):
         assert rel(grads[lo:hi], flat[lo:hi]) <= 3e-2
 
 
+def test_frozen_layers_get_no_weight_gradient(torch_cuda):
+    """With a trainable mask that leaves layers 1 and 2 wholly frozen, their weight gradients
+    are not computed (they stay zero), while the input cotangents are the same bits as
+    without the mask and the last layer's gradient the same up to the order of its atomic
+    FP32 sums over CTAs."""
+    torch = torch_cuda
+    from paper_2404_02218_gb300 import native as N
+    from paper_2404_02218_gb300.closure import output_weight_mask
+    dims = (40, 18, 16)
+    shape = tuple(reversed(dims))
+    up, un, gout = _fields(shape, 100, 3)
+    cn = 0.3 + 0.7 * synthetic.uniform_field(103, shape).astype(np.float64)
+    cl, _, _ = _closure8(torch, int(np.prod(dims)), t=2.0)
+    T = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (up, un, cn, gout)]
+    res = []
+    for mask in (None, output_weight_mask(taps="all")):
+        N.closure_set_trainable(cl.h, mask)
+        g_up, g_un = torch.empty_like(T[0]), torch.empty_like(T[0])
+        N.closure_backward(cl.h, T[0].data_ptr(), T[1].data_ptr(), T[2].data_ptr(), dims, T[3].data_ptr(),
+                           g_up.data_ptr(), g_un.data_ptr(), False)
+        torch.cuda.synchronize()
+        res.append((cl.get_grads(), g_up.cpu().numpy(), g_un.cpu().numpy()))
+    cl.close()
+    (g0, up0, un0), (g1, up1, un1) = res
+    last = 16 * 8 * 27 + 16 + 16 * 16 * 27 + 16  # first parameter of layer 3
+    assert np.linalg.norm(g1[last:] - g0[last:]) <= 1e-5 * np.linalg.norm(g0[last:])
+    assert not np.any(g1[:last]) and np.any(g0[:last])
+    assert np.array_equal(up1, up0) and np.array_equal(un1, un0)
+
+
 def test_rollout_gradient_matches_oracle(torch_cuda):
     """stencil_closure_rollout_grad (three corrected steps of an attached closure, no source)
     against the FP64 chain rule of oracle.closure.rollout_loss_and_grads."""
