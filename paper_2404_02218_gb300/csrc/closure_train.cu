@@ -240,6 +240,106 @@ __global__ void __launch_bounds__(kFX *kFY) k_lap_z(DenseDims d, const float *__
     }
 }
 
+// lu = L u^n as k_lap_z (the same sums in the same order, so the same bits), four
+// consecutive x points per thread (rows a multiple of 4 points, 16-byte aligned arrays):
+// a block owns a 128 x 8 (x, y) tile and a chunk of kFZC planes; the own points and
+// the y neighbours are 16-byte loads, the x neighbours outside the thread's four points
+// 8- or 16-byte loads, the z neighbours a register queue of 2R + 1 planes whose slots
+// are compile-time constants (the z-loop unrolled by 2R + 1).  Points outside the grid
+// read as 0, which adds nothing to a sum that starts at 0 (k_lap_z skips them).
+template <int R>
+__global__ void __launch_bounds__(kFX *kFY) k_lap4_z(DenseDims d, const float *__restrict__ un, float4 w03,
+                                                     float w4, float *__restrict__ lu)
+{
+    constexpr int QN = 2 * R + 1;
+    const float w[5] = {w03.x, w03.y, w03.z, w03.w, w4};
+    const int x0 = (blockIdx.x * kFX + threadIdx.x) * 4, y = blockIdx.y * kFY + threadIdx.y;
+    if (x0 >= d.nx || y >= d.ny)
+        return;
+    const int z0 = blockIdx.z * kFZC, z1 = min(d.nz, z0 + kFZC);
+    const int64_t sy = d.nx, sz = static_cast<int64_t>(d.nx) * d.ny, pxy = static_cast<int64_t>(y) * d.nx + x0;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto ld4 = [&](int64_t p) { return *reinterpret_cast<const float4 *>(un + p); };
+    float4 q[QN];  // u^n at planes z - R .. z + R of the thread's four points (slot = plane mod QN)
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) {
+        const int zz = z0 - R + k;
+        q[(k + QN - R) % QN] = (zz >= 0 && zz < d.nz) ? ld4(zz * sz + pxy) : zero4;
+    }
+    for (int c0 = z0; c0 < z1; c0 += QN) {
+#pragma unroll
+        for (int k = 0; k < QN; ++k) {
+            const int z = c0 + k;
+            if (z < z1) {
+                // plane z + R into its slot; the slot of plane z is k mod QN (c0 - z0 is a multiple of QN)
+                const int zn = z + R;
+                q[(k + R) % QN] = zn < d.nz ? ld4(zn * sz + pxy) : zero4;
+                const int64_t p = z * sz + pxy;
+                const float4 c = q[k % QN];
+                const float cv[4] = {c.x, c.y, c.z, c.w};
+                // x neighbours: elements x0 - R .. x0 - 1 and x0 + 4 .. x0 + 3 + R
+                float xl[4] = {0.f, 0.f, 0.f, 0.f}, xr[4] = {0.f, 0.f, 0.f, 0.f};
+                if (x0 > 0) {
+                    if (R <= 2) {
+                        const float2 t = *reinterpret_cast<const float2 *>(un + p - 2);
+                        xl[2] = t.x;
+                        xl[3] = t.y;
+                    } else {
+                        const float4 t = ld4(p - 4);
+                        xl[0] = t.x;
+                        xl[1] = t.y;
+                        xl[2] = t.z;
+                        xl[3] = t.w;
+                    }
+                }
+                if (x0 + 4 < d.nx) {
+                    if (R <= 2) {
+                        const float2 t = *reinterpret_cast<const float2 *>(un + p + 4);
+                        xr[0] = t.x;
+                        xr[1] = t.y;
+                    } else {
+                        const float4 t = ld4(p + 4);
+                        xr[0] = t.x;
+                        xr[1] = t.y;
+                        xr[2] = t.z;
+                        xr[3] = t.w;
+                    }
+                }
+                // element e in [-4, 8) of the thread's row
+                auto xe = [&](int e) { return e < 0 ? xl[4 + e] : e >= 4 ? xr[e - 4] : cv[e]; };
+                float4 ym[R], yp[R];
+#pragma unroll
+                for (int m = 1; m <= R; ++m) {
+                    ym[m - 1] = y - m >= 0 ? ld4(p - m * sy) : zero4;
+                    yp[m - 1] = y + m < d.ny ? ld4(p + m * sy) : zero4;
+                }
+                float o[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float s = 3.0f * w[0] * cv[i];
+#pragma unroll
+                    for (int m = 1; m <= R; ++m) {
+                        const float yl[4] = {ym[m - 1].x, ym[m - 1].y, ym[m - 1].z, ym[m - 1].w};
+                        const float yh[4] = {yp[m - 1].x, yp[m - 1].y, yp[m - 1].z, yp[m - 1].w};
+                        const float4 zl = q[(k - m + 2 * QN) % QN], zh = q[(k + m) % QN];
+                        const float zlv[4] = {zl.x, zl.y, zl.z, zl.w}, zhv[4] = {zh.x, zh.y, zh.z, zh.w};
+                        float a = 0.0f;
+                        a += xe(i - m);
+                        a += xe(i + m);
+                        a += yl[i];
+                        a += yh[i];
+                        a += zlv[i];
+                        a += zhv[i];
+                        s = fmaf(w[m], a, s);
+                    }
+                    o[i] = s;
+                }
+                *reinterpret_cast<float4 *>(lu + p) = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+    }
+}
+
 // The packed network input from u+, u^n, c_n and lu = L u^n: cn2 and g_a as
 // k_cn2_grads, t6 and t5 as the k_star calls of closure_features_forward, the
 // channels as k_pack_features.  R: the radius of L; w6: the sixth-difference star;
@@ -604,11 +704,24 @@ gbst_status closure_features_forward(const float *up, const float *un, const flo
                                       static_cast<float>(kSixth[2]), static_cast<float>(kSixth[3]));
         const FeatScales sc = to_scales(scales);
         const dim3 g = zmarch_grid(d), t(kFX, kFY);
-        switch (r) {
-        case 1: k_lap_z<1><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
-        case 2: k_lap_z<2><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
-        case 3: k_lap_z<3><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
-        default: k_lap_z<4><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+        // four points per thread where rows and arrays allow 16-byte accesses
+        const bool vec4 =
+            d.nx % 4 == 0 && ((reinterpret_cast<uintptr_t>(un) | reinterpret_cast<uintptr_t>(b.lu)) & 15) == 0;
+        if (vec4) {
+            const dim3 g4((d.nx / 4 + kFX - 1) / kFX, g.y, g.z);
+            switch (r) {
+            case 1: k_lap4_z<1><<<g4, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+            case 2: k_lap4_z<2><<<g4, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+            case 3: k_lap4_z<3><<<g4, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+            default: k_lap4_z<4><<<g4, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+            }
+        } else {
+            switch (r) {
+            case 1: k_lap_z<1><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+            case 2: k_lap_z<2><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+            case 3: k_lap_z<3><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+            default: k_lap_z<4><<<g, t, 0, s>>>(d, un, w03, wf[4], b.lu); break;
+            }
         }
         if ((st = launched("closure features")) != GBST_OK)
             return st;
