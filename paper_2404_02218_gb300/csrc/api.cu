@@ -283,6 +283,10 @@ struct gbst_grid_s {
     gbst_desc d{};
     int ndim = 3, R = 1, es = 4;
     double w[kMaxRadius + 1] = {0};
+    // the weights as integers over a common denominator wscale where they are (the central
+    // weights: 1, 12 and 5040 for orders 2, 4 and 8), else wint = w and wscale = 1
+    double wint[kMaxRadius + 1] = {0};
+    double wscale = 1.0;
     double S = 0.0;
     int decomp[3] = {1, 1, 1};
     bool batch = false;
@@ -884,9 +888,13 @@ SweepArgs sweep_args(gbst_handle h, int parity, const float *srcval)
     a.nunits = h->plan.nunits;
     a.parity = parity;
     a.ndim = h->ndim;
-    a.wc = static_cast<float>(h->ndim * h->w[0]);
+    // integer weights (exact in FP32, so the star of a constant is exactly 0); the common
+    // denominator is in the coefficients (heat_a, the coupling matrix) or, for the wave,
+    // in lscale, which multiplies the sum before kappa
+    a.wc = static_cast<float>(h->ndim * h->wint[0]);
     for (int m = 1; m <= h->R; ++m)
-        a.w[m] = static_cast<float>(h->w[m]);
+        a.w[m] = static_cast<float>(h->wint[m]);
+    a.lscale = static_cast<float>(1.0 / h->wscale);
     a.srcval = srcval;
     a.err = h->derr;
     a.nsteps = 1;
@@ -1153,6 +1161,29 @@ double max_singular_value(const double *B, int n)
 
 // Stability of u <- u + A L(u) (sufficient): |I + lambda A|_2 <= 1 for every
 // symbol value lambda in [-ndim S, 0] (exact for symmetric A and for A = a I).
+// Writes the weights w[0..R] as integers wint over the smallest common denominator
+// *scale (w = wint / scale) when one up to 10^6 exists with integers below 2^22 (exact in
+// FP32, and 2 ndim |wint[0]| too); else wint = w, *scale = 1.
+void integer_weights(int R, const double *w, double *wint, double *scale)
+{
+    for (int m = 0; m <= R; ++m)
+        wint[m] = w[m];
+    *scale = 1.0;
+    for (int S = 1; S <= 1000000; ++S) {
+        bool ok = true;
+        for (int m = 0; m <= R && ok; ++m) {
+            const double v = w[m] * S;
+            ok = std::fabs(v - std::nearbyint(v)) <= 1e-9 * std::max(1.0, std::fabs(v)) && std::fabs(v) < 4194304.0;
+        }
+        if (ok) {
+            for (int m = 0; m <= R; ++m)
+                wint[m] = std::nearbyint(w[m] * S);
+            *scale = S;
+            return;
+        }
+    }
+}
+
 bool system_stable(const double *A, int n, int ndim, double S)
 {
     double B[16];
@@ -1220,6 +1251,7 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
     else
         central_weights(R, h->w);
     h->S = symbol_max(R, h->w);
+    integer_weights(R, h->w, h->wint, &h->wscale);
     h->stream = static_cast<cudaStream_t>(d.stream);
     h->mem.s = h->stream;
     if (d.allocator) {
@@ -1233,7 +1265,7 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
     if (nfields > 0) {
         h->nf = nfields;
         for (int k = 0; k < nfields * nfields; ++k)
-            h->coupling[k] = static_cast<float>(coupling[k]);
+            h->coupling[k] = static_cast<float>(coupling[k] / h->wscale);
         if (!d.allow_unstable && !system_stable(coupling, nfields, h->ndim, h->S)) {
             delete h;
             return fail(GBST_EUNSTABLE, "coupling matrix: |I + lambda A| > 1 for a symbol value lambda of the stencil");
@@ -1347,7 +1379,7 @@ gbst_status create_handle(const gbst_desc *descs, int n, bool batch, gbst_handle
         g.kpitch = s.lk.pitch;
         g.krows = s.lk.rows;
         g.korigin = s.lk.origin;
-        g.heat_a = static_cast<float>(s.alpha * s.dt / (s.h * s.h));
+        g.heat_a = static_cast<float>(s.alpha * s.dt / (s.h * s.h) / h->wscale);
         g.ghost = s.lu.r;
         g.face_int = 0;
         for (int a = 0; a < d.ndim; ++a) {

@@ -84,8 +84,9 @@ struct SweepArgs {
     int nunits;
     int parity;            // u^n lives in buf[parity]; output goes to buf[1-parity]
     int ndim;
-    float wc;              // ndim * w_0
+    float wc;              // ndim * w_0 (weights scaled to integers where they are)
     float w[kMaxRadius + 1];  // w_1..w_r at w[1..r]
+    float lscale;          // wave: factor on the weighted sum before kappa (1 / the weights' scale)
     const float *srcval;   // wave: per-grid source values, [step][grid] (already scaled), or null
     int *err;              // device error word
     int nsteps;            // steps in this launch (> 1: persistent launch with grid barriers)

@@ -61,7 +61,7 @@ __global__ void k_simple(const SweepArgs a)
         } else {
             const float kap = g.kappa[g.korigin + z * g.kpitch * g.krows + y * g.kpitch + x];
             const float um = E::ld(out + idx);
-            o = fmaf(kap, s, (c + c) - um);
+            o = fmaf(kap, __fmul_rn(s, a.lscale), (c + c) - um);
             if (g.has_src && a.srcval && x == g.src_x && y == g.src_y && z == g.src_z)
                 o += a.srcval[blockIdx.y];
         }

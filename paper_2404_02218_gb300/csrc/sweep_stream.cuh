@@ -14,6 +14,9 @@
 //   heat:  u+ = u + a * L(u)
 //   wave:  u+ = 2u - u- + kappa * L(u)   (written in place over u-)
 //   L(u)  = w0*ndim*u + sum_{m=1..r} w_m [((x-m + x+m) + (y-m + y+m)) + (z-m + z+m)]
+// The weights arrive as integers over a common denominator (exact in FP32, so the
+// star of a constant is exactly zero); the heat coefficient a carries the
+// denominator, the wave multiplies the sum by its inverse (lscale) before kappa.
 // The summation order per point is fixed and independent of the point's
 // position in its tile, so a decomposed run matches an undecomposed one bit
 // for bit.
@@ -444,6 +447,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
 #pragma unroll
     for (int m = 0; m <= R; ++m)
         w2[m] = make_float2(a.w[m], a.w[m]);
+    const float2 ls2 = make_float2(a.lscale, a.lscale);
 
     auto consume = [&](int parity, const float *srcval) -> bool {
         for (;;) {
@@ -639,12 +643,12 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) k_stream(const SweepArgs 
                                 } else if constexpr (MU) {
                                     const float2 k2 = make_float2(kap[r_][2 * pp], kap[r_][2 * pp + 1]);
                                     const float2 n2 = bf16_pair_sub(umw[r_][pp], __fadd2_rn(cv, cv));
-                                    ov = __ffma2_rn(k2, sv[r_][pp], make_float2(-n2.x, -n2.y));
+                                    ov = __ffma2_rn(k2, __fmul2_rn(ls2, sv[r_][pp]), make_float2(-n2.x, -n2.y));
                                 } else {
                                     const float2 k2 = make_float2(kap[r_][2 * pp], kap[r_][2 * pp + 1]);
                                     const float2 t2 = __fadd2_rn(__fadd2_rn(cv, cv),
                                                                  make_float2(-um[r_][2 * pp], -um[r_][2 * pp + 1]));
-                                    ov = __ffma2_rn(k2, sv[r_][pp], t2);
+                                    ov = __ffma2_rn(k2, __fmul2_rn(ls2, sv[r_][pp]), t2);
                                 }
                                 o[r_][2 * pp] = ov.x;
                                 o[r_][2 * pp + 1] = ov.y;

@@ -140,12 +140,11 @@ def test_batch64_300_steps_within_fp32_rounding_bound(batch64_errors):
     assert max(errs.values()) <= bound, (errs, bound)
 
 
-FP32_300_STEPS = ("FP32 rounding accumulated over the configured 300 leapfrog steps reaches the 1e-5 "
-                  "of the stated tolerance: one of the three members measures 1.07e-5, the others "
-                  "9.0e-6 and below (within the rounding bound of the test above)")
-
-
-@pytest.mark.xfail(strict=True, reason=FP32_300_STEPS)
 def test_batch64_300_steps_within_1e5(batch64_errors):
+    """The stated FP32 tolerance over the configured 300 steps.  It holds because the sweep
+    takes the star's weights as integers over a common denominator (exact in FP32, so the
+    star of a constant is exactly zero): with the weights rounded to FP32 the zeroth moment
+    of the star was off by about 1e-8, a spurious term the leapfrog carries coherently,
+    and one member measured 1.07e-5."""
     _, errs = batch64_errors
     assert max(errs.values()) <= 1e-5, errs
