@@ -79,7 +79,12 @@ typedef struct gbst_desc {
     double h;              /* grid spacing */
     double dt;             /* time step */
     double alpha;          /* heat: diffusivity, a = alpha dt / h^2 */
-    const double *coeffs;  /* optional r+1 one-sided weights w_0..w_r; NULL = standard central */
+    const double *coeffs;  /* optional r+1 one-sided weights w_0..w_r; NULL = standard central.
+                              Weights that are integers over a common denominator D <= 10^6
+                              (the central ones: D = 1, 12, 5040 for orders 2, 4, 8) are
+                              applied as those integers, exact in FP32, with 1/D in the
+                              coefficient (heat: a / D; wave: the weighted sum times 1/D
+                              before kappa), so the FP32 star of a constant is exactly 0 */
     int decomp[3];         /* subdomains per axis ({0,0,0} or {1,1,1} = none; e.g. {2,2,2}) */
     int allow_unstable;    /* 0: reject time steps above the von Neumann limit (GBST_EUNSTABLE) */
     int kernel;            /* GBST_KERNEL_AUTO / STREAM (TMA 2.5D) / SIMPLE (one thread per point) */
