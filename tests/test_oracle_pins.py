@@ -46,6 +46,28 @@ def test_weights_differentiate_polynomials_exactly(so):
     assert sum(w[abs(m)] for m in range(-r, r + 1)) == 0
 
 
+@pytest.mark.parametrize("so,den,ints", [(2, 1, [-2, 1]), (4, 12, [-30, 16, -1]),
+                                         (8, 5040, [-14350, 8064, -1008, 128, -9])])
+def test_weights_over_their_common_denominator(so, den, ints):
+    """The sweeps apply the central weights as integers over their least common
+    denominator (exact in FP32); rounded one by one to FP32 instead, the weights of the
+    3D star no longer sum to zero, so the star of a constant is not exactly zero."""
+    w = central_weights(so)
+    assert math.lcm(*(x.denominator for x in w)) == den
+    assert [x * den for x in w] == [Fraction(v) for v in ints]
+    r = so // 2
+    # the 3D star of the constant 1 as the sweeps evaluate it in FP32: s = ndim * w0, then
+    # s = fma(w_m, 6, s) per offset (the FP64 sum below is exact, so it rounds once, as an FMA)
+    def star_of_one(wc, wm):
+        s = np.float32(wc)
+        for m in range(1, r + 1):
+            s = np.float32(np.float64(s) + np.float64(wm[m]) * 6.0)
+        return s
+    assert star_of_one(np.float32(3 * ints[0]), [np.float32(v) for v in ints]) == 0
+    if so > 2:
+        assert star_of_one(np.float32(3 * float(w[0])), [np.float32(float(x)) for x in w]) != 0
+
+
 @pytest.mark.parametrize("so", SOS)
 def test_symbol_max_matches_recipe(so):
     S = symbol_max(central_weights(so))
